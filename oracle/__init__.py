@@ -1,0 +1,282 @@
+"""CPU oracle for the DPR1 eigensolver (arXiv 1405.7537) -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
+may import this package.  The CUDA library never calls it, and it never calls the
+CUDA library.
+
+Two references live here:
+
+* ``dpr1eig`` / ``eig_all``: Algorithm 1 (dpr1eig) step by step in binary64 with
+  its own double-double code (``dpr1_oracle.c``).
+* ``quad_eig``: the plain definition of the eigenpairs -- the zeros of the secular
+  function Eq. (Pick) bisected in binary128, and x = (D - lambda I)^{-1} z
+  (``quad_ref.c``).
+
+``eig_full`` adds the paper's deflation (Sec. 1: zeta_j = 0 gives the eigenpair
+(d_j, e_j); d_i = d_j gives the eigenvalue d_i after a Givens rotation in the
+(i, j) plane) and the sign flip for rho < 0 (Sec. 1) around ``eig_all``.
+``backward`` is the adjoint of (lambda, V) with respect to (d, z, rho).
+"""
+import ctypes
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+from .build import build_oracle
+
+_LIB = None
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("dd_mode", ctypes.c_int), ("T_kappa", ctypes.c_double), ("T_Knu", ctypes.c_double),
+                ("T_zero", ctypes.c_double), ("remedies", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("shift", ctypes.c_int), ("first_shift", ctypes.c_int), ("used_dd", ctypes.c_int),
+                ("remedy", ctypes.c_int), ("zero_path", ctypes.c_int), ("steps", ctypes.c_int),
+                ("sigma", ctypes.c_double), ("mu", ctypes.c_double), ("nu", ctypes.c_double),
+                ("lam", ctypes.c_double), ("b", ctypes.c_double), ("K_nu", ctypes.c_double),
+                ("K_nu_final", ctypes.c_double), ("kappa_nu", ctypes.c_double)]
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        path = build_oracle()
+        L = ctypes.CDLL(path)
+        L.oracle_dpr1eig.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_int,
+                                     ctypes.POINTER(Opts), _dp, _dp, ctypes.POINTER(Info)]
+        L.oracle_dpr1eig_range.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_int,
+                                           ctypes.c_int, ctypes.POINTER(Opts), _dp, _dp, _dp, _dp,
+                                           _ip, _ip]
+        L.oracle_backward.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _dp, _dp, _dp,
+                                      _dp, _dp, _dp]
+        L.quad_eigpair.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp]
+        L.quad_eigpair2.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp,
+                                    _dp, _ip, _dp]
+        L.quad_secular.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double]
+        L.quad_secular.restype = ctypes.c_double
+        for name in ("oracle_dd_add", "oracle_dd_mul", "oracle_dd_div"):
+            getattr(L, name).argtypes = [ctypes.c_double] * 4 + [_dp]
+        L.oracle_default_opts.argtypes = [ctypes.POINTER(Opts)]
+        _LIB = L
+    return _LIB
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def default_opts(**kw):
+    o = Opts()
+    lib().oracle_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def dpr1eig(d, z, rho, k, opts=None):
+    """Algorithm 1 for the k-th eigenpair (0-based, lambda_0 the largest).
+
+    Returns (lambda, v, info) where info is a dict of the decisions taken."""
+    d, z = _f64(d), _f64(z)
+    n = d.size
+    v = np.empty(n)
+    lam = ctypes.c_double()
+    info = Info()
+    o = opts if opts is not None else default_opts()
+    rc = lib().oracle_dpr1eig(n, _ptr(d), _ptr(z), float(rho), int(k), ctypes.byref(o),
+                              ctypes.byref(lam), _ptr(v), ctypes.byref(info))
+    if rc:
+        raise ValueError("oracle_dpr1eig failed with code %d" % rc)
+    return lam.value, v, {f[0]: getattr(info, f[0]) for f in Info._fields_}
+
+
+def eig_all(d, z, rho, opts=None, ks=None, threads=1, want_vectors=True):
+    """All (or the listed) eigenpairs of an irreducible, strictly ordered problem.
+
+    Returns dict(lam, Vt, sigma, mu, shift, flags) indexed by the position in ks.
+    flags: bit0-1 remedy (1 = R1, 2 = R2), bit2 near-zero recompute, bit3 double-double used.
+    The eigenpairs are independent; ``threads`` > 1 splits them over host threads
+    (the C calls release the interpreter lock)."""
+    d, z = _f64(d), _f64(z)
+    n = d.size
+    ks = np.arange(n) if ks is None else np.asarray(ks, dtype=np.int64)
+    m = ks.size
+    o = opts if opts is not None else default_opts()
+    out = dict(lam=np.empty(m), sigma=np.empty(m), mu=np.empty(m),
+               shift=np.empty(m, dtype=np.int32), flags=np.empty(m, dtype=np.int32),
+               Vt=np.empty((m, n)) if want_vectors else None)
+
+    def run(idx):
+        v = np.empty(n)
+        lam = ctypes.c_double()
+        info = Info()
+        L = lib()
+        for p in idx:
+            rc = L.oracle_dpr1eig(n, _ptr(d), _ptr(z), float(rho), int(ks[p]), ctypes.byref(o),
+                                  ctypes.byref(lam), _ptr(v), ctypes.byref(info))
+            if rc:
+                raise ValueError("oracle_dpr1eig failed with code %d" % rc)
+            out["lam"][p] = lam.value
+            out["sigma"][p] = info.sigma
+            out["mu"][p] = info.mu
+            out["shift"][p] = info.shift
+            out["flags"][p] = info.remedy | (info.zero_path << 2) | (info.used_dd << 3)
+            if want_vectors:
+                out["Vt"][p] = v
+
+    if threads <= 1 or m < 2:
+        run(range(m))
+    else:
+        parts = np.array_split(np.arange(m), threads)
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(run, parts))
+    return out
+
+
+def backward(d, z, rho, sigma, mu, grad_lam=None, grad_Vt=None):
+    """Adjoint of (lambda, V) -> (d, z, rho) from the pairs (sigma, mu); returns (gd, gz, grho)."""
+    d, z, sigma, mu = _f64(d), _f64(z), _f64(sigma), _f64(mu)
+    n = d.size
+    gl = _f64(grad_lam) if grad_lam is not None else None
+    gV = _f64(grad_Vt) if grad_Vt is not None else None
+    gd, gz, gr = np.empty(n), np.empty(n), ctypes.c_double()
+    rc = lib().oracle_backward(n, _ptr(d), _ptr(z), float(rho), _ptr(sigma), _ptr(mu), _ptr(gl),
+                               _ptr(gV), _ptr(gd), _ptr(gz), ctypes.byref(gr))
+    if rc:
+        raise ValueError("oracle_backward failed with code %d" % rc)
+    return gd, gz, gr.value
+
+
+def quad_eig(d, z, rho, k, want_vector=True, full=False):
+    """binary128 reference for eigenpair k: (lam_hi, lam_lo, v).
+
+    With full=True returns dict(hi, lo, mu_hi, mu_lo, pole, v): lambda = d[pole] + mu."""
+    d, z = _f64(d), _f64(z)
+    n = d.size
+    v = np.empty(n) if want_vector else None
+    hi, lo, mh, ml = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    pole = ctypes.c_int()
+    rc = lib().quad_eigpair2(n, _ptr(d), _ptr(z), float(rho), int(k), ctypes.byref(hi), ctypes.byref(lo),
+                             ctypes.byref(mh), ctypes.byref(ml), ctypes.byref(pole), _ptr(v))
+    if rc < 0:
+        raise ValueError("quad_eigpair: bad arguments")
+    if full:
+        return dict(hi=hi.value, lo=lo.value, mu_hi=mh.value, mu_lo=ml.value, pole=pole.value, v=v)
+    return hi.value, lo.value, v
+
+
+def quad_all(d, z, rho, ks=None, threads=1, want_vectors=True):
+    """binary128 reference for several eigenpairs: dict(hi, lo, mu_hi, mu_lo, pole, Vt)."""
+    d, z = _f64(d), _f64(z)
+    n = d.size
+    ks = np.arange(n) if ks is None else np.asarray(ks, dtype=np.int64)
+    m = ks.size
+    out = dict(hi=np.empty(m), lo=np.empty(m), mu_hi=np.empty(m), mu_lo=np.empty(m),
+               pole=np.empty(m, dtype=np.int64), Vt=np.empty((m, n)) if want_vectors else None)
+
+    def run(idx):
+        for p in idx:
+            r = quad_eig(d, z, rho, ks[p], want_vectors, full=True)
+            for key in ("hi", "lo", "mu_hi", "mu_lo", "pole"):
+                out[key][p] = r[key]
+            if want_vectors:
+                out["Vt"][p] = r["v"]
+
+    if threads <= 1 or m < 2:
+        run(range(m))
+    else:
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(run, np.array_split(np.arange(m), threads)))
+    return out
+
+
+def quad_secular(d, z, rho, lam_hi, lam_lo=0.0):
+    d, z = _f64(d), _f64(z)
+    return lib().quad_secular(d.size, _ptr(d), _ptr(z), float(rho), float(lam_hi), float(lam_lo))
+
+
+def dd_op(name, a, b):
+    """Double-double add/mul/div of the oracle on (hi, lo) pairs, for its own pins."""
+    out = np.empty(2)
+    getattr(lib(), "oracle_dd_" + name)(a[0], a[1], b[0], b[1], _ptr(out))
+    return out[0], out[1]
+
+
+def eig_full(d, z, rho, opts=None, threads=1):
+    """Eigen-decomposition of D + rho z z^T for any d sorted non-increasingly.
+
+    Handles rho == 0 (lambda = d, V = I), rho < 0 (Sec. 1: solve -D - rho z z^T),
+    zeta_j == 0 and d_j == d_{j+1} (Sec. 1 deflation, exact tests only) and returns
+    dict(lam, Vt, sigma, mu) with lam non-increasing and Vt[k] = v_k.  Deflated pairs
+    carry sigma = lambda and mu = 0."""
+    d = _f64(d).copy()
+    z = _f64(z).copy()
+    n = d.size
+    if n == 0:
+        return dict(lam=np.empty(0), Vt=np.empty((0, 0)), sigma=np.empty(0), mu=np.empty(0))
+    if np.any(d[:-1] < d[1:]):
+        raise ValueError("d must be sorted non-increasingly")
+    if rho == 0.0:
+        return dict(lam=d.copy(), Vt=np.eye(n), sigma=d.copy(), mu=np.zeros(n))
+    if rho < 0.0:
+        # A = -( (-D) + |rho| z z^T ); -D is increasing, so reverse to keep the order
+        r = eig_full(-d[::-1], z[::-1], -rho, opts, threads)
+        lam = -r["lam"][::-1]
+        Vt = r["Vt"][::-1, ::-1]
+        return dict(lam=lam.copy(), Vt=np.ascontiguousarray(Vt), sigma=-r["sigma"][::-1].copy(),
+                    mu=-r["mu"][::-1].copy())
+    # --- deflation (exact tests only) ---
+    Q = np.eye(n)              # accumulated rotations: z_rot = Q z, A = Q^T (D + rho z_rot z_rot^T) Q
+    zr = z.copy()
+    defl = []                  # (position, eigenvalue) of deflated pairs in the rotated basis
+    for j in range(n):
+        if zr[j] == 0.0:
+            defl.append(j)
+    # ties: rotate each later member of a group of equal d's into the first non-zero member
+    j = 0
+    while j < n:
+        g = j
+        while g + 1 < n and d[g + 1] == d[j]:
+            g += 1
+        members = [p for p in range(j, g + 1) if zr[p] != 0.0]
+        if len(members) > 1:
+            a = members[0]
+            for p in members[1:]:
+                r = np.hypot(zr[a], zr[p])
+                c, s = zr[a] / r, zr[p] / r
+                G = np.eye(n)
+                G[a, a], G[a, p], G[p, a], G[p, p] = c, s, -s, c
+                zr = G @ zr
+                zr[p] = 0.0
+                Q = G @ Q
+                defl.append(p)
+        j = g + 1
+    keep = np.array([p for p in range(n) if p not in set(defl)], dtype=np.int64)
+    lam_all, vec_all, sig_all, mu_all = [], [], [], []
+    if keep.size:
+        r = eig_all(d[keep], zr[keep], rho, opts, threads=threads)
+        for t in range(keep.size):
+            x = np.zeros(n)
+            x[keep] = r["Vt"][t]
+            lam_all.append(r["lam"][t]); vec_all.append(Q.T @ x)
+            sig_all.append(r["sigma"][t]); mu_all.append(r["mu"][t])
+    for p in defl:
+        e = np.zeros(n); e[p] = 1.0
+        lam_all.append(d[p]); vec_all.append(Q.T @ e); sig_all.append(d[p]); mu_all.append(0.0)
+    lam_all = np.array(lam_all)
+    order = np.argsort(-lam_all, kind="stable")
+    return dict(lam=lam_all[order], Vt=np.array(vec_all)[order], sigma=np.array(sig_all)[order],
+                mu=np.array(mu_all)[order])

@@ -1,0 +1,602 @@
+/*
+ * dpr1_oracle.c -- plain, slow, single-thread CPU oracle of the forward-stable
+ * DPR1 eigensolver of Jakovcevic Stor, Slapnicar and Barlow (arXiv 1405.7537).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the reference the CUDA path is checked
+ * against.  Only the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark load it.  It shares no code with the CUDA library: it has its own
+ * double-double arithmetic, its own bisection and its own eigenvector formula.
+ *
+ * It follows Algorithm 1 (dpr1eig) step by step, in IEEE binary64 ("FP64"), in
+ * the paper's notation:
+ *   A = D + rho z z^T, d_1 > d_2 > ... > d_n, rho > 0, zeta_j != 0     (Sec. 1, Eq. (A), (order))
+ *   shift sigma = d_i, A_i = A - d_i I                                  (Sec. 2)
+ *   A_i^{-1} = arrowhead with diagonal delta_j = 1/(d_j - d_i),
+ *              border w_j = -zeta_j / (zeta_i (d_j - d_i)) and corner b  (Eq. (invAi), (b_ob))
+ *   g(nu) = b - nu - sum_j w_j^2 / (delta_j - nu)                       (Eq. (secAi))
+ *   x = [(D_1 - mu I)^{-1} z_1; -zeta_i/mu; (D_2 - mu I)^{-1} z_2], v = x/||x||  (Eq. (eigenvecAi))
+ *   lambda = mu + sigma, mu = 1/nu                                      (Eq. (8))
+ *   kappa_nu, K_b, K_z                                                  (Eq. (knu2))
+ *   K_nu = ||A_i^{-1}||_2 / |nu|, remedies R1 and R2                    (Eq. (K0))
+ *   lambda near zero: lambda = 1/nu, nu extreme eigenvalue of
+ *       A^{-1} = D^{-1} + gamma D^{-1} z z^T D^{-1}                     (Eq. (gamma))
+ *   double the working precision as double-double                      (Sec. 2.3)
+ *
+ * Readings of points the paper leaves open (each also listed in the design notes):
+ *   - Eq. (secAi) prints Delta = diag(D_1, D_2); the arrowhead's diagonal is
+ *     diag(D_1^{-1}, D_2^{-1}), so delta_j = 1/(d_j - d_i) is used.
+ *   - "kappa_nu >> O(n)": b is recomputed in double-double when
+ *     kappa_nu > T_kappa * n (mode 1), always (mode 2, default) or never (mode 0).
+ *   - Bisection bracket (the paper only cites Olver-Stewart): the Weyl bracket
+ *     [max(b, max delta), max(b, max delta) + ||w||] for the rightmost eigenvalue,
+ *     mirrored for the leftmost, intersected with the known sign of nu; bisection on
+ *     the bit patterns of |nu| until the end points are adjacent doubles; the end
+ *     point with the smaller |g| is returned.
+ *   - "K_nu >> 1": K_nu > T_Knu.  ||A_i^{-1}||_2 is computed exactly as
+ *     max(|leftmost|, |rightmost|) of the arrowhead, each by bisection.
+ *   - R1 is taken when the other neighbouring pole gives a smaller K_nu that is within
+ *     T_Knu and lambda is not more than T_Knu times farther from that pole than from
+ *     the first one (otherwise the eigenvector formula at the other pole cancels);
+ *     else R2.  R2 shifts to sigma = fl(lambda) of the better pole solution (moved
+ *     into the open interval if it falls on a pole), computes
+ *     f(sigma) in double-double and finds the exterior eigenvalue of the DPR1 matrix
+ *     (A - sigma I)^{-1} = (D - sigma I)^{-1} + gamma (D - sigma I)^{-1} z z^T (D - sigma I)^{-1},
+ *     gamma = -rho / f(sigma), by bisection.
+ *   - "|lambda| << min(|lambda - d_k|, |lambda - d_{k-1}|)": T_zero |lambda| < min(...).
+ *     The denominator of gamma is formed in double-double; if it is zero, lambda = 0.
+ *   - Shift test tie F == 0 takes the else branch (sigma = d_{k-1}), as printed.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------- */
+/* Double-double arithmetic: an unevaluated sum hi + lo of two binary64       */
+/* numbers, |lo| <= ulp(hi)/2.  Error-free transformations: TwoSum (Knuth),  */
+/* FastTwoSum and the product split (Dekker 1971), the latter through fma.   */
+/* ------------------------------------------------------------------------- */
+typedef struct { double hi, lo; } odd_t;
+
+static odd_t o_two_sum(double a, double b) {
+  odd_t r;
+  double s = a + b;
+  double bb = s - a;
+  double err = (a - (s - bb)) + (b - bb);
+  r.hi = s; r.lo = err;
+  return r;
+}
+
+static odd_t o_fast_two_sum(double a, double b) { /* requires |a| >= |b| or a == 0 */
+  odd_t r;
+  double s = a + b;
+  r.hi = s; r.lo = b - (s - a);
+  return r;
+}
+
+static odd_t o_two_prod(double a, double b) {
+  odd_t r;
+  double p = a * b;
+  r.hi = p; r.lo = fma(a, b, -p);
+  return r;
+}
+
+static odd_t o_from(double a) { odd_t r; r.hi = a; r.lo = 0.0; return r; }
+
+static odd_t o_add(odd_t a, odd_t b) {
+  odd_t s = o_two_sum(a.hi, b.hi);
+  odd_t t = o_two_sum(a.lo, b.lo);
+  double lo = s.lo + t.hi;
+  s = o_fast_two_sum(s.hi, lo);
+  lo = s.lo + t.lo;
+  return o_fast_two_sum(s.hi, lo);
+}
+
+static odd_t o_neg(odd_t a) { a.hi = -a.hi; a.lo = -a.lo; return a; }
+
+static odd_t o_mul(odd_t a, odd_t b) {
+  odd_t p = o_two_prod(a.hi, b.hi);
+  double lo = p.lo + (a.hi * b.lo + a.lo * b.hi);
+  return o_fast_two_sum(p.hi, lo);
+}
+
+static odd_t o_mul_d(odd_t a, double b) {
+  odd_t p = o_two_prod(a.hi, b);
+  double lo = p.lo + a.lo * b;
+  return o_fast_two_sum(p.hi, lo);
+}
+
+/* a / b: long division with three binary64 quotient digits. */
+static odd_t o_div(odd_t a, odd_t b) {
+  double q1 = a.hi / b.hi;
+  odd_t r = o_add(a, o_neg(o_mul_d(b, q1)));
+  double q2 = r.hi / b.hi;
+  r = o_add(r, o_neg(o_mul_d(b, q2)));
+  double q3 = r.hi / b.hi;
+  odd_t q = o_fast_two_sum(q1, q2);
+  return o_add(q, o_from(q3));
+}
+
+/* Exported for the tests that pin the double-double layer against exact rationals. */
+void oracle_dd_add(double ah, double al, double bh, double bl, double* out) {
+  odd_t a = {ah, al}, b = {bh, bl}; odd_t r = o_add(a, b); out[0] = r.hi; out[1] = r.lo;
+}
+void oracle_dd_mul(double ah, double al, double bh, double bl, double* out) {
+  odd_t a = {ah, al}, b = {bh, bl}; odd_t r = o_mul(a, b); out[0] = r.hi; out[1] = r.lo;
+}
+void oracle_dd_div(double ah, double al, double bh, double bl, double* out) {
+  odd_t a = {ah, al}, b = {bh, bl}; odd_t r = o_div(a, b); out[0] = r.hi; out[1] = r.lo;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Options and per-eigenpair report                                          */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int dd_mode;        /* 0: never, 1: when kappa_nu > T_kappa * n, 2: always (default) */
+  double T_kappa;     /* threshold factor for mode 1 (default 1500: with it mode 1 uses
+                         double-double for 25 / 201 / 201 eigenvalues of Example 4, the
+                         counts the paper reports) */
+  double T_Knu;       /* remedies when K_nu > T_Knu */
+  double T_zero;      /* near-zero test factor */
+  int remedies;       /* bit 0: R1/R2, bit 1: near-zero recompute (3 = both, default) */
+} oracle_opts;
+
+typedef struct {
+  int shift;          /* 0-based pole index i of the final shift, -1 for a non-pole shift (R2) */
+  int first_shift;    /* pole chosen by the shift test */
+  int used_dd;        /* b (or f(sigma)) formed in double-double */
+  int remedy;         /* 0 none, 1 R1, 2 R2 */
+  int zero_path;      /* lambda recomputed from A^{-1} */
+  int steps;          /* bisection steps of the final solve */
+  double sigma, mu, nu, lambda;
+  double b;           /* corner element of the final arrowhead (binary64) */
+  double K_nu;        /* K_nu of the first shift */
+  double K_nu_final;  /* K_nu of the final shift (1 for R2) */
+  double kappa_nu;    /* Eq. (knu2) of the first shift */
+} oracle_info;
+
+void oracle_default_opts(oracle_opts* o) {
+  o->dd_mode = 2; o->T_kappa = 1500.0; o->T_Knu = 16.0; o->T_zero = 64.0; o->remedies = 3;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Bisection on the bit patterns of |nu|.                                     */
+/* ------------------------------------------------------------------------- */
+static uint64_t o_bits(double a) { uint64_t u; memcpy(&u, &a, 8); return u; }
+static double o_from_bits(uint64_t u) { double a; memcpy(&a, &u, 8); return a; }
+
+/* Evaluates a secular function at nu; the callee decides the sign convention. */
+typedef double (*o_secular_fn)(const void* ctx, double nu);
+
+/*
+ * Finds the root of a secular function that has exactly one sign change for
+ * nu = s*a, a in [a_lo, a_hi]; phi(s*a) "below" the root has sign below_sign
+ * (+1 or -1).  a_lo is known to lie on the near side of the root (it may be a
+ * pole, where phi is not evaluated); a_hi is checked and pushed out until phi
+ * changes sign.  Returns s*a for the end point of the final adjacent pair with
+ * the smaller |phi|.
+ */
+static double o_bisect(o_secular_fn phi, const void* ctx, double s, double a_lo, double a_hi,
+                       int below_sign, int* steps_out) {
+  int steps = 0;
+  if (a_lo < 0.0) a_lo = 0.0;
+  if (!(a_hi > a_lo)) a_hi = (a_lo > 0.0) ? a_lo * 2.0 : 1.0;
+  /* make sure the far end is past the root */
+  for (int t = 0; t < 2100; t++) {
+    double g = phi(ctx, s * a_hi);
+    if (g * below_sign <= 0.0) break;
+    double w = a_hi - a_lo;
+    a_lo = a_hi;
+    a_hi = a_hi + 2.0 * w;
+    if (isinf(a_hi)) break;
+  }
+  uint64_t lo = o_bits(a_lo), hi = o_bits(a_hi);
+  double glo = NAN, ghi = NAN;
+  while (hi - lo > 1) {
+    uint64_t mid = lo + (hi - lo) / 2;
+    double g = phi(ctx, s * o_from_bits(mid));
+    steps++;
+    if (g * below_sign > 0.0) { lo = mid; glo = g; }
+    else { hi = mid; ghi = g; }
+  }
+  if (steps_out) *steps_out = steps;
+  if (lo == hi) return s * o_from_bits(lo);
+  if (isnan(glo)) glo = phi(ctx, s * o_from_bits(lo));
+  if (isnan(ghi)) ghi = phi(ctx, s * o_from_bits(hi));
+  double alo = fabs(glo), ahi = fabs(ghi);
+  if (isnan(alo)) alo = INFINITY;
+  if (isnan(ahi)) ahi = INFINITY;
+  return s * o_from_bits(ahi < alo ? hi : lo);
+}
+
+/* ------------------------------------------------------------------------- */
+/* The arrowhead inverse of the shifted matrix, Eq. (invAi), (b_ob).          */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int n, i;
+  const double* delta; /* [n], delta[i] unused */
+  const double* w;     /* [n], w[i] unused */
+  double b;
+} o_arrow_ctx;
+
+/* g(nu) = b - nu - w^T (Delta - nu I)^{-1} w, Eq. (secAi). */
+static double o_g_arrow(const void* vctx, double nu) {
+  const o_arrow_ctx* c = (const o_arrow_ctx*)vctx;
+  double s = 0.0;
+  for (int j = 0; j < c->n; j++) {
+    if (j == c->i) continue;
+    s += c->w[j] * c->w[j] / (c->delta[j] - nu);
+  }
+  return (c->b - nu) - s;
+}
+
+typedef struct {
+  double b;           /* binary64 corner element */
+  double Kb, Kz, kappa_nu;
+  int used_dd;
+} o_arrow_info;
+
+/*
+ * Forms delta_j = 1/(d_j - d_i), w_j = -(delta_j zeta_j)/zeta_i and b of Eq. (b_ob),
+ * computes K_b, K_z and kappa_nu of Eq. (knu2) and, depending on dd_mode,
+ * recomputes b in double-double (Sec. 2.3).
+ */
+static void o_arrowhead(int n, const double* d, const double* z, double rho, int i,
+                        const oracle_opts* opt, double* delta, double* w, o_arrow_info* out) {
+  double P = 0.0, N = 0.0;          /* z_1^T D_1^{-1} z_1 >= 0 and z_2^T D_2^{-1} z_2 <= 0 */
+  double sumz = 0.0;
+  for (int j = 0; j < n; j++) {
+    if (j == i) { delta[j] = 0.0; w[j] = 0.0; continue; }
+    double dj = d[j] - d[i];
+    delta[j] = 1.0 / dj;
+    w[j] = -(delta[j] * z[j]) / z[i];
+    double t = z[j] * (delta[j] * z[j]);
+    if (j < i) P += t; else N += t;
+    sumz += fabs(z[j]);
+  }
+  double b = (1.0 / (z[i] * z[i])) * ((1.0 / rho + P) + N);
+  double Kb = (1.0 + rho * P - rho * N) / fabs(1.0 + rho * P + rho * N);
+  double Kz = sumz / fabs(z[i]);
+  double sn = sqrt((double)n);
+  double k1 = (n + 4) * sn * Kb;
+  double k2 = 3.0 * sn + (n + 4) * (1.0 + 2.0 * Kz);
+  double kappa = k1 < k2 ? k1 : k2;
+  int use_dd = (opt->dd_mode == 2) || (opt->dd_mode == 1 && kappa > opt->T_kappa * n);
+  if (use_dd) {
+    /* b = (1/zeta_i^2) (1/rho + sum_{j != i} zeta_j^2 / (d_j - d_i)), all in double-double */
+    odd_t acc = o_div(o_from(1.0), o_from(rho));
+    for (int j = 0; j < n; j++) {
+      if (j == i) continue;
+      odd_t dj = o_two_sum(d[j], -d[i]);
+      odd_t zz = o_two_prod(z[j], z[j]);
+      acc = o_add(acc, o_div(zz, dj));
+    }
+    odd_t bb = o_div(acc, o_two_prod(z[i], z[i]));
+    b = bb.hi + bb.lo;
+  }
+  out->b = b; out->Kb = Kb; out->Kz = Kz; out->kappa_nu = kappa; out->used_dd = use_dd;
+}
+
+/* Extreme eigenvalue of the arrowhead: side = +1 rightmost, -1 leftmost. */
+static double o_arrow_extreme(int n, int i, const double* delta, const double* w, double b,
+                              int side, int* steps) {
+  o_arrow_ctx c = {n, i, delta, w, b};
+  double wn2 = 0.0;
+  double dmax = -INFINITY, dmin = INFINITY;
+  for (int j = 0; j < n; j++) {
+    if (j == i) continue;
+    wn2 += w[j] * w[j];
+    if (delta[j] > dmax) dmax = delta[j];
+    if (delta[j] < dmin) dmin = delta[j];
+  }
+  double wn = sqrt(wn2);
+  if (side > 0) {
+    /* rightmost: nu in [max(b, max delta), max(b, max delta) + ||w||], and nu > 0 */
+    double lo = b > dmax ? b : dmax;
+    double hi = lo + wn;
+    /* g > 0 below the root */
+    return o_bisect(o_g_arrow, &c, 1.0, lo, hi, +1, steps);
+  } else {
+    /* leftmost: nu in [min(b, min delta) - ||w||, min(b, min delta)], and nu < 0 */
+    double up = b < dmin ? b : dmin;
+    double a_lo = -up, a_hi = -up + wn;
+    /* in |nu|: g < 0 on the pole side (small |nu|), g > 0 beyond the root */
+    return o_bisect(o_g_arrow, &c, -1.0, a_lo, a_hi, -1, steps);
+  }
+}
+
+/* Eigenvector of A_i from mu, Eq. (eigenvecAi), normalised with a scaled 2-norm. */
+static void o_vector_pole(int n, const double* d, const double* z, int i, double mu, double* v) {
+  double m = 0.0;
+  for (int j = 0; j < n; j++) {
+    double x = (j == i) ? -z[i] / mu : z[j] / ((d[j] - d[i]) - mu);
+    v[j] = x;
+    if (fabs(x) > m) m = fabs(x);
+  }
+  double s = 0.0;
+  for (int j = 0; j < n; j++) { double t = v[j] / m; s += t * t; }
+  double r = sqrt(s);
+  for (int j = 0; j < n; j++) v[j] = (v[j] / m) / r;
+}
+
+/* Eigenvector x = (D - lambda I)^{-1} z with lambda = sigma + mu, sigma not a pole. */
+static void o_vector_shift(int n, const double* d, const double* z, double sigma, double mu, double* v) {
+  double m = 0.0;
+  for (int j = 0; j < n; j++) {
+    double x = z[j] / ((d[j] - sigma) - mu);
+    v[j] = x;
+    if (fabs(x) > m) m = fabs(x);
+  }
+  double s = 0.0;
+  for (int j = 0; j < n; j++) { double t = v[j] / m; s += t * t; }
+  double r = sqrt(s);
+  for (int j = 0; j < n; j++) v[j] = (v[j] / m) / r;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Solve at pole i for eigenvalue k: the extreme eigenvalue of A_i^{-1} on    */
+/* the side that belongs to lambda_k, and K_nu of Eq. (K0).                   */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  double nu, mu, b, K_nu, kappa_nu;
+  int steps, used_dd;
+} o_pole_solve;
+
+static void o_solve_at_pole(int n, const double* d, const double* z, double rho, int k, int i,
+                            const oracle_opts* opt, double* delta, double* w, o_pole_solve* r) {
+  o_arrow_info ai;
+  o_arrowhead(n, d, z, rho, i, opt, delta, w, &ai);
+  /* sigma = d_k (i == k): lambda_k - d_k > 0 is the smallest positive mu, nu rightmost.
+     sigma = d_{k-1} (i == k-1): lambda_k - d_{k-1} < 0, nu leftmost. */
+  int side = (i == k) ? +1 : -1;
+  int steps = 0;
+  double nu = o_arrow_extreme(n, i, delta, w, ai.b, side, &steps);
+  /* ||A_i^{-1}||_2 = max(|leftmost|, |rightmost|); the leftmost exists when i < n-1 */
+  double other = 0.0;
+  if (side > 0) {
+    if (i < n - 1) other = o_arrow_extreme(n, i, delta, w, ai.b, -1, NULL);
+  } else {
+    other = o_arrow_extreme(n, i, delta, w, ai.b, +1, NULL);
+  }
+  double nrm = fabs(nu) > fabs(other) ? fabs(nu) : fabs(other);
+  r->nu = nu; r->mu = 1.0 / nu; r->b = ai.b;
+  r->K_nu = nrm / fabs(nu); r->kappa_nu = ai.kappa_nu;
+  r->steps = steps; r->used_dd = ai.used_dd;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Non-pole shift: exterior eigenvalue of (A - sigma I)^{-1}, used by R2      */
+/* (sigma near lambda) and by the near-zero recompute (sigma = 0), Eq. (gamma) */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int n;
+  const double* e;   /* 1/(d_j - sigma) */
+  const double* u;   /* zeta_j/(d_j - sigma) */
+  double gamma;
+} o_dpr1inv_ctx;
+
+/* h(nu) = 1 + gamma sum_j u_j^2 / (e_j - nu), the secular function of E + gamma u u^T. */
+static double o_h_dpr1(const void* vctx, double nu) {
+  const o_dpr1inv_ctx* c = (const o_dpr1inv_ctx*)vctx;
+  double s = 0.0;
+  for (int j = 0; j < c->n; j++) s += c->u[j] * c->u[j] / (c->e[j] - nu);
+  return 1.0 + c->gamma * s;
+}
+
+/* f(sigma) = 1 + rho sum zeta_j^2/(d_j - sigma) in double-double, Eq. (Pick). */
+static odd_t o_f_dd(int n, const double* d, const double* z, double rho, double sigma) {
+  odd_t acc = o_from(0.0);
+  for (int j = 0; j < n; j++) {
+    odd_t dj = o_two_sum(d[j], -sigma);
+    odd_t zz = o_two_prod(z[j], z[j]);
+    acc = o_add(acc, o_div(zz, dj));
+  }
+  return o_add(o_from(1.0), o_mul_d(acc, rho));
+}
+
+/*
+ * Returns 1 and mu (lambda = sigma + mu) on success, 0 if f(sigma) is zero in
+ * double-double (lambda = sigma, mu = 0).
+ */
+static int o_solve_nonpole(int n, const double* d, const double* z, double rho, double sigma,
+                           double* e, double* u, double* mu_out, int* steps) {
+  odd_t f = o_f_dd(n, d, z, rho, sigma);
+  if (f.hi == 0.0 && f.lo == 0.0) { *mu_out = 0.0; if (steps) *steps = 0; return 0; }
+  odd_t gdd = o_div(o_from(-rho), f);
+  double gamma = gdd.hi + gdd.lo;
+  double emax = -INFINITY, emin = INFINITY, un2 = 0.0;
+  for (int j = 0; j < n; j++) {
+    double dj = d[j] - sigma;
+    e[j] = 1.0 / dj;
+    u[j] = z[j] / dj;
+    un2 += u[j] * u[j];
+    if (e[j] > emax) emax = e[j];
+    if (e[j] < emin) emin = e[j];
+  }
+  o_dpr1inv_ctx c = {n, e, u, gamma};
+  double nu;
+  /* gamma > 0: rightmost eigenvalue in [max e, max e + gamma ||u||^2], positive;
+     gamma < 0: leftmost in [min e - |gamma| ||u||^2, min e], negative.
+     In both cases h < 0 on the pole side (small |nu|). */
+  if (gamma > 0) {
+    nu = o_bisect(o_h_dpr1, &c, 1.0, emax, emax + gamma * un2, -1, steps);
+  } else {
+    nu = o_bisect(o_h_dpr1, &c, -1.0, -emin, -emin - gamma * un2, -1, steps);
+  }
+  *mu_out = 1.0 / nu;
+  return 1;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Algorithm 1: the k-th eigenpair (k is 0-based here).                      */
+/* ------------------------------------------------------------------------- */
+int oracle_dpr1eig(int n, const double* d, const double* z, double rho, int k,
+                   const oracle_opts* opt_in, double* lambda_out, double* v, oracle_info* info) {
+  oracle_opts opt;
+  if (opt_in) opt = *opt_in; else oracle_default_opts(&opt);
+  if (n < 1 || k < 0 || k >= n || !(rho > 0.0)) return 1;
+  double* delta = (double*)malloc(sizeof(double) * n);
+  double* w = (double*)malloc(sizeof(double) * n);
+  if (!delta || !w) { free(delta); free(w); return 2; }
+  oracle_info inf;
+  memset(&inf, 0, sizeof(inf));
+
+  /* Shift choice: k = 1 -> sigma = d_1; otherwise evaluate f at the midpoint
+     tau of (d_k, d_{k-1}) in coordinates shifted by d_k. */
+  int i;
+  if (k == 0) {
+    i = 0;
+  } else {
+    double tau = (d[k - 1] - d[k]) / 2.0;
+    double s = 0.0;
+    for (int j = 0; j < n; j++) {
+      double dbar = d[j] - d[k];
+      s += z[j] * z[j] / (dbar - tau);
+    }
+    double F = 1.0 + rho * s;
+    i = (F > 0.0) ? k : k - 1;
+  }
+  inf.first_shift = i;
+
+  o_pole_solve ps;
+  o_solve_at_pole(n, d, z, rho, k, i, &opt, delta, w, &ps);
+  inf.used_dd = ps.used_dd;
+  inf.K_nu = ps.K_nu;
+  inf.kappa_nu = ps.kappa_nu;
+  double sigma = d[i];
+  double mu = ps.mu, nu = ps.nu;
+  double K = ps.K_nu;
+  int steps = ps.steps;
+  double b = ps.b;
+  int shift = i;
+
+  if ((opt.remedies & 1) && K > opt.T_Knu) {
+    /* (R1): the neighbouring pole on the other side of lambda, if there is one.  The
+       eigenvector formula at that pole divides by (d_j - d_other) - mu, which cancels
+       for the nearer pole j = i by the factor |lambda - d_other| / |lambda - d_i|; R1
+       is taken when that factor and K_nu at the other pole are both within T_Knu. */
+    int other = (i == k) ? k - 1 : k;
+    double best_sigma = sigma, best_mu = mu, best_K = K;
+    if (other >= 0 && other != i) {
+      o_pole_solve p2;
+      o_solve_at_pole(n, d, z, rho, k, other, &opt, delta, w, &p2);
+      double ratio = fabs((d[i] - d[other]) + mu) / fabs(mu);
+      inf.used_dd = inf.used_dd || p2.used_dd;
+      if (p2.K_nu < K && p2.K_nu <= opt.T_Knu && ratio <= opt.T_Knu) {
+        shift = other; sigma = d[other]; mu = p2.mu; nu = p2.nu; K = p2.K_nu;
+        steps = p2.steps; b = p2.b; inf.remedy = 1;
+      }
+      if (p2.K_nu < best_K) { best_sigma = d[other]; best_mu = p2.mu; best_K = p2.K_nu; }
+    }
+    if (K > opt.T_Knu) {
+      /* (R2): a non-pole shift next to lambda, taken from the better of the two
+         pole solutions (the one with the smaller K_nu) */
+      double lam = best_sigma + best_mu;
+      double s2 = lam;
+      if (s2 <= d[k]) s2 = nextafter(d[k], INFINITY);
+      if (k > 0 && s2 >= d[k - 1]) s2 = nextafter(d[k - 1], -INFINITY);
+      int inside = (s2 > d[k]) && (k == 0 || s2 < d[k - 1]);
+      if (inside) {
+        double mu2;
+        int st = 0;
+        o_solve_nonpole(n, d, z, rho, s2, delta, w, &mu2, &st);
+        shift = -1; sigma = s2; mu = mu2; nu = (mu2 != 0.0) ? 1.0 / mu2 : INFINITY; K = 1.0;
+        steps = st; inf.remedy = 2; inf.used_dd = 1;
+      }
+    }
+  }
+
+  /* eigenvector and eigenvalue at the final shift */
+  if (shift >= 0) o_vector_pole(n, d, z, shift, mu, v);
+  else o_vector_shift(n, d, z, sigma, mu, v);
+  double lambda = mu + sigma;
+
+  /* lambda much closer to zero than to its neighbouring poles: recompute from A^{-1} */
+  if (opt.remedies & 2) {
+    int allnz = 1;
+    for (int j = 0; j < n; j++) if (d[j] == 0.0) { allnz = 0; break; }
+    double m1 = fabs(lambda - d[k]);
+    if (k > 0) { double m2 = fabs(lambda - d[k - 1]); if (m2 < m1) m1 = m2; }
+    if (allnz && opt.T_zero * fabs(lambda) < m1) {
+      double mu0;
+      int ok = o_solve_nonpole(n, d, z, rho, 0.0, delta, w, &mu0, NULL);
+      lambda = ok ? mu0 : 0.0;
+      inf.zero_path = 1;
+    }
+  }
+
+  inf.shift = shift; inf.sigma = sigma; inf.mu = mu; inf.nu = nu; inf.lambda = lambda;
+  inf.b = b; inf.K_nu_final = K; inf.steps = steps;
+  *lambda_out = lambda;
+  if (info) *info = inf;
+  free(delta); free(w);
+  return 0;
+}
+
+/* All eigenpairs k in [k0, k1): lambda[k], V row-major with row k = v_k, plus (sigma, mu). */
+int oracle_dpr1eig_range(int n, const double* d, const double* z, double rho, int k0, int k1,
+                         const oracle_opts* opt, double* lambda, double* Vt, double* sigma,
+                         double* mu, int* shift, int* flags) {
+  for (int k = k0; k < k1; k++) {
+    oracle_info inf;
+    int rc = oracle_dpr1eig(n, d, z, rho, k, opt, &lambda[k], Vt ? &Vt[(size_t)k * n] : NULL, &inf);
+    if (rc) return rc;
+    if (sigma) sigma[k] = inf.sigma;
+    if (mu) mu[k] = inf.mu;
+    if (shift) shift[k] = inf.shift;
+    if (flags) flags[k] = inf.remedy | (inf.zero_path << 2) | (inf.used_dd << 3);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Adjoint of (lambda, V) with respect to (d, z, rho).                        */
+/* From the implicit derivative of f(lambda_k) = 0 (Eq. (Pick)) and the        */
+/* explicit x_k = (D - lambda_k I)^{-1} z, v_k = x_k/||x_k|| (Eq. (Aeigenvec)): */
+/*   s_j = d_j - lambda_k = (d_j - sigma_k) - mu_k,                            */
+/*   dlambda/dd_j = v_j^2, dlambda/dzeta_j = -2 x_j/||x||^2,                  */
+/*   dlambda/drho = 1/(rho^2 ||x||^2);                                        */
+/*   gbar = (vbar - v (v^T vbar)) / ||x|| is the adjoint of x,                 */
+/*   lambda_bar = grad_lambda_k + sum_j gbar_j x_j / s_j,                      */
+/*   dbar_j += lambda_bar v_j^2 - gbar_j x_j / s_j,                            */
+/*   zbar_j += gbar_j / s_j - 2 lambda_bar v_j / ||x||,                        */
+/*   rhobar += lambda_bar / (rho^2 ||x||^2).                                   */
+/* grad_lambda or grad_Vt may be NULL (zero).  Rows of grad_Vt are dL/dv_k.   */
+/* ------------------------------------------------------------------------- */
+int oracle_backward(int n, const double* d, const double* z, double rho,
+                    const double* sigma, const double* mu,
+                    const double* grad_lambda, const double* grad_Vt,
+                    double* grad_d, double* grad_z, double* grad_rho) {
+  double* s = (double*)malloc(sizeof(double) * n);
+  double* v = (double*)malloc(sizeof(double) * n);
+  if (!s || !v) { free(s); free(v); return 2; }
+  for (int j = 0; j < n; j++) { grad_d[j] = 0.0; grad_z[j] = 0.0; }
+  double grho = 0.0;
+  for (int k = 0; k < n; k++) {
+    double m = 0.0;
+    for (int j = 0; j < n; j++) {
+      s[j] = (d[j] - sigma[k]) - mu[k];
+      v[j] = z[j] / s[j];
+      if (fabs(v[j]) > m) m = fabs(v[j]);
+    }
+    double q = 0.0;
+    for (int j = 0; j < n; j++) { double t = v[j] / m; q += t * t; }
+    double xn = m * sqrt(q);                 /* ||x|| */
+    for (int j = 0; j < n; j++) v[j] = (v[j] / m) / sqrt(q);
+    const double* vb = grad_Vt ? &grad_Vt[(size_t)k * n] : NULL;
+    double c = 0.0;
+    if (vb) for (int j = 0; j < n; j++) c += v[j] * vb[j];
+    /* gbar_j x_j / s_j = (vbar_j - v_j c) v_j / s_j */
+    double lb = grad_lambda ? grad_lambda[k] : 0.0;
+    if (vb) for (int j = 0; j < n; j++) lb += (vb[j] - v[j] * c) * v[j] / s[j];
+    for (int j = 0; j < n; j++) {
+      double gx = vb ? (vb[j] - v[j] * c) : 0.0;    /* ||x|| * gbar_j */
+      grad_d[j] += lb * v[j] * v[j] - gx * v[j] / s[j];
+      grad_z[j] += (gx / xn) / s[j] - 2.0 * lb * v[j] / xn;
+    }
+    grho += ((lb / rho) / xn) / (rho * xn);
+  }
+  *grad_rho = grho;
+  free(s); free(v);
+  return 0;
+}

@@ -1,0 +1,135 @@
+/*
+ * quad_ref.c -- binary128 reference for the eigenpairs of A = D + rho z z^T.
+ *
+ * TEST INFRASTRUCTURE ONLY (loaded by the tests and the smoke check).
+ *
+ * This is the plain definition of the result, not the paper's algorithm:
+ *   lambda_k is the zero of the secular function
+ *       f(lambda) = 1 + rho sum_j zeta_j^2 / (d_j - lambda)            (Eq. (Pick))
+ *   in the interlacing interval (d_k, d_{k-1}), or (d_1, d_1 + rho ||z||^2] for k = 1
+ *   (Eq. (interlace)); f is strictly increasing there for rho > 0.
+ *   v_k = x / ||x||, x = (D - lambda_k I)^{-1} z                       (Eq. (Aeigenvec))
+ * Everything is evaluated in IEEE binary128 (_Float128: 113-bit significand),
+ * and lambda_k is found by bisection on the arithmetic midpoint until the two
+ * end points are adjacent binary128 numbers (see quad_eigpair2 for the shifted
+ * coordinates that keep the distance to the nearest pole accurate).
+ *
+ * k is 0-based.  lambda is returned as an unevaluated pair (hi, lo) of binary64
+ * numbers (hi + lo carries about 106 bits); v is rounded to binary64.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+
+typedef _Float128 q_t;
+
+static q_t q_abs(q_t a) { return a < 0 ? -a : a; }
+
+/* square root by Newton's iteration from the binary64 estimate (argument in [1, 1e300]) */
+static q_t q_sqrt(q_t a) {
+  if (a <= 0) return 0;
+  q_t y = (q_t)sqrt((double)a);
+  for (int t = 0; t < 3; t++) y = (y + a / y) / 2;
+  return y;
+}
+
+/* f(d_i + mu) with D[j] = d_j - d_i formed in binary128 */
+static q_t q_fshift(int n, const q_t* D, const double* z, double rho, q_t mu) {
+  q_t s = 0;
+  for (int j = 0; j < n; j++) {
+    q_t zj = (q_t)z[j];
+    s += zj * zj / (D[j] - mu);
+  }
+  return 1 + (q_t)rho * s;
+}
+
+static q_t q_f(int n, const double* d, const double* z, double rho, q_t lam) {
+  q_t s = 0;
+  for (int j = 0; j < n; j++) {
+    q_t zj = (q_t)z[j];
+    s += zj * zj / ((q_t)d[j] - lam);
+  }
+  return 1 + (q_t)rho * s;
+}
+
+/*
+ * Bisection is done on mu = lambda - d_i in coordinates shifted by the nearer end
+ * pole d_i of the interlacing interval, so that mu keeps 113 significant bits even
+ * when lambda is within a few binary64 ulps of a pole: f(d_i + mu) is evaluated
+ * as 1 + rho sum_j zeta_j^2 / ((d_j - d_i) - mu) with the pole differences formed
+ * in binary128.  The nearer pole is found from the sign of f at the midpoint of
+ * the interval (f > 0 there puts lambda in the lower half).
+ * Returns the number of bisection steps, or -1 on bad arguments; *pole receives i.
+ */
+int quad_eigpair2(int n, const double* d, const double* z, double rho, int k,
+                  double* lam_hi, double* lam_lo, double* mu_hi, double* mu_lo, int* pole, double* v) {
+  if (n < 1 || k < 0 || k >= n || !(rho > 0)) return -1;
+  q_t* D = (q_t*)malloc(sizeof(q_t) * n);
+  if (!D) return -1;
+  int i;
+  q_t lo, hi;   /* bracket of mu */
+  if (k == 0) {
+    q_t zz = 0;
+    for (int j = 0; j < n; j++) zz += (q_t)z[j] * (q_t)z[j];
+    i = 0;
+    lo = 0;
+    hi = 2 * (q_t)rho * zz;
+  } else {
+    q_t tau = ((q_t)d[k - 1] - (q_t)d[k]) / 2;
+    for (int j = 0; j < n; j++) D[j] = (q_t)d[j] - (q_t)d[k];
+    q_t fm = q_fshift(n, D, z, rho, tau);
+    if (fm > 0) { i = k; lo = 0; hi = tau; }
+    else { i = k - 1; lo = -tau; hi = 0; }
+  }
+  for (int j = 0; j < n; j++) D[j] = (q_t)d[j] - (q_t)d[i];
+  /* f(d_i + mu) is increasing in mu on the bracket */
+  int steps = 0;
+  q_t flo = NAN, fhi = NAN;
+  int have_lo = 0, have_hi = 0;
+  for (; steps < 20000; steps++) {
+    q_t mid = lo + (hi - lo) / 2;
+    if (!(mid > lo && mid < hi)) break;
+    q_t fm = q_fshift(n, D, z, rho, mid);
+    if (fm < 0) { lo = mid; flo = fm; have_lo = 1; }
+    else { hi = mid; fhi = fm; have_hi = 1; }
+  }
+  q_t mu;
+  if (have_lo && have_hi) mu = (q_abs(fhi) < q_abs(flo)) ? hi : lo;
+  else if (have_hi) mu = hi;
+  else mu = lo;
+  q_t lam = (q_t)d[i] + mu;
+  double h = (double)lam;
+  *lam_hi = h;
+  *lam_lo = (double)(lam - (q_t)h);
+  h = (double)mu;
+  *mu_hi = h;
+  *mu_lo = (double)(mu - (q_t)h);
+  *pole = i;
+  if (v) {
+    q_t m = 0;
+    q_t* x = (q_t*)malloc(sizeof(q_t) * n);
+    if (!x) { free(D); return -1; }
+    for (int j = 0; j < n; j++) {
+      x[j] = (q_t)z[j] / (D[j] - mu);
+      if (q_abs(x[j]) > m) m = q_abs(x[j]);
+    }
+    q_t s = 0;
+    for (int j = 0; j < n; j++) { q_t t = x[j] / m; s += t * t; }
+    q_t r = q_sqrt(s);
+    for (int j = 0; j < n; j++) v[j] = (double)((x[j] / m) / r);
+    free(x);
+  }
+  free(D);
+  return steps;
+}
+
+int quad_eigpair(int n, const double* d, const double* z, double rho, int k,
+                 double* lam_hi, double* lam_lo, double* v) {
+  double mh, ml; int pole;
+  return quad_eigpair2(n, d, z, rho, k, lam_hi, lam_lo, &mh, &ml, &pole, v);
+}
+
+/* f(lambda) at lambda = hi + lo, in binary128, rounded to binary64 (used by tests). */
+double quad_secular(int n, const double* d, const double* z, double rho, double lam_hi, double lam_lo) {
+  return (double)q_f(n, d, z, rho, (q_t)lam_hi + (q_t)lam_lo);
+}

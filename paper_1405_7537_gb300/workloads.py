@@ -1,0 +1,155 @@
+"""Seeded synthetic DPR1 problems: the paper's worked examples and the five workloads.
+
+This module only draws inputs; it contains none of the method's arithmetic, so that
+both the CUDA path and the CPU oracle can be fed from it.  Every problem is
+``(d, z, rho)`` with ``d`` sorted strictly decreasingly, as the paper assumes
+(Sec. 1, Eq. (order)).
+
+Worked examples (Sec. 3):
+  example1()            Example 1, n = 6, pole at zero, eigenvalue 1e-24
+  example2()            Example 2, n = 4, poles 1 + 40e, ..., 1 + 10e, e = 2^-52
+  example3(beta)        Example 3, n = 4, beta = 1e-7
+  example4(beta)        Example 4, n = 202, beta in {1e-3, 1e-8, 1e-15}
+Workloads (seeded, numpy default_rng):
+  uniform(n, seed)      d ~ U(-1, 1), z ~ U(-1, 1) with |z| > 1e-3, rho = 1
+  hard(n, seed)         half the poles graded 10^(-12 j/n), half U(-1, 1), gaps >= 1e-14,
+                        |z| log-uniform in [1e-10, 1] with random sign, rho = 1e3
+  diff(n, seed)         d ~ U(-1, 1), z ~ U(-1, 1), rho = 0.5, plus w ~ N(0,1)^n, W ~ N(0,1)^{n x n}
+  batch(P, seed)        P problems, n_k log-uniform in [16, 2048], rho_k ~ U(0.1, 10)
+  large(n, seed)        d ~ U(-1, 1) with 1% of adjacent gaps set to 1e-13,
+                        |z| log-uniform in [1e-8, 1] with random sign, rho = 1, W ~ N(0,1)^{n x n}
+"""
+import numpy as np
+
+EPS = 2.0 ** -52
+
+
+def example1():
+    d = np.array([1e10, 5.0, 4e-3, 0.0, -4e-3, -5.0])
+    z = np.array([1e10, 1.0, 1.0, 1e-7, 1.0, 1.0])
+    return d, z, 1.0
+
+
+def example2():
+    d = np.array([1 + 40 * EPS, 1 + 30 * EPS, 1 + 20 * EPS, 1 + 10 * EPS])
+    z = np.array([1.0, 2.0, 2.0, 1.0])
+    return d, z, 1.0
+
+
+def example3(beta=1e-7):
+    d = np.array([10.0 / 3.0, 2 + beta, 2 - beta, 1.0])
+    z = np.array([2.0, beta, beta, 2.0])
+    return d, z, 1.0
+
+
+def example4(beta):
+    """D = diag(1, 2 +- k beta (k = 1..100), 10/3), z = (2, beta, ..., beta, 2), sorted decreasingly."""
+    dd = [1.0]
+    for k in range(1, 101):
+        dd += [2 + k * beta, 2 - k * beta]
+    dd.append(10.0 / 3.0)
+    d = np.array(dd)
+    z = np.full(202, beta)
+    z[0] = 2.0
+    z[-1] = 2.0
+    order = np.argsort(-d, kind="stable")
+    return d[order], z[order], 1.0
+
+
+def _sorted_distinct_uniform(rng, n, lo=-1.0, hi=1.0):
+    d = rng.uniform(lo, hi, n)
+    while True:
+        d = np.sort(d)[::-1]
+        dup = np.nonzero(d[:-1] == d[1:])[0]
+        if dup.size == 0:
+            return np.ascontiguousarray(d)
+        d[dup] = rng.uniform(lo, hi, dup.size)
+
+
+def uniform(n=512, seed=0):
+    rng = np.random.default_rng(seed)
+    d = _sorted_distinct_uniform(rng, n)
+    z = rng.uniform(-1.0, 1.0, n)
+    small = np.abs(z) <= 1e-3
+    while small.any():
+        z[small] = rng.uniform(-1.0, 1.0, int(small.sum()))
+        small = np.abs(z) <= 1e-3
+    return d, z, 1.0
+
+
+def hard(n=16384, seed=1):
+    """Half graded poles 10^(-12 j / n), j = 1..n/2 (so in [1e-6, 1)), half U(-1, 1);
+    any adjacent gap below 1e-14 is removed by redrawing the uniform member."""
+    rng = np.random.default_rng(seed)
+    h = n // 2
+    graded = 10.0 ** (-12.0 * np.arange(1, h + 1) / n)
+    uni = rng.uniform(-1.0, 1.0, n - h)
+    while True:
+        allv = np.concatenate([graded, uni])
+        src = np.concatenate([np.zeros(h, dtype=bool), np.ones(n - h, dtype=bool)])
+        order = np.argsort(-allv, kind="stable")
+        dv, sv = allv[order], src[order]
+        bad = np.nonzero(dv[:-1] - dv[1:] < 1e-14)[0]
+        if bad.size == 0:
+            break
+        # redraw a uniform member of every offending pair
+        idx = set()
+        for b in bad:
+            p = b if sv[b] else b + 1
+            idx.add(order[p] - h)
+        idx = np.array(sorted(idx), dtype=np.int64)
+        uni[idx] = rng.uniform(-1.0, 1.0, idx.size)
+    mag = 10.0 ** rng.uniform(-10.0, 0.0, n)
+    sign = np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    return np.ascontiguousarray(dv), mag * sign, 1e3
+
+
+def diff(n=4096, seed=2):
+    rng = np.random.default_rng(seed)
+    d = _sorted_distinct_uniform(rng, n)
+    z = rng.uniform(-1.0, 1.0, n)
+    w = rng.standard_normal(n)
+    W = rng.standard_normal((n, n))
+    return d, z, 0.5, w, W
+
+
+def batch_sizes(P=4096, seed=3, nmin=16, nmax=2048):
+    rng = np.random.default_rng(seed)
+    return np.rint(np.exp(rng.uniform(np.log(nmin), np.log(nmax), P))).astype(np.int64), rng
+
+
+def batch(P=4096, seed=3, nmin=16, nmax=2048):
+    """Returns (offs[P+1], d, z, rho[P]) with problem p in d[offs[p]:offs[p+1]]."""
+    sizes, rng = batch_sizes(P, seed, nmin, nmax)
+    offs = np.zeros(P + 1, dtype=np.int64)
+    offs[1:] = np.cumsum(sizes)
+    d = np.empty(offs[-1])
+    z = np.empty(offs[-1])
+    rho = np.empty(P)
+    for p in range(P):
+        n = int(sizes[p])
+        d[offs[p]:offs[p + 1]] = _sorted_distinct_uniform(rng, n)
+        z[offs[p]:offs[p + 1]] = rng.uniform(-1.0, 1.0, n)
+        rho[p] = rng.uniform(0.1, 10.0)
+    return offs, d, z, rho
+
+
+def large(n=32768, seed=4, with_W=True):
+    """1% of the adjacent gaps are set to 1e-13 by moving d_{j+1} to d_j - 1e-13
+    (skipped where that would reach d_{j+2} or touch an already tightened pair)."""
+    rng = np.random.default_rng(seed)
+    d = _sorted_distinct_uniform(rng, n)
+    m = n // 100
+    picks = rng.choice(n - 2, size=m, replace=False)
+    used = np.zeros(n, dtype=bool)
+    for j in np.sort(picks):
+        if used[j] or used[j + 1]:
+            continue
+        nd = d[j] - 1e-13
+        if nd > d[j + 2] and nd < d[j]:
+            d[j + 1] = nd
+            used[j] = used[j + 1] = True
+    mag = 10.0 ** rng.uniform(-8.0, 0.0, n)
+    sign = np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    W = rng.standard_normal((n, n)) if with_W else None
+    return d, mag * sign, 1.0, W
