@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark of the DPR1 eigensolver on GB300: eigenpairs/s for the n = 16384 hard-spectrum
+forward solve (eigenvalues and the full eigenvector matrix, binary64).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 run under torch.distributed.run: every rank solves its own independent problem
+of the same workload (weak scaling, no collective on the data path); the reported value
+is all eigenpairs of all ranks divided by the slowest rank's time.
+
+One JSON line is printed by rank 0.  Timing: W untimed warm-up steps, then K steps, each
+a full dpr1_eig call timed with CUDA events on the launching stream, L2 flushed (256 MiB
+write) before every step outside the timed events; nvidia-smi clocks are sampled during
+the timed region.  ``--impl reference`` times the CPU oracle (Algorithm 1 in binary64 on
+the host cores) on bounded samples of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "DPR1 eigenpairs/s at n=16384 FP64, % roofline; fwd+bwd and batched vs plain"
+N_DEFAULT = 16384
+SEED = 1
+RHO = 1e3
+# binary64 peak derived from the nominal GB300 figure of 1.25 TFLOP/s: 0.625e12 fma/s, i.e.
+# 2 binary64 instructions per clock per SM on 152 SMs at the 2070 MHz maximum clock
+NOMINAL_FP64_OPS = 2 * 152 * 2070e6
+# algorithmic binary64 operations per secular term (sub, fma, mul, div, add; fma and div = 1 op)
+OPS_PER_TERM = 5
+
+
+def workload_config(n):
+    return {"workload": "DPR1 forward, hard spectrum: half the poles graded 10^(-12 j/n), half U(-1,1), "
+                        "gaps >= 1e-14; |z| log-uniform [1e-10, 1], random sign; rho = 1e3; eigenvalues "
+                        "and full V",
+            "n": n, "rho": RHO, "seed": SEED, "dtype": "binary64",
+            "l2": "flushed before every timed step (256 MiB write); V (8 n^2 B) exceeds L2"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                if int(p[0]) != self.gpu:
+                    continue
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+                power.append(float(p[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------------ reference (CPU oracle) arm
+def cpu_oracle_rate(d, z, rho, nsample, seed=7, threads=None):
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    rng = np.random.default_rng(seed)
+    ks = np.sort(rng.choice(d.size, size=min(nsample, d.size), replace=False))
+    t0 = time.perf_counter()
+    oracle.eig_all(d, z, rho, ks=ks, threads=threads)
+    dt = time.perf_counter() - t0
+    return ks.size / dt, threads, ks.size, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1405_7537_gb300 import workloads as W
+    d, z, rho = W.hard(args.n, SEED)
+    per_step = 48
+    for _ in range(args.warmup):
+        cpu_oracle_rate(d, z, rho, per_step, seed=99)
+    times = []
+    threads = os.cpu_count() or 1
+    for s in range(args.steps):
+        _, threads, m, dt = cpu_oracle_rate(d, z, rho, per_step, seed=1000 + s)
+        times.append(dt)
+    total = sum(times)
+    value = per_step * args.steps / total
+    line = {"metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.n), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "eigenpairs/s", "cores": threads, "kind": "oracle",
+                             "sample": "%d random eigenpairs of the n=%d workload per step, all host cores"
+                                       % (per_step, args.n)},
+            "e2e": {"value": value, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1405_7537_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(n):
+    """DRAM bytes per launch of the bisection kernel from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_solve_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_hash") != kernel_source_hash():
+        return None
+    per_unit = rec.get("dram_bytes_per_eigenpair")
+    return per_unit * n if per_unit else None
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_1405_7537_gb300 import binding as B
+    from paper_1405_7537_gb300 import workloads as W
+
+    n = args.n
+    d, z, rho = W.hard(n, SEED + rank)
+    dev = torch.device("cuda", local)
+    dt_ = torch.tensor(np.array(d), device=dev)
+    zt_ = torch.tensor(np.array(z), device=dev)
+    ws = B.workspace(n, dev)
+    out = dict(lam=torch.empty(n, dtype=torch.float64, device=dev),
+               Vt=torch.empty((n, n), dtype=torch.float64, device=dev),
+               sigma=torch.empty(n, dtype=torch.float64, device=dev),
+               mu=torch.empty(n, dtype=torch.float64, device=dev),
+               xnorm=torch.empty(n, dtype=torch.float64, device=dev))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    pe = B.PhaseEvents()
+    opts = pe.attach(B.default_options())
+    stream = torch.cuda.current_stream()
+
+    def step():
+        B.eig(dt_, zt_, rho, ws=ws, out=out, options=opts, check=False)
+
+    # warm-up
+    for _ in range(max(args.warmup, 0)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    st = B.stream_status(ws)
+    if st != 0:
+        raise B.DPR1Error(st, "bench warm-up")
+    stats = B.workspace_stats(ws)
+
+    # timed region
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms, solve_ms, fix_ms, vec_ms = [], [], [], []
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        a, b, c = pe.times_ms()
+        solve_ms.append(a); fix_ms.append(b); vec_ms.append(c)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+    value = world * n * args.steps / (total_ms * 1e-3)
+    st = B.stream_status(ws)
+    if st != 0:
+        raise B.DPR1Error(st, "bench timed region")
+
+    # roofline of the dominant kernel (the bisection kernel k_solve)
+    evals = stats["evals_solve"]
+    ops = OPS_PER_TERM * (n - 1) * (evals + 2 * n)
+    t_solve = statistics.mean(solve_ms) * 1e-3
+    achieved = ops / t_solve
+    # live binary64 fma rate of this GPU at this clock (same process, after the timed region)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.empty(sms * 4 * 256, dtype=torch.float64, device=dev)
+    B.probe_dfma(sms * 4, 256, 64, sink)
+    torch.cuda.synchronize()
+    pe0 = torch.cuda.Event(enable_timing=True); pe1 = torch.cuda.Event(enable_timing=True)
+    pe0.record(stream)
+    B.probe_dfma(sms * 4, 256, 4096, sink)
+    pe1.record(stream)
+    pe1.synchronize()
+    measured_fma = sms * 4 * 256 * 4096 * 8 / (pe0.elapsed_time(pe1) * 1e-3)
+    roof = {"bound": "alu", "kernel": "k_solve (shift test, double-double b, bisection)",
+            "achieved": achieved / 1e12, "peak": NOMINAL_FP64_OPS / 1e12, "unit": "T binary64-op/s",
+            "frac": achieved / NOMINAL_FP64_OPS, "traffic": committed_traffic(n),
+            "peak_source": "nominal GB300 binary64 1.25 TFLOP/s = 2 fma/clk/SM x 152 SMs x 2070 MHz "
+                           "(MEASURED_PEAKS.json has no binary64 entry)",
+            "measured_fma_rate": measured_fma / 1e12,
+            "frac_of_measured_fma_rate": achieved / measured_fma,
+            "ops_per_launch": ops, "ops_definition": "5 ops (sub, fma, mul, div, add) per secular term "
+                                                     "x (n-1) x (bisection evaluations + 2 passes per eigenvalue)",
+            "launch_ms": 1e3 * t_solve, "bisection_evaluations": evals}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        d_h = torch.from_numpy(np.array(d)).pin_memory()
+        z_h = torch.from_numpy(np.array(z)).pin_memory()
+        lam_h = torch.empty(n, dtype=torch.float64).pin_memory()
+        sig_h = torch.empty(n, dtype=torch.float64).pin_memory()
+        mu_h = torch.empty(n, dtype=torch.float64).pin_memory()
+        Vt_h = torch.empty((n, n), dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            r = B.eig(d_h, z_h, rho, ws=ws, out=out, check=False)
+            lam_h.copy_(r["lam"], non_blocking=True)
+            sig_h.copy_(r["sigma"], non_blocking=True)
+            mu_h.copy_(r["mu"], non_blocking=True)
+            Vt_h.copy_(r["Vt"], non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        ee = []
+        for _ in range(args.e2e_steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            e2e_step()
+            e1.record(stream)
+            e1.synchronize()
+            ee.append(e0.elapsed_time(e1))
+        e2e_ms = sum(ee)
+        if world > 1:
+            t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = t.item()
+        e2e = {"value": world * n * args.e2e_steps / (e2e_ms * 1e-3), "unit": "eigenpairs/s",
+               "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 3 * 8 * n + 8 * n * n,
+               "ms_per_step": e2e_ms / args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, threads, m, dtc = cpu_oracle_rate(d, z, rho, args.cpu_sample)
+        cpu = {"value": rate, "unit": "eigenpairs/s", "cores": threads, "kind": "oracle",
+               "sample": "%d random eigenpairs of the same n=%d workload (%.1f s wall on %d threads)"
+                         % (m, n, dtc, threads)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": workload_config(n), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": 10 * args.steps, "clocks": clocks,
+                "phases_ms": {"bisection": statistics.mean(solve_ms), "remedies": statistics.mean(fix_ms),
+                              "eigenvectors": statistics.mean(vec_ms)},
+                "remedy_counts": {"flagged": stats["flagged"], "r1": stats["r1"], "r2": stats["r2"],
+                                  "zero_path": stats["zero_path"]},
+                "wall_s_timed_region": wall}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,180 @@
+/*
+ * dpr1.h -- C ABI of the GB300 (sm_103a) forward-stable eigensolver for
+ * diagonal-plus-rank-one (DPR1) matrices
+ *
+ *     A = D + rho z z^T,  D = diag(d_1, ..., d_n),  d_1 >= d_2 >= ... >= d_n,  rho >= 0,
+ *
+ * after N. Jakovcevic Stor, I. Slapnicar, J. L. Barlow, "Forward stable eigenvalue
+ * decomposition of rank-one modifications of diagonal matrices" (arXiv 1405.7537).
+ * Each eigenpair (lambda_k, v_k) is computed independently (Algorithm 1, dpr1eig):
+ * shift to the nearer pole d_i of lambda_k, form the arrowhead inverse of A - d_i I
+ * (Eq. (invAi)) with its corner element b (Eq. (b_ob)) in double-double, bisect its
+ * secular equation (Eq. (secAi)) for the extreme eigenvalue nu, recover
+ * lambda_k = d_i + 1/nu (Eq. (8)) and v_k = x / ||x||, x = (D - lambda_k I)^{-1} z
+ * (Eq. (Aeigenvec), (eigenvecAi)); apply the remedies R1/R2 when K_nu (Eq. (K0)) is
+ * large, and recompute lambda_k from A^{-1} (Eq. (gamma)) when it is much closer to
+ * zero than to its poles.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Working precision is IEEE binary64.  All array arguments are DEVICE pointers
+ *   owned by the caller, unless a parameter says "host".  The library allocates no
+ *   memory: it works in the caller's workspace, sized by dpr1_workspace_size*().
+ * - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *   stream).  The return value reports argument errors found on the host and launch
+ *   failures.  Conditions found on the device (unsorted or non-finite input, an
+ *   iteration cap reached) are recorded in a status word inside the workspace;
+ *   dpr1_stream_status() synchronises the stream and returns it.
+ * - Output order: lambda_1 >= lambda_2 >= ... (Eq. (interlace)); row k of Vt
+ *   (Vt[k*ldv + j], 0-based) is v_k with the paper's sign, v = x / ||x||.
+ * - Each eigenvalue is also returned as the unevaluated pair (sigma_k, mu_k),
+ *   lambda_k = sigma_k + mu_k exactly in real arithmetic (the representation of
+ *   Example 2): sigma_k is the shift (a pole, or a non-pole shift chosen by R2) and
+ *   mu_k the computed eigenvalue of A - sigma_k I.  Components of v_k are formed as
+ *   zeta_j / ((d_j - sigma_k) - mu_k).
+ * - Deflation (Sec. 1): zeta_j == 0 gives the eigenpair (d_j, e_j); d_j == d_{j+1}
+ *   gives the eigenvalue d_j after a Givens rotation in the (j, j+1) plane.  Both are
+ *   exact tests.  Deflated pairs carry sigma = lambda, mu = 0.
+ * - The functions never throw, never exit and never wait on the device except in
+ *   dpr1_stream_status().
+ */
+#ifndef DPR1_H
+#define DPR1_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DPR1_API __attribute__((visibility("default")))
+#else
+#define DPR1_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* dpr1_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+  DPR1_OK = 0,
+  DPR1_ERR_ARG = 1,            /* bad size, stride or NULL pointer (host check) */
+  DPR1_ERR_UNSORTED = 2,       /* d is not non-increasing (device check) */
+  DPR1_ERR_RHO = 3,            /* rho < 0 or not finite (host check); use A -> -(-D - rho z z^T) */
+  DPR1_ERR_NONFINITE = 4,      /* d, z or a gradient holds Inf/NaN (device check) */
+  DPR1_ERR_NOT_CONVERGED = 5,  /* a bisection did not close within its iteration cap (device) */
+  DPR1_ERR_CUDA = 6,           /* a CUDA launch or runtime call failed */
+  DPR1_ERR_WORKSPACE = 7       /* workspace NULL, misaligned (256 B) or smaller than required */
+} dpr1_status;
+
+/* Tunables; pass NULL for the defaults (dpr1_default_options). */
+typedef struct {
+  double T_Knu;          /* remedies when K_nu > T_Knu (default 16) */
+  double T_zero;         /* near-zero recompute when T_zero |lambda| < distance to its poles (64) */
+  int lanes;             /* threads per eigenvalue in the solve kernels: 0 = auto, else 8, 16 or 32 */
+  int warps_per_block;   /* 0 = auto */
+  int blocks_per_sm;     /* 0 = auto */
+  int max_bisect;        /* iteration cap per bisection (default 96; >= 64 needed in general) */
+  void* const* phase_events; /* instrumentation: NULL, or 4 cudaEvent_t recorded on `stream`
+                                before the bisection kernel, after it, after the remedies and
+                                after the eigenvector kernel */
+} dpr1_options;
+
+DPR1_API void dpr1_default_options(dpr1_options* opt);
+
+/* Human-readable name of a status code (static storage). */
+DPR1_API const char* dpr1_status_string(dpr1_status s);
+
+/*
+ * Bytes of workspace for dpr1_eig on a problem of order n (the workspace must be
+ * 256-byte aligned; its contents need not be initialised).
+ */
+DPR1_API size_t dpr1_workspace_size(int64_t n);
+
+/*
+ * dpr1_eig -- all eigenpairs of one DPR1 matrix (Algorithm 1 for k = 1..n).
+ *
+ *   n        order (n >= 0; n == 0 is a no-op)
+ *   d, z     device double[n]; d non-increasing, any z (zeros and ties are deflated)
+ *   rho      rho >= 0 (rho == 0 gives lambda = d, V = I)
+ *   lambda   device double[n], out: eigenvalues, non-increasing
+ *   Vt       device double[n*ldv] or NULL, out: row k = v_k (ldv >= n)
+ *   sigma,mu device double[n] or NULL, out: lambda_k = sigma_k + mu_k
+ *   xnorm    device double[n] or NULL, out: ||x_k||_2, x_k = (D - lambda_k I)^{-1} z
+ *   workspace, workspace_bytes: see dpr1_workspace_size
+ *   opt      NULL or tunables
+ *   stream   CUDA stream
+ * Errors: DPR1_ERR_ARG, DPR1_ERR_RHO, DPR1_ERR_WORKSPACE, DPR1_ERR_CUDA synchronously;
+ * DPR1_ERR_UNSORTED, DPR1_ERR_NONFINITE, DPR1_ERR_NOT_CONVERGED via dpr1_stream_status.
+ */
+DPR1_API dpr1_status dpr1_eig(int64_t n, const double* d, const double* z, double rho,
+                     double* lambda, double* Vt, int64_t ldv,
+                     double* sigma, double* mu, double* xnorm,
+                     void* workspace, size_t workspace_bytes,
+                     const dpr1_options* opt, dpr1_stream_t stream);
+
+/*
+ * Bytes of workspace for dpr1_eig_backward on order n (256-byte aligned, uninitialised).
+ */
+DPR1_API size_t dpr1_backward_workspace_size(int64_t n);
+
+/*
+ * dpr1_eig_backward -- adjoint of (lambda, V) with respect to (d, z, rho).  No
+ * counterpart in the paper: it differentiates the secular equation f(lambda_k) = 0
+ * (Eq. (Pick)) implicitly and the eigenvector formula x_k = (D - lambda_k I)^{-1} z,
+ * v_k = x_k / ||x_k|| (Eq. (Aeigenvec)) explicitly; the eigenvectors are recomputed from
+ * the pairs (sigma_k, mu_k) that dpr1_eig returned, V is not needed.
+ *
+ *   n, d, z, rho     the forward problem (irreducible: no zero zeta_j, no equal d_j)
+ *   sigma, mu        device double[n] from dpr1_eig
+ *   grad_lambda      device double[n] or NULL (zero): dL/dlambda_k
+ *   grad_Vt, ldg     device double[n*ldg] or NULL (zero): row k = dL/dv_k
+ *   grad_d, grad_z   device double[n], out (overwritten)
+ *   grad_rho         device double[1], out
+ * The sum over eigenpairs is done in a fixed order: results are reproducible.
+ * Errors as dpr1_eig; a non-finite intermediate (e.g. a deflated input) is reported as
+ * DPR1_ERR_NONFINITE through dpr1_stream_status on this workspace.
+ */
+DPR1_API dpr1_status dpr1_eig_backward(int64_t n, const double* d, const double* z, double rho,
+                                       const double* sigma, const double* mu,
+                                       const double* grad_lambda, const double* grad_Vt, int64_t ldg,
+                                       double* grad_d, double* grad_z, double* grad_rho,
+                                       void* workspace, size_t workspace_bytes,
+                                       const dpr1_options* opt, dpr1_stream_t stream);
+
+/*
+ * Synchronises `stream` and returns the status the device recorded in `workspace`
+ * during the last call that used it (DPR1_OK if none), then clears it.
+ */
+DPR1_API dpr1_status dpr1_stream_status(void* workspace, dpr1_stream_t stream);
+
+
+/*
+ * Instrumentation (no counterpart in the paper): synchronises `stream` and copies the
+ * counters of the last dpr1_eig call on `workspace` into out[0..7]:
+ *   0 order of the reduced problem, 1 eigenvalues flagged by K_nu, 2 remedies taken
+ *   with R1, 3 with R2, 4 secular-function evaluations in the bisection kernel,
+ *   5 evaluations in the remedy kernel, 6 eigenvalues recomputed from A^{-1}, 7 deflated pairs.
+ */
+DPR1_API dpr1_status dpr1_workspace_stats(void* workspace, int64_t* out, dpr1_stream_t stream);
+
+/*
+ * Measurement helper (no counterpart in the paper): launches `blocks` x `threads`
+ * threads that each run `iters` iterations of 8 independent binary64 fma chains
+ * (8 * iters * blocks * threads fma in total) and write one double to sink[thread].
+ * Timed by the caller, it gives the device's binary64 fma issue rate.
+ */
+DPR1_API dpr1_status dpr1_probe_dfma(int blocks, int threads, int iters, double* sink, dpr1_stream_t stream);
+
+/*
+ * Test hook (no counterpart in the paper): out[t] = the library's binary64
+ * reciprocal of x[t] for t < count, as used in the secular sums.  Lets tests bound
+ * its error against correctly rounded division.
+ */
+DPR1_API dpr1_status dpr1_probe_reciprocal(int64_t count, const double* x, double* out, dpr1_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DPR1_H */

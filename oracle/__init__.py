@@ -57,6 +57,8 @@ def lib():
                                            _ip, _ip]
         L.oracle_backward.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _dp, _dp, _dp,
                                       _dp, _dp, _dp]
+        L.oracle_backward_rows.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_int, _ip, _dp, _dp,
+                                           _dp, _dp, _dp, _dp, _dp]
         L.quad_eigpair.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp]
         L.quad_eigpair2.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp,
                                     _dp, _ip, _dp]
@@ -157,6 +159,21 @@ def backward(d, z, rho, sigma, mu, grad_lam=None, grad_Vt=None):
                                _ptr(gV), _ptr(gd), _ptr(gz), ctypes.byref(gr))
     if rc:
         raise ValueError("oracle_backward failed with code %d" % rc)
+    return gd, gz, gr.value
+
+
+def backward_rows(d, z, rho, sigma, mu, grad_lam=None, grad_Vt=None):
+    """The adjoint summed over the eigenpairs whose (sigma, mu) are given (any subset);
+    grad_lam[t] and grad_Vt[t] belong to the pair (sigma[t], mu[t])."""
+    d, z, sigma, mu = _f64(d), _f64(z), _f64(sigma), _f64(mu)
+    n, m = d.size, sigma.size
+    gl = _f64(grad_lam) if grad_lam is not None else None
+    gV = _f64(grad_Vt) if grad_Vt is not None else None
+    gd, gz, gr = np.empty(n), np.empty(n), ctypes.c_double()
+    rc = lib().oracle_backward_rows(n, _ptr(d), _ptr(z), float(rho), m, None, _ptr(sigma), _ptr(mu), _ptr(gl),
+                                    _ptr(gV), _ptr(gd), _ptr(gz), ctypes.byref(gr))
+    if rc:
+        raise ValueError("oracle_backward_rows failed with code %d" % rc)
     return gd, gz, gr.value
 
 

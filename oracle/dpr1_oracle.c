@@ -563,26 +563,41 @@ int oracle_dpr1eig_range(int n, const double* d, const double* z, double rho, in
 /*   rhobar += lambda_bar / (rho^2 ||x||^2).                                   */
 /* grad_lambda or grad_Vt may be NULL (zero).  Rows of grad_Vt are dL/dv_k.   */
 /* ------------------------------------------------------------------------- */
+int oracle_backward_rows(int n, const double* d, const double* z, double rho, int m, const int* rows,
+                         const double* sigma, const double* mu,
+                         const double* grad_lambda, const double* grad_Vt,
+                         double* grad_d, double* grad_z, double* grad_rho);
+
 int oracle_backward(int n, const double* d, const double* z, double rho,
                     const double* sigma, const double* mu,
                     const double* grad_lambda, const double* grad_Vt,
                     double* grad_d, double* grad_z, double* grad_rho) {
+  return oracle_backward_rows(n, d, z, rho, n, NULL, sigma, mu, grad_lambda, grad_Vt, grad_d, grad_z, grad_rho);
+}
+
+/* The same sum restricted to the eigenpairs rows[0..m) (rows == NULL: 0..m-1); sigma, mu,
+   grad_lambda and the rows of grad_Vt are indexed by position in that list. */
+int oracle_backward_rows(int n, const double* d, const double* z, double rho, int m, const int* rows,
+                         const double* sigma, const double* mu,
+                         const double* grad_lambda, const double* grad_Vt,
+                         double* grad_d, double* grad_z, double* grad_rho) {
   double* s = (double*)malloc(sizeof(double) * n);
   double* v = (double*)malloc(sizeof(double) * n);
   if (!s || !v) { free(s); free(v); return 2; }
   for (int j = 0; j < n; j++) { grad_d[j] = 0.0; grad_z[j] = 0.0; }
   double grho = 0.0;
-  for (int k = 0; k < n; k++) {
-    double m = 0.0;
+  (void)rows;
+  for (int k = 0; k < m; k++) {
+    double mx = 0.0;
     for (int j = 0; j < n; j++) {
       s[j] = (d[j] - sigma[k]) - mu[k];
       v[j] = z[j] / s[j];
-      if (fabs(v[j]) > m) m = fabs(v[j]);
+      if (fabs(v[j]) > mx) mx = fabs(v[j]);
     }
     double q = 0.0;
-    for (int j = 0; j < n; j++) { double t = v[j] / m; q += t * t; }
-    double xn = m * sqrt(q);                 /* ||x|| */
-    for (int j = 0; j < n; j++) v[j] = (v[j] / m) / sqrt(q);
+    for (int j = 0; j < n; j++) { double t = v[j] / mx; q += t * t; }
+    double xn = mx * sqrt(q);                /* ||x|| */
+    for (int j = 0; j < n; j++) v[j] = (v[j] / mx) / sqrt(q);
     const double* vb = grad_Vt ? &grad_Vt[(size_t)k * n] : NULL;
     double c = 0.0;
     if (vb) for (int j = 0; j < n; j++) c += v[j] * vb[j];

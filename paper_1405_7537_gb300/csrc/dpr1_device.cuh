@@ -1,0 +1,141 @@
+// dpr1_device.cuh -- device arithmetic shared by the DPR1 kernels (sm_103a).
+//
+// * double-double ("dd") numbers: unevaluated sums hi + lo of two binary64 numbers,
+//   used for the paper's one element computed in double the working precision
+//   (Sec. 2.3): the corner b of Eq. (b_ob), and f(sigma) / the denominator of gamma
+//   for the non-pole shifts (R2, Eq. (gamma)).  Error-free transformations: Knuth's
+//   TwoSum, Dekker's FastTwoSum and the exact product through fma.
+// * a binary64 reciprocal: the sm_103a approximate reciprocal instruction
+//   (rcp.approx.ftz.f64, about 20 correct bits) refined by one third-order
+//   Newton-Raphson step r = r0 (1 + e + e^2), e = 1 - x r0; the result is within
+//   one unit in the last place of 1/x for |x| in [2^-1020, 2^1020] (outside that
+//   range the IEEE quotient is used).
+// * lane-group reductions with xor shuffles: every lane of a group ends with the
+//   bit-identical total (IEEE addition is commutative), so every lane takes the
+//   same bisection decisions without a broadcast.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dpr1 {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// status bits recorded on the device
+enum : unsigned {
+  ST_NONFINITE = 1u,
+  ST_UNSORTED = 2u,
+  ST_NOT_CONVERGED = 4u,
+  ST_DEFLATED = 8u,
+  ST_ZERO_POLE = 16u,   // some d_j == 0 (the near-zero recompute is then skipped, Eq. (gamma))
+};
+
+struct dd {
+  double hi, lo;
+};
+
+__device__ __forceinline__ dd two_sum(double a, double b) {
+  double s = __dadd_rn(a, b);
+  double bb = __dsub_rn(s, a);
+  double e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+  return {s, e};
+}
+
+__device__ __forceinline__ dd fast_two_sum(double a, double b) {  // |a| >= |b| or a == 0
+  double s = __dadd_rn(a, b);
+  return {s, __dsub_rn(b, __dsub_rn(s, a))};
+}
+
+__device__ __forceinline__ dd two_prod(double a, double b) {
+  double p = __dmul_rn(a, b);
+  return {p, __fma_rn(a, b, -p)};
+}
+
+// dd + dd with both the high and the low parts summed error-free
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+  dd s = two_sum(a.hi, b.hi);
+  dd t = two_sum(a.lo, b.lo);
+  s = fast_two_sum(s.hi, __dadd_rn(s.lo, t.hi));
+  return fast_two_sum(s.hi, __dadd_rn(s.lo, t.lo));
+}
+
+__device__ __forceinline__ double rcp_approx(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  return r;
+}
+
+// 1/x within one ulp (see the file comment).
+__device__ __forceinline__ double rcp(double x) {
+  double r0 = rcp_approx(x);
+  double e = __fma_rn(-x, r0, 1.0);
+  double p = __fma_rn(e, e, e);
+  double r = __fma_rn(r0, p, r0);
+  // exponent field of x outside [1023-1020, 1023+1020]: take the IEEE quotient
+  unsigned ex = (unsigned)(__double_as_longlong(x) >> 52) & 0x7ffu;
+  if (ex - 3u > 2040u) r = 1.0 / x;
+  return r;
+}
+
+// dd / dd to about 2^-104 relative: q1 = a.hi/b.hi, then one correction digit from the
+// exact residual a.hi - q1 b.hi (fma), the low parts and the divisor's reciprocal.
+__device__ __forceinline__ dd dd_div(dd a, dd b) {
+  double r = rcp(b.hi);
+  double q1 = __dmul_rn(a.hi, r);
+  // make q1 faithful so that the fma residual below is exact
+  double res = __fma_rn(-q1, b.hi, a.hi);
+  q1 = __fma_rn(res, r, q1);
+  res = __fma_rn(-q1, b.hi, a.hi);                       // exact
+  double rest = __dadd_rn(res, __fma_rn(-q1, b.lo, a.lo));
+  double q2 = __dmul_rn(rest, r);
+  return fast_two_sum(q1, q2);
+}
+
+__device__ __forceinline__ double dd_to_double(dd a) { return __dadd_rn(a.hi, a.lo); }
+
+// A lane group is L consecutive lanes of a warp (L = 8, 16 or 32); gm is its lane mask,
+// so groups of one warp may run different iterations independently.
+template <int L>
+__device__ __forceinline__ unsigned group_mask() {
+  if (L == 32) return FULL;
+  return ((1u << (L & 31)) - 1u) << ((threadIdx.x & 31) & ~(L - 1));
+}
+
+template <int L>
+__device__ __forceinline__ double group_sum(double v, unsigned gm) {
+#pragma unroll
+  for (int o = L / 2; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(gm, v, o));
+  return v;
+}
+
+template <int L>
+__device__ __forceinline__ dd group_sum_dd(dd v, unsigned gm) {
+#pragma unroll
+  for (int o = L / 2; o > 0; o >>= 1) {
+    dd w;
+    w.hi = __shfl_xor_sync(gm, v.hi, o);
+    w.lo = __shfl_xor_sync(gm, v.lo, o);
+    v = dd_add(v, w);
+  }
+  return v;
+}
+
+template <int L>
+__device__ __forceinline__ double group_max(double v, unsigned gm) {
+#pragma unroll
+  for (int o = L / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(gm, v, o));
+  return v;
+}
+
+__device__ __forceinline__ uint64_t dbits(double a) { return (uint64_t)__double_as_longlong(a); }
+
+// neighbouring binary64 numbers of a finite x
+__device__ __forceinline__ double dnext_up(double x) {
+  if (x == 0.0) return __longlong_as_double(1ll);
+  long long b = __double_as_longlong(x);
+  return __longlong_as_double(x > 0.0 ? b + 1 : b - 1);
+}
+__device__ __forceinline__ double dnext_down(double x) { return -dnext_up(-x); }
+__device__ __forceinline__ double dfrom(uint64_t u) { return __longlong_as_double((long long)u); }
+
+}  // namespace dpr1

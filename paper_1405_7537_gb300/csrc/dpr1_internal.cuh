@@ -1,0 +1,49 @@
+// dpr1_internal.cuh -- host/device structures shared by the library's translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/dpr1.h"
+
+namespace dpr1 {
+
+// Views into the caller's workspace for one problem (see ws_layout).
+struct Ws {
+  unsigned* hdr;       // 64 words: status, counters, sizes
+  unsigned* status;    // hdr[0]: ST_* bits
+  unsigned* counters;  // hdr[8..15]: 0 solve queue, 1 fix-list length, 2 fix queue, 3 zero-list length
+  int* nred;           // hdr[32]: order of the reduced (deflated) problem
+  int* ndefl;          // hdr[33]: number of deflated pairs
+  double *dr, *zr, *zz;       // reduced problem: d, z, z^2
+  double *sig, *mu;           // eigenvalue pairs of the reduced problem
+  int *shift, *flag, *list;   // pole index (-1: non-pole shift), remedy flag, work lists
+  double* lamz;               // eigenvalue from A^{-1} (NaN: not recomputed)
+  int* src;                   // deflation: reduced index feeding position p (-1: none)
+  double* coef;               // deflation: zeta_p / zeta_survivor
+  int *rpos, *dpos;           // output rows of reduced / deflated pairs
+  int* gst;                   // first position of p's group of equal poles
+  double *rprev, *rcur;       // Givens chain prefix norms
+  int* dlist;                 // deflated positions, increasing
+  int* zlist;                 // near-zero candidates
+  double* fixinfo;            // per flagged slot: K_nu, K_nu at the other pole, distance ratio
+};
+
+struct Options {
+  double T_Knu, T_zero;
+  int lanes, warps, bps, cap;
+  void* const* events;
+};
+
+// hdr counters (Ws::counters index)
+enum : int {
+  C_SOLVE_Q = 0, C_FIX_N = 1, C_FIX_Q = 2, C_ZERO_N = 3, C_EVAL_SOLVE = 4, C_EVAL_FIX = 5,
+  C_R2 = 6, C_R1 = 7
+};
+
+size_t ws_layout(int64_t n, Ws* w, char* base);
+Options resolve(const dpr1_options* o);
+int sm_count();
+
+}  // namespace dpr1
