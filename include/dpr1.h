@@ -150,6 +150,32 @@ DPR1_API dpr1_status dpr1_stream_status(void* workspace, dpr1_stream_t stream);
 
 
 /*
+ * dpr1_eig_noalloc -- dpr1_eig without a caller-provided workspace.  The paper has no
+ * counterpart: this is an interface for callers that cannot allocate device memory,
+ * such as code running inside another framework's memory pool or a plugin that may
+ * not grow the device footprint at run time.  The scratch memory is a static array
+ * inside the library (640 KiB, held on every device that loads the library until the
+ * process exits), so n is limited to DPR1_NOALLOC_MAX_N; larger n returns
+ * DPR1_ERR_ARG without launching anything.  The call allocates nothing.
+ *
+ *   arguments     as dpr1_eig (same outputs, same conventions), without the workspace
+ *   wait          0: asynchronous, like dpr1_eig (device-detected problems are then not
+ *                 reported); non-zero: synchronise `stream` at the end and return the
+ *                 device-detected status as dpr1_stream_status would
+ *
+ * The first call on a device looks up the device address of the static array (with
+ * that device current); make that first call before any stream capture.  All calls
+ * share the one array and it keeps the last call's contents (the call clears what must
+ * start at zero).  Calls that overlap on the GPU -- on different streams or from
+ * host threads without ordering -- race on it and give wrong results.
+ */
+#define DPR1_NOALLOC_MAX_N 4096
+DPR1_API dpr1_status dpr1_eig_noalloc(int64_t n, const double* d, const double* z, double rho,
+                                      double* lambda, double* Vt, int64_t ldv,
+                                      double* sigma, double* mu, double* xnorm,
+                                      const dpr1_options* opt, int wait, dpr1_stream_t stream);
+
+/*
  * Instrumentation (no counterpart in the paper): synchronises `stream` and copies the
  * counters of the last dpr1_eig call on `workspace` into out[0..7]:
  *   0 order of the reduced problem, 1 eigenvalues flagged by K_nu, 2 remedies taken
