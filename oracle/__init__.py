@@ -62,6 +62,8 @@ def lib():
         L.quad_eigpair.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp]
         L.quad_eigpair2.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp,
                                     _dp, _ip, _dp]
+        L.quad_backward.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_int, _ip, _dp, _dp, _dp,
+                                    _dp, _dp]
         L.quad_secular.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_double]
         L.quad_secular.restype = ctypes.c_double
@@ -218,6 +220,21 @@ def quad_all(d, z, rho, ks=None, threads=1, want_vectors=True):
         with ThreadPoolExecutor(threads) as ex:
             list(ex.map(run, np.array_split(np.arange(m), threads)))
     return out
+
+
+def quad_backward(d, z, rho, grad_lam=None, grad_Vt=None, ks=None):
+    """binary128 adjoint summed over eigenpairs ks (default all); grad rows belong to ks."""
+    d, z = _f64(d), _f64(z)
+    n = d.size
+    ks = np.arange(n, dtype=np.int32) if ks is None else np.ascontiguousarray(ks, dtype=np.int32)
+    gl = _f64(grad_lam) if grad_lam is not None else None
+    gV = _f64(grad_Vt) if grad_Vt is not None else None
+    gd, gz, gr = np.empty(n), np.empty(n), ctypes.c_double()
+    rc = lib().quad_backward(n, _ptr(d), _ptr(z), float(rho), ks.size, ks.ctypes.data_as(_ip), _ptr(gl), _ptr(gV),
+                             _ptr(gd), _ptr(gz), ctypes.byref(gr))
+    if rc:
+        raise ValueError("quad_backward failed")
+    return gd, gz, gr.value
 
 
 def quad_secular(d, z, rho, lam_hi, lam_lo=0.0):

@@ -556,11 +556,22 @@ int oracle_dpr1eig_range(int n, const double* d, const double* z, double rho, in
 /*   s_j = d_j - lambda_k = (d_j - sigma_k) - mu_k,                            */
 /*   dlambda/dd_j = v_j^2, dlambda/dzeta_j = -2 x_j/||x||^2,                  */
 /*   dlambda/drho = 1/(rho^2 ||x||^2);                                        */
-/*   gbar = (vbar - v (v^T vbar)) / ||x|| is the adjoint of x,                 */
-/*   lambda_bar = grad_lambda_k + sum_j gbar_j x_j / s_j,                      */
-/*   dbar_j += lambda_bar v_j^2 - gbar_j x_j / s_j,                            */
-/*   zbar_j += gbar_j / s_j - 2 lambda_bar v_j / ||x||,                        */
-/*   rhobar += lambda_bar / (rho^2 ||x||^2).                                   */
+/*   with vbar = dL/dv_k and c = v^T vbar, g = vbar - v c; gbar = g/||x||     */
+/*   is the adjoint of x, and                                                 */
+/*   lambda_bar = grad_lambda_k + sum_j g_j v_j / s_j,                         */
+/*   dbar_j += lambda_bar v_j^2 - g_j v_j / s_j,                               */
+/*   zbar_j += (g_j / s_j - 2 lambda_bar v_j) / ||x||,                         */
+/*   rhobar += lambda_bar / (rho ||x||)^2.                                     */
+/* Evaluation: let p be the index of the largest |v_p|.  When v is close to   */
+/* e_p (lambda_k next to the pole d_p), g_p and the two parts of dbar_p cancel */
+/* at the scale 1/s_p; with S2 = sum_{j != p} v_j^2 = 1 - v_p^2 and            */
+/* P = sum_{j != p} v_j vbar_j the same quantities are                         */
+/*   g_p = vbar_p S2 - v_p P,                                                  */
+/*   lambda_bar = Lam + T_p, Lam = grad_lambda_k + sum_{j != p} g_j v_j / s_j,  */
+/*   T_p = g_p v_p / s_p,                                                      */
+/*   dbar_p += Lam v_p^2 - T_p S2,                                             */
+/*   zbar_p += (g_p / s_p (S2 - v_p^2) - 2 Lam v_p) / ||x||,                   */
+/* which have no such cancellation.                                            */
 /* grad_lambda or grad_Vt may be NULL (zero).  Rows of grad_Vt are dL/dv_k.   */
 /* ------------------------------------------------------------------------- */
 int oracle_backward_rows(int n, const double* d, const double* z, double rho, int m, const int* rows,
@@ -575,43 +586,58 @@ int oracle_backward(int n, const double* d, const double* z, double rho,
   return oracle_backward_rows(n, d, z, rho, n, NULL, sigma, mu, grad_lambda, grad_Vt, grad_d, grad_z, grad_rho);
 }
 
-/* The same sum restricted to the eigenpairs rows[0..m) (rows == NULL: 0..m-1); sigma, mu,
-   grad_lambda and the rows of grad_Vt are indexed by position in that list. */
+/* The same sum restricted to m eigenpairs; sigma, mu, grad_lambda and the rows of grad_Vt
+   are indexed by position in that list (rows is unused and may be NULL). */
 int oracle_backward_rows(int n, const double* d, const double* z, double rho, int m, const int* rows,
                          const double* sigma, const double* mu,
                          const double* grad_lambda, const double* grad_Vt,
                          double* grad_d, double* grad_z, double* grad_rho) {
   double* s = (double*)malloc(sizeof(double) * n);
   double* v = (double*)malloc(sizeof(double) * n);
-  if (!s || !v) { free(s); free(v); return 2; }
+  double* g = (double*)malloc(sizeof(double) * n);
+  if (!s || !v || !g) { free(s); free(v); free(g); return 2; }
+  (void)rows;
   for (int j = 0; j < n; j++) { grad_d[j] = 0.0; grad_z[j] = 0.0; }
   double grho = 0.0;
-  (void)rows;
   for (int k = 0; k < m; k++) {
     double mx = 0.0;
+    int p = 0;
     for (int j = 0; j < n; j++) {
       s[j] = (d[j] - sigma[k]) - mu[k];
       v[j] = z[j] / s[j];
-      if (fabs(v[j]) > mx) mx = fabs(v[j]);
+      if (fabs(v[j]) > mx) { mx = fabs(v[j]); p = j; }
     }
     double q = 0.0;
     for (int j = 0; j < n; j++) { double t = v[j] / mx; q += t * t; }
     double xn = mx * sqrt(q);                /* ||x|| */
     for (int j = 0; j < n; j++) v[j] = (v[j] / mx) / sqrt(q);
     const double* vb = grad_Vt ? &grad_Vt[(size_t)k * n] : NULL;
-    double c = 0.0;
-    if (vb) for (int j = 0; j < n; j++) c += v[j] * vb[j];
-    /* gbar_j x_j / s_j = (vbar_j - v_j c) v_j / s_j */
-    double lb = grad_lambda ? grad_lambda[k] : 0.0;
-    if (vb) for (int j = 0; j < n; j++) lb += (vb[j] - v[j] * c) * v[j] / s[j];
+    double S2 = 0.0, P = 0.0;
     for (int j = 0; j < n; j++) {
-      double gx = vb ? (vb[j] - v[j] * c) : 0.0;    /* ||x|| * gbar_j */
-      grad_d[j] += lb * v[j] * v[j] - gx * v[j] / s[j];
-      grad_z[j] += (gx / xn) / s[j] - 2.0 * lb * v[j] / xn;
+      if (j == p) continue;
+      S2 += v[j] * v[j];
+      if (vb) P += v[j] * vb[j];
     }
-    grho += ((lb / rho) / xn) / (rho * xn);
+    double c = vb ? v[p] * vb[p] + P : 0.0;
+    for (int j = 0; j < n; j++) g[j] = vb ? vb[j] - v[j] * c : 0.0;
+    if (vb) g[p] = vb[p] * S2 - v[p] * P;
+    double Lam = grad_lambda ? grad_lambda[k] : 0.0;
+    for (int j = 0; j < n; j++) if (j != p) Lam += g[j] * v[j] / s[j];
+    double Tp = g[p] * v[p] / s[p];
+    double lb = Lam + Tp;
+    for (int j = 0; j < n; j++) {
+      if (j == p) {
+        grad_d[j] += Lam * v[j] * v[j] - Tp * S2;
+        grad_z[j] += ((g[j] / s[j]) * (S2 - v[j] * v[j]) - 2.0 * Lam * v[j]) / xn;
+      } else {
+        grad_d[j] += lb * v[j] * v[j] - g[j] * v[j] / s[j];
+        grad_z[j] += (g[j] / s[j] - 2.0 * lb * v[j]) / xn;
+      }
+    }
+    double t = 1.0 / (rho * xn);
+    grho += lb * t * t;
   }
   *grad_rho = grho;
-  free(s); free(v);
+  free(s); free(v); free(g);
   return 0;
 }

@@ -129,6 +129,65 @@ int quad_eigpair(int n, const double* d, const double* z, double rho, int k,
   return quad_eigpair2(n, d, z, rho, k, lam_hi, lam_lo, &mh, &ml, &pole, v);
 }
 
+/*
+ * Adjoint of (lambda, V) with respect to (d, z, rho) in binary128, from the plain
+ * formulas (implicit derivative of f(lambda_k) = 0, explicit x = (D - lambda_k I)^{-1} z):
+ *   s_j = d_j - lambda_k, v = x/||x||, c = v . vbar, g = vbar - v c,
+ *   lambda_bar = grad_lambda_k + sum_j g_j v_j / s_j,
+ *   dbar_j += lambda_bar v_j^2 - g_j v_j / s_j,
+ *   zbar_j += (g_j / s_j - 2 lambda_bar v_j) / ||x||,  rhobar += lambda_bar / (rho ||x||)^2,
+ * with lambda_k from the shifted binary128 bisection (s_j = (d_j - d_i) - mu).
+ * Sums over the m eigenpairs ks[0..m); grad_lambda[t] and grad_Vt row t belong to ks[t].
+ */
+int quad_backward(int n, const double* d, const double* z, double rho, int m, const int* ks,
+                  const double* grad_lambda, const double* grad_Vt, double* gd, double* gz, double* grho) {
+  q_t* D = (q_t*)malloc(sizeof(q_t) * n);
+  q_t* x = (q_t*)malloc(sizeof(q_t) * n);
+  q_t* S = (q_t*)malloc(sizeof(q_t) * n);
+  q_t* Gd = (q_t*)malloc(sizeof(q_t) * n);
+  q_t* Gz = (q_t*)malloc(sizeof(q_t) * n);
+  if (!D || !x || !S || !Gd || !Gz) { free(D); free(x); free(S); free(Gd); free(Gz); return -1; }
+  for (int j = 0; j < n; j++) { Gd[j] = 0; Gz[j] = 0; }
+  q_t Gr = 0;
+  for (int t = 0; t < m; t++) {
+    int k = ks ? ks[t] : t;
+    double lh, ll, mh, ml;
+    int pole;
+    if (quad_eigpair2(n, d, z, rho, k, &lh, &ll, &mh, &ml, &pole, NULL) < 0) return -1;
+    q_t mu = (q_t)mh + (q_t)ml;
+    q_t mx = 0;
+    for (int j = 0; j < n; j++) {
+      S[j] = ((q_t)d[j] - (q_t)d[pole]) - mu;
+      x[j] = (q_t)z[j] / S[j];
+      if (q_abs(x[j]) > mx) mx = q_abs(x[j]);
+    }
+    q_t sq = 0;
+    for (int j = 0; j < n; j++) { q_t u = x[j] / mx; sq += u * u; }
+    q_t xn = mx * q_sqrt(sq);
+    const double* vb = grad_Vt ? &grad_Vt[(size_t)t * n] : NULL;
+    q_t c = 0;
+    if (vb) for (int j = 0; j < n; j++) c += (x[j] / xn) * (q_t)vb[j];
+    q_t lb = grad_lambda ? (q_t)grad_lambda[t] : 0;
+    for (int j = 0; j < n; j++) {
+      q_t v = x[j] / xn;
+      q_t g = vb ? (q_t)vb[j] - v * c : 0;
+      lb += g * v / S[j];
+    }
+    for (int j = 0; j < n; j++) {
+      q_t v = x[j] / xn;
+      q_t g = vb ? (q_t)vb[j] - v * c : 0;
+      Gd[j] += lb * v * v - g * v / S[j];
+      Gz[j] += (g / S[j] - 2 * lb * v) / xn;
+    }
+    q_t r = 1 / ((q_t)rho * xn);
+    Gr += lb * r * r;
+  }
+  for (int j = 0; j < n; j++) { gd[j] = (double)Gd[j]; gz[j] = (double)Gz[j]; }
+  *grho = (double)Gr;
+  free(D); free(x); free(S); free(Gd); free(Gz);
+  return 0;
+}
+
 /* f(lambda) at lambda = hi + lo, in binary128, rounded to binary64 (used by tests). */
 double quad_secular(int n, const double* d, const double* z, double rho, double lam_hi, double lam_lo) {
   return (double)q_f(n, d, z, rho, (q_t)lam_hi + (q_t)lam_lo);

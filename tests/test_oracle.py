@@ -438,3 +438,22 @@ def test_backward_trace_identities():
     assert np.max(np.abs(gd - 1.0)) <= 1e-12
     assert np.max(np.abs(gz - 2 * rho * z) / np.abs(2 * rho * z)) <= 1e-9
     assert abs(gr - np.dot(z, z)) <= 1e-12 * np.dot(z, z)
+
+
+@pytest.mark.parametrize("gen,n,seed", [("uniform", 64, 2), ("hard", 200, 5), ("large", 300, 4)])
+def test_backward_against_binary128_adjoint(gen, n, seed):
+    """The adjoint formulas evaluated in binary128 at binary128 eigenpairs; the hard and
+    large spectra have eigenvectors within 1e-10 of a unit vector, where the plain
+    binary64 evaluation of g = vbar - v (v . vbar) cancels."""
+    if gen == "large":
+        d, z, rho, _ = W.large(n, seed, with_W=False)
+    else:
+        d, z, rho = getattr(W, gen)(n, seed)
+    rng = np.random.default_rng(seed)
+    w, Wm = rng.standard_normal(n), rng.standard_normal((n, n))
+    r = oracle.eig_all(d, z, rho, threads=8)
+    od, oz, orho = oracle.backward(d, z, rho, r["sigma"], r["mu"], w, Wm)
+    qd, qz, qrho = oracle.quad_backward(d, z, rho, w, Wm)
+    assert np.linalg.norm(od - qd) <= 1e-10 * np.linalg.norm(qd)
+    assert np.linalg.norm(oz - qz) <= 1e-10 * np.linalg.norm(qz)
+    assert abs(orho - qrho) <= 1e-10 * abs(qrho)
