@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-vs-loop and forward+backward measurements")
+    ap.add_argument("--large", action="store_true", help="also time the n=32768 forward+backward workload")
     return ap.parse_args()
 
 
@@ -157,14 +160,138 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ multi-rank aggregation
+def aggregate(total_ms, units_per_rank, steps, world, dist=None, device="cpu"):
+    """Whole-job rate over `world` ranks that each processed `units_per_rank` units per step:
+    the slowest rank's time (max over ranks) divides all ranks' units.  Returns
+    (value, max_ms)."""
+    if world > 1:
+        import torch
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+    return world * units_per_rank * steps / (total_ms * 1e-3), total_ms
+
+
+# ------------------------------------------------------------------ extras
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def bench_batched(B, dev, steps):
+    """4096 uneven problems: one graph-captured dpr1_eig_batched vs a loop of dpr1_eig calls."""
+    import torch
+    from paper_1405_7537_gb300 import tune
+    from paper_1405_7537_gb300 import workloads as W
+    offs, d, z, rho = W.batch()
+    sizes = np.diff(offs)
+    bt = B.Batch(sizes, device=dev)
+    dt = torch.tensor(d, device=dev)
+    zt = torch.tensor(z, device=dev)
+    rt = torch.tensor(rho, device=dev)
+    shape = tune.tune(sizes, device=dev)
+    opts = B.default_options(lanes=shape[0], warps_per_block=shape[1], blocks_per_sm=shape[2])
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        bt.solve(dt, zt, rt, options=opts)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    st = B.stream_status(bt.ws)
+    if st != 0:
+        raise B.DPR1Error(st, "batched warm-up")
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        bt.solve(dt, zt, rt, options=opts)
+    g.replay()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(max(1, steps)):
+        e0, e1 = _events()
+        e0.record()
+        g.replay()
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    batched_ms = statistics.mean(ms)
+    # the same problems, one dpr1_eig call each (default launch shape, shared workspace)
+    ws = B.workspace(int(sizes.max()), dev)
+    lam, Vt = bt.lam, bt.Vt
+    outs = []
+    for p in range(bt.P):
+        a, b = int(offs[p]), int(offs[p + 1])
+        n = b - a
+        va = int(bt.voffs_host[p])
+        outs.append((dt[a:b], zt[a:b], float(rho[p]),
+                     dict(lam=lam[a:b], Vt=Vt[va:va + n * n].view(n, n), sigma=bt.sigma[a:b], mu=bt.mu[a:b],
+                          xnorm=bt.xnorm[a:b])))
+    for dp, zp, rp, out in outs[:64]:
+        B.eig(dp, zp, rp, ws=ws, out=out, check=False)
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record()
+    for dp, zp, rp, out in outs:
+        B.eig(dp, zp, rp, ws=ws, out=out, check=False)
+    e1.record()
+    e1.synchronize()
+    loop_ms = e0.elapsed_time(e1)
+    total = int(offs[-1])
+    return {"workload": "4096 problems, n_k = round(exp(U(ln 16, ln 2048))), d, z ~ U(-1,1), rho_k ~ U(0.1, 10), "
+                        "seed 3; eigenvalues and all V blocks",
+            "eigenpairs": total, "v_bytes": int(bt.voffs_host[-1]) * 8,
+            "batched_ms": batched_ms, "value": total / (batched_ms * 1e-3),
+            "loop_ms": loop_ms, "loop_value": total / (loop_ms * 1e-3),
+            "speedup_vs_loop": loop_ms / batched_ms, "unit": "eigenpairs/s",
+            "launch": "one CUDA-graph replay of dpr1_eig_batched vs 4096 dpr1_eig calls from Python",
+            "tuned_shape": {"lanes": shape[0], "warps_per_block": shape[1], "blocks_per_sm": shape[2]}}
+
+
+def bench_fwd_bwd(B, dev, n, seed, steps, with_w):
+    """Forward (lambda and V) and backward (recomputing V) times for loss = w.lambda + sum W o V."""
+    import torch
+    from paper_1405_7537_gb300 import workloads as W
+    if with_w:
+        d, z, rho, w, Wm = W.diff(n, seed)
+    else:
+        d, z, rho, Wm = W.large(n, seed)
+        w = None
+    dt = torch.tensor(np.array(d), device=dev)
+    zt = torch.tensor(np.array(z), device=dev)
+    wt = torch.tensor(w, device=dev) if w is not None else None
+    gVt = torch.tensor(Wm.T.copy(), device=dev)            # dL/dVt = W^T for V[:, k] = v_k
+    del Wm
+    ws = B.workspace(n, dev)
+    bws = B.backward_workspace(n, dev)
+    out = B.eig(dt, zt, rho, ws=ws)
+    B.eig_backward(dt, zt, rho, out["sigma"], out["mu"], wt, gVt, ws=bws)
+    torch.cuda.synchronize()
+    fw, bw = [], []
+    for _ in range(max(1, steps)):
+        e0, e1 = _events()
+        e2, e3 = _events()
+        e0.record()
+        B.eig(dt, zt, rho, ws=ws, out=out, check=False)
+        e1.record()
+        e2.record()
+        B.eig_backward(dt, zt, rho, out["sigma"], out["mu"], wt, gVt, ws=bws, check=False)
+        e3.record()
+        e3.synchronize()
+        fw.append(e0.elapsed_time(e1))
+        bw.append(e2.elapsed_time(e3))
+    f, b = statistics.mean(fw), statistics.mean(bw)
+    return {"n": n, "seed": seed, "fwd_ms": f, "bwd_ms": b, "fwd_plus_bwd_over_fwd": (f + b) / f,
+            "loss": ("w . lambda + " if with_w else "") + "sum W o V, W ~ N(0,1)",
+            "note": "the backward recomputes the eigenvector columns from (sigma, mu); V is not saved"}
+
+
 # ------------------------------------------------------------------ our arm
-def kernel_source_hash():
+def kernel_source_hash(files):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1405_7537_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+    for f in files:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -177,7 +304,10 @@ def committed_traffic(n):
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    if rec.get("source_hash") != kernel_source_hash():
+    try:
+        if rec.get("source_hash") != kernel_source_hash(rec.get("source_files", [])):
+            return None
+    except OSError:
         return None
     per_unit = rec.get("dram_bytes_per_eigenpair")
     return per_unit * n if per_unit else None
@@ -197,6 +327,7 @@ def run_ours(args):
     n = args.n
     d, z, rho = W.hard(n, SEED + rank)
     dev = torch.device("cuda", local)
+    B.lib()
     dt_ = torch.tensor(np.array(d), device=dev)
     zt_ = torch.tensor(np.array(z), device=dev)
     ws = B.workspace(n, dev)
@@ -248,12 +379,7 @@ def run_ours(args):
         dist.barrier()
     wall = time.perf_counter() - t_wall0
     clocks = sampler.stop()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
-    value = world * n * args.steps / (total_ms * 1e-3)
+    value, total_ms = aggregate(sum(step_ms), n, args.steps, world, dist, dev)
     st = B.stream_status(ws)
     if st != 0:
         raise B.DPR1Error(st, "bench timed region")
@@ -314,14 +440,17 @@ def run_ours(args):
             e1.record(stream)
             e1.synchronize()
             ee.append(e0.elapsed_time(e1))
-        e2e_ms = sum(ee)
-        if world > 1:
-            t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = t.item()
-        e2e = {"value": world * n * args.e2e_steps / (e2e_ms * 1e-3), "unit": "eigenpairs/s",
+        e2e_value, e2e_ms = aggregate(sum(ee), n, args.e2e_steps, world, dist, dev)
+        e2e = {"value": e2e_value, "unit": "eigenpairs/s",
                "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 3 * 8 * n + 8 * n * n,
                "ms_per_step": e2e_ms / args.e2e_steps}
+
+    extras = {}
+    if not args.no_extras:
+        extras["fwd_bwd"] = bench_fwd_bwd(B, dev, 4096, 2, 3, True)
+        if args.large:
+            extras["fwd_bwd_large"] = bench_fwd_bwd(B, dev, 32768, 4, 1, False)
+        extras["batched"] = bench_batched(B, dev, 2)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -341,6 +470,7 @@ def run_ours(args):
                 "remedy_counts": {"flagged": stats["flagged"], "r1": stats["r1"], "r2": stats["r2"],
                                   "zero_path": stats["zero_path"]},
                 "wall_s_timed_region": wall}
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

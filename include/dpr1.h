@@ -114,6 +114,35 @@ DPR1_API dpr1_status dpr1_eig(int64_t n, const double* d, const double* z, doubl
                      const dpr1_options* opt, dpr1_stream_t stream);
 
 /*
+ * Bytes of workspace for dpr1_eig_batched on nprob problems with total_n eigenpairs in all.
+ */
+DPR1_API size_t dpr1_batched_workspace_size(int64_t nprob, int64_t total_n);
+
+/*
+ * dpr1_eig_batched -- all eigenpairs of nprob independent DPR1 problems of uneven sizes in
+ * one launch sequence (no counterpart in the paper: divide-and-conquer merges produce
+ * many such problems, Sec. 1).  Problem p occupies elements offs[p] .. offs[p+1]-1 of the
+ * concatenated arrays d, z, lambda, sigma, mu, xnorm (n_p = offs[p+1] - offs[p], any n_p
+ * >= 0), has weight rho[p], and its eigenvector block is Vt + voffs[p], an n_p x n_p
+ * row-major matrix whose row k is v_k.  Every eigenpair of every problem is one work item
+ * of the same persistent kernels (Algorithm 1 per item), so small and large problems
+ * share the GPU without per-problem launches.  The call launches a fixed number of
+ * kernels and never synchronises, so the whole sequence can be captured in a CUDA graph.
+ *
+ *   nprob, total_n   problem count, offs[nprob] (host values, must match the device offsets)
+ *   offs, voffs      device int64[nprob+1]; voffs may be NULL when Vt is NULL
+ *   d, z, rho        device double[total_n], double[total_n], double[nprob]
+ *   lambda, ...      outputs as dpr1_eig, concatenated per problem
+ * Errors: as dpr1_eig; inconsistent offsets are reported as DPR1_ERR_ARG and a bad rho[p]
+ * as DPR1_ERR_RHO through dpr1_stream_status.
+ */
+DPR1_API dpr1_status dpr1_eig_batched(int64_t nprob, int64_t total_n, const int64_t* offs, const int64_t* voffs,
+                                      const double* d, const double* z, const double* rho,
+                                      double* lambda, double* Vt, double* sigma, double* mu, double* xnorm,
+                                      void* workspace, size_t workspace_bytes,
+                                      const dpr1_options* opt, dpr1_stream_t stream);
+
+/*
  * Bytes of workspace for dpr1_eig_backward on order n (256-byte aligned, uninitialised).
  */
 DPR1_API size_t dpr1_backward_workspace_size(int64_t n);
@@ -177,10 +206,11 @@ DPR1_API dpr1_status dpr1_eig_noalloc(int64_t n, const double* d, const double* 
 
 /*
  * Instrumentation (no counterpart in the paper): synchronises `stream` and copies the
- * counters of the last dpr1_eig call on `workspace` into out[0..7]:
- *   0 order of the reduced problem, 1 eigenvalues flagged by K_nu, 2 remedies taken
- *   with R1, 3 with R2, 4 secular-function evaluations in the bisection kernel,
- *   5 evaluations in the remedy kernel, 6 eigenvalues recomputed from A^{-1}, 7 deflated pairs.
+ * counters of the last dpr1_eig / dpr1_eig_batched call on `workspace` into out[0..7]:
+ *   0 eigenvalues solved by the bisection kernel, 1 eigenvalues flagged by K_nu,
+ *   2 remedies taken with R1, 3 with R2, 4 secular-function evaluations in the bisection
+ *   kernel, 5 evaluations in the remedy kernel, 6 eigenvalues recomputed from A^{-1},
+ *   7 deflated pairs.
  */
 DPR1_API dpr1_status dpr1_workspace_stats(void* workspace, int64_t* out, dpr1_stream_t stream);
 

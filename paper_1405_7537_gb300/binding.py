@@ -65,6 +65,8 @@ def lib():
         L.dpr1_probe_dfma.restype = ctypes.c_int
         L.dpr1_backward_workspace_size.argtypes = [_i64]
         L.dpr1_backward_workspace_size.restype = ctypes.c_size_t
+        L.dpr1_batched_workspace_size.argtypes = [_i64, _i64]
+        L.dpr1_batched_workspace_size.restype = ctypes.c_size_t
         for name, argt in _extra_signatures().items():
             if hasattr(L, name):
                 getattr(L, name).argtypes = argt
@@ -75,7 +77,7 @@ def lib():
 
 def _extra_signatures():
     return {
-        "dpr1_eig_batched": [_i64, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+        "dpr1_eig_batched": [_i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                              ctypes.c_size_t, ctypes.POINTER(Options), _vp],
         "dpr1_eig_backward": [_i64, _vp, _vp, _dbl, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp,
                               ctypes.c_size_t, ctypes.POINTER(Options), _vp],
@@ -165,7 +167,7 @@ def probe_reciprocal(x):
     return out
 
 
-STAT_NAMES = ("n_reduced", "flagged", "r1", "r2", "evals_solve", "evals_fix", "zero_path", "deflated")
+STAT_NAMES = ("solved", "flagged", "r1", "r2", "evals_solve", "evals_fix", "zero_path", "deflated")
 
 
 def workspace_stats(ws, stream=None):
@@ -250,3 +252,55 @@ class DPR1Eig(torch.autograd.Function):
 def eigh_dpr1(d, z, rho):
     """Differentiable eigen-decomposition of D + rho z z^T: returns (lambda, V), V[:, k] = v_k."""
     return DPR1Eig.apply(d, z, rho)
+
+
+def batched_workspace(nprob, total_n, device="cuda"):
+    nb = int(lib().dpr1_batched_workspace_size(int(nprob), int(total_n)))
+    return torch.empty(max(nb, 256), dtype=torch.uint8, device=device)
+
+
+class Batch:
+    """A batch of independent DPR1 problems laid out for dpr1_eig_batched.
+
+    sizes: problem orders n_p; d, z: concatenated (device, float64); rho: per problem.
+    Allocates the outputs (eigenvalues and eigenvector blocks) and the workspace once,
+    so that repeated solves and CUDA-graph replays reuse them."""
+
+    def __init__(self, sizes, device="cuda", want_vectors=True):
+        sizes = np.asarray(sizes, dtype=np.int64)
+        self.P = int(sizes.size)
+        offs = np.zeros(self.P + 1, dtype=np.int64)
+        offs[1:] = np.cumsum(sizes)
+        voffs = np.zeros(self.P + 1, dtype=np.int64)
+        voffs[1:] = np.cumsum(sizes * sizes)
+        self.total = int(offs[-1])
+        self.sizes = sizes
+        self.offs_host, self.voffs_host = offs, voffs
+        self.device = torch.device(device)
+        self.offs = torch.tensor(offs, device=device)
+        self.voffs = torch.tensor(voffs, device=device)
+        f64 = dict(dtype=torch.float64, device=device)
+        self.lam = torch.empty(self.total, **f64)
+        self.sigma = torch.empty(self.total, **f64)
+        self.mu = torch.empty(self.total, **f64)
+        self.xnorm = torch.empty(self.total, **f64)
+        self.Vt = torch.empty(int(voffs[-1]), **f64) if want_vectors else None
+        self.ws = batched_workspace(self.P, self.total, device)
+
+    def solve(self, d, z, rho, options=None, check=False, stream=None):
+        o = options if options is not None else default_options()
+        code = lib().dpr1_eig_batched(self.P, self.total, _ptr(self.offs), _ptr(self.voffs), _ptr(d), _ptr(z),
+                                      _ptr(rho), _ptr(self.lam), _ptr(self.Vt), _ptr(self.sigma), _ptr(self.mu),
+                                      _ptr(self.xnorm), _ptr(self.ws), self.ws.numel(), ctypes.byref(o),
+                                      _stream(stream))
+        _check(code, "dpr1_eig_batched")
+        if check:
+            _check(stream_status(self.ws, stream), "dpr1_eig_batched (device)")
+
+    def block(self, p):
+        """(lambda, Vt) views of problem p."""
+        a, b = int(self.offs_host[p]), int(self.offs_host[p + 1])
+        n = b - a
+        va = int(self.voffs_host[p])
+        Vt = self.Vt[va:va + n * n].view(n, n) if self.Vt is not None else None
+        return self.lam[a:b], Vt

@@ -26,8 +26,8 @@ enum : unsigned {
   ST_NONFINITE = 1u,
   ST_UNSORTED = 2u,
   ST_NOT_CONVERGED = 4u,
-  ST_DEFLATED = 8u,
-  ST_ZERO_POLE = 16u,   // some d_j == 0 (the near-zero recompute is then skipped, Eq. (gamma))
+  ST_BADARG = 8u,       // inconsistent batch offsets
+  ST_RHO = 16u,         // a rho_p < 0 or not finite
 };
 
 struct dd {
@@ -65,17 +65,26 @@ __device__ __forceinline__ double rcp_approx(double x) {
   return r;
 }
 
-// 1/x within one ulp (see the file comment).
-__device__ __forceinline__ double rcp(double x) {
+// 1/x within one ulp for |x| in [2^-1020, 2^1021) (see the file comment); no range handling.
+__device__ __forceinline__ double rcp_nr(double x) {
   double r0 = rcp_approx(x);
   double e = __fma_rn(-x, r0, 1.0);
   double p = __fma_rn(e, e, e);
-  double r = __fma_rn(r0, p, r0);
-  // exponent field of x outside [1023-1020, 1023+1020]: take the IEEE quotient
-  unsigned ex = (unsigned)(__double_as_longlong(x) >> 52) & 0x7ffu;
-  if (ex - 3u > 2040u) r = 1.0 / x;
-  return r;
+  return __fma_rn(r0, p, r0);
 }
+
+// the exponent field of x lies in [1023-1020, 1023+1020]: rcp_nr is within one ulp
+__device__ __forceinline__ bool rcp_in_range(double x) {
+  unsigned ex = (unsigned)(__double_as_longlong(x) >> 52) & 0x7ffu;
+  return ex - 3u <= 2040u;
+}
+
+// IEEE quotient for the rare out-of-range operands; kept out of line so that the compiler
+// does not evaluate it speculatively next to every fast reciprocal
+static __device__ __noinline__ double rcp_ieee(double x) { return 1.0 / x; }
+
+// 1/x within one ulp for every x (the IEEE quotient outside the fast range)
+__device__ __forceinline__ double rcp(double x) { return rcp_in_range(x) ? rcp_nr(x) : rcp_ieee(x); }
 
 // dd / dd to about 2^-104 relative: q1 = a.hi/b.hi, then one correction digit from the
 // exact residual a.hi - q1 b.hi (fma), the low parts and the divisor's reciprocal.
@@ -93,38 +102,77 @@ __device__ __forceinline__ dd dd_div(dd a, dd b) {
 
 __device__ __forceinline__ double dd_to_double(dd a) { return __dadd_rn(a.hi, a.lo); }
 
-// A lane group is L consecutive lanes of a warp (L = 8, 16 or 32); gm is its lane mask,
-// so groups of one warp may run different iterations independently.
+// A lane group is L consecutive lanes of a warp (L = 8, 16 or 32; gm is its lane mask, so
+// groups of one warp may run different iterations independently), or the whole thread
+// block (L = 64, 128 or 256 = blockDim.x; gm unused), whose reductions go through shared
+// memory between two block barriers and sum the warp partials in warp order, so every
+// thread again holds the bit-identical total.
 template <int L>
 __device__ __forceinline__ unsigned group_mask() {
-  if (L == 32) return FULL;
+  if (L >= 32) return FULL;
   return ((1u << (L & 31)) - 1u) << ((threadIdx.x & 31) & ~(L - 1));
 }
 
 template <int L>
 __device__ __forceinline__ double group_sum(double v, unsigned gm) {
+  constexpr int W = L < 32 ? L : 32;
 #pragma unroll
-  for (int o = L / 2; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(gm, v, o));
+  for (int o = W / 2; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(gm, v, o));
+  if constexpr (L > 32) {
+    __shared__ double part[L / 32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    v = part[0];
+#pragma unroll
+    for (int t = 1; t < L / 32; t++) v = __dadd_rn(v, part[t]);
+    __syncthreads();
+  }
   return v;
 }
 
 template <int L>
 __device__ __forceinline__ dd group_sum_dd(dd v, unsigned gm) {
+  constexpr int W = L < 32 ? L : 32;
 #pragma unroll
-  for (int o = L / 2; o > 0; o >>= 1) {
+  for (int o = W / 2; o > 0; o >>= 1) {
     dd w;
     w.hi = __shfl_xor_sync(gm, v.hi, o);
     w.lo = __shfl_xor_sync(gm, v.lo, o);
     v = dd_add(v, w);
+  }
+  if constexpr (L > 32) {
+    __shared__ double ph[L / 32], pl[L / 32];
+    if ((threadIdx.x & 31) == 0) { ph[threadIdx.x >> 5] = v.hi; pl[threadIdx.x >> 5] = v.lo; }
+    __syncthreads();
+    v.hi = ph[0]; v.lo = pl[0];
+#pragma unroll
+    for (int t = 1; t < L / 32; t++) v = dd_add(v, dd{ph[t], pl[t]});
+    __syncthreads();
   }
   return v;
 }
 
 template <int L>
 __device__ __forceinline__ double group_max(double v, unsigned gm) {
+  constexpr int W = L < 32 ? L : 32;
 #pragma unroll
-  for (int o = L / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(gm, v, o));
+  for (int o = W / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(gm, v, o));
+  if constexpr (L > 32) {
+    __shared__ double part[L / 32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    v = part[0];
+#pragma unroll
+    for (int t = 1; t < L / 32; t++) v = fmax(v, part[t]);
+    __syncthreads();
+  }
   return v;
+}
+
+template <int L>
+__device__ __forceinline__ bool group_any(bool b, unsigned gm) {
+  if constexpr (L > 32) return __syncthreads_or(b) != 0;
+  else return __any_sync(gm, b) != 0;
 }
 
 __device__ __forceinline__ uint64_t dbits(double a) { return (uint64_t)__double_as_longlong(a); }

@@ -11,11 +11,14 @@ namespace dpr1 {
 
 // Views into the caller's workspace for one problem (see ws_layout).
 struct Ws {
-  unsigned* hdr;       // 64 words: status, counters, sizes
+  unsigned* hdr;       // 64 words: status and counters
   unsigned* status;    // hdr[0]: ST_* bits
-  unsigned* counters;  // hdr[8..15]: 0 solve queue, 1 fix-list length, 2 fix queue, 3 zero-list length
-  int* nred;           // hdr[32]: order of the reduced (deflated) problem
-  int* ndefl;          // hdr[33]: number of deflated pairs
+  unsigned* counters;  // hdr[8..]: see the C_* indices
+  unsigned long long* counters64;  // hdr[24..25]: the solve queue
+  int* nred;           // [P]: order of each reduced (deflated) problem
+  int* ndefl;          // [P]: deflated pairs of each problem
+  unsigned* pst;       // [P]: PT_* bits of each problem
+  int* owner;          // [total]: problem of each element (batch only)
   double *dr, *zr, *zz;       // reduced problem: d, z, z^2
   double *sig, *mu;           // eigenvalue pairs of the reduced problem
   int *shift, *flag, *list;   // pole index (-1: non-pole shift), remedy flag, work lists
@@ -38,8 +41,15 @@ struct Options {
 
 // hdr counters (Ws::counters index)
 enum : int {
-  C_SOLVE_Q = 0, C_FIX_N = 1, C_FIX_Q = 2, C_ZERO_N = 3, C_EVAL_SOLVE = 4, C_EVAL_FIX = 5,
-  C_R2 = 6, C_R1 = 7
+  C_FIX_N = 1, C_FIX_Q = 2, C_ZERO_N = 3, C_EVAL_SOLVE = 4, C_EVAL_FIX = 5,
+  C_R2 = 6, C_R1 = 7, C_SOLVED = 8, C_DEFL = 9
+};
+
+// per-problem bits (Ws::pst)
+enum : unsigned {
+  PT_TRIVIAL = 1u,     // rho == 0
+  PT_DEFLATE = 2u,     // a zero weight or equal poles
+  PT_ZERO_POLE = 4u,   // some d_j == 0 (the near-zero recompute is then skipped, Eq. (gamma))
 };
 
 size_t ws_layout(int64_t n, Ws* w, char* base);
