@@ -43,9 +43,9 @@ __device__ __forceinline__ double arrow_sum_pass(const double* __restrict__ d, c
       r0 = rcp_nr(x0); r1 = rcp_nr(x1);
       b |= (!rcp_in_range(x0) && j != i) || (!rcp_in_range(x1) && j + L != i);
     }
-    double c0 = __dmul_rn(zz[j], r0), c1 = __dmul_rn(zz[j + L], r1);
-    s0 = __dadd_rn(s0, (j == i) ? 0.0 : c0);
-    s1 = __dadd_rn(s1, (j + L == i) ? 0.0 : c1);
+    // the excluded term j == i (0 * inf) is removed by selecting a zero reciprocal
+    s0 = __fma_rn(zz[j], (j == i) ? 0.0 : r0, s0);
+    s1 = __fma_rn(zz[j + L], (j + L == i) ? 0.0 : r1, s1);
   }
   if (j < n) {
     double D0 = __dsub_rn(d[j], di);
@@ -54,8 +54,7 @@ __device__ __forceinline__ double arrow_sum_pass(const double* __restrict__ d, c
     double r0;
     if (SAFE) r0 = rcp(x0);
     else { r0 = rcp_nr(x0); b |= !rcp_in_range(x0) && j != i; }
-    double c0 = __dmul_rn(zz[j], r0);
-    s0 = __dadd_rn(s0, (j == i) ? 0.0 : c0);
+    s0 = __fma_rn(zz[j], (j == i) ? 0.0 : r0, s0);
   }
   *bad = b;
   return group_sum<L>(__dadd_rn(s0, s1), gm);
@@ -151,25 +150,24 @@ __device__ double bisect(Phi phi, double side, double floor, double alo, double 
   uint64_t lo = dbits(alo), hi = dbits(ahi);
   double glo = 0.0, ghi = 0.0;
   bool have_lo = false, have_hi = false;
-  // far end
-  for (int t = 0; t < 8; t++) {
+  // far end: pushed out geometrically (in bit space) while it is still below the root
+  for (int t = 0; t < 64; t++) {
     double g = phi(side * dfrom(hi));
     steps++;
     bool below = below_positive ? (g > 0.0) : (g < 0.0);
     if (!below) { ghi = g; have_hi = true; break; }
     uint64_t wd = hi - lo;
     lo = hi; glo = g; have_lo = true;
-    hi = hi + 2 * wd + (1ull << 40);
-    if (hi >= 0x7ff0000000000000ull) hi = 0x7fefffffffffffffull;
+    hi = hi + 2 * wd + 64;
+    if (hi >= 0x7ff0000000000000ull) { hi = 0x7fefffffffffffffull; }
   }
-  // near end, never below the floor
-  for (int t = 0; t < 8 && !have_lo && lo > fl; t++) {
+  // near end (when above the floor): if the root lies below it, fall back to the floor
+  if (!have_lo && lo > fl) {
     double g = phi(side * dfrom(lo));
     steps++;
     bool below = below_positive ? (g > 0.0) : (g < 0.0);
-    if (below) { glo = g; have_lo = true; break; }
-    hi = lo; ghi = g; have_hi = true;
-    lo = (lo > fl + (1ull << 52)) ? lo - (1ull << 52) : fl;
+    if (below) { glo = g; have_lo = true; }
+    else { hi = lo; ghi = g; have_hi = true; lo = fl; }
   }
   int it = 0;
   while (hi - lo > 1) {
@@ -232,20 +230,26 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
   // floor: the pole of g next to the extreme eigenvalue (largest delta_j for the
   // rightmost, smallest for the leftmost), or 0 when all poles lie on the other side.
   double floor;
+  // Corner bound: for the rightmost eigenvalue nu >= b and nu - b = sum_j w_j^2 / (nu - delta_j)
+  // <= ||w||^2 / (b - max delta) when b > max delta (mirrored for the leftmost).  Next to a
+  // pole b ~ 1/zeta_i^2 dominates and this bracket is narrow.
   if (side > 0) {
     // largest delta_j: the nearest pole above d_i, or for i = 0 the farthest pole below
     double dmax = (i > 0) ? 1.0 / (d[i - 1] - di) : (n > 1 ? 1.0 / (d[n - 1] - di) : -INFINITY);
     floor = fmax(dmax, 0.0);
-    alo = fmax(alo, b * (1.0 - 0x1p-30));
+    alo = fmax(alo, b);
     ahi = fmin(ahi, fmax(b, dmax) + wn);
+    if (b > dmax) ahi = fmin(ahi, b + wn2 / (b - dmax));
   } else {
     double dmin = (i + 1 < n) ? 1.0 / (d[i + 1] - di) : INFINITY;
     floor = fmax(-dmin, 0.0);
-    alo = fmax(alo, -b * (1.0 - 0x1p-30));
+    alo = fmax(alo, -b);
     ahi = fmin(ahi, -fmin(b, dmin) + wn);
+    if (b < dmin) ahi = fmin(ahi, -b + wn2 / (dmin - b));
   }
-  alo = alo * (1.0 - 0x1p-30);
-  ahi = ahi * (1.0 + 0x1p-30);
+  // a few ulps of margin for the rounding of the bounds; bisect() checks both ends
+  alo = alo * (1.0 - 0x1p-48);
+  ahi = ahi * (1.0 + 0x1p-48);
   auto phi = [&](double nu) {
     double S = arrow_sum<L>(d, zz, n, i, di, nu, lane, gm);
     return __dsub_rn(__dsub_rn(b, nu), __dmul_rn(S, inv_zi2));
@@ -302,7 +306,7 @@ __device__ double solve_nonpole(const double* __restrict__ d, const double* __re
     alo = -emin;
     ahi = -emin - gamma * un2;
   }
-  ahi *= (1.0 + 0x1p-30);
+  ahi *= (1.0 + 0x1p-48);
   auto phi = [&](double nu) { return __fma_rn(gamma, shift_sum<L>(d, zz, n, sigma, nu, lane, gm), 1.0); };
   int steps;
   // the floor is the pole e_max (or e_min), or 0 when all e_j lie on the other side
