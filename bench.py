@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-vs-loop and forward+backward measurements")
+    ap.add_argument("--extras", default="fwd_bwd,batched",
+                    help="comma list of extra measurements: fwd_bwd, batched")
     ap.add_argument("--large", action="store_true", help="also time the n=32768 forward+backward workload")
     return ap.parse_args()
 
@@ -446,10 +448,12 @@ def run_ours(args):
                "ms_per_step": e2e_ms / args.e2e_steps}
 
     extras = {}
-    if not args.no_extras:
+    which = set() if args.no_extras else set(x.strip() for x in args.extras.split(",") if x.strip())
+    if "fwd_bwd" in which:
         extras["fwd_bwd"] = bench_fwd_bwd(B, dev, 4096, 2, 3, True)
         if args.large:
             extras["fwd_bwd_large"] = bench_fwd_bwd(B, dev, 32768, 4, 1, False)
+    if "batched" in which:
         extras["batched"] = bench_batched(B, dev, 2)
 
     cpu = None
