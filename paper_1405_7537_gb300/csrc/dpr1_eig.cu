@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(256) k_fix(Prob pb, Ws w, double T_Knu, int ca
       if (s > lo && s < hi) {
         bool ok;
         int st2 = 0;
-        double m2 = solve_nonpole<L>(d, z, zz, n, rho, s, cap, lane, gm, &ok, &st2);
+        double m2 = solve_nonpole<L>(d, z, zz, n, rho, s, k > 0 ? k - 1 : -1, k, cap, lane, gm, &ok, &st2);
         if (!ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
         if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)st2);
         new_sig = s; new_mu = m2; new_shift = -1;
@@ -495,9 +495,20 @@ __global__ void k_zero_solve(Prob pb, Ws w, int cap) {
     const int64_t g = w.zlist[t];
     const int p = p_owner(pb, w, g);
     const int64_t base = p_base(pb, p);
+    const int n = w.nred[p];
+    const double* d = w.dr + base;
+    // poles next to 0: the first negative pole and the one before it (no pole is zero here)
+    int lo = 0, hi = n;
+    while (lo < hi) {
+      int mid = (lo + hi) >> 1;
+      if (d[mid] > 0.0) lo = mid + 1;
+      else hi = mid;
+    }
+    const int below = lo < n ? lo : -1;
+    const int above = lo - 1;
     bool ok;
-    double lam0 = solve_nonpole<32>(w.dr + base, w.zr + base, w.zz + base, w.nred[p], p_rho(pb, p), 0.0, cap,
-                                    lane, FULL, &ok);
+    double lam0 = solve_nonpole<32>(d, w.zr + base, w.zz + base, n, p_rho(pb, p), 0.0, above, below, cap, lane,
+                                    FULL, &ok);
     if (lane == 0) {
       w.lamz[g] = lam0;
       if (!ok) atomicOr(w.status, ST_NOT_CONVERGED);

@@ -113,18 +113,23 @@ __device__ __forceinline__ double shift_sum(const double* __restrict__ d, const 
 // sum_{j != skip} zeta_j^2 / (d_j - s)^2 in binary64 (the squared norm of the border).
 template <int L>
 __device__ __forceinline__ dd dd_pole_sum(const double* __restrict__ d, const double* __restrict__ z, int n,
-                                          int skip, double s, int lane, unsigned gm, double* sq) {
+                                          int skip, double s, int lane, unsigned gm, double* sq,
+                                          double* cub = nullptr) {
   dd acc = {0.0, 0.0};
-  double q = 0.0;
+  double q = 0.0, c3 = 0.0;
   for (int j = lane; j < n; j += L) {
     if (j == skip) continue;
     dd D = two_sum(d[j], -s);
     dd Z = two_prod(z[j], z[j]);
     dd c = dd_div(Z, D);
     acc = dd_add(acc, c);
-    q = __fma_rn(c.hi, rcp(D.hi), q);
+    double r = rcp(D.hi);
+    double c2 = __dmul_rn(c.hi, r);
+    q = __dadd_rn(q, c2);
+    if (cub) c3 = __fma_rn(c2, r, c3);
   }
   *sq = group_sum<L>(q, gm);
+  if (cub) *cub = group_sum<L>(c3, gm);
   return group_sum_dd<L>(acc, gm);
 }
 
@@ -278,39 +283,39 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
 // ---------------------------------------------------------------------------------
 template <int L>
 __device__ double solve_nonpole(const double* __restrict__ d, const double* __restrict__ z,
-                                const double* __restrict__ zz, int n, double rho, double sigma, int cap, int lane,
-                                unsigned gm, bool* ok, int* steps_out = nullptr) {
-  double un2;
-  dd acc = dd_pole_sum<L>(d, z, n, -1, sigma, lane, gm, &un2);
+                                const double* __restrict__ zz, int n, double rho, double sigma, int above, int below,
+                                int cap, int lane, unsigned gm, bool* ok, int* steps_out = nullptr) {
+  // above / below: indices of the poles next to sigma (-1: none on that side)
+  double un2, cub;
+  dd acc = dd_pole_sum<L>(d, z, n, -1, sigma, lane, gm, &un2, &cub);
   dd f = dd_add({1.0, 0.0}, two_prod(acc.hi, rho));
   f = dd_add(f, {__dmul_rn(acc.lo, rho), 0.0});
   *ok = true;
   if (f.hi == 0.0 && f.lo == 0.0) return 0.0;
   double gamma = dd_to_double(dd_div({-rho, 0.0}, f));
-  // largest / smallest e_j: the poles next to sigma
-  double emax = -INFINITY, emin = INFINITY;
-  for (int j = lane; j < n; j += L) {
-    double e = 1.0 / __dsub_rn(d[j], sigma);
-    emax = fmax(emax, e);
-    emin = fmin(emin, e);
-  }
-  emax = group_max<L>(emax, gm);
-  emin = -group_max<L>(-emin, gm);
-  double side, alo, ahi;
+  // extreme e_j = 1/(d_j - sigma): the poles next to sigma
+  const double emax = above >= 0 ? 1.0 / __dsub_rn(d[above], sigma) : -INFINITY;
+  const double emin = below >= 0 ? 1.0 / __dsub_rn(d[below], sigma) : INFINITY;
+  // Rayleigh quotient of u: (sum_j e_j u_j^2)/||u||^2 + gamma ||u||^2, a lower bound of the
+  // largest and an upper bound of the smallest eigenvalue of diag(e) + gamma u u^T; with
+  // sigma next to lambda, gamma ||u||^2 dominates and the bracket below is narrow.
+  const double rq = cub / un2 + gamma * un2;
+  double side, floor, alo, ahi;
   if (gamma > 0.0) {
     side = 1.0;
-    alo = fmax(emax, 0.0);
-    ahi = fmax(emax, 0.0) + gamma * un2;
+    floor = fmax(emax, 0.0);
+    alo = fmax(floor, rq * (1.0 - 0x1p-48));
+    ahi = floor + gamma * un2;
   } else {
     side = -1.0;
-    alo = -emin;
-    ahi = -emin - gamma * un2;
+    floor = fmax(-emin, 0.0);
+    alo = fmax(floor, -rq * (1.0 - 0x1p-48));
+    ahi = floor - gamma * un2;
   }
   ahi *= (1.0 + 0x1p-48);
   auto phi = [&](double nu) { return __fma_rn(gamma, shift_sum<L>(d, zz, n, sigma, nu, lane, gm), 1.0); };
   int steps;
-  // the floor is the pole e_max (or e_min), or 0 when all e_j lie on the other side
-  double nu = bisect(phi, side, alo, alo, ahi, false, cap, ok, &steps);
+  double nu = bisect(phi, side, floor, alo, ahi, false, cap, ok, &steps);
   if (steps_out) *steps_out = steps;
   return 1.0 / nu;
 }
