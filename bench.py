@@ -38,6 +38,7 @@ RHO = 1e3
 NOMINAL_FP64_OPS = 2 * 152 * 2070e6
 # algorithmic binary64 operations per secular term (sub, fma, mul, div, add; fma and div = 1 op)
 OPS_PER_TERM = 5
+ACCEL_OPS_PER_TERM = 8
 
 
 def workload_config(n):
@@ -60,8 +61,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-vs-loop and forward+backward measurements")
-    ap.add_argument("--extras", default="fwd_bwd,batched",
-                    help="comma list of extra measurements: fwd_bwd, batched")
+    ap.add_argument("--extras", default="fwd_bwd,batched,accel",
+                    help="comma list of extra measurements: fwd_bwd, batched, accel")
     ap.add_argument("--large", action="store_true", help="also time the n=32768 forward+backward workload")
     return ap.parse_args()
 
@@ -287,6 +288,48 @@ def bench_fwd_bwd(B, dev, n, seed, steps, with_w):
             "note": "the backward recomputes the eigenvector columns from (sigma, mu); V is not saved"}
 
 
+def bench_accel(B, dev, d, z, rho, ws, out, flush, steps, bisection_ms):
+    """The same workload with the accelerated bracketed solve (zero_finder = 1) in place of
+    bisection: eigenpairs/s, phase times and evaluations of the secular function."""
+    import torch
+    n = d.numel()
+    pe = B.PhaseEvents()
+    opts = pe.attach(B.default_options(zero_finder=B.ACCELERATED))
+    for _ in range(2):
+        B.eig(d, z, rho, ws=ws, out=out, options=opts, check=False)
+    torch.cuda.synchronize()
+    st = B.stream_status(ws)
+    if st != 0:
+        raise B.DPR1Error(st, "accelerated warm-up")
+    stats = B.workspace_stats(ws)
+    ms, ph = [], []
+    for _ in range(max(1, steps)):
+        flush.zero_()
+        e0, e1 = _events()
+        e0.record()
+        B.eig(d, z, rho, ws=ws, out=out, options=opts, check=False)
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        ph.append(pe.times_ms())
+    st = B.stream_status(ws)
+    if st != 0:
+        raise B.DPR1Error(st, "accelerated timed")
+    t = statistics.mean(ms)
+    solve = statistics.mean(p[0] for p in ph)
+    ops = ACCEL_OPS_PER_TERM * (n - 1) * stats["evals_solve"] + OPS_PER_TERM * (n - 1) * 2 * n
+    return {"zero_finder": "accelerated bracketed solve (nearest-pole rational model, value and slope)",
+            "value": n / (t * 1e-3), "unit": "eigenpairs/s", "ms_per_step": t, "steps": len(ms),
+            "phases_ms": {"solve": solve, "remedies": statistics.mean(p[1] for p in ph),
+                          "eigenvectors": statistics.mean(p[2] for p in ph)},
+            "evaluations": stats["evals_solve"], "evaluations_per_eigenpair": stats["evals_solve"] / n,
+            "speedup_vs_bisection": bisection_ms / t,
+            "solve_kernel_rate": {"achieved": ops / (solve * 1e-3) / 1e12, "unit": "T binary64-op/s",
+                                  "frac": ops / (solve * 1e-3) / NOMINAL_FP64_OPS,
+                                  "ops_definition": "8 ops per secular term and evaluation (5 for the value, "
+                                                    "3 for the slope) + the two 5-op passes per eigenvalue"}}
+
+
 # ------------------------------------------------------------------ our arm
 def kernel_source_hash(files):
     h = hashlib.sha256()
@@ -455,6 +498,8 @@ def run_ours(args):
             extras["fwd_bwd_large"] = bench_fwd_bwd(B, dev, 32768, 4, 1, False)
     if "batched" in which:
         extras["batched"] = bench_batched(B, dev, 2)
+    if "accel" in which:
+        extras["accelerated"] = bench_accel(B, dev, dt_, zt_, rho, ws, out, flush, 3, total_ms / args.steps / world)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -78,6 +78,12 @@ typedef struct {
   void* const* phase_events; /* instrumentation: NULL, or 4 cudaEvent_t recorded on `stream`
                                 before the bisection kernel, after it, after the remedies and
                                 after the eigenvector kernel */
+  int zero_finder;       /* 0 (default): bisection of the arrowhead secular function, as
+                            Algorithm 1 states; 1: the accelerated bracketed solve (a
+                            rational model with the nearest pole, fitted to the value and
+                            slope, kept inside the bisection bracket; the fast zero finder
+                            alternative of Sec. 2.2).  Both stop at the
+                            adjacent pair of doubles across the sign change. */
 } dpr1_options;
 
 DPR1_API void dpr1_default_options(dpr1_options* opt);

@@ -20,7 +20,9 @@ _LIB = None
 class Options(ctypes.Structure):
     _fields_ = [("T_Knu", ctypes.c_double), ("T_zero", ctypes.c_double), ("lanes", ctypes.c_int),
                 ("warps_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("max_bisect", ctypes.c_int),
-                ("phase_events", ctypes.POINTER(ctypes.c_void_p))]
+                ("phase_events", ctypes.POINTER(ctypes.c_void_p)), ("zero_finder", ctypes.c_int)]
+
+BISECTION, ACCELERATED = 0, 1   # dpr1_options.zero_finder
 
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "d is not sorted non-increasingly", 3: "rho must be finite and >= 0",

@@ -254,7 +254,7 @@ __global__ void k_deflate(Prob pb, Ws w) {
 // (solve_pole checks the near end, so a wrong sign of a rounded F costs steps, not accuracy).
 // ---------------------------------------------------------------------------------
 template <int L>
-__global__ void __launch_bounds__(256) k_solve(Prob pb, Ws w, int cap) {
+__global__ void __launch_bounds__(256) k_solve(Prob pb, Ws w, int cap, bool fast) {
   if (*w.status & ST_FATAL) return;
   const int lane = threadIdx.x & (L - 1);
   const unsigned gm = group_mask<L>();
@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(256) k_solve(Prob pb, Ws w, int cap) {
         ahi = (-1.0 - rho * sn) / (rho * zz[k - 1]);
       }
     }
-    PoleResult pr = solve_pole<L>(d, z, zz, n, rho, k, i, alo, ahi, cap, lane, gm);
+    PoleResult pr = solve_pole<L>(d, z, zz, n, rho, k, i, alo, ahi, cap, fast, lane, gm);
     if (lane == 0) {
       w.sig[g] = d[i];
       w.mu[g] = pr.mu;
@@ -380,7 +380,7 @@ __global__ void k_classify(Prob pb, Ws w, double T_Knu) {
 //       the open interval (d_k, d_{k-1}) if it falls on a pole, and solve_nonpole.
 // ---------------------------------------------------------------------------------
 template <int L>
-__global__ void __launch_bounds__(256) k_fix(Prob pb, Ws w, double T_Knu, int cap) {
+__global__ void __launch_bounds__(256) k_fix(Prob pb, Ws w, double T_Knu, int cap, bool fast) {
   if (*w.status & ST_FATAL) return;
   const int nfix = (int)w.counters[C_FIX_N];
   const int lane = threadIdx.x & (L - 1);
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(256) k_fix(Prob pb, Ws w, double T_Knu, int ca
     double best_sig = di, best_mu = mu;
     int o = (i == k) ? k - 1 : k;
     if (o >= 0 && o < n && o != i && K2 < K) {
-      PoleResult pr = solve_pole<L>(d, z, zz, n, rho, k, o, 0.0, INFINITY, cap, lane, gm);
+      PoleResult pr = solve_pole<L>(d, z, zz, n, rho, k, o, 0.0, INFINITY, cap, fast, lane, gm);
       if (!pr.ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
       if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)pr.steps);
       best_sig = d[o];
@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(256) k_fix(Prob pb, Ws w, double T_Knu, int ca
       if (s > lo && s < hi) {
         bool ok;
         int st2 = 0;
-        double m2 = solve_nonpole<L>(d, z, zz, n, rho, s, k > 0 ? k - 1 : -1, k, cap, lane, gm, &ok, &st2);
+        double m2 = solve_nonpole<L>(d, z, zz, n, rho, s, k > 0 ? k - 1 : -1, k, cap, fast, lane, gm, &ok, &st2);
         if (!ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
         if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)st2);
         new_sig = s; new_mu = m2; new_shift = -1;
@@ -485,7 +485,7 @@ __global__ void k_zero_detect(Prob pb, Ws w, double T_zero) {
   }
 }
 
-__global__ void k_zero_solve(Prob pb, Ws w, int cap) {
+__global__ void k_zero_solve(Prob pb, Ws w, int cap, bool fast) {
   if (*w.status & ST_FATAL) return;
   const int nz = (int)w.counters[C_ZERO_N];
   const int lane = threadIdx.x & 31;
@@ -507,7 +507,7 @@ __global__ void k_zero_solve(Prob pb, Ws w, int cap) {
     const int below = lo < n ? lo : -1;
     const int above = lo - 1;
     bool ok;
-    double lam0 = solve_nonpole<32>(d, w.zr + base, w.zz + base, n, p_rho(pb, p), 0.0, above, below, cap, lane,
+    double lam0 = solve_nonpole<32>(d, w.zr + base, w.zz + base, n, p_rho(pb, p), 0.0, above, below, cap, fast, lane,
                                     FULL, &ok);
     if (lane == 0) {
       w.lamz[g] = lam0;
@@ -747,6 +747,7 @@ Options resolve(const dpr1_options* o) {
   r.bps = s->blocks_per_sm > 0 && s->blocks_per_sm <= 8 ? s->blocks_per_sm : 2;
   r.cap = s->max_bisect >= 64 && s->max_bisect <= 4096 ? s->max_bisect : def.max_bisect;
   r.events = s->phase_events;
+  r.fast = s->zero_finder == 1;
   return r;
 }
 
@@ -757,13 +758,13 @@ static void record(const Options& o, int t, cudaStream_t st) {
 template <int L>
 static void launch_solve_fix(const Prob& pb, const Ws& w, const Options& o, int grid, cudaStream_t st) {
   record(o, 0, st);
-  k_solve<L><<<grid, 32 * o.warps, 0, st>>>(pb, w, o.cap);
+  k_solve<L><<<grid, 32 * o.warps, 0, st>>>(pb, w, o.cap, o.fast);
   record(o, 1, st);
   int64_t cg = (pb.total + 255) / 256;
   if (cg > sm_count() * 8) cg = sm_count() * 8;
   k_classify<<<cg > 0 ? (int)cg : 1, 256, 0, st>>>(pb, w, o.T_Knu);
   // the flagged eigenvalues are few: one block of 256 threads each keeps the GPU busy
-  k_fix<256><<<sm_count() * 2, 256, 0, st>>>(pb, w, o.T_Knu, o.cap);
+  k_fix<256><<<sm_count() * 2, 256, 0, st>>>(pb, w, o.T_Knu, o.cap, o.fast);
   record(o, 2, st);
 }
 
@@ -797,7 +798,7 @@ static dpr1_status run_table(const Prob& pb, void* workspace, const Options& o, 
   else if (L == 16) launch_solve_fix<16>(pb, w, o, grid, st);
   else launch_solve_fix<32>(pb, w, o, grid, st);
   k_zero_detect<<<sgrid, 256, 0, st>>>(pb, w, o.T_zero);
-  k_zero_solve<<<4, 128, 0, st>>>(pb, w, o.cap);
+  k_zero_solve<<<4, 128, 0, st>>>(pb, w, o.cap, o.fast);
   k_defl_positions<<<sgrid, 256, 0, st>>>(pb, w);
   int64_t vg = (pb.total + 7) / 8;
   if (vg > sms * 16) vg = sms * 16;
@@ -842,6 +843,7 @@ void dpr1_default_options(dpr1_options* opt) {
   opt->blocks_per_sm = 0;
   opt->max_bisect = 96;
   opt->phase_events = nullptr;
+  opt->zero_finder = 0;
 }
 
 const char* dpr1_status_string(dpr1_status s) {

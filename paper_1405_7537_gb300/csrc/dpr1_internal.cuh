@@ -37,6 +37,7 @@ struct Options {
   double T_Knu, T_zero;
   int lanes, warps, bps, cap;
   void* const* events;
+  bool fast;   // accelerated solve instead of bisection
 };
 
 // hdr counters (Ws::counters index)

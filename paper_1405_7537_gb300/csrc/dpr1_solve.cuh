@@ -27,10 +27,13 @@ namespace dpr1 {
 // The hot sums use the fast reciprocal without a per-term range test; each lane records
 // whether any denominator left the fast range and, if a lane of the group saw one, the
 // group recomputes the sum with the range-safe reciprocal (never the case for sane data).
-template <int L, bool SAFE>
+// With DERIV the pass also returns dS/dnu = sum_{j != i} zz_j / (1 - nu Delta_j)^2 (for the
+// accelerated solve); i = -1 excludes no term (non-pole shifts, Delta_j = d_j - sigma).
+template <int L, bool SAFE, bool DERIV>
 __device__ __forceinline__ double arrow_sum_pass(const double* __restrict__ d, const double* __restrict__ zz, int n,
-                                                 int i, double di, double nu, int lane, unsigned gm, bool* bad) {
-  double s0 = 0.0, s1 = 0.0;
+                                                 int i, double di, double nu, int lane, unsigned gm, bool* bad,
+                                                 double* dsum) {
+  double s0 = 0.0, s1 = 0.0, q0 = 0.0, q1 = 0.0;
   bool b = false;
   int j = lane;
   for (; j + L < n; j += 2 * L) {
@@ -44,8 +47,15 @@ __device__ __forceinline__ double arrow_sum_pass(const double* __restrict__ d, c
       b |= (!rcp_in_range(x0) && j != i) || (!rcp_in_range(x1) && j + L != i);
     }
     // the excluded term j == i (0 * inf) is removed by selecting a zero reciprocal
-    s0 = __fma_rn(zz[j], (j == i) ? 0.0 : r0, s0);
-    s1 = __fma_rn(zz[j + L], (j + L == i) ? 0.0 : r1, s1);
+    r0 = (j == i) ? 0.0 : r0;
+    r1 = (j + L == i) ? 0.0 : r1;
+    s0 = __fma_rn(zz[j], r0, s0);
+    s1 = __fma_rn(zz[j + L], r1, s1);
+    if (DERIV) {
+      double u0 = __dmul_rn(D0, r0), u1 = __dmul_rn(D1, r1);   // 1 / (1 - nu Delta_j)
+      q0 = __fma_rn(__dmul_rn(zz[j], u0), u0, q0);
+      q1 = __fma_rn(__dmul_rn(zz[j + L], u1), u1, q1);
+    }
   }
   if (j < n) {
     double D0 = __dsub_rn(d[j], di);
@@ -54,9 +64,15 @@ __device__ __forceinline__ double arrow_sum_pass(const double* __restrict__ d, c
     double r0;
     if (SAFE) r0 = rcp(x0);
     else { r0 = rcp_nr(x0); b |= !rcp_in_range(x0) && j != i; }
-    s0 = __fma_rn(zz[j], (j == i) ? 0.0 : r0, s0);
+    r0 = (j == i) ? 0.0 : r0;
+    s0 = __fma_rn(zz[j], r0, s0);
+    if (DERIV) {
+      double u0 = __dmul_rn(D0, r0);
+      q0 = __fma_rn(__dmul_rn(zz[j], u0), u0, q0);
+    }
   }
   *bad = b;
+  if (DERIV) *dsum = group_sum<L>(__dadd_rn(q0, q1), gm);
   return group_sum<L>(__dadd_rn(s0, s1), gm);
 }
 
@@ -64,73 +80,61 @@ template <int L>
 __device__ __forceinline__ double arrow_sum(const double* __restrict__ d, const double* __restrict__ zz, int n,
                                             int i, double di, double nu, int lane, unsigned gm) {
   bool bad;
-  double s = arrow_sum_pass<L, false>(d, zz, n, i, di, nu, lane, gm, &bad);
-  if (group_any<L>(bad, gm)) s = arrow_sum_pass<L, true>(d, zz, n, i, di, nu, lane, gm, &bad);
+  double s = arrow_sum_pass<L, false, false>(d, zz, n, i, di, nu, lane, gm, &bad, nullptr);
+  if (group_any<L>(bad, gm)) s = arrow_sum_pass<L, true, false>(d, zz, n, i, di, nu, lane, gm, &bad, nullptr);
+  return s;
+}
+
+// the sum and its derivative with respect to nu
+template <int L>
+__device__ __forceinline__ double arrow_sum_d(const double* __restrict__ d, const double* __restrict__ zz, int n,
+                                              int i, double di, double nu, int lane, unsigned gm, double* dsum) {
+  bool bad;
+  double s = arrow_sum_pass<L, false, true>(d, zz, n, i, di, nu, lane, gm, &bad, dsum);
+  if (group_any<L>(bad, gm)) s = arrow_sum_pass<L, true, true>(d, zz, n, i, di, nu, lane, gm, &bad, dsum);
   return s;
 }
 
 // Same terms with Delta_j = d_j - sigma for a non-pole shift (no excluded index):
 // sum_j u_j^2 / (e_j - nu), e_j = 1/(d_j - sigma), u_j = zeta_j/(d_j - sigma).
-template <int L, bool SAFE>
-__device__ __forceinline__ double shift_sum_pass(const double* __restrict__ d, const double* __restrict__ zz, int n,
-                                                 double sigma, double nu, int lane, unsigned gm, bool* bad) {
-  double s0 = 0.0, s1 = 0.0;
-  bool b = false;
-  int j = lane;
-  for (; j + L < n; j += 2 * L) {
-    double D0 = __dsub_rn(d[j], sigma), D1 = __dsub_rn(d[j + L], sigma);
-    double t0 = __fma_rn(-nu, D0, 1.0), t1 = __fma_rn(-nu, D1, 1.0);
-    double x0 = __dmul_rn(D0, t0), x1 = __dmul_rn(D1, t1);
-    double r0, r1;
-    if (SAFE) { r0 = rcp(x0); r1 = rcp(x1); }
-    else { r0 = rcp_nr(x0); r1 = rcp_nr(x1); b |= !rcp_in_range(x0) || !rcp_in_range(x1); }
-    s0 = __fma_rn(zz[j], r0, s0);
-    s1 = __fma_rn(zz[j + L], r1, s1);
-  }
-  if (j < n) {
-    double D0 = __dsub_rn(d[j], sigma);
-    double t0 = __fma_rn(-nu, D0, 1.0);
-    double x0 = __dmul_rn(D0, t0);
-    double r0;
-    if (SAFE) r0 = rcp(x0);
-    else { r0 = rcp_nr(x0); b |= !rcp_in_range(x0); }
-    s0 = __fma_rn(zz[j], r0, s0);
-  }
-  *bad = b;
-  return group_sum<L>(__dadd_rn(s0, s1), gm);
-}
-
 template <int L>
 __device__ __forceinline__ double shift_sum(const double* __restrict__ d, const double* __restrict__ zz, int n,
                                             double sigma, double nu, int lane, unsigned gm) {
-  bool bad;
-  double s = shift_sum_pass<L, false>(d, zz, n, sigma, nu, lane, gm, &bad);
-  if (group_any<L>(bad, gm)) s = shift_sum_pass<L, true>(d, zz, n, sigma, nu, lane, gm, &bad);
-  return s;
+  return arrow_sum<L>(d, zz, n, -1, sigma, nu, lane, gm);
 }
 
 // sum_{j != skip} zeta_j^2 / (d_j - s) in double-double (skip = -1: all j); also returns
 // sum_{j != skip} zeta_j^2 / (d_j - s)^2 in binary64 (the squared norm of the border).
+// Each term zeta_j^2 / (d_j - s) is formed from the exact difference D = Dh + Dl (two_sum)
+// and the exact square Z = Zh + Zl (fma) as q + e_q, q = Zh / Dh rounded, with the first-order
+// correction e_q = ((Zh - q Dh) + (Zl - q Dl)) / Dh.  The q are summed by compensated
+// summation (Sum2 of Ogita, Rump and Oishi, SIAM J. Sci. Comput. 26 (2005)): two_sum keeps
+// each rounding error, and the errors and the e_q go to a second binary64 accumulator, which
+// gives the sum as accurately as accumulation in twice the working precision (Sec. 2.3).
 template <int L>
 __device__ __forceinline__ dd dd_pole_sum(const double* __restrict__ d, const double* __restrict__ z, int n,
                                           int skip, double s, int lane, unsigned gm, double* sq,
                                           double* cub = nullptr) {
-  dd acc = {0.0, 0.0};
-  double q = 0.0, c3 = 0.0;
+  double hi = 0.0, lo = 0.0, q2 = 0.0, c3 = 0.0;
   for (int j = lane; j < n; j += L) {
     if (j == skip) continue;
-    dd D = two_sum(d[j], -s);
-    dd Z = two_prod(z[j], z[j]);
-    dd c = dd_div(Z, D);
-    acc = dd_add(acc, c);
-    double r = rcp(D.hi);
-    double c2 = __dmul_rn(c.hi, r);
-    q = __dadd_rn(q, c2);
+    const dd D = two_sum(d[j], -s);
+    const double zj = z[j];
+    const double Zh = __dmul_rn(zj, zj);
+    const double Zl = __fma_rn(zj, zj, -Zh);
+    const double r = rcp(D.hi);
+    const double q = __dmul_rn(Zh, r);
+    const double eq = __dmul_rn(__dadd_rn(__fma_rn(-q, D.hi, Zh), __fma_rn(-q, D.lo, Zl)), r);
+    const dd t = two_sum(hi, q);
+    hi = t.hi;
+    lo = __dadd_rn(lo, __dadd_rn(t.lo, eq));
+    const double c2 = __dmul_rn(q, r);
+    q2 = __dadd_rn(q2, c2);
     if (cub) c3 = __fma_rn(c2, r, c3);
   }
-  *sq = group_sum<L>(q, gm);
+  *sq = group_sum<L>(q2, gm);
   if (cub) *cub = group_sum<L>(c3, gm);
-  return group_sum_dd<L>(acc, gm);
+  return group_sum_dd<L>(two_sum(hi, lo), gm);
 }
 
 // ---------------------------------------------------------------------------------
@@ -197,6 +201,120 @@ __device__ double bisect(Phi phi, double side, double floor, double alo, double 
 }
 
 // ---------------------------------------------------------------------------------
+// Accelerated bracketed solve (a fast zero finder in place of bisection, Sec. 2.2).
+//
+// On t = |nu| the secular functions of both solvers have the form
+//   F(t) = a0 - a1 t + Psi(t),   Psi(t) = sum_j w_j^2 / (t - e_j),   every pole e_j < root,
+// (a1 = 1 for the arrowhead function g, a1 = 0 for the non-pole function h after scaling),
+// with F > 0 below the root.  Psi is positive, decreasing and convex above its poles.
+// Model: Psi(t') ~ c + s / (t' - E), E the nearest pole (the largest e_j), with c and s
+// fitted to Psi and Psi' at the current point t:  s = -Psi'(t) (t - E)^2,
+// c = Psi(t) + Psi'(t) (t - E).  For one term w^2/(t' - e) with e <= E the fitted model
+// minus the term is  c (t' - t)^2 / ((t' - E)(t' - e)) >= 0,  c = w^2 (E - e)/(t - e)^2 >= 0,
+// so the model lies above Psi everywhere above E and the model's root
+//   a1 x^2 - A x - s = 0,  x = t' - E,  A = a0 + c - a1 E
+// lies at or above the true root, from any t: in exact arithmetic the iterates come down
+// to the root from above (quadratically; exactly in one step when one pole carries all
+// the weight).  The candidates are kept strictly inside the bracket [lo, hi] of doubles
+// (bit patterns, as in bisect); when the model no longer moves the upper end by more than
+// one double, back-off steps hi - 1, hi - 4, hi - 16, ... find a point below the root (and
+// lo + 1, lo + 4, ... a point above it when the model puts the root at the lower end), and
+// the loop ends, like bisect, with an adjacent pair of doubles across the sign change.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ double model_root(double t, double F, double psi, double dpsi, double E, double a0,
+                                             double a1, double fscale) {
+  const double x0 = __dsub_rn(t, E);
+  if (x0 > 0.0 && x0 <= 1.0e300 && dpsi < 0.0) {
+    const double s = -dpsi * x0 * x0;
+    const double c = __fma_rn(dpsi, x0, psi);
+    const double A = (a0 + c) - a1 * E;
+    double x;
+    if (a1 > 0.0) {
+      const double disc = (A != 0.0) ? fabs(A) * sqrt(1.0 + (4.0 * a1 * s / A) / A) : sqrt(4.0 * a1 * s);
+      x = (A > 0.0) ? (A + disc) / (2.0 * a1) : (2.0 * s) / (disc - A);
+    } else {
+      x = (A < 0.0) ? -s / A : INFINITY;
+    }
+    return E + x;
+  }
+  // no usable pole: Newton's step on F = fscale (a0 - a1 t + Psi)
+  const double dF = fscale * (dpsi - a1);
+  return (dF < 0.0) ? t - F / dF : NAN;
+}
+
+// ev(t, want, &psi, &dpsi) returns F(t) times a positive constant fscale and, when want is
+// set, Psi(t) and Psi'(t) (back-off steps, which usually close the bracket, skip them).
+// floor, alo, ahi as in bisect.
+template <class Ev>
+__device__ double accel_solve(Ev ev, double floor, double alo, double ahi, double E, double a0, double a1,
+                              double fscale, int cap, bool* ok, int* steps_out) {
+  if (!(floor >= 0.0)) floor = 0.0;
+  if (!(alo >= floor)) alo = floor;
+  if (!(ahi > alo)) ahi = (alo > 0.0) ? alo * 2.0 : 1.0;
+  const uint64_t top = 0x7fefffffffffffffull;
+  uint64_t lo = dbits(floor), hi = top;
+  bool have_lo = false, have_hi = false, good = true;
+  double Flo = 0.0, Fhi = 0.0;
+  uint64_t t = dbits(ahi);
+  uint64_t span = dbits(ahi) - dbits(alo) + 64;
+  uint64_t back = 1, back_lo = 1, wref = 0;
+  int steps = 0, model_steps = 0, since = 0;
+  bool want = true, from_lo = false;
+  const int limit = cap + 32;
+  for (;;) {
+    if (steps >= limit) { good = false; break; }
+    const double tv = dfrom(t);
+    double psi = 0.0, dpsi = 0.0;
+    const double F = ev(tv, want, &psi, &dpsi);
+    steps++;
+    if (F > 0.0) { lo = t; Flo = F; have_lo = true; }
+    else { hi = t; Fhi = F; have_hi = true; }
+    if (hi - lo <= 1) break;
+    const double tc = want ? model_root(tv, F, psi, dpsi, E, a0, a1, fscale) : NAN;
+    const uint64_t c = (tc > 0.0 && tc <= 1.7e308) ? dbits(tc) : 0ull;
+    want = true;
+    uint64_t nxt;
+    if (!have_hi) {
+      // every point so far lies below the root; the model's root lies above it
+      if (c > t) nxt = c;
+      else { nxt = (top - t > span) ? t + span : top; span *= 2; }
+    } else {
+      const bool use_model = c > lo && c + 1 < hi && model_steps < 24;
+      bool force_mid = false;
+      if (have_lo) {
+        // both ends evaluated: the bracket must halve at least every second step
+        const uint64_t wdt = hi - lo;
+        if (wref == 0 || wdt <= wref / 2) { wref = wdt; since = 0; }
+        else if (++since >= 2) force_mid = true;
+      }
+      if (force_mid) nxt = lo + ((hi - lo) >> 1);
+      else if (use_model) { nxt = c; model_steps++; }
+      else if (have_lo && (c != 0ull ? c <= lo : from_lo)) {
+        // the model puts the root at the lower end (within rounding): step up from it
+        nxt = (hi - lo > back_lo) ? lo + back_lo : lo + ((hi - lo) >> 1);
+        back_lo = (back_lo < (1ull << 60)) ? back_lo * 4 : back_lo;
+        want = false;
+        from_lo = true;
+      } else {
+        nxt = (hi - lo > back) ? hi - back : lo + ((hi - lo) >> 1);
+        back = (back < (1ull << 60)) ? back * 4 : back;
+        want = false;
+        from_lo = false;
+      }
+    }
+    if (nxt <= lo || nxt >= hi) nxt = lo + ((hi - lo) >> 1);
+    t = nxt;
+  }
+  double alo_g = have_lo ? fabs(Flo) : INFINITY;
+  double ahi_g = have_hi ? fabs(Fhi) : INFINITY;
+  if (isnan(alo_g)) alo_g = INFINITY;
+  if (isnan(ahi_g)) ahi_g = INFINITY;
+  *ok = good && have_hi;
+  if (steps_out) *steps_out = steps;
+  return dfrom((ahi_g < alo_g || !have_lo) && have_hi ? hi : lo);
+}
+
+// ---------------------------------------------------------------------------------
 // Solve at a pole: extreme eigenvalue of the arrowhead inverse of A - d_i I.
 // ---------------------------------------------------------------------------------
 struct PoleResult {
@@ -222,7 +340,7 @@ __device__ __forceinline__ double corner_b(const double* __restrict__ d, const d
 template <int L>
 __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __restrict__ z,
                                  const double* __restrict__ zz, int n, double rho, int k, int i, double alo,
-                                 double ahi, int cap, int lane, unsigned gm) {
+                                 double ahi, int cap, bool fast, int lane, unsigned gm) {
   PoleResult r;
   double wn2;
   double b = corner_b<L>(d, z, n, i, rho, lane, gm, &wn2);
@@ -234,7 +352,7 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
   double wn = sqrt(wn2);
   // floor: the pole of g next to the extreme eigenvalue (largest delta_j for the
   // rightmost, smallest for the leftmost), or 0 when all poles lie on the other side.
-  double floor;
+  double floor, E;   // E: the nearest pole on |nu| (the accelerated solve's model pole)
   // Corner bound: for the rightmost eigenvalue nu >= b and nu - b = sum_j w_j^2 / (nu - delta_j)
   // <= ||w||^2 / (b - max delta) when b > max delta (mirrored for the leftmost).  Next to a
   // pole b ~ 1/zeta_i^2 dominates and this bracket is narrow.
@@ -242,12 +360,15 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
     // largest delta_j: the nearest pole above d_i, or for i = 0 the farthest pole below
     double dmax = (i > 0) ? 1.0 / (d[i - 1] - di) : (n > 1 ? 1.0 / (d[n - 1] - di) : -INFINITY);
     floor = fmax(dmax, 0.0);
+    E = dmax;
     alo = fmax(alo, b);
     ahi = fmin(ahi, fmax(b, dmax) + wn);
     if (b > dmax) ahi = fmin(ahi, b + wn2 / (b - dmax));
   } else {
     double dmin = (i + 1 < n) ? 1.0 / (d[i + 1] - di) : INFINITY;
     floor = fmax(-dmin, 0.0);
+    // smallest delta_j: the nearest pole below d_i, or for i = n-1 the farthest pole above
+    E = (i + 1 < n) ? -dmin : (n > 1 ? -1.0 / (d[0] - di) : -INFINITY);
     alo = fmax(alo, -b);
     ahi = fmin(ahi, -fmin(b, dmin) + wn);
     if (b < dmin) ahi = fmin(ahi, -b + wn2 / (dmin - b));
@@ -255,15 +376,32 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
   // a few ulps of margin for the rounding of the bounds; bisect() checks both ends
   alo = alo * (1.0 - 0x1p-48);
   ahi = ahi * (1.0 + 0x1p-48);
-  auto phi = [&](double nu) {
-    double S = arrow_sum<L>(d, zz, n, i, di, nu, lane, gm);
-    return __dsub_rn(__dsub_rn(b, nu), __dmul_rn(S, inv_zi2));
-  };
   bool ok;
   int steps;
-  // g(nu) > 0 below the root for the rightmost; for the leftmost, |nu| below the root
-  // means nu above it, where g < 0.
-  double nu = bisect(phi, side, floor, alo, ahi, side > 0, cap, &ok, &steps);
+  double nu;
+  if (fast) {
+    // F(t) = side * g(side * t) = side b - t + Psi(t), Psi = -side S / zeta_i^2
+    auto ev = [&](double t, bool want, double* psi, double* dpsi) {
+      const double v = side * t;
+      double dS = 0.0;
+      const double S = want ? arrow_sum_d<L>(d, zz, n, i, di, v, lane, gm, &dS)
+                            : arrow_sum<L>(d, zz, n, i, di, v, lane, gm);
+      const double Sz = __dmul_rn(S, inv_zi2);
+      *psi = -side * Sz;
+      *dpsi = -__dmul_rn(dS, inv_zi2);
+      const double g = __dsub_rn(__dsub_rn(b, v), Sz);
+      return side > 0 ? g : -g;
+    };
+    nu = side * accel_solve(ev, floor, alo, ahi, E, side * b, 1.0, 1.0, cap, &ok, &steps);
+  } else {
+    auto phi = [&](double v) {
+      double S = arrow_sum<L>(d, zz, n, i, di, v, lane, gm);
+      return __dsub_rn(__dsub_rn(b, v), __dmul_rn(S, inv_zi2));
+    };
+    // g(nu) > 0 below the root for the rightmost; for the leftmost, |nu| below the root
+    // means nu above it, where g < 0.
+    nu = bisect(phi, side, floor, alo, ahi, side > 0, cap, &ok, &steps);
+  }
   r.nu = nu;
   r.mu = 1.0 / nu;
   r.b = b;
@@ -284,7 +422,7 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
 template <int L>
 __device__ double solve_nonpole(const double* __restrict__ d, const double* __restrict__ z,
                                 const double* __restrict__ zz, int n, double rho, double sigma, int above, int below,
-                                int cap, int lane, unsigned gm, bool* ok, int* steps_out = nullptr) {
+                                int cap, bool fast, int lane, unsigned gm, bool* ok, int* steps_out = nullptr) {
   // above / below: indices of the poles next to sigma (-1: none on that side)
   double un2, cub;
   dd acc = dd_pole_sum<L>(d, z, n, -1, sigma, lane, gm, &un2, &cub);
@@ -313,9 +451,27 @@ __device__ double solve_nonpole(const double* __restrict__ d, const double* __re
     ahi = floor - gamma * un2;
   }
   ahi *= (1.0 + 0x1p-48);
-  auto phi = [&](double nu) { return __fma_rn(gamma, shift_sum<L>(d, zz, n, sigma, nu, lane, gm), 1.0); };
   int steps;
-  double nu = bisect(phi, side, floor, alo, ahi, false, cap, ok, &steps);
+  double nu;
+  if (fast) {
+    // F(t) = -h(side * t) = |gamma| (Psi(t) - 1/|gamma|), Psi = -side S; model pole: the
+    // largest e_j on |nu| (with no pole above sigma, the one farthest below it)
+    const double E = (gamma > 0.0) ? (above >= 0 ? emax : 1.0 / __dsub_rn(d[n - 1], sigma))
+                                   : (below >= 0 ? -emin : -1.0 / __dsub_rn(d[0], sigma));
+    const double ag = fabs(gamma);
+    auto ev = [&](double t, bool want, double* psi, double* dpsi) {
+      double dS = 0.0;
+      const double S = want ? arrow_sum_d<L>(d, zz, n, -1, sigma, side * t, lane, gm, &dS)
+                            : arrow_sum<L>(d, zz, n, -1, sigma, side * t, lane, gm);
+      *psi = -side * S;
+      *dpsi = -dS;
+      return -__fma_rn(gamma, S, 1.0);
+    };
+    nu = side * accel_solve(ev, floor, alo, ahi, E, -1.0 / ag, 0.0, ag, cap, ok, &steps);
+  } else {
+    auto phi = [&](double v) { return __fma_rn(gamma, shift_sum<L>(d, zz, n, sigma, v, lane, gm), 1.0); };
+    nu = bisect(phi, side, floor, alo, ahi, false, cap, ok, &steps);
+  }
   if (steps_out) *steps_out = steps;
   return 1.0 / nu;
 }

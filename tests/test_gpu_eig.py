@@ -7,8 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_common import (eig_errors, strict_interlacing_ok, tol, trace_defect, two_sum, vec_rel,
-                        lam_minus_ref, pair_minus_ref)
+from gpu_common import check_full, run_gpu, sampled as _sampled, tol
 from paper_1405_7537_gb300 import workloads as W
 
 torch = pytest.importorskip("torch")
@@ -22,32 +21,6 @@ def B():
     from paper_1405_7537_gb300 import binding
     binding.lib()
     return binding
-
-
-def run_gpu(B, d, z, rho, **opt):
-    o = B.default_options(**opt) if opt else None
-    r = B.eig(torch.tensor(np.array(d), device="cuda"), torch.tensor(np.array(z), device="cuda"), rho, options=o)
-    torch.cuda.synchronize()
-    return {k: (v.cpu().numpy() if v is not None else None) for k, v in r.items()}
-
-
-def check_full(B, d, z, rho, threads=16, **opt):
-    n = d.size
-    g = run_gpu(B, d, z, rho, **opt)
-    q = oracle.quad_all(d, z, rho, threads=threads)
-    r = oracle.eig_all(d, z, rho, threads=threads)
-    el, ep, ev = eig_errors(g, "quad", q)
-    # rows recomputed from A^{-1}: lambda is accurate, sigma + mu need not be
-    zp = g["lam"] != g["sigma"] + g["mu"]
-    ep = np.where(zp, 0.0, ep)
-    assert el.max() <= tol(n), ("lambda vs quad", el.max(), tol(n), int(el.argmax()))
-    assert ep.max() <= tol(n), ("pair vs quad", ep.max(), tol(n), int(ep.argmax()))
-    assert ev.max() <= tol(n), ("vector vs quad", ev.max(), tol(n), int(ev.argmax()))
-    ol, op, ov = eig_errors(g, "oracle", r)
-    assert ol.max() <= tol(n), ("lambda vs oracle", ol.max())
-    assert ov.max() <= tol(n), ("vector vs oracle", ov.max())
-    assert strict_interlacing_ok(np.where(zp, g["lam"], g["sigma"]), np.where(zp, 0.0, g["mu"]), d)
-    return g, r
 
 
 def test_reciprocal_within_one_ulp(B):
@@ -80,7 +53,6 @@ def test_paper_example1(B):
 
 
 def test_paper_example2_pairs(B):
-    mp = pytest.importorskip("mpmath").mp
     d, z, rho = W.example2()
     g, _ = check_full(B, d, z, rho)
 
@@ -104,31 +76,6 @@ def test_uniform_512_full_config(B):
     """The n = 512 workload exactly as benchmarked: all pairs vs oracle and binary128."""
     d, z, rho = W.uniform(512, 0)
     check_full(B, d, z, rho)
-
-
-def _sampled(B, d, z, rho, nsample_oracle=48, nsample_quad=12, seed=0):
-    n = d.size
-    g = run_gpu(B, d, z, rho)
-    rng = np.random.default_rng(seed)
-    ks = np.unique(np.concatenate([[0, 1, n // 2, n - 2, n - 1], rng.choice(n, nsample_oracle, replace=False)]))
-    r = oracle.eig_all(d, z, rho, ks=ks, threads=16)
-    ol, op, ov = eig_errors(g, "oracle", r, ks)
-    assert ol.max() <= tol(n) and ov.max() <= tol(n), (ol.max(), ov.max(), tol(n))
-    kq = ks[:: max(1, ks.size // nsample_quad)]
-    q = oracle.quad_all(d, z, rho, ks=kq, threads=16)
-    ql, qp, qv = eig_errors(g, "quad", q, kq)
-    assert ql.max() <= tol(n) and qv.max() <= tol(n), (ql.max(), qv.max(), tol(n))
-    # properties at full size
-    zp = g["lam"] != g["sigma"] + g["mu"]
-    assert strict_interlacing_ok(np.where(zp, g["lam"], g["sigma"]), np.where(zp, 0.0, g["mu"]), d)
-    assert trace_defect(g["sigma"], g["mu"], d, z, rho) <= 4 * n * 2.0 ** -52
-    Vt = torch.tensor(g["Vt"], device="cuda")
-    idx = torch.tensor(rng.choice(n, 256, replace=False), device="cuda")
-    blk = Vt[idx] @ Vt[idx].T - torch.eye(256, dtype=torch.float64, device="cuda")
-    assert blk.abs().max().item() <= n * 2.0 ** -52
-    nrm = torch.linalg.vector_norm(Vt, dim=1)
-    assert (nrm - 1).abs().max().item() <= 64 * 2.0 ** -52
-    return g
 
 
 def test_hard_16384_sampled(B):
