@@ -567,6 +567,8 @@ __global__ void k_defl_positions(Prob pb, Ws w) {
 // k_vectors: one warp per eigenvalue row.  x_j = zeta_j / ((d_j - sigma) - mu) (for a
 // pole shift d_i this is Eq. (eigenvecAi), with x_i = -zeta_i / mu), ||x|| with a
 // scaled fallback when the plain sum of squares over- or underflows, v = x / ||x||.
+// Each x_j is evaluated once: the first pass stores it in the output row while summing
+// the squares, the second rescales the row in place (FP64 work once, the row written twice).
 // Writes lambda, sigma, mu, ||x|| and row k of the problem's V^T block (coalesced along
 // j).  In a deflated problem the row of reduced eigenvalue k goes to output row rpos and
 // component q takes coef[q] * x_{src[q]}; deflated pairs are written by k_defl_rows.
@@ -588,16 +590,28 @@ __global__ void __launch_bounds__(256) k_vectors(Prob pb, Ws w) {
     const double* __restrict__ d = w.dr + base;
     const double* __restrict__ z = w.zr + base;
     const double s = w.sig[g], m = w.mu[g];
-    double mx = 0.0, q = 0.0;
+    const int row = defl ? w.rpos[g] : k;
+    double* vr = pb.Vt ? pb.Vt + p_vbase(pb, p) + (int64_t)row * p_ld(pb, p) : nullptr;
+    // First pass: x_j (fast reciprocal, range flag) and sum x_j^2; without deflation x_j is
+    // stored in its row at once and the second pass only rescales it.
+    const bool store = vr && !defl;
+    double q = 0.0;
+    bool bad = false;
     for (int j = lane; j < n; j += 32) {
-      double x = __dmul_rn(z[j], rcp(__dsub_rn(__dsub_rn(d[j], s), m)));
-      mx = fmax(mx, fabs(x));
+      const double den = __dsub_rn(__dsub_rn(d[j], s), m);
+      const double x = __dmul_rn(z[j], rcp_nr(den));
+      bad |= !rcp_in_range(den);
+      if (store) vr[j] = x;
       q = __fma_rn(x, x, q);
     }
-    mx = group_max<32>(mx, FULL);
     q = group_sum<32>(q, FULL);
+    bad = group_any<32>(bad, FULL);
     double scale = 1.0;                  // v_j = x_j * scale / sqrt(q)
-    if (!(q < 1e300) || !(mx > 1e-140)) {
+    bool rewrite = false;                // the stored x_j are not usable: write v_j from scratch
+    if (bad || !(q < 1e300) || !(q > 1e-280)) {
+      double mx = 0.0;
+      for (int j = lane; j < n; j += 32) mx = fmax(mx, fabs(__dmul_rn(z[j], rcp(__dsub_rn(__dsub_rn(d[j], s), m)))));
+      mx = group_max<32>(mx, FULL);
       scale = 1.0 / mx;
       q = 0.0;
       for (int j = lane; j < n; j += 32) {
@@ -605,10 +619,10 @@ __global__ void __launch_bounds__(256) k_vectors(Prob pb, Ws w) {
         q = __fma_rn(x, x, q);
       }
       q = group_sum<32>(q, FULL);
+      rewrite = true;
     }
     const double nrm = sqrt(q);          // ||x|| * scale
     const double c = scale / nrm;
-    const int row = defl ? w.rpos[g] : k;
     if (lane == 0) {
       double lz = w.lamz[g];
       pb.lambda[base + row] = isnan(lz) ? __dadd_rn(s, m) : lz;
@@ -616,9 +630,10 @@ __global__ void __launch_bounds__(256) k_vectors(Prob pb, Ws w) {
       if (pb.mu) pb.mu[base + row] = m;
       if (pb.xnorm) pb.xnorm[base + row] = nrm / scale;
     }
-    if (!pb.Vt) continue;
-    double* vr = pb.Vt + p_vbase(pb, p) + (int64_t)row * p_ld(pb, p);
-    if (!defl) {
+    if (!vr) continue;
+    if (!defl && !rewrite) {
+      for (int j = lane; j < n; j += 32) vr[j] = __dmul_rn(vr[j], c);
+    } else if (!defl) {
       for (int j = lane; j < n; j += 32) vr[j] = __dmul_rn(z[j], rcp(__dsub_rn(__dsub_rn(d[j], s), m))) * c;
     } else {
       for (int qq = lane; qq < nfull; qq += 32) {
