@@ -39,6 +39,9 @@ NOMINAL_FP64_OPS = 2 * 152 * 2070e6
 # algorithmic binary64 operations per secular term (sub, fma, mul, div, add; fma and div = 1 op)
 OPS_PER_TERM = 5
 ACCEL_OPS_PER_TERM = 8
+# kernels one dpr1_eig call launches: k_scan, k_deflate, k_solve, k_classify, k_fix, k_zero_detect,
+# k_zero_solve, k_defl_positions, k_vectors, k_defl_rows, k_trivial
+LAUNCHES_PER_CALL = 11
 
 
 def workload_config(n):
@@ -64,6 +67,8 @@ def parse():
     ap.add_argument("--extras", default="fwd_bwd,batched,accel",
                     help="comma list of extra measurements: fwd_bwd, batched, accel")
     ap.add_argument("--large", action="store_true", help="also time the n=32768 forward+backward workload")
+    ap.add_argument("--zero-finder", type=int, choices=[0, 1], default=0,
+                    help="0: bisection (the method as stated, default); 1: the accelerated bracketed solve")
     return ap.parse_args()
 
 
@@ -340,8 +345,8 @@ def kernel_source_hash(files):
     return h.hexdigest()[:16]
 
 
-def committed_traffic(n):
-    """DRAM bytes per launch of the bisection kernel from the committed ncu summary, if it was
+def committed_traffic(n, zero_finder=0):
+    """DRAM bytes per launch of the solve kernel from the committed ncu summary, if it was
     taken on the current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "k_solve_traffic.json")
     try:
@@ -354,7 +359,7 @@ def committed_traffic(n):
             return None
     except OSError:
         return None
-    per_unit = rec.get("dram_bytes_per_eigenpair")
+    per_unit = rec.get("dram_bytes_per_eigenpair", {}).get("accelerated" if zero_finder else "bisection")
     return per_unit * n if per_unit else None
 
 
@@ -383,7 +388,8 @@ def run_ours(args):
                xnorm=torch.empty(n, dtype=torch.float64, device=dev))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     pe = B.PhaseEvents()
-    opts = pe.attach(B.default_options())
+    zf = args.zero_finder
+    opts = pe.attach(B.default_options(zero_finder=zf))
     stream = torch.cuda.current_stream()
 
     def step():
@@ -431,7 +437,16 @@ def run_ours(args):
 
     # roofline of the dominant kernel (the bisection kernel k_solve)
     evals = stats["evals_solve"]
-    ops = OPS_PER_TERM * (n - 1) * (evals + 2 * n)
+    if zf == 0:
+        ops = OPS_PER_TERM * (n - 1) * (evals + 2 * n)
+        kname = "k_solve (shift test, double-double b, bisection)"
+        odef = ("5 ops (sub, fma, mul, div, add) per secular term x (n-1) x (bisection evaluations + 2 passes "
+                "per eigenvalue)")
+    else:
+        ops = (n - 1) * (ACCEL_OPS_PER_TERM * evals + OPS_PER_TERM * 2 * n)
+        kname = "k_solve (shift test, double-double b, accelerated bracketed solve)"
+        odef = ("8 ops per secular term and evaluation (5 for the value, 3 for the slope) x (n-1) + the two "
+                "5-op passes per eigenvalue")
     t_solve = statistics.mean(solve_ms) * 1e-3
     achieved = ops / t_solve
     # live binary64 fma rate of this GPU at this clock (same process, after the timed region)
@@ -445,15 +460,14 @@ def run_ours(args):
     pe1.record(stream)
     pe1.synchronize()
     measured_fma = sms * 4 * 256 * 4096 * 8 / (pe0.elapsed_time(pe1) * 1e-3)
-    roof = {"bound": "alu", "kernel": "k_solve (shift test, double-double b, bisection)",
+    roof = {"bound": "alu", "kernel": kname,
             "achieved": achieved / 1e12, "peak": NOMINAL_FP64_OPS / 1e12, "unit": "T binary64-op/s",
-            "frac": achieved / NOMINAL_FP64_OPS, "traffic": committed_traffic(n),
+            "frac": achieved / NOMINAL_FP64_OPS, "traffic": committed_traffic(n, zf),
             "peak_source": "nominal GB300 binary64 1.25 TFLOP/s = 2 fma/clk/SM x 152 SMs x 2070 MHz "
                            "(MEASURED_PEAKS.json has no binary64 entry)",
             "measured_fma_rate": measured_fma / 1e12,
             "frac_of_measured_fma_rate": achieved / measured_fma,
-            "ops_per_launch": ops, "ops_definition": "5 ops (sub, fma, mul, div, add) per secular term "
-                                                     "x (n-1) x (bisection evaluations + 2 passes per eigenvalue)",
+            "ops_per_launch": ops, "ops_definition": odef,
             "launch_ms": 1e3 * t_solve, "bisection_evaluations": evals}
 
     # end to end through the public API with host buffers
@@ -466,8 +480,10 @@ def run_ours(args):
         mu_h = torch.empty(n, dtype=torch.float64).pin_memory()
         Vt_h = torch.empty((n, n), dtype=torch.float64).pin_memory()
 
+        e2e_opts = B.default_options(zero_finder=zf)
+
         def e2e_step():
-            r = B.eig(d_h, z_h, rho, ws=ws, out=out, check=False)
+            r = B.eig(d_h, z_h, rho, ws=ws, out=out, options=e2e_opts, check=False)
             lam_h.copy_(r["lam"], non_blocking=True)
             sig_h.copy_(r["sigma"], non_blocking=True)
             mu_h.copy_(r["mu"], non_blocking=True)
@@ -512,8 +528,9 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": workload_config(n), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": 10 * args.steps, "clocks": clocks,
+                "config": dict(workload_config(n), zero_finder=("bisection" if zf == 0 else "accelerated")),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": LAUNCHES_PER_CALL * args.steps, "clocks": clocks,
                 "phases_ms": {"bisection": statistics.mean(solve_ms), "remedies": statistics.mean(fix_ms),
                               "eigenvectors": statistics.mean(vec_ms)},
                 "remedy_counts": {"flagged": stats["flagged"], "r1": stats["r1"], "r2": stats["r2"],

@@ -30,7 +30,10 @@
 
 namespace dpr1 {
 
-constexpr int NWB = 1024;          // warps of the row kernel (128 blocks x 8 warps)
+// warps of the row kernel: 152 blocks of 7 warps, one block per SM of a GB300 (a fixed
+// number, so that the partial sums and their order do not depend on the device)
+constexpr int WPB = 7;
+constexpr int NWB = 152 * WPB;
 
 static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -208,7 +211,7 @@ dpr1_status dpr1_eig_backward(int64_t n, const double* d, const double* z, doubl
   BwdWs w;
   bwd_layout(n, &w, (char*)workspace);
   if (cudaMemsetAsync(w.status, 0, 256, st) != cudaSuccess) return DPR1_ERR_CUDA;
-  k_bwd_rows<<<NWB / 8, 256, 0, st>>>((int)n, d, z, rho, sigma, mu, grad_lambda, grad_Vt, ldg, w);
+  k_bwd_rows<<<NWB / WPB, 32 * WPB, 0, st>>>((int)n, d, z, rho, sigma, mu, grad_lambda, grad_Vt, ldg, w);
   int g = (int)((n + 255) / 256);
   if (g > 4 * sm_count()) g = 4 * sm_count();
   k_bwd_reduce<<<g, 256, 0, st>>>((int)n, w, grad_d, grad_z, grad_rho);
