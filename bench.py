@@ -64,8 +64,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-vs-loop and forward+backward measurements")
-    ap.add_argument("--extras", default="fwd_bwd,batched,accel",
-                    help="comma list of extra measurements: fwd_bwd, batched, accel")
+    ap.add_argument("--extras", default="fwd_bwd,batched,accel,hermitian",
+                    help="comma list of extra measurements: fwd_bwd, batched, accel, hermitian")
     ap.add_argument("--large", action="store_true", help="also time the n=32768 forward+backward workload")
     ap.add_argument("--zero-finder", type=int, choices=[0, 1], default=0,
                     help="0: bisection (the method as stated, default); 1: the accelerated bracketed solve")
@@ -360,6 +360,38 @@ def bench_accel(B, dev, d, z, rho, ws, out, flush, steps, bisection_ms):
                                                     "3 for the slope) + the two 5-op passes per eigenvalue"}}
 
 
+def bench_hermitian(B, dev, n, seed, steps, flush):
+    """The complex Hermitian D + rho z z^* (the hard spectrum with random phases on z):
+    eigenvalues and the complex V (16 n^2 B), both zero finders."""
+    import torch
+    from paper_1405_7537_gb300 import workloads as W
+    d, z, rho = W.hermitian(n, seed)
+    dt = torch.tensor(d, device=dev)
+    zt = torch.tensor(z, device=dev)
+    ws = B.hermitian_workspace(n, dev)
+    res = {"workload": "hard spectrum n=%d (seed %d) with phases exp(i theta), theta ~ U(0, 2 pi)" % (n, seed),
+           "unit": "eigenpairs/s", "v_bytes": 16 * n * n}
+    for name, zf in (("bisection", 0), ("accelerated", 1)):
+        o = B.default_options(zero_finder=zf)
+        B.eig_hermitian(dt, zt, rho, options=o, ws=ws)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(max(1, steps)):
+            flush.zero_()
+            e0, e1 = _events()
+            e0.record()
+            B.eig_hermitian(dt, zt, rho, options=o, ws=ws, check=False)
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        st = B.stream_status(ws)
+        if st != 0:
+            raise B.DPR1Error(st, "hermitian")
+        t = statistics.mean(ms)
+        res[name] = {"value": n / (t * 1e-3), "ms_per_step": t}
+    return res
+
+
 # ------------------------------------------------------------------ our arm
 def kernel_source_hash(files):
     h = hashlib.sha256()
@@ -539,6 +571,8 @@ def run_ours(args):
             extras["fwd_bwd_large"] = bench_fwd_bwd(B, dev, 32768, 4, 1, False)
     if "batched" in which:
         extras["batched"] = bench_batched(B, dev, 2)
+    if "hermitian" in which:
+        extras["hermitian"] = bench_hermitian(B, dev, n, SEED, 2, flush)
     if "accel" in which:
         extras["accelerated"] = bench_accel(B, dev, dt_, zt_, rho, ws, out, flush, 3, total_ms / args.steps / world)
 

@@ -178,6 +178,35 @@ DPR1_API dpr1_status dpr1_eig_backward(int64_t n, const double* d, const double*
                                        const dpr1_options* opt, dpr1_stream_t stream);
 
 /*
+ * Bytes of workspace for dpr1_eig_hermitian on order n (256-byte aligned, uninitialised).
+ */
+DPR1_API size_t dpr1_hermitian_workspace_size(int64_t n);
+
+/*
+ * dpr1_eig_hermitian -- all eigenpairs of the complex Hermitian DPR1 matrix A = D + rho z z^*
+ * (the extension of Algorithm 1 to the Hermitian case that the paper states after it).
+ * With z_j = |z_j| phi_j, |phi_j| = 1, A = Phi (D + rho |z| |z|^T) Phi^*, Phi = diag(phi): the
+ * eigenvalues are those of the real DPR1 matrix with weights |z_j| (computed by the dpr1_eig
+ * path) and v_k = Phi u_k = (D - lambda_k I)^{-1} z / ||.|| (Eq. (Aeigenvec) with complex z).
+ *
+ *   n, d, rho  as dpr1_eig (d real, non-increasing; rho >= 0)
+ *   z          device complex double[n], interleaved (re, im), 16-byte aligned
+ *   lambda, sigma, mu, xnorm   as dpr1_eig (real)
+ *   Vt         device complex double[n*ldv] (interleaved, 16-byte aligned) or NULL; out: row k
+ *              = v_k; ldv >= n counts complex entries
+ *   workspace  dpr1_hermitian_workspace_size(n) bytes, 256-byte aligned; its first part is a
+ *              dpr1_eig workspace, so dpr1_stream_status(workspace, stream) reports the
+ *              device-detected conditions
+ * Errors: as dpr1_eig (a non-finite re or im part gives DPR1_ERR_NONFINITE); a misaligned z or
+ * Vt is DPR1_ERR_ARG.
+ */
+DPR1_API dpr1_status dpr1_eig_hermitian(int64_t n, const double* d, const double* z, double rho,
+                                        double* lambda, double* Vt, int64_t ldv,
+                                        double* sigma, double* mu, double* xnorm,
+                                        void* workspace, size_t workspace_bytes,
+                                        const dpr1_options* opt, dpr1_stream_t stream);
+
+/*
  * Synchronises `stream` and returns the status the device recorded in `workspace`
  * during the last call that used it (DPR1_OK if none), then clears it.
  */

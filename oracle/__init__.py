@@ -16,6 +16,8 @@ Two references live here:
 (d_j, e_j); d_i = d_j gives the eigenvalue d_i after a Givens rotation in the
 (i, j) plane) and the sign flip for rho < 0 (Sec. 1) around ``eig_all``.
 ``backward`` is the adjoint of (lambda, V) with respect to (d, z, rho).
+``eig_hermitian`` reduces the complex Hermitian D + rho z z^* to the real problem with
+weights |z_j| by the diagonal unitary of the phases of z.
 """
 import ctypes
 import os
@@ -314,3 +316,28 @@ def eig_full(d, z, rho, opts=None, threads=1):
     order = np.argsort(-lam_all, kind="stable")
     return dict(lam=lam_all[order], Vt=np.array(vec_all)[order], sigma=np.array(sig_all)[order],
                 mu=np.array(mu_all)[order])
+
+
+def eig_hermitian(d, z, rho, opts=None, threads=1, ks=None):
+    """Eigenpairs of the complex Hermitian D + rho z z^* (d real, non-increasing).
+
+    With phi_j = z_j / |z_j| (phi_j = 1 for z_j = 0) and Phi = diag(phi),
+    Phi^* (D + rho z z^*) Phi = D + rho |z| |z|^T: the eigenvalues are those of the real
+    problem with weights |z_j| (Algorithm 1 through ``eig_all``, or ``eig_full`` when it
+    deflates) and v_k = Phi u_k.  Returns dict(lam, Vt, sigma, mu) with complex Vt[k] = v_k."""
+    d = _f64(d)
+    z = np.ascontiguousarray(z, dtype=np.complex128)
+    a = np.abs(z)
+    phi = np.ones(z.size, dtype=np.complex128)
+    nz = a > 0
+    phi[nz] = z.real[nz] / a[nz] + 1j * (z.imag[nz] / a[nz])   # each part correctly rounded
+    irreducible = rho > 0 and np.all(nz) and np.all(d[:-1] > d[1:])
+    if irreducible:
+        r = eig_all(d, a, rho, opts, ks=ks, threads=threads)
+    else:
+        if ks is not None:
+            raise ValueError("sampled rows need an irreducible problem")
+        r = eig_full(d, a, rho, opts, threads=threads)
+    out = dict(r)
+    out["Vt"] = r["Vt"] * phi[None, :]
+    return out

@@ -69,6 +69,8 @@ def lib():
         L.dpr1_backward_workspace_size.restype = ctypes.c_size_t
         L.dpr1_batched_workspace_size.argtypes = [_i64, _i64]
         L.dpr1_batched_workspace_size.restype = ctypes.c_size_t
+        L.dpr1_hermitian_workspace_size.argtypes = [_i64]
+        L.dpr1_hermitian_workspace_size.restype = ctypes.c_size_t
         for name, argt in _extra_signatures().items():
             if hasattr(L, name):
                 getattr(L, name).argtypes = argt
@@ -83,6 +85,8 @@ def _extra_signatures():
                              ctypes.c_size_t, ctypes.POINTER(Options), _vp],
         "dpr1_eig_backward": [_i64, _vp, _vp, _dbl, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp,
                               ctypes.c_size_t, ctypes.POINTER(Options), _vp],
+        "dpr1_eig_hermitian": [_i64, _vp, _vp, _dbl, _vp, _vp, _i64, _vp, _vp, _vp, _vp, ctypes.c_size_t,
+                               ctypes.POINTER(Options), _vp],
     }
 
 
@@ -158,6 +162,39 @@ def eig(d, z, rho, want_vectors=True, options=None, ws=None, out=None, check=Tru
     _check(code, "dpr1_eig")
     if check and n > 0:
         _check(stream_status(ws, stream), "dpr1_eig (device)")
+    return out
+
+
+def hermitian_workspace(n, device="cuda"):
+    return torch.empty(max(int(lib().dpr1_hermitian_workspace_size(int(n))), 256), dtype=torch.uint8, device=device)
+
+
+def eig_hermitian(d, z, rho, want_vectors=True, options=None, ws=None, check=True, stream=None):
+    """All eigenpairs of the Hermitian D + rho z z^* (d real non-increasing, z complex, rho >= 0).
+
+    Returns dict(lam, Vt, sigma, mu, xnorm); Vt is complex128 with row k = v_k."""
+    dev = d.device if isinstance(d, torch.Tensor) and d.is_cuda else torch.device("cuda", torch.cuda.current_device())
+    d = _dev_f64(d, dev)
+    if not isinstance(z, torch.Tensor):
+        z = torch.from_numpy(np.array(z, dtype=np.complex128, copy=True))
+    z = z.to(device=dev, dtype=torch.complex128).contiguous()
+    n = d.numel()
+    if z.numel() != n:
+        raise ValueError("d and z must have the same length")
+    f64 = dict(dtype=torch.float64, device=dev)
+    out = dict(lam=torch.empty(n, **f64), sigma=torch.empty(n, **f64), mu=torch.empty(n, **f64),
+               xnorm=torch.empty(n, **f64),
+               Vt=torch.empty((n, n), dtype=torch.complex128, device=dev) if want_vectors else None)
+    if ws is None:
+        ws = hermitian_workspace(n, dev)
+    o = options if options is not None else default_options()
+    Vt = out["Vt"]
+    code = lib().dpr1_eig_hermitian(n, _ptr(d), _ptr(z), float(rho), _ptr(out["lam"]), _ptr(Vt),
+                                    n if Vt is not None else 0, _ptr(out["sigma"]), _ptr(out["mu"]),
+                                    _ptr(out["xnorm"]), _ptr(ws), ws.numel(), ctypes.byref(o), _stream(stream))
+    _check(code, "dpr1_eig_hermitian")
+    if check and n > 0:
+        _check(stream_status(ws, stream), "dpr1_eig_hermitian (device)")
     return out
 
 

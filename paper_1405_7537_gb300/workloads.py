@@ -153,3 +153,12 @@ def large(n=32768, seed=4, with_W=True):
     sign = np.where(rng.random(n) < 0.5, -1.0, 1.0)
     W = rng.standard_normal((n, n)) if with_W else None
     return d, mag * sign, 1.0, W
+
+
+def hermitian(n=16384, seed=1, base="hard"):
+    """A complex Hermitian DPR1 problem: the real workload `base` (its d, rho and |z|) with a
+    phase exp(i theta_j), theta_j ~ U(0, 2 pi) from an independent stream, on every z_j."""
+    d, z, rho = (hard if base == "hard" else uniform)(n, seed)
+    rng = np.random.default_rng(seed + 1000)
+    theta = rng.uniform(0.0, 2.0 * np.pi, n)
+    return d, np.abs(z) * np.exp(1j * theta), rho
