@@ -341,3 +341,79 @@ def eig_hermitian(d, z, rho, opts=None, threads=1, ks=None):
     out = dict(r)
     out["Vt"] = r["Vt"] * phi[None, :]
     return out
+
+
+def tridiag_tree(n, t):
+    """Node boundaries at depth t of the divide-and-conquer tree of order n:
+    node i covers [s_i, s_{i+1}), s_i = floor(i n / 2^t); its children are nodes 2i and
+    2i + 1 at depth t + 1, so every boundary between consecutive indices is split once."""
+    return [(i * n) >> t for i in range((1 << t) + 1)]
+
+
+def tridiag_dc(a, b, threads=1):
+    """Eigen-decomposition of the symmetric tridiagonal T (diagonal a, off-diagonal b) by
+    divide and conquer down to single elements, every merge a DPR1 problem (Sec. 1: the
+    merges of Cuppen's method are DPR1 eigenproblems).
+
+    Tear at the boundary between m - 1 and m of a node: T = diag(T1, T2) + rho v v^T with
+    rho = |b_{m-1}|, v = e_{m-1} + sign(b_{m-1}) e_m, and T1, T2 with |b_{m-1}| taken off
+    their corner diagonal entries; so a single element i carries a_i - |b_{i-1}| - |b_i|.
+    Merge: with T1 = Q1 L1 Q1^T and T2 = Q2 L2 Q2^T, T = Q (L + rho u u^T) Q^T,
+    Q = diag(Q1, Q2), u = Q^T v = (last row of Q1, sign * first row of Q2).  The poles
+    L1, L2 are merged into one non-increasing order (stable: T1's entry first on ties),
+    the DPR1 problem is solved by ``eig_full`` (Algorithm 1 with the paper's deflation),
+    and the eigenvectors of T are Q times the DPR1 eigenvectors mapped back to the
+    unsorted order.  Returns (lam non-increasing, Qt) with Qt[k] the k-th eigenvector."""
+    a = _f64(a)
+    b = _f64(b)
+    n = a.size
+    if n == 0:
+        return np.empty(0), np.empty((0, 0))
+    if b.size != max(n - 1, 0):
+        raise ValueError("b must have n - 1 entries")
+    bl = np.concatenate([[0.0], np.abs(b)])
+    br = np.concatenate([np.abs(b), [0.0]])
+    leaf = (a - bl) - br
+    T = 0
+    while (1 << T) < n:
+        T += 1
+    # depth T: every node has at most one element
+    lam = leaf.copy()
+    blocks = {}
+    s = tridiag_tree(n, T)
+    for i in range(1 << T):
+        if s[i + 1] - s[i] == 1:
+            blocks[i] = np.ones((1, 1))
+    for t in range(T - 1, -1, -1):
+        s = tridiag_tree(n, t)
+        lam_t = np.empty(n)
+        new = {}
+        for i in range(1 << t):
+            lo, hi = s[i], s[i + 1]
+            N = hi - lo
+            if N == 0:
+                continue
+            if N == 1:
+                lam_t[lo] = leaf[lo]
+                new[i] = np.ones((1, 1))
+                continue
+            mid = ((2 * i + 1) * n) >> (t + 1)
+            n1 = mid - lo
+            Q1, Q2 = blocks[2 * i], blocks[2 * i + 1]
+            beta = b[mid - 1]
+            rho = abs(beta)
+            sgn = 1.0 if beta >= 0 else -1.0
+            vals = lam[lo:hi]
+            u = np.concatenate([Q1[:, n1 - 1], sgn * Q2[:, 0]])
+            order = np.argsort(-vals, kind="stable")
+            r = eig_full(vals[order], u[order], rho, threads=threads)
+            pos = np.empty(N, dtype=np.int64)
+            pos[order] = np.arange(N)
+            Gt = r["Vt"][:, pos]                      # Gt[k, src] = w_k at the sorted position of src
+            Qt = np.empty((N, N))
+            Qt[:, :n1] = Gt[:, :n1] @ Q1
+            Qt[:, n1:] = Gt[:, n1:] @ Q2
+            lam_t[lo:hi] = r["lam"]
+            new[i] = Qt
+        lam, blocks = lam_t, new
+    return lam, blocks[0]

@@ -162,3 +162,24 @@ def hermitian(n=16384, seed=1, base="hard"):
     rng = np.random.default_rng(seed + 1000)
     theta = rng.uniform(0.0, 2.0 * np.pi, n)
     return d, np.abs(z) * np.exp(1j * theta), rho
+
+
+def tridiagonal(n=4096, seed=5):
+    """A symmetric tridiagonal matrix: diagonal a and off-diagonal b ~ U(-1, 1)."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-1.0, 1.0, n), rng.uniform(-1.0, 1.0, max(n - 1, 0))
+
+
+def wilkinson(n=21):
+    """Wilkinson's W_n^+ (n = 2m + 1): diagonal |m - j|, j = 0..n-1, off-diagonal ones."""
+    m = (n - 1) // 2
+    return np.abs(m - np.arange(n)).astype(np.float64), np.ones(n - 1)
+
+
+def glued_wilkinson(n=21, copies=4, glue=1e-10):
+    """`copies` Wilkinson W_n^+ blocks coupled by off-diagonal entries `glue`: clusters of
+    very close eigenvalues, a hard case for divide and conquer."""
+    a0, b0 = wilkinson(n)
+    a = np.tile(a0, copies)
+    b = np.concatenate([np.concatenate([b0, [glue]]) for _ in range(copies)])[:-1]
+    return a, b
