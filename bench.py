@@ -64,8 +64,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-vs-loop and forward+backward measurements")
-    ap.add_argument("--extras", default="fwd_bwd,batched,accel,hermitian",
-                    help="comma list of extra measurements: fwd_bwd, batched, accel, hermitian")
+    ap.add_argument("--extras", default="fwd_bwd,batched,accel,hermitian,tridiag",
+                    help="comma list of extra measurements: fwd_bwd, batched, accel, hermitian, tridiag")
     ap.add_argument("--large", action="store_true", help="also time the n=32768 forward+backward workload")
     ap.add_argument("--zero-finder", type=int, choices=[0, 1], default=0,
                     help="0: bisection (the method as stated, default); 1: the accelerated bracketed solve")
@@ -392,6 +392,61 @@ def bench_hermitian(B, dev, n, seed, steps, flush):
     return res
 
 
+def bench_tridiag(B, dev, n, seed, steps):
+    """Divide and conquer for a random symmetric tridiagonal matrix (every merge a DPR1 problem,
+    each tree depth one batched launch), eigenvalues and eigenvectors, both zero finders;
+    cuSOLVER's dense symmetric solver on the same matrix (torch.linalg.eigh) as context."""
+    import torch
+    from paper_1405_7537_gb300 import workloads as W
+    a, b = W.tridiagonal(n, seed)
+    at = torch.tensor(a, device=dev)
+    bt = torch.tensor(b, device=dev)
+    ws = B.tridiag_workspace(n, dev)
+    T = 0
+    while (1 << T) < n:
+        T += 1
+    # binary64 flops of the eigenvector products: 2 N (N1^2 + N2^2) per merge
+    flops = 0
+    for t in range(T):
+        P = 1 << t
+        for i in range(P):
+            lo, hi = (i * n) >> t, ((i + 1) * n) >> t
+            if hi - lo >= 2:
+                mid = ((2 * i + 1) * n) >> (t + 1)
+                flops += 2 * (hi - lo) * ((mid - lo) ** 2 + (hi - mid) ** 2)
+    res = {"workload": "symmetric tridiagonal n=%d, a, b ~ U(-1, 1), seed %d; eigenvalues and Q" % (n, seed),
+           "unit": "eigenpairs/s", "depths": T, "gemm_flops": flops}
+    for name, zf in (("bisection", 0), ("accelerated", 1)):
+        o = B.default_options(zero_finder=zf)
+        B.eigh_tridiagonal(at, bt, options=o, ws=ws)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(max(1, steps)):
+            e0, e1 = _events()
+            e0.record()
+            B.eigh_tridiagonal(at, bt, options=o, ws=ws, check=False)
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        st = B.stream_status(ws)
+        if st != 0:
+            raise B.DPR1Error(st, "tridiag")
+        t = statistics.mean(ms)
+        res[name] = {"value": n / (t * 1e-3), "ms_per_step": t}
+    Td = torch.diag(at) + torch.diag(bt, 1) + torch.diag(bt, -1)
+    torch.linalg.eigh(Td)
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record()
+    torch.linalg.eigh(Td)
+    e1.record()
+    e1.synchronize()
+    ref_ms = e0.elapsed_time(e1)
+    res["cusolver_dense_eigh"] = {"value": n / (ref_ms * 1e-3), "ms_per_step": ref_ms,
+                                  "note": "torch.linalg.eigh on the dense n x n matrix (library, context only)"}
+    return res
+
+
 # ------------------------------------------------------------------ our arm
 def kernel_source_hash(files):
     h = hashlib.sha256()
@@ -571,6 +626,8 @@ def run_ours(args):
             extras["fwd_bwd_large"] = bench_fwd_bwd(B, dev, 32768, 4, 1, False)
     if "batched" in which:
         extras["batched"] = bench_batched(B, dev, 2)
+    if "tridiag" in which:
+        extras["tridiag"] = bench_tridiag(B, dev, 4096, 5, 3)
     if "hermitian" in which:
         extras["hermitian"] = bench_hermitian(B, dev, n, SEED, 2, flush)
     if "accel" in which:

@@ -34,7 +34,9 @@
  *   zeta_j / ((d_j - sigma_k) - mu_k).
  * - Deflation (Sec. 1): zeta_j == 0 gives the eigenpair (d_j, e_j); d_j == d_{j+1}
  *   gives the eigenvalue d_j after a Givens rotation in the (j, j+1) plane.  Both are
- *   exact tests.  Deflated pairs carry sigma = lambda, mu = 0.
+ *   exact tests.  A weight whose square is not a normal binary64 number (|zeta_j| <
+ *   2^-511) counts as zero: the secular function only sees zeta_j^2, and dropping it
+ *   changes A by less than 2^-510 rho ||z||.  Deflated pairs carry sigma = lambda, mu = 0.
  * - The functions never throw, never exit and never wait on the device except in
  *   dpr1_stream_status().
  */
@@ -101,7 +103,8 @@ DPR1_API size_t dpr1_workspace_size(int64_t n);
  * dpr1_eig -- all eigenpairs of one DPR1 matrix (Algorithm 1 for k = 1..n).
  *
  *   n        order (n >= 0; n == 0 is a no-op)
- *   d, z     device double[n]; d non-increasing, any z (zeros and ties are deflated)
+ *   d, z     device double[n]; d non-increasing, any z (zeros and ties are deflated, and so is
+ *            a weight whose square is not a normal binary64 number, |z_j| < 2^-511)
  *   rho      rho >= 0 (rho == 0 gives lambda = d, V = I)
  *   lambda   device double[n], out: eigenvalues, non-increasing
  *   Vt       device double[n*ldv] or NULL, out: row k = v_k (ldv >= n)
@@ -205,6 +208,36 @@ DPR1_API dpr1_status dpr1_eig_hermitian(int64_t n, const double* d, const double
                                         double* sigma, double* mu, double* xnorm,
                                         void* workspace, size_t workspace_bytes,
                                         const dpr1_options* opt, dpr1_stream_t stream);
+
+/*
+ * Bytes of workspace for dpr1_tridiag_eig on order n (256-byte aligned, uninitialised):
+ * about 22 n^2 bytes (the eigenvector blocks of two tree depths, the DPR1 eigenvectors of
+ * one depth) plus O(n).
+ */
+DPR1_API size_t dpr1_tridiag_workspace_size(int64_t n);
+
+/*
+ * dpr1_tridiag_eig -- all eigenpairs of the symmetric tridiagonal matrix T with diagonal a
+ * and off-diagonal b, by divide and conquer whose merges are DPR1 eigenproblems (Sec. 1:
+ * divide and conquer is where DPR1 problems arise), each tree depth's merges solved by one
+ * dpr1_eig_batched launch sequence (Algorithm 1 per eigenpair).  The tree halves down to
+ * single indices; the tear at a split m is rho v v^T with rho = |b_{m-1}| >= 0 and
+ * v = e_{m-1} + sign(b_{m-1}) e_m.  Eigenvector blocks are formed by binary64 products on
+ * the GPU (no library GEMM).
+ *
+ *   n          order (n >= 0; n == 0 is a no-op)
+ *   a, b       device double[n], double[n-1] (b may be NULL for n == 1)
+ *   lambda     device double[n], out: eigenvalues, non-increasing
+ *   Qt         device double[n*ldq] or NULL (eigenvalues only), out: row k = eigenvector k
+ *   workspace  dpr1_tridiag_workspace_size(n) bytes, 256-byte aligned; dpr1_stream_status on
+ *              it reports the device-detected conditions of all merge levels
+ *   opt        NULL or tunables of the DPR1 solves (zero_finder, lanes, ...)
+ * Errors: DPR1_ERR_ARG, DPR1_ERR_WORKSPACE, DPR1_ERR_CUDA synchronously; DPR1_ERR_NONFINITE,
+ * DPR1_ERR_NOT_CONVERGED through dpr1_stream_status.
+ */
+DPR1_API dpr1_status dpr1_tridiag_eig(int64_t n, const double* a, const double* b, double* lambda,
+                                      double* Qt, int64_t ldq, void* workspace, size_t workspace_bytes,
+                                      const dpr1_options* opt, dpr1_stream_t stream);
 
 /*
  * Synchronises `stream` and returns the status the device recorded in `workspace`

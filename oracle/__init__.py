@@ -251,11 +251,19 @@ def dd_op(name, a, b):
     return out[0], out[1]
 
 
+def zero_weight(z):
+    """A weight whose square is below the normal range of binary64 (|zeta| < 2^-511) counts as
+    zero: the secular function sees only zeta^2, which is not representable, and deflating it
+    changes A = D + rho z z^T by less than 2^-510 rho ||z||."""
+    return np.abs(z) < 2.0 ** -511
+
+
 def eig_full(d, z, rho, opts=None, threads=1):
     """Eigen-decomposition of D + rho z z^T for any d sorted non-increasingly.
 
     Handles rho == 0 (lambda = d, V = I), rho < 0 (Sec. 1: solve -D - rho z z^T),
-    zeta_j == 0 and d_j == d_{j+1} (Sec. 1 deflation, exact tests only) and returns
+    zeta_j == 0 and d_j == d_{j+1} (Sec. 1 deflation, exact tests only; a weight whose square
+    is not a normal binary64 number counts as zero, see ``zero_weight``) and returns
     dict(lam, Vt, sigma, mu) with lam non-increasing and Vt[k] = v_k.  Deflated pairs
     carry sigma = lambda and mu = 0."""
     d = _f64(d).copy()
@@ -279,7 +287,7 @@ def eig_full(d, z, rho, opts=None, threads=1):
     zr = z.copy()
     defl = []                  # (position, eigenvalue) of deflated pairs in the rotated basis
     for j in range(n):
-        if zr[j] == 0.0:
+        if zero_weight(zr[j]):
             defl.append(j)
     # ties: rotate each later member of a group of equal d's into the first non-zero member
     j = 0
@@ -287,7 +295,7 @@ def eig_full(d, z, rho, opts=None, threads=1):
         g = j
         while g + 1 < n and d[g + 1] == d[j]:
             g += 1
-        members = [p for p in range(j, g + 1) if zr[p] != 0.0]
+        members = [p for p in range(j, g + 1) if not zero_weight(zr[p])]
         if len(members) > 1:
             a = members[0]
             for p in members[1:]:
@@ -331,7 +339,7 @@ def eig_hermitian(d, z, rho, opts=None, threads=1, ks=None):
     phi = np.ones(z.size, dtype=np.complex128)
     nz = a > 0
     phi[nz] = z.real[nz] / a[nz] + 1j * (z.imag[nz] / a[nz])   # each part correctly rounded
-    irreducible = rho > 0 and np.all(nz) and np.all(d[:-1] > d[1:])
+    irreducible = rho > 0 and not np.any(zero_weight(a)) and np.all(d[:-1] > d[1:])
     if irreducible:
         r = eig_all(d, a, rho, opts, ks=ks, threads=threads)
     else:
@@ -359,7 +367,10 @@ def tridiag_dc(a, b, threads=1):
     rho = |b_{m-1}|, v = e_{m-1} + sign(b_{m-1}) e_m, and T1, T2 with |b_{m-1}| taken off
     their corner diagonal entries; so a single element i carries a_i - |b_{i-1}| - |b_i|.
     Merge: with T1 = Q1 L1 Q1^T and T2 = Q2 L2 Q2^T, T = Q (L + rho u u^T) Q^T,
-    Q = diag(Q1, Q2), u = Q^T v = (last row of Q1, sign * first row of Q2).  The poles
+    Q = diag(Q1, Q2), u = Q^T v = (last row of Q1, sign * first row of Q2).  Weights with
+    rho |u_j| <= 8 u ||T|| (u = 2^-53, ||T|| the largest Gershgorin row sum) are set to zero,
+    the usual backward-stable deflation of divide and conquer; beyond the exact deflation
+    of Sec. 1 it keeps the squares u_j^2 in the normal range of binary64.  The poles
     L1, L2 are merged into one non-increasing order (stable: T1's entry first on ties),
     the DPR1 problem is solved by ``eig_full`` (Algorithm 1 with the paper's deflation),
     and the eigenvectors of T are Q times the DPR1 eigenvectors mapped back to the
@@ -374,6 +385,9 @@ def tridiag_dc(a, b, threads=1):
     bl = np.concatenate([[0.0], np.abs(b)])
     br = np.concatenate([np.abs(b), [0.0]])
     leaf = (a - bl) - br
+    # deflation tolerance of every merge: 8 u ||T||, u = 2^-53, ||T|| bounded by the largest
+    # Gershgorin row sum (|a_i| + |b_{i-1}|) + |b_i|
+    tol = np.ldexp(np.max((np.abs(a) + bl) + br), -50)
     T = 0
     while (1 << T) < n:
         T += 1
@@ -405,6 +419,9 @@ def tridiag_dc(a, b, threads=1):
             sgn = 1.0 if beta >= 0 else -1.0
             vals = lam[lo:hi]
             u = np.concatenate([Q1[:, n1 - 1], sgn * Q2[:, 0]])
+            # a weight with rho |u_j| <= tol is deflated (its pole is an eigenvalue of T to
+            # within the backward error 8 u ||T|| of the whole method)
+            u[rho * np.abs(u) <= tol] = 0.0
             order = np.argsort(-vals, kind="stable")
             r = eig_full(vals[order], u[order], rho, threads=threads)
             pos = np.empty(N, dtype=np.int64)

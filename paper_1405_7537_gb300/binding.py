@@ -71,6 +71,8 @@ def lib():
         L.dpr1_batched_workspace_size.restype = ctypes.c_size_t
         L.dpr1_hermitian_workspace_size.argtypes = [_i64]
         L.dpr1_hermitian_workspace_size.restype = ctypes.c_size_t
+        L.dpr1_tridiag_workspace_size.argtypes = [_i64]
+        L.dpr1_tridiag_workspace_size.restype = ctypes.c_size_t
         for name, argt in _extra_signatures().items():
             if hasattr(L, name):
                 getattr(L, name).argtypes = argt
@@ -87,6 +89,7 @@ def _extra_signatures():
                               ctypes.c_size_t, ctypes.POINTER(Options), _vp],
         "dpr1_eig_hermitian": [_i64, _vp, _vp, _dbl, _vp, _vp, _i64, _vp, _vp, _vp, _vp, ctypes.c_size_t,
                                ctypes.POINTER(Options), _vp],
+        "dpr1_tridiag_eig": [_i64, _vp, _vp, _vp, _vp, _i64, _vp, ctypes.c_size_t, ctypes.POINTER(Options), _vp],
     }
 
 
@@ -196,6 +199,33 @@ def eig_hermitian(d, z, rho, want_vectors=True, options=None, ws=None, check=Tru
     if check and n > 0:
         _check(stream_status(ws, stream), "dpr1_eig_hermitian (device)")
     return out
+
+
+def tridiag_workspace(n, device="cuda"):
+    return torch.empty(max(int(lib().dpr1_tridiag_workspace_size(int(n))), 256), dtype=torch.uint8, device=device)
+
+
+def eigh_tridiagonal(a, b, want_vectors=True, options=None, ws=None, check=True, stream=None):
+    """All eigenpairs of the symmetric tridiagonal matrix with diagonal a and off-diagonal b
+    (divide and conquer with DPR1 merges).  Returns (lam non-increasing, Qt) with Qt[k] the
+    k-th eigenvector (None when want_vectors is False)."""
+    dev = a.device if isinstance(a, torch.Tensor) and a.is_cuda else torch.device("cuda", torch.cuda.current_device())
+    a = _dev_f64(a, dev)
+    n = a.numel()
+    b = _dev_f64(b, dev) if n > 1 else None
+    if n > 1 and b.numel() != n - 1:
+        raise ValueError("b must have n - 1 entries")
+    lam = torch.empty(n, dtype=torch.float64, device=dev)
+    Qt = torch.empty((n, n), dtype=torch.float64, device=dev) if want_vectors else None
+    if ws is None:
+        ws = tridiag_workspace(n, dev)
+    o = options if options is not None else default_options()
+    code = lib().dpr1_tridiag_eig(n, _ptr(a), _ptr(b), _ptr(lam), _ptr(Qt), n if Qt is not None else 0, _ptr(ws),
+                                  ws.numel(), ctypes.byref(o), _stream(stream))
+    _check(code, "dpr1_tridiag_eig")
+    if check and n > 0:
+        _check(stream_status(ws, stream), "dpr1_tridiag_eig (device)")
+    return lam, Qt
 
 
 def probe_reciprocal(x):

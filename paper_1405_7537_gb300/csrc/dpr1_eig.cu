@@ -169,7 +169,7 @@ __global__ void k_scan(Prob pb, Ws w) {
       if (dj < dn) bits |= ST_UNSORTED;
       if (dj == dn) pbits |= PT_DEFLATE;
     }
-    if (zj == 0.0) pbits |= PT_DEFLATE;
+    if (zero_weight(zj)) pbits |= PT_DEFLATE;
     if (dj == 0.0) pbits |= PT_ZERO_POLE;
     if (pbits) atomicOr(&w.pst[p], pbits);
     w.dr[g] = dj;
@@ -208,7 +208,7 @@ __global__ void k_deflate(Prob pb, Ws w) {
       double r = 0.0;
       for (int q = j; q <= e; q++) {
         w.gst[base + q] = j;
-        if (z[q] == 0.0) {
+        if (zero_weight(z[q])) {
           w.src[base + q] = -1; w.coef[base + q] = 0.0; w.rprev[base + q] = 0.0; w.rcur[base + q] = 0.0;
           w.dlist[base + nd++] = q;
           continue;
@@ -222,7 +222,7 @@ __global__ void k_deflate(Prob pb, Ws w) {
       if (first >= 0) {
         double zs = (z[first] > 0.0) ? r : -r;
         for (int q = j; q <= e; q++) {
-          if (z[q] == 0.0) continue;
+          if (zero_weight(z[q])) continue;
           w.src[base + q] = nr;
           w.coef[base + q] = z[q] / zs;
         }
@@ -679,11 +679,11 @@ __global__ void k_defl_rows(Prob pb, Ws w) {
     const double rc = w.rcur[base + q], rp = w.rprev[base + q];
     for (int j = lane; j < nfull; j += 32) {
       double v = 0.0;
-      if (zq == 0.0) {
+      if (zero_weight(zq)) {
         v = (j == q) ? 1.0 : 0.0;
       } else if (j == q) {
         v = rp / rc;
-      } else if (j >= g0 && j < q && zfull[j] != 0.0) {
+      } else if (j >= g0 && j < q && !zero_weight(zfull[j])) {
         v = -(zq / rc) * (zfull[j] / rp);
       }
       vr[j] = v;

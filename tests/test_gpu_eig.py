@@ -129,3 +129,20 @@ def test_deflation(B):
         for k in simple:
             s = np.sign(np.dot(g["Vt"][k], r["Vt"][k]))
             assert np.max(np.abs(s * g["Vt"][k] - r["Vt"][k])) <= 1e-14
+
+
+def test_tiny_weights_are_zero_weights(B):
+    """Weights whose squares are not normal binary64 numbers (|z_j| < 2^-511) deflate like
+    zeros; the rest of the spectrum matches the oracle, and A V = V diag(lambda)."""
+    d, z, rho = W.uniform(64, 3)
+    z = z.copy()
+    z[[5, 20, 40]] = [1e-170, 1e-200, 1e-155]
+    z[[6, 30]] = [3e-162, -2e-158]
+    g = run_gpu(B, d, z, rho)
+    r = oracle.eig_full(d, z, rho)
+    n = d.size
+    assert np.max(np.abs(g["lam"] - r["lam"]) / np.abs(r["lam"])) <= tol(n)
+    A = np.diag(d) + rho * np.outer(z, z)
+    V = g["Vt"].T
+    assert np.max(np.abs(A @ V - V * g["lam"])) <= 1e-14
+    assert np.max(np.abs(V.T @ V - np.eye(n))) <= 1e-14

@@ -22,7 +22,7 @@ def B():
 
 
 def cu(a):
-    return torch.tensor(np.ascontiguousarray(a), device="cuda")
+    return torch.tensor(np.array(a, copy=True, order="C"), device="cuda")
 
 
 def run(B, d, z, rho, **opt):

@@ -457,3 +457,23 @@ def test_backward_against_binary128_adjoint(gen, n, seed):
     assert np.linalg.norm(od - qd) <= 1e-10 * np.linalg.norm(qd)
     assert np.linalg.norm(oz - qz) <= 1e-10 * np.linalg.norm(qz)
     assert abs(orho - qrho) <= 1e-10 * abs(qrho)
+
+
+def test_tiny_weights_are_zero_weights():
+    """A weight whose square is not a normal binary64 number is deflated (the secular
+    function cannot see it): the remaining eigenvalues equal the binary128 eigenvalues of
+    the reduced problem, the deflated ones are their poles, and A V = V diag(lambda)."""
+    d, z, rho = W.uniform(64, 3)
+    z = z.copy()
+    z[[5, 20, 40]] = [1e-170, 1e-200, 1e-155]
+    z[[6, 30]] = [3e-162, -2e-158]
+    r = oracle.eig_full(d, z, rho)
+    A = np.diag(d) + rho * np.outer(z, z)
+    V = r["Vt"].T
+    assert np.max(np.abs(A @ V - V * r["lam"])) <= 1e-14
+    assert np.max(np.abs(V.T @ V - np.eye(64))) <= 1e-14
+    keep = ~oracle.zero_weight(z)
+    assert keep.sum() == 59 and oracle.zero_weight(2.0 ** -512) and not oracle.zero_weight(2.0 ** -511)
+    q = oracle.quad_all(d[keep], z[keep], rho)
+    lk = np.sort(np.concatenate([q["hi"] + q["lo"], d[~keep]]))[::-1]
+    assert np.max(np.abs(r["lam"] - lk) / np.abs(lk)) <= 16 * 64 * 2.0 ** -53
