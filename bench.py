@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--extras", default="fwd_bwd,batched,accel,hermitian,tridiag",
                     help="comma list of extra measurements: fwd_bwd, batched, accel, hermitian, tridiag")
     ap.add_argument("--large", action="store_true", help="also time the n=32768 forward+backward workload")
+    ap.add_argument("--only", choices=["tridiag", "hermitian", "fwd_bwd"], default=None,
+                    help="run one extra measurement alone at size --n (a small case for profiling) and print it")
     ap.add_argument("--zero-finder", type=int, choices=[0, 1], default=0,
                     help="0: bisection (the method as stated, default); 1: the accelerated bracketed solve")
     return ap.parse_args()
@@ -433,17 +435,20 @@ def bench_tridiag(B, dev, n, seed, steps):
             raise B.DPR1Error(st, "tridiag")
         t = statistics.mean(ms)
         res[name] = {"value": n / (t * 1e-3), "ms_per_step": t}
-    Td = torch.diag(at) + torch.diag(bt, 1) + torch.diag(bt, -1)
-    torch.linalg.eigh(Td)
-    torch.cuda.synchronize()
-    e0, e1 = _events()
-    e0.record()
-    torch.linalg.eigh(Td)
-    e1.record()
-    e1.synchronize()
-    ref_ms = e0.elapsed_time(e1)
-    res["cusolver_dense_eigh"] = {"value": n / (ref_ms * 1e-3), "ms_per_step": ref_ms,
-                                  "note": "torch.linalg.eigh on the dense n x n matrix (library, context only)"}
+    try:
+        Td = torch.diag(at) + torch.diag(bt, 1) + torch.diag(bt, -1)
+        torch.linalg.eigh(Td)
+        torch.cuda.synchronize()
+        e0, e1 = _events()
+        e0.record()
+        torch.linalg.eigh(Td)
+        e1.record()
+        e1.synchronize()
+        ref_ms = e0.elapsed_time(e1)
+        res["cusolver_dense_eigh"] = {"value": n / (ref_ms * 1e-3), "ms_per_step": ref_ms,
+                                      "note": "torch.linalg.eigh on the dense n x n matrix (library, context only)"}
+    except RuntimeError as e:            # torch's solver library may not load (e.g. under a profiler)
+        res["cusolver_dense_eigh"] = {"unavailable": str(e).splitlines()[0]}
     return res
 
 
@@ -659,10 +664,30 @@ def run_ours(args):
     return 0
 
 
+def run_only(args):
+    """One extra measurement alone (used for small ncu captures of its kernels)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1405_7537_gb300 import binding as B
+    dev = torch.device("cuda", 0)
+    B.lib()
+    if args.only == "tridiag":
+        res = bench_tridiag(B, dev, args.n, 5, args.steps)
+    elif args.only == "hermitian":
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        res = bench_hermitian(B, dev, args.n, SEED, args.steps, flush)
+    else:
+        res = bench_fwd_bwd(B, dev, args.n, 2, args.steps, True)
+    print(json.dumps({"only": args.only, "n": args.n, args.only: res}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_only(args)
     return run_ours(args)
 
 
