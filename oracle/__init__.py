@@ -72,6 +72,9 @@ def lib():
         for name in ("oracle_dd_add", "oracle_dd_mul", "oracle_dd_div"):
             getattr(L, name).argtypes = [ctypes.c_double] * 4 + [_dp]
         L.oracle_default_opts.argtypes = [ctypes.POINTER(Opts)]
+        L.oracle_arroweig.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp, _dp,
+                                      _ip, _ip]
+        L.quad_arrow_eigpair.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp]
         _LIB = L
     return _LIB
 
@@ -434,3 +437,61 @@ def tridiag_dc(a, b, threads=1):
             new[i] = Qt
         lam, blocks = lam_t, new
     return lam, blocks[0]
+
+
+def _split_run(run, m, threads):
+    if threads <= 1 or m < 2:
+        run(range(m))
+    else:
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(run, np.array_split(np.arange(m), threads)))
+
+
+def arrow_eig_all(d, z, alpha, ks=None, threads=1):
+    """Eigenpairs of the arrowhead [diag(d) z; z^T alpha] (order n + 1, irreducible) by the
+    steps of Algorithm 1 on its shifted inverse (``oracle_arroweig``): dict(lam, sigma, mu,
+    shift, Vt) with rows of length n + 1, for k in ks (default 0..n)."""
+    d, z = _f64(d), _f64(z)
+    n = d.size
+    ks = np.arange(n + 1) if ks is None else np.asarray(ks, dtype=np.int64)
+    m = ks.size
+    out = dict(lam=np.empty(m), sigma=np.empty(m), mu=np.empty(m), shift=np.empty(m, dtype=np.int32),
+               Vt=np.empty((m, n + 1)))
+
+    def run(idx):
+        v = np.empty(n + 1)
+        lam, sig, mu = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        sh, st = ctypes.c_int(), ctypes.c_int()
+        for p in idx:
+            rc = lib().oracle_arroweig(n, _ptr(d), _ptr(z), float(alpha), int(ks[p]), ctypes.byref(lam), _ptr(v),
+                                       ctypes.byref(sig), ctypes.byref(mu), ctypes.byref(sh), ctypes.byref(st))
+            if rc:
+                raise ValueError("oracle_arroweig failed with code %d" % rc)
+            out["lam"][p], out["sigma"][p], out["mu"][p], out["shift"][p] = lam.value, sig.value, mu.value, sh.value
+            out["Vt"][p] = v
+
+    _split_run(run, m, threads)
+    return out
+
+
+def quad_arrow_all(d, z, alpha, ks=None, threads=1):
+    """binary128 reference for the arrowhead: dict(hi, lo, Vt), lambda_k = hi + lo."""
+    d, z = _f64(d), _f64(z)
+    n = d.size
+    ks = np.arange(n + 1) if ks is None else np.asarray(ks, dtype=np.int64)
+    m = ks.size
+    out = dict(hi=np.empty(m), lo=np.empty(m), Vt=np.empty((m, n + 1)))
+
+    def run(idx):
+        v = np.empty(n + 1)
+        hi, lo = ctypes.c_double(), ctypes.c_double()
+        for p in idx:
+            rc = lib().quad_arrow_eigpair(n, _ptr(d), _ptr(z), float(alpha), int(ks[p]), ctypes.byref(hi),
+                                          ctypes.byref(lo), _ptr(v))
+            if rc < 0:
+                raise ValueError("quad_arrow_eigpair failed")
+            out["hi"][p], out["lo"][p] = hi.value, lo.value
+            out["Vt"][p] = v
+
+    _split_run(run, m, threads)
+    return out

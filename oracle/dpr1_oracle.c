@@ -641,3 +641,114 @@ int oracle_backward_rows(int n, const double* d, const double* z, double rho, in
   free(s); free(v); free(g);
   return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Real symmetric arrowhead matrices A = [D z; z^T alpha] of order n + 1      */
+/* (the companion problem the paper relates its method to, Sec. 1).  The same */
+/* steps as Algorithm 1: shift to the nearer pole d_i, form the inverse of    */
+/* A - d_i I, which is again an arrowhead, bisect its secular equation for    */
+/* the extreme eigenvalue nu, lambda = d_i + 1/nu, v = [x; -1] / ||.||,       */
+/* x = (D - lambda I)^{-1} z.  Irreducible input only (d strictly decreasing, */
+/* no zero weight); no remedies.                                              */
+/*                                                                            */
+/* (A - d_i I)^{-1}: with Delta_j = d_j - d_i (j != i) it has the diagonal    */
+/* delta_j = 1/Delta_j, b at position i and 0 at position n, and the border   */
+/* (row i) w_j = -zeta_j / (zeta_i Delta_j), 1/zeta_i at position n, where    */
+/*   b = (1/zeta_i^2) (sum_{j != i} zeta_j^2 / Delta_j - (alpha - d_i))       */
+/* (the DPR1 corner of Eq. (b_ob) with 1/rho replaced by d_i - alpha).  Its   */
+/* secular function has one more pole, at 0, of weight 1/zeta_i^2:            */
+/*   g(nu) = b - nu - sum_{j != i} w_j^2/(delta_j - nu) + (1/zeta_i^2)/nu.    */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int n, i;
+  const double* delta;
+  const double* w;
+  double b, wz2;       /* corner and 1/zeta_i^2 */
+} o_ah_ctx;
+
+static double o_g_ah(const void* vctx, double nu) {
+  const o_ah_ctx* c = (const o_ah_ctx*)vctx;
+  double s = 0.0;
+  for (int j = 0; j < c->n; j++) {
+    if (j == c->i) continue;
+    s += c->w[j] * c->w[j] / (c->delta[j] - nu);
+  }
+  return ((c->b - nu) - s) + c->wz2 / nu;
+}
+
+/* eigenvalue k (0-based, 0..n) of the arrowhead; v has n + 1 entries */
+int oracle_arroweig(int n, const double* d, const double* z, double alpha, int k, double* lambda_out,
+                    double* v, double* sigma_out, double* mu_out, int* shift_out, int* steps_out) {
+  if (n < 1 || k < 0 || k > n) return 1;
+  for (int j = 0; j < n; j++) {
+    if (z[j] == 0.0 || (j + 1 < n && !(d[j] > d[j + 1]))) return 3;   /* reducible */
+  }
+  double* delta = (double*)malloc(sizeof(double) * n);
+  double* w = (double*)malloc(sizeof(double) * n);
+  if (!delta || !w) { free(delta); free(w); return 2; }
+  /* shift: lambda_0 > d_0 (pole 0), lambda_n < d_{n-1} (pole n-1); otherwise
+     lambda_k lies in (d_k, d_{k-1}) and f(lambda) = alpha - lambda - sum z_j^2/(d_j - lambda),
+     decreasing there, is evaluated at the midpoint: f < 0 puts lambda in the lower half */
+  int i, side;
+  if (k == 0) { i = 0; side = 1; }
+  else if (k == n) { i = n - 1; side = -1; }
+  else {
+    double tau = (d[k - 1] - d[k]) / 2.0;
+    double s = 0.0;
+    for (int j = 0; j < n; j++) s += z[j] * z[j] / ((d[j] - d[k]) - tau);
+    double F = (alpha - d[k]) - tau - s;
+    if (F < 0.0) { i = k; side = 1; } else { i = k - 1; side = -1; }
+  }
+  /* the arrowhead inverse of A - d_i I */
+  odd_t acc = o_two_sum(d[i], -alpha);
+  for (int j = 0; j < n; j++) {
+    if (j == i) { delta[j] = 0.0; w[j] = 0.0; continue; }
+    delta[j] = 1.0 / (d[j] - d[i]);
+    w[j] = -(delta[j] * z[j]) / z[i];
+    acc = o_add(acc, o_div(o_two_prod(z[j], z[j]), o_two_sum(d[j], -d[i])));
+  }
+  odd_t bb = o_div(acc, o_two_prod(z[i], z[i]));
+  double b = bb.hi + bb.lo;
+  double wz = 1.0 / z[i];
+  o_ah_ctx c = {n, i, delta, w, b, wz * wz};
+  /* Weyl bracket of the extreme eigenvalue of the order-(n+1) arrowhead (diagonal delta,
+     b, 0; border w, 1/zeta_i): within ||border|| of max(b, max delta, 0) (rightmost) or
+     min(b, min delta, 0) (leftmost) */
+  double wn2 = wz * wz, dmax = 0.0, dmin = 0.0;
+  for (int j = 0; j < n; j++) {
+    if (j == i) continue;
+    wn2 += w[j] * w[j];
+    if (delta[j] > dmax) dmax = delta[j];
+    if (delta[j] < dmin) dmin = delta[j];
+  }
+  double wn = sqrt(wn2);
+  double nu;
+  int steps = 0;
+  if (side > 0) {
+    double lo = b > dmax ? b : dmax;
+    nu = o_bisect(o_g_ah, &c, 1.0, lo, lo + wn, +1, &steps);
+  } else {
+    double up = b < dmin ? b : dmin;
+    nu = o_bisect(o_g_ah, &c, -1.0, -up, -up + wn, -1, &steps);
+  }
+  double mu = 1.0 / nu;
+  /* eigenvector [x; -1] / ||.||, x_j = zeta_j / ((d_j - d_i) - mu), scaled 2-norm */
+  double m = 1.0;
+  for (int j = 0; j < n; j++) {
+    double x = (j == i) ? -z[i] / mu : z[j] / ((d[j] - d[i]) - mu);
+    v[j] = x;
+    if (fabs(x) > m) m = fabs(x);
+  }
+  v[n] = -1.0;
+  double s = 0.0;
+  for (int j = 0; j <= n; j++) { double t = v[j] / m; s += t * t; }
+  double r = sqrt(s);
+  for (int j = 0; j <= n; j++) v[j] = (v[j] / m) / r;
+  *lambda_out = d[i] + mu;
+  if (sigma_out) *sigma_out = d[i];
+  if (mu_out) *mu_out = mu;
+  if (shift_out) *shift_out = i;
+  if (steps_out) *steps_out = steps;
+  free(delta); free(w);
+  return 0;
+}

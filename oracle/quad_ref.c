@@ -192,3 +192,77 @@ int quad_backward(int n, const double* d, const double* z, double rho, int m, co
 double quad_secular(int n, const double* d, const double* z, double rho, double lam_hi, double lam_lo) {
   return (double)q_f(n, d, z, rho, (q_t)lam_hi + (q_t)lam_lo);
 }
+
+/*
+ * Arrowhead A = [D z; z^T alpha] of order n + 1 (irreducible): lambda_k (k = 0..n) is the zero
+ * of f(lambda) = alpha - lambda - sum_j zeta_j^2 / (d_j - lambda), strictly decreasing between
+ * consecutive poles, in (d_0, inf) for k = 0, (d_k, d_{k-1}) for 0 < k < n and (-inf, d_{n-1})
+ * for k = n; v_k = [x; -1] / ||.||, x = (D - lambda_k I)^{-1} z.  Bisection in binary128 on
+ * mu = lambda - d_i, with the pole differences d_j - d_i formed in binary128, i the nearer end
+ * pole of the interval (from the sign of f at its midpoint; the exterior intervals use the
+ * pole they touch).  Returns the number of steps, or -1.
+ */
+static q_t q_fa(int n, const q_t* D, const double* z, q_t a, q_t mu) {
+  q_t s = 0;
+  for (int j = 0; j < n; j++) {
+    q_t zj = (q_t)z[j];
+    s += zj * zj / (D[j] - mu);
+  }
+  return (a - mu) - s;
+}
+
+int quad_arrow_eigpair(int n, const double* d, const double* z, double alpha, int k,
+                       double* lam_hi, double* lam_lo, double* v) {
+  if (n < 1 || k < 0 || k > n) return -1;
+  q_t* D = (q_t*)malloc(sizeof(q_t) * n);
+  if (!D) return -1;
+  q_t zn = 0;
+  for (int j = 0; j < n; j++) zn += (q_t)z[j] * (q_t)z[j];
+  zn = q_sqrt(zn) + 1;
+  int i;
+  q_t lo, hi;
+  if (k == 0 || k == n) {
+    i = (k == 0) ? 0 : n - 1;
+    q_t gap = (k == 0) ? (q_t)alpha - (q_t)d[0] : (q_t)d[n - 1] - (q_t)alpha;
+    q_t U = (gap > 0 ? gap : 0) + zn;          /* Weyl: |lambda - d_i| <= max(0, gap) + ||z|| */
+    if (k == 0) { lo = 0; hi = U; } else { lo = -U; hi = 0; }
+  } else {
+    q_t tau = ((q_t)d[k - 1] - (q_t)d[k]) / 2;
+    for (int j = 0; j < n; j++) D[j] = (q_t)d[j] - (q_t)d[k];
+    q_t fm = q_fa(n, D, z, (q_t)alpha - (q_t)d[k], tau);
+    if (fm < 0) { i = k; lo = 0; hi = tau; }
+    else { i = k - 1; lo = -tau; hi = 0; }
+  }
+  for (int j = 0; j < n; j++) D[j] = (q_t)d[j] - (q_t)d[i];
+  q_t a = (q_t)alpha - (q_t)d[i];
+  int steps = 0;
+  /* f decreasing in mu on (lo, hi): f > 0 below the root */
+  for (; steps < 20000; steps++) {
+    q_t mid = lo + (hi - lo) / 2;
+    if (!(mid > lo && mid < hi)) break;
+    if (mid == 0) { /* never evaluate the pole itself */
+      mid = (lo == 0) ? hi / 2 : lo / 2;
+      if (!(mid > lo && mid < hi)) break;
+    }
+    q_t f = q_fa(n, D, z, a, mid);
+    if (f > 0) lo = mid; else hi = mid;
+  }
+  q_t mu = lo + (hi - lo) / 2;
+  q_t lam = (q_t)d[i] + mu;
+  double h = (double)lam;
+  *lam_hi = h;
+  *lam_lo = (double)(lam - (q_t)h);
+  if (v) {
+    q_t nrm = 1;
+    q_t* x = (q_t*)malloc(sizeof(q_t) * n);
+    if (!x) { free(D); return -1; }
+    for (int j = 0; j < n; j++) { x[j] = (q_t)z[j] / (D[j] - mu); nrm += x[j] * x[j]; }
+    /* scale-safe square root: nrm >= 1 here */
+    q_t r = q_sqrt(nrm);
+    for (int j = 0; j < n; j++) v[j] = (double)(x[j] / r);
+    v[n] = (double)(-1 / r);
+    free(x);
+  }
+  free(D);
+  return steps;
+}

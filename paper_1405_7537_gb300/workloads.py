@@ -183,3 +183,11 @@ def glued_wilkinson(n=21, copies=4, glue=1e-10):
     a = np.tile(a0, copies)
     b = np.concatenate([np.concatenate([b0, [glue]]) for _ in range(copies)])[:-1]
     return a, b
+
+
+def arrowhead(n=16384, seed=6):
+    """A real symmetric arrowhead [diag(d) z; z^T alpha] of order n + 1: d ~ U(-1, 1) sorted
+    decreasing and distinct, z ~ U(-1, 1) redrawn while |z| <= 1e-3, alpha ~ U(-1, 1)."""
+    d, z, _ = uniform(n, seed)
+    rng = np.random.default_rng(seed + 2000)
+    return d, z, float(rng.uniform(-1.0, 1.0))
