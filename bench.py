@@ -64,10 +64,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-vs-loop and forward+backward measurements")
-    ap.add_argument("--extras", default="fwd_bwd,batched,accel,hermitian,tridiag",
-                    help="comma list of extra measurements: fwd_bwd, batched, accel, hermitian, tridiag")
+    ap.add_argument("--extras", default="fwd_bwd,batched,accel,hermitian,tridiag,arrow",
+                    help="comma list of extra measurements: fwd_bwd, batched, accel, hermitian, tridiag, arrow")
     ap.add_argument("--large", action="store_true", help="also time the n=32768 forward+backward workload")
-    ap.add_argument("--only", choices=["tridiag", "hermitian", "fwd_bwd"], default=None,
+    ap.add_argument("--only", choices=["tridiag", "hermitian", "fwd_bwd", "arrow"], default=None,
                     help="run one extra measurement alone at size --n (a small case for profiling) and print it")
     ap.add_argument("--zero-finder", type=int, choices=[0, 1], default=0,
                     help="0: bisection (the method as stated, default); 1: the accelerated bracketed solve")
@@ -452,6 +452,38 @@ def bench_tridiag(B, dev, n, seed, steps):
     return res
 
 
+def bench_arrow(B, dev, n, seed, steps, flush):
+    """The real symmetric arrowhead [D z; z^T alpha] of order n + 1 (d, z ~ U(-1, 1)): all
+    eigenvalues and the (n+1)^2 eigenvector matrix, both zero finders."""
+    import torch
+    from paper_1405_7537_gb300 import workloads as W
+    d, z, alpha = W.arrowhead(n, seed)
+    dt = torch.tensor(np.array(d), device=dev)
+    zt = torch.tensor(np.array(z), device=dev)
+    ws = B.arrow_workspace(n, dev)
+    res = {"workload": "arrowhead, n=%d poles (order n+1), d, z ~ U(-1, 1), alpha ~ U(-1, 1), seed %d" % (n, seed),
+           "unit": "eigenpairs/s"}
+    for name, zf in (("bisection", 0), ("accelerated", 1)):
+        o = B.default_options(zero_finder=zf)
+        B.eig_arrowhead(dt, zt, alpha, options=o, ws=ws)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(max(1, steps)):
+            flush.zero_()
+            e0, e1 = _events()
+            e0.record()
+            B.eig_arrowhead(dt, zt, alpha, options=o, ws=ws, check=False)
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        st = B.stream_status(ws)
+        if st != 0:
+            raise B.DPR1Error(st, "arrow")
+        t = statistics.mean(ms)
+        res[name] = {"value": (n + 1) / (t * 1e-3), "ms_per_step": t}
+    return res
+
+
 # ------------------------------------------------------------------ our arm
 def kernel_source_hash(files):
     h = hashlib.sha256()
@@ -631,6 +663,8 @@ def run_ours(args):
             extras["fwd_bwd_large"] = bench_fwd_bwd(B, dev, 32768, 4, 1, False)
     if "batched" in which:
         extras["batched"] = bench_batched(B, dev, 2)
+    if "arrow" in which:
+        extras["arrow"] = bench_arrow(B, dev, n, 6, 2, flush)
     if "tridiag" in which:
         extras["tridiag"] = bench_tridiag(B, dev, 4096, 5, 3)
     if "hermitian" in which:
@@ -676,6 +710,9 @@ def run_only(args):
     elif args.only == "hermitian":
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
         res = bench_hermitian(B, dev, args.n, SEED, args.steps, flush)
+    elif args.only == "arrow":
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        res = bench_arrow(B, dev, args.n, 6, args.steps, flush)
     else:
         res = bench_fwd_bwd(B, dev, args.n, 2, args.steps, True)
     print(json.dumps({"only": args.only, "n": args.n, args.only: res}), flush=True)

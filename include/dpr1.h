@@ -240,6 +240,40 @@ DPR1_API dpr1_status dpr1_tridiag_eig(int64_t n, const double* a, const double* 
                                       const dpr1_options* opt, dpr1_stream_t stream);
 
 /*
+ * Bytes of workspace for dpr1_arrow_eig with n poles (256-byte aligned, uninitialised).
+ */
+DPR1_API size_t dpr1_arrow_workspace_size(int64_t n);
+
+/*
+ * dpr1_arrow_eig -- all n + 1 eigenpairs of the real symmetric arrowhead matrix
+ * A = [D z; z^T alpha], D = diag(d), the companion problem the paper relates its method to
+ * (Sec. 1), by the steps of Algorithm 1 on the shifted inverse: (A - d_i I)^{-1} is again an
+ * arrowhead, with the corner b = (1/zeta_i^2)(sum_{j != i} zeta_j^2/(d_j - d_i) - (alpha - d_i))
+ * formed in double-double and one more pole, at 0, of weight 1/zeta_i^2; lambda = d_i + 1/nu
+ * for its extreme eigenvalue nu (bisection, or the accelerated solve with opt->zero_finder),
+ * v = [x; -1] / ||.||, x = (D - lambda I)^{-1} z.  The K_nu remedies of dpr1_eig are not
+ * applied to this problem.
+ *
+ *   n          number of poles (n >= 0; the matrix has order n + 1)
+ *   d, z       device double[n]: d strictly decreasing, every |z_j| >= 2^-511 (the matrix is
+ *              irreducible; deflate equal poles and zero weights before the call)
+ *   alpha      the corner entry
+ *   lambda     device double[n+1], out: eigenvalues, non-increasing; they interlace d
+ *   Vt         device double[(n+1)*ldv] or NULL, out: row k = v_k (n + 1 entries, ldv >= n + 1)
+ *   sigma, mu  device double[n+1] or NULL, out: lambda_k = sigma_k + mu_k, sigma_k the pole
+ *   xnorm      device double[n+1] or NULL, out: ||[x; -1]||
+ *   workspace  dpr1_arrow_workspace_size(n) bytes, 256-byte aligned
+ * Errors: DPR1_ERR_ARG, DPR1_ERR_WORKSPACE, DPR1_ERR_CUDA synchronously; through
+ * dpr1_stream_status: DPR1_ERR_ARG (equal poles or a zero weight), DPR1_ERR_UNSORTED,
+ * DPR1_ERR_NONFINITE, DPR1_ERR_NOT_CONVERGED.
+ */
+DPR1_API dpr1_status dpr1_arrow_eig(int64_t n, const double* d, const double* z, double alpha,
+                                    double* lambda, double* Vt, int64_t ldv,
+                                    double* sigma, double* mu, double* xnorm,
+                                    void* workspace, size_t workspace_bytes,
+                                    const dpr1_options* opt, dpr1_stream_t stream);
+
+/*
  * Synchronises `stream` and returns the status the device recorded in `workspace`
  * during the last call that used it (DPR1_OK if none), then clears it.
  */

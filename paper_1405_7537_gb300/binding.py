@@ -73,6 +73,8 @@ def lib():
         L.dpr1_hermitian_workspace_size.restype = ctypes.c_size_t
         L.dpr1_tridiag_workspace_size.argtypes = [_i64]
         L.dpr1_tridiag_workspace_size.restype = ctypes.c_size_t
+        L.dpr1_arrow_workspace_size.argtypes = [_i64]
+        L.dpr1_arrow_workspace_size.restype = ctypes.c_size_t
         for name, argt in _extra_signatures().items():
             if hasattr(L, name):
                 getattr(L, name).argtypes = argt
@@ -90,6 +92,8 @@ def _extra_signatures():
         "dpr1_eig_hermitian": [_i64, _vp, _vp, _dbl, _vp, _vp, _i64, _vp, _vp, _vp, _vp, ctypes.c_size_t,
                                ctypes.POINTER(Options), _vp],
         "dpr1_tridiag_eig": [_i64, _vp, _vp, _vp, _vp, _i64, _vp, ctypes.c_size_t, ctypes.POINTER(Options), _vp],
+        "dpr1_arrow_eig": [_i64, _vp, _vp, _dbl, _vp, _vp, _i64, _vp, _vp, _vp, _vp, ctypes.c_size_t,
+                           ctypes.POINTER(Options), _vp],
     }
 
 
@@ -226,6 +230,35 @@ def eigh_tridiagonal(a, b, want_vectors=True, options=None, ws=None, check=True,
     if check and n > 0:
         _check(stream_status(ws, stream), "dpr1_tridiag_eig (device)")
     return lam, Qt
+
+
+def arrow_workspace(n, device="cuda"):
+    return torch.empty(max(int(lib().dpr1_arrow_workspace_size(int(n))), 256), dtype=torch.uint8, device=device)
+
+
+def eig_arrowhead(d, z, alpha, want_vectors=True, options=None, ws=None, check=True, stream=None):
+    """All n + 1 eigenpairs of the arrowhead [diag(d) z; z^T alpha] (d strictly decreasing, no
+    zero weight).  Returns dict(lam, Vt, sigma, mu, xnorm); Vt is (n+1) x (n+1), row k = v_k."""
+    dev = d.device if isinstance(d, torch.Tensor) and d.is_cuda else torch.device("cuda", torch.cuda.current_device())
+    d = _dev_f64(d, dev)
+    z = _dev_f64(z, dev)
+    n = d.numel()
+    if z.numel() != n:
+        raise ValueError("d and z must have the same length")
+    f64 = dict(dtype=torch.float64, device=dev)
+    out = dict(lam=torch.empty(n + 1, **f64), sigma=torch.empty(n + 1, **f64), mu=torch.empty(n + 1, **f64),
+               xnorm=torch.empty(n + 1, **f64), Vt=torch.empty((n + 1, n + 1), **f64) if want_vectors else None)
+    if ws is None:
+        ws = arrow_workspace(n, dev)
+    o = options if options is not None else default_options()
+    Vt = out["Vt"]
+    code = lib().dpr1_arrow_eig(n, _ptr(d), _ptr(z), float(alpha), _ptr(out["lam"]), _ptr(Vt),
+                                n + 1 if Vt is not None else 0, _ptr(out["sigma"]), _ptr(out["mu"]),
+                                _ptr(out["xnorm"]), _ptr(ws), ws.numel(), ctypes.byref(o), _stream(stream))
+    _check(code, "dpr1_arrow_eig")
+    if check:
+        _check(stream_status(ws, stream), "dpr1_arrow_eig (device)")
+    return out
 
 
 def probe_reciprocal(x):

@@ -1,0 +1,345 @@
+// dpr1_arrow.cu -- eigenpairs of a real symmetric arrowhead matrix A = [D z; z^T alpha] of
+// order n + 1 (D = diag(d), d strictly decreasing, no zero weight), the companion problem the
+// paper relates its method to (Sec. 1), by the steps of Algorithm 1 on the shifted inverse.
+//
+// The eigenvalues interlace the poles, lambda_0 > d_0 > lambda_1 > ... > d_{n-1} > lambda_n,
+// and are the zeros of f(lambda) = alpha - lambda - sum_j zeta_j^2 / (d_j - lambda), which
+// decreases between consecutive poles.  Eigenvalue k is computed at the nearer pole d_i of
+// its interval (lambda_0 at d_0, lambda_n at d_{n-1}; otherwise the sign of f at the
+// midpoint decides).  (A - d_i I)^{-1} is again an arrowhead: with Delta_j = d_j - d_i its
+// diagonal is 1/Delta_j (j != i), b at position i and 0 at position n; its border is
+// w_j = -zeta_j / (zeta_i Delta_j) and 1/zeta_i at position n, and
+//   b = (1/zeta_i^2) (sum_{j != i} zeta_j^2 / Delta_j - (alpha - d_i))
+// is the DPR1 corner of Eq. (b_ob) with 1/rho replaced by d_i - alpha (double-double).  Its
+// secular function is the DPR1 one plus a pole at 0 of weight 1/zeta_i^2,
+//   g(nu) = b - nu - (1/zeta_i^2) sum_{j != i} zeta_j^2 / (Delta_j (1 - nu Delta_j))
+//           + (1/zeta_i^2) / nu,
+// and lambda = d_i + 1/nu for its extreme eigenvalue nu (bisection or the accelerated solve).
+// The eigenvector is v = [x; -1] / ||.||, x_j = zeta_j / ((d_j - d_i) - mu).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "../../include/dpr1.h"
+#include "dpr1_device.cuh"
+#include "dpr1_internal.cuh"
+#include "dpr1_solve.cuh"
+
+namespace dpr1 {
+
+static size_t a256a(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct ArrowWs {
+  unsigned* status;              // word 0: status; words 8..: counters (as the DPR1 header)
+  unsigned* counters;
+  unsigned long long* queue;     // work counter of the solve kernel
+  double* zz;                    // zeta_j^2
+  double* sig;                   // pole of eigenvalue k
+  double* mu;
+  int* shift;
+};
+
+static size_t arrow_layout(int64_t n, ArrowWs* w, char* base) {
+  size_t nn = (size_t)(n > 0 ? n : 1) + 1;
+  size_t off = 0;
+  size_t o_h = off; off += 256;
+  size_t o_zz = off; off += a256a(8 * nn);
+  size_t o_s = off; off += a256a(8 * nn);
+  size_t o_m = off; off += a256a(8 * nn);
+  size_t o_sh = off; off += a256a(4 * nn);
+  if (w && base) {
+    w->status = (unsigned*)(base + o_h);
+    w->counters = (unsigned*)(base + o_h) + 8;
+    w->queue = (unsigned long long*)((unsigned*)(base + o_h) + 24);
+    w->zz = (double*)(base + o_zz);
+    w->sig = (double*)(base + o_s);
+    w->mu = (double*)(base + o_m);
+    w->shift = (int*)(base + o_sh);
+  }
+  return off;
+}
+
+constexpr unsigned ST_FATAL_A = ST_NONFINITE | ST_UNSORTED | ST_BADARG;
+
+// input checks (finite, strictly decreasing d, no zero weight) and zeta^2
+__global__ void k_arrow_check(int n, const double* __restrict__ d, const double* __restrict__ z, double alpha,
+                              double* __restrict__ zz, unsigned* __restrict__ status) {
+  unsigned bits = 0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const double dj = d[j], zj = z[j];
+    if (!isfinite(dj) || !isfinite(zj)) bits |= ST_NONFINITE;
+    if (j + 1 < n) {
+      if (dj < d[j + 1]) bits |= ST_UNSORTED;
+      else if (dj == d[j + 1]) bits |= ST_BADARG;       // equal poles: reducible
+    }
+    if (zero_weight(zj)) bits |= ST_BADARG;               // zero weight: reducible
+    zz[j] = __dmul_rn(zj, zj);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && !isfinite(alpha)) bits |= ST_NONFINITE;
+  bits = __reduce_or_sync(FULL, bits);
+  if ((threadIdx.x & 31) == 0 && bits) atomicOr(status, bits);
+}
+
+// Extreme eigenvalue nu of (A - d_i I)^{-1} on the side of eigenvalue k (rightmost when
+// i == k, leftmost when i == k - 1); [alo, ahi] an estimate of the bracket of |nu|.
+template <int L>
+__device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const double* __restrict__ z,
+                                       const double* __restrict__ zz, int n, double alpha, int k, int i, double alo,
+                                       double ahi, int cap, bool fast, int lane, unsigned gm) {
+  PoleResult r;
+  double sq;
+  const double di = d[i];
+  dd acc = dd_pole_sum<L>(d, z, n, i, di, lane, gm, &sq);
+  dd B = dd_add(two_sum(di, -alpha), acc);
+  dd Zi = two_prod(z[i], z[i]);
+  const double b = dd_to_double(dd_div(B, Zi));
+  const double inv = 1.0 / zz[i];
+  const double wn2 = sq / Zi.hi + inv;          // squared border: w_j (j != i) and 1/zeta_i
+  const double wn = sqrt(wn2);
+  const double side = (i == k) ? 1.0 : -1.0;
+  double floor, E;
+  if (side > 0) {
+    // largest pole of g: the nearest pole above d_i (or, for i = 0, the farthest below), or 0
+    const double dmax = (i > 0) ? 1.0 / (d[i - 1] - di) : (n > 1 ? 1.0 / (d[n - 1] - di) : -INFINITY);
+    const double pmax = fmax(dmax, 0.0);
+    floor = pmax;
+    E = pmax;
+    alo = fmax(alo, b);
+    ahi = fmin(ahi, fmax(b, pmax) + wn);
+    if (b > pmax) ahi = fmin(ahi, b + wn2 / (b - pmax));
+  } else {
+    const double dmin = (i + 1 < n) ? 1.0 / (d[i + 1] - di) : (n > 1 ? 1.0 / (d[0] - di) : INFINITY);
+    const double pmin = fmin(dmin, 0.0);
+    floor = -pmin;
+    E = -pmin;
+    alo = fmax(alo, -b);
+    ahi = fmin(ahi, -fmin(b, pmin) + wn);
+    if (b < pmin) ahi = fmin(ahi, -b + wn2 / (pmin - b));
+  }
+  alo = alo * (1.0 - 0x1p-48);
+  ahi = ahi * (1.0 + 0x1p-48);
+  bool ok;
+  int steps;
+  double nu;
+  if (fast) {
+    // F(t) = side g(side t) = side b - t + Psi(t), Psi(t) = -side S / zeta_i^2 + (1/zeta_i^2) / t
+    auto ev = [&](double t, bool want, double* psi, double* dpsi) {
+      const double v = side * t;
+      double dS = 0.0;
+      const double S = want ? arrow_sum_d<L>(d, zz, n, i, di, v, lane, gm, &dS)
+                            : arrow_sum<L>(d, zz, n, i, di, v, lane, gm);
+      const double Sz = __dmul_rn(S, inv);
+      const double ex = inv / t;
+      *psi = -side * Sz + ex;
+      *dpsi = -__dmul_rn(dS, inv) - ex / t;
+      const double g = __dadd_rn(__dsub_rn(__dsub_rn(b, v), Sz), inv / v);
+      return side > 0 ? g : -g;
+    };
+    nu = side * accel_solve(ev, floor, alo, ahi, E, side * b, 1.0, 1.0, cap, &ok, &steps);
+  } else {
+    auto phi = [&](double v) {
+      const double S = arrow_sum<L>(d, zz, n, i, di, v, lane, gm);
+      return __dadd_rn(__dsub_rn(__dsub_rn(b, v), __dmul_rn(S, inv)), inv / v);
+    };
+    // g > 0 below the root for the rightmost eigenvalue, g < 0 for the leftmost
+    nu = bisect(phi, side, floor, alo, ahi, side > 0, cap, &ok, &steps);
+  }
+  r.nu = nu;
+  r.mu = 1.0 / nu;
+  r.b = b;
+  r.ok = ok;
+  r.steps = steps;
+  return r;
+}
+
+// One lane group per eigenvalue k = 0..n (persistent grid, work counter).
+template <int L>
+__global__ void __launch_bounds__(256) k_arrow_solve(int n, const double* __restrict__ d,
+                                                     const double* __restrict__ z, double alpha, ArrowWs w, int cap,
+                                                     bool fast) {
+  if (*w.status & ST_FATAL_A) return;
+  const int lane = threadIdx.x & (L - 1);
+  const unsigned gm = group_mask<L>();
+  const int leader = (threadIdx.x & 31) & ~(L - 1);
+  const double* __restrict__ zz = w.zz;
+  for (;;) {
+    long long gl = 0;
+    if (lane == 0) gl = (long long)atomicAdd(w.queue, 1ull);
+    gl = __shfl_sync(gm, gl, leader, 32);
+    if (gl > n) break;
+    const int k = (int)gl;
+    int i;
+    double alo = 0.0, ahi = INFINITY;
+    if (k == 0 || k == n) {
+      // exterior: the 2 x 2 principal matrix [d_i zeta_i; zeta_i alpha] bounds |mu| from
+      // below (interlacing), Weyl with ||z|| bounds it from above
+      i = (k == 0) ? 0 : n - 1;
+      double s = 0.0;
+      for (int j = lane; j < n; j += L) s = __dadd_rn(s, zz[j]);
+      s = group_sum<L>(s, gm);
+      const double h = (k == 0) ? 0.5 * (d[0] - alpha) : 0.5 * (d[n - 1] - alpha);
+      const double rt = sqrt(h * h + zz[i]);
+      const double mlo = (k == 0) ? (h >= 0.0 ? zz[i] / (h + rt) : rt - h) : (h >= 0.0 ? h + rt : zz[i] / (rt - h));
+      const double gap = (k == 0) ? alpha - d[0] : d[n - 1] - alpha;
+      alo = 1.0 / (fmax(gap, 0.0) + sqrt(s));
+      ahi = 1.0 / mlo;
+    } else {
+      // shift test at the midpoint m = d_k + tau: F = f(m), f decreasing
+      const double dk = d[k];
+      const double tau = __dmul_rn(__dsub_rn(d[k - 1], dk), 0.5);
+      double sp = 0.0, sn = 0.0;
+      for (int j = lane; j < n; j += L) {
+        const double t = __dmul_rn(zz[j], rcp(__dsub_rn(__dsub_rn(d[j], dk), tau)));
+        if (j < k) sp = __dadd_rn(sp, t);
+        else sn = __dadd_rn(sn, t);
+      }
+      sp = group_sum<L>(sp, gm);
+      sn = group_sum<L>(sn, gm);
+      const double F = ((alpha - dk) - tau) - (sp + sn);
+      alo = 1.0 / tau;
+      if (F < 0.0) {
+        // mu in (0, tau]: zeta_k^2 nu <= sum_{j<k} zeta_j^2/((d_j - d_k) - tau) + d_k - alpha + tau
+        i = k;
+        ahi = (sp + (dk - alpha) + tau) / zz[k];
+      } else {
+        // mu in [-tau, 0): zeta_{k-1}^2 |nu| <= -sum_{j>=k} zeta_j^2/((d_j - d_k) - tau) + alpha - d_{k-1} + tau
+        i = k - 1;
+        ahi = (-sn + (alpha - d[k - 1]) + tau) / zz[k - 1];
+      }
+      if (!(ahi > alo)) ahi = INFINITY;
+    }
+    PoleResult pr = solve_pole_arrow<L>(d, z, zz, n, alpha, k, i, alo, ahi, cap, fast, lane, gm);
+    if (lane == 0) {
+      w.sig[k] = d[i];
+      w.mu[k] = pr.mu;
+      w.shift[k] = i;
+      atomicAdd(&w.counters[C_EVAL_SOLVE], (unsigned)pr.steps);
+      atomicAdd(&w.counters[C_SOLVED], 1u);
+      if (!pr.ok) atomicOr(w.status, ST_NOT_CONVERGED);
+    }
+  }
+}
+
+// Rows v_k = [x; -1] / ||.|| (one warp per row), lambda, sigma, mu, ||[x; -1]||.
+__global__ void __launch_bounds__(256) k_arrow_vectors(int n, const double* __restrict__ d,
+                                                       const double* __restrict__ z, ArrowWs w,
+                                                       double* __restrict__ lambda, double* __restrict__ Vt,
+                                                       int64_t ldv, double* __restrict__ sigma,
+                                                       double* __restrict__ mu, double* __restrict__ xnorm) {
+  if (*w.status & ST_FATAL_A) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t k = wid; k <= n; k += nw) {
+    const double s = w.sig[k], m = w.mu[k];
+    double* vr = Vt ? Vt + k * ldv : nullptr;
+    double q = 0.0;
+    bool bad = false;
+    for (int j = lane; j < n; j += 32) {
+      const double den = __dsub_rn(__dsub_rn(d[j], s), m);
+      const double x = __dmul_rn(z[j], rcp_nr(den));
+      bad |= !rcp_in_range(den);
+      if (vr) vr[j] = x;
+      q = __fma_rn(x, x, q);
+    }
+    q = group_sum<32>(q, FULL);
+    q = __dadd_rn(q, 1.0);                        // the last component, -1
+    bad = group_any<32>(bad, FULL);
+    double scale = 1.0;
+    bool rewrite = false;
+    if (bad || !(q < 1e300)) {
+      double mx = 1.0;
+      for (int j = lane; j < n; j += 32) mx = fmax(mx, fabs(__dmul_rn(z[j], rcp(__dsub_rn(__dsub_rn(d[j], s), m)))));
+      mx = group_max<32>(mx, FULL);
+      scale = 1.0 / mx;
+      q = 0.0;
+      for (int j = lane; j < n; j += 32) {
+        const double x = __dmul_rn(z[j], rcp(__dsub_rn(__dsub_rn(d[j], s), m))) * scale;
+        q = __fma_rn(x, x, q);
+      }
+      q = group_sum<32>(q, FULL);
+      q = __fma_rn(scale, scale, q);
+      rewrite = true;
+    }
+    const double nrm = sqrt(q);
+    const double c = scale / nrm;
+    if (lane == 0) {
+      lambda[k] = __dadd_rn(s, m);
+      if (sigma) sigma[k] = s;
+      if (mu) mu[k] = m;
+      if (xnorm) xnorm[k] = nrm / scale;
+      if (vr) vr[n] = -c;
+    }
+    if (!vr) continue;
+    if (!rewrite) {
+      for (int j = lane; j < n; j += 32) vr[j] = __dmul_rn(vr[j], c);
+    } else {
+      for (int j = lane; j < n; j += 32) vr[j] = __dmul_rn(z[j], rcp(__dsub_rn(__dsub_rn(d[j], s), m))) * c;
+    }
+  }
+}
+
+// n = 0: the 1 x 1 matrix [alpha]
+__global__ void k_arrow_one(double alpha, double* lambda, double* Vt, double* sigma, double* mu, double* xnorm) {
+  lambda[0] = alpha;
+  if (sigma) sigma[0] = alpha;
+  if (mu) mu[0] = 0.0;
+  if (xnorm) xnorm[0] = 1.0;
+  if (Vt) Vt[0] = -1.0;
+}
+
+template <int L>
+static void launch_arrow(int n, const double* d, const double* z, double alpha, const ArrowWs& w, const Options& o,
+                         cudaStream_t st) {
+  const int groups_per_block = (32 * o.warps) / L;
+  int64_t want = ((int64_t)n + 1 + groups_per_block - 1) / groups_per_block;
+  int grid = sm_count() * o.bps;
+  if (want < grid) grid = (int)(want > 0 ? want : 1);
+  k_arrow_solve<L><<<grid, 32 * o.warps, 0, st>>>(n, d, z, alpha, w, o.cap, o.fast);
+}
+
+}  // namespace dpr1
+
+using namespace dpr1;
+
+extern "C" {
+
+size_t dpr1_arrow_workspace_size(int64_t n) {
+  if (n < 0) return 0;
+  return arrow_layout(n, nullptr, nullptr);
+}
+
+dpr1_status dpr1_arrow_eig(int64_t n, const double* d, const double* z, double alpha, double* lambda, double* Vt,
+                           int64_t ldv, double* sigma, double* mu, double* xnorm, void* workspace,
+                           size_t workspace_bytes, const dpr1_options* opt, dpr1_stream_t stream) {
+  if (n < 0 || n > (int64_t)0x3fffffff - 1) return DPR1_ERR_ARG;
+  if (!lambda || (n > 0 && (!d || !z))) return DPR1_ERR_ARG;
+  if (Vt && ldv < n + 1) return DPR1_ERR_ARG;
+  if (!workspace || ((uintptr_t)workspace & 255) || workspace_bytes < dpr1_arrow_workspace_size(n))
+    return DPR1_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  ArrowWs w;
+  arrow_layout(n, &w, (char*)workspace);
+  if (cudaMemsetAsync(w.status, 0, 256, st) != cudaSuccess) return DPR1_ERR_CUDA;
+  if (n == 0) {
+    if (!std::isfinite(alpha)) return DPR1_ERR_NONFINITE;
+    k_arrow_one<<<1, 1, 0, st>>>(alpha, lambda, Vt, sigma, mu, xnorm);
+    return cudaGetLastError() == cudaSuccess ? DPR1_OK : DPR1_ERR_CUDA;
+  }
+  const Options o = resolve(opt);
+  const int sms = sm_count();
+  int cg = (int)((n + 255) / 256);
+  if (cg > sms * 8) cg = sms * 8;
+  k_arrow_check<<<cg, 256, 0, st>>>((int)n, d, z, alpha, w.zz, w.status);
+  const int L = o.lanes ? o.lanes : (n <= 96 ? 8 : (n <= 384 ? 16 : 32));
+  if (L == 8) launch_arrow<8>((int)n, d, z, alpha, w, o, st);
+  else if (L == 16) launch_arrow<16>((int)n, d, z, alpha, w, o, st);
+  else launch_arrow<32>((int)n, d, z, alpha, w, o, st);
+  int64_t vg = (n + 1 + 7) / 8;
+  if (vg > sms * 16) vg = sms * 16;
+  k_arrow_vectors<<<(int)vg, 256, 0, st>>>((int)n, d, z, w, lambda, Vt, ldv, sigma, mu, xnorm);
+  return cudaGetLastError() == cudaSuccess ? DPR1_OK : DPR1_ERR_CUDA;
+}
+
+}  // extern "C"
