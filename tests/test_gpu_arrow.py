@@ -112,3 +112,10 @@ def test_edges_and_errors(B):
     with pytest.raises(B.DPR1Error) as e:
         B.eig_arrowhead(cu(d), cu(z), float("nan"))
     assert e.value.code == 4
+
+
+@pytest.mark.parametrize("alpha", [0.3, 1e-8, -2.0])
+def test_hard_spectrum(B, alpha):
+    d, z, _ = W.hard(1000, 2)
+    for zf in (0, 1):
+        check(B, d, z, alpha, zero_finder=zf)

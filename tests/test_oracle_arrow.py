@@ -61,3 +61,16 @@ def test_graded_spectrum_relative_accuracy():
     q = oracle.quad_arrow_all(d, z, alpha)
     lq = q["hi"] + q["lo"]
     assert np.max(np.abs(r["lam"] - lq) / np.abs(lq)) <= 16 * (n + 1) * EPS
+
+
+@pytest.mark.parametrize("alpha", [0.3, 1e-8, -2.0])
+def test_hard_spectrum_without_remedies(alpha):
+    """Graded poles and weights down to 1e-10 (the hard DPR1 spectrum): every eigenvalue and
+    eigenvector component within the bound of binary128 with the plain pole solves."""
+    d, z, _ = W.hard(300, 1)
+    r = oracle.arrow_eig_all(d, z, alpha, threads=8)
+    q = oracle.quad_arrow_all(d, z, alpha, threads=8)
+    lq = q["hi"] + q["lo"]
+    tol = 16 * 301 * EPS
+    assert np.max(np.abs(r["lam"] - lq) / np.abs(lq)) <= tol
+    assert np.max(np.abs(r["Vt"] - q["Vt"]) / np.maximum(np.abs(q["Vt"]), 1e-300)) <= tol
