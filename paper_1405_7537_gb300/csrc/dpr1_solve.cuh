@@ -24,6 +24,7 @@ namespace dpr1 {
 // numerator and denominator by Delta_j leaves one division per term and forms
 // 1 - nu Delta_j with a single rounding (fma).  For the extreme eigenvalue every term
 // has the same sign.
+// The bisection sums (neither SAFE nor DERIV) take two terms over one reciprocal (below).
 // The hot sums use the fast reciprocal without a per-term range test; each lane records
 // whether any denominator left the fast range and, if a lane of the group saw one, the
 // group recomputes the sum with the range-safe reciprocal (never the case for sane data).
@@ -40,6 +41,18 @@ __device__ __forceinline__ double arrow_sum_pass(const double* __restrict__ d, c
     double D0 = __dsub_rn(d[j], di), D1 = __dsub_rn(d[j + L], di);
     double t0 = __fma_rn(-nu, D0, 1.0), t1 = __fma_rn(-nu, D1, 1.0);
     double x0 = __dmul_rn(D0, t0), x1 = __dmul_rn(D1, t1);
+    if (!SAFE && !DERIV) {
+      // Two terms over one reciprocal: zz0/x0 + zz1/x1 = (zz0 x1 + zz1 x0) / (x0 x1).  Beyond
+      // every pole (the only place the solvers evaluate) all x_j have one sign, so the
+      // numerator does not cancel.  The excluded term j == i enters as zz = 0, x = 1.
+      const double y0 = (j == i) ? 1.0 : x0, y1 = (j + L == i) ? 1.0 : x1;
+      const double w0 = (j == i) ? 0.0 : zz[j], w1 = (j + L == i) ? 0.0 : zz[j + L];
+      const double num = __fma_rn(w0, y1, __dmul_rn(w1, y0));
+      const double den = __dmul_rn(y0, y1);
+      b |= !rcp_in_range(den) || !rcp_in_range(num);
+      s0 = __fma_rn(num, rcp_nr(den), s0);
+      continue;
+    }
     double r0, r1;
     if (SAFE) { r0 = rcp(x0); r1 = rcp(x1); }
     else {
