@@ -161,7 +161,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args.n), "impl": "reference",
+            "config": dict(workload_config(args.n), zero_finder="bisection"), "impl": "reference",
             "cpu_baseline": {"value": value, "unit": "eigenpairs/s", "cores": threads, "kind": "oracle",
                              "sample": "%d random eigenpairs of the n=%d workload per step, all host cores"
                                        % (per_step, args.n)},
