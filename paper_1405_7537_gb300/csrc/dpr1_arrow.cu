@@ -108,6 +108,9 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
     alo = fmax(alo, b);
     ahi = fmin(ahi, fmax(b, pmax) + wn);
     if (b > pmax) ahi = fmin(ahi, b + wn2 / (b - pmax));
+    // smallest pole: the nearest delta_j below d_i (or the farthest above), or 0
+    const double dmin = (i + 1 < n) ? 1.0 / (d[i + 1] - di) : (n > 1 ? 1.0 / (d[0] - di) : INFINITY);
+    quad_bracket(b, fmin(dmin, 0.0), pmax, wn2, &alo, &ahi);
   } else {
     const double dmin = (i + 1 < n) ? 1.0 / (d[i + 1] - di) : (n > 1 ? 1.0 / (d[0] - di) : INFINITY);
     const double pmin = fmin(dmin, 0.0);
@@ -116,6 +119,8 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
     alo = fmax(alo, -b);
     ahi = fmin(ahi, -fmin(b, pmin) + wn);
     if (b < pmin) ahi = fmin(ahi, -b + wn2 / (pmin - b));
+    const double dmx = (i > 0) ? 1.0 / (d[i - 1] - di) : (n > 1 ? 1.0 / (d[n - 1] - di) : -INFINITY);
+    quad_bracket(-b, -fmax(dmx, 0.0), -pmin, wn2, &alo, &ahi);
   }
   alo = alo * (1.0 - 0x1p-48);
   ahi = ahi * (1.0 + 0x1p-48);

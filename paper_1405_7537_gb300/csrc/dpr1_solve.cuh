@@ -327,6 +327,28 @@ __device__ double accel_solve(Ev ev, double floor, double alo, double ahi, doubl
   return dfrom((ahi_g < alo_g || !have_lo) && have_hi ? hi : lo);
 }
 
+// Larger root t of (t - B)(t - E) = W (W >= 0), evaluated without cancellation; +-inf or
+// NaN when an argument is not finite (callers then ignore the bound).
+__device__ __forceinline__ double qroot(double B, double E, double W) {
+  const double c = E - B;
+  const double s = sqrt(__fma_rn(c, c, 4.0 * W));
+  const double x = (c > 0.0) ? (2.0 * W) / (c + s) : 0.5 * (s - c);
+  return E + x;
+}
+
+// Quadratic bracket of the extreme eigenvalue t = |nu| > every pole e_j of the secular
+// function t - B = sum_j w_j^2 / (t - e_j), W = sum_j w_j^2, poles in [Efar, Enear]: every
+// denominator lies in [t - Enear, t - Efar], so t - B lies between W / (t - Efar) and
+// W / (t - Enear), and t between the larger roots of (t - B)(t - Efar) = W and
+// (t - B)(t - Enear) = W.  (The corner bound B + W / (B - Enear) is this upper bound with
+// t - Enear replaced by B - Enear.)
+__device__ __forceinline__ void quad_bracket(double B, double Efar, double Enear, double W, double* alo,
+                                             double* ahi) {
+  const double lo = qroot(B, Efar, W), hi = qroot(B, Enear, W);
+  if (isfinite(lo)) *alo = fmax(*alo, lo);
+  if (isfinite(hi)) *ahi = fmin(*ahi, hi);
+}
+
 // ---------------------------------------------------------------------------------
 // Solve at a pole: extreme eigenvalue of the arrowhead inverse of A - d_i I.
 // ---------------------------------------------------------------------------------
@@ -377,6 +399,9 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
     alo = fmax(alo, b);
     ahi = fmin(ahi, fmax(b, dmax) + wn);
     if (b > dmax) ahi = fmin(ahi, b + wn2 / (b - dmax));
+    // smallest delta_j: the nearest pole below d_i, or for i = n-1 the farthest pole above
+    const double dmin = (i + 1 < n) ? 1.0 / (d[i + 1] - di) : (n > 1 ? 1.0 / (d[0] - di) : -INFINITY);
+    quad_bracket(b, dmin, dmax, wn2, &alo, &ahi);
   } else {
     double dmin = (i + 1 < n) ? 1.0 / (d[i + 1] - di) : INFINITY;
     floor = fmax(-dmin, 0.0);
@@ -385,6 +410,9 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
     alo = fmax(alo, -b);
     ahi = fmin(ahi, -fmin(b, dmin) + wn);
     if (b < dmin) ahi = fmin(ahi, -b + wn2 / (dmin - b));
+    // on t = -nu the poles are -delta_j: the nearest is -dmin, the farthest -(largest delta_j)
+    const double dmx = (i > 0) ? 1.0 / (d[i - 1] - di) : (n > 1 ? 1.0 / (d[n - 1] - di) : INFINITY);
+    quad_bracket(-b, -dmx, -dmin, wn2, &alo, &ahi);
   }
   // a few ulps of margin for the rounding of the bounds; bisect() checks both ends
   alo = alo * (1.0 - 0x1p-48);
