@@ -37,8 +37,12 @@ RHO = 1e3
 # 2 binary64 instructions per clock per SM on 152 SMs at the 2070 MHz maximum clock
 NOMINAL_FP64_OPS = 2 * 152 * 2070e6
 # algorithmic binary64 operations per secular term (sub, fma, mul, div, add; fma and div = 1 op)
-OPS_PER_TERM = 5
-ACCEL_OPS_PER_TERM = 8
+OPS_PER_TERM = 5          # a secular term: sub, fma, mul, div, add
+ACCEL_OPS_PER_TERM = 8    # the same with its slope (mul, mul, fma)
+# a double-double term zeta_j^2 / (d_j - d_i) of the corner b: TwoSum of the difference (6),
+# TwoProd of the square (2), quotient and its first-order correction (5), compensated
+# accumulation (7)
+DD_OPS_PER_TERM = 20
 # kernels one dpr1_eig call launches: k_scan, k_deflate, k_solve, k_classify, k_fix, k_zero_detect,
 # k_zero_solve, k_defl_positions, k_vectors, k_defl_rows, k_trivial
 LAUNCHES_PER_CALL = 11
@@ -349,7 +353,7 @@ def bench_accel(B, dev, d, z, rho, ws, out, flush, steps, bisection_ms):
         raise B.DPR1Error(st, "accelerated timed")
     t = statistics.mean(ms)
     solve = statistics.mean(p[0] for p in ph)
-    ops = ACCEL_OPS_PER_TERM * (n - 1) * stats["evals_solve"] + OPS_PER_TERM * (n - 1) * 2 * n
+    ops = (n - 1) * (ACCEL_OPS_PER_TERM * stats["evals_solve"] + (OPS_PER_TERM + DD_OPS_PER_TERM) * n)
     return {"zero_finder": "accelerated bracketed solve (nearest-pole rational model, value and slope)",
             "value": n / (t * 1e-3), "unit": "eigenpairs/s", "ms_per_step": t, "steps": len(ms),
             "phases_ms": {"solve": solve, "remedies": statistics.mean(p[1] for p in ph),
@@ -358,8 +362,9 @@ def bench_accel(B, dev, d, z, rho, ws, out, flush, steps, bisection_ms):
             "speedup_vs_bisection": bisection_ms / t,
             "solve_kernel_rate": {"achieved": ops / (solve * 1e-3) / 1e12, "unit": "T binary64-op/s",
                                   "frac": ops / (solve * 1e-3) / NOMINAL_FP64_OPS,
-                                  "ops_definition": "8 ops per secular term and evaluation (5 for the value, "
-                                                    "3 for the slope) + the two 5-op passes per eigenvalue"}}
+                                  "ops_definition": "(n-1) x (8 ops per secular term and evaluation (5 for the "
+                                                    "value, 3 for the slope) + per eigenvalue the 5-op shift-test "
+                                                    "pass and the 20-op double-double pass)"}}
 
 
 def bench_hermitian(B, dev, n, seed, steps, flush):
@@ -587,15 +592,16 @@ def run_ours(args):
     # roofline of the dominant kernel (the bisection kernel k_solve)
     evals = stats["evals_solve"]
     if zf == 0:
-        ops = OPS_PER_TERM * (n - 1) * (evals + 2 * n)
+        ops = (n - 1) * (OPS_PER_TERM * (evals + n) + DD_OPS_PER_TERM * n)
         kname = "k_solve (shift test, double-double b, bisection)"
-        odef = ("5 ops (sub, fma, mul, div, add) per secular term x (n-1) x (bisection evaluations + 2 passes "
-                "per eigenvalue)")
+        odef = ("(n-1) x (5 ops (sub, fma, mul, div, add) per secular term x (bisection evaluations + the "
+                "shift-test pass) + 20 ops per double-double term of b (TwoSum 6, TwoProd 2, quotient and "
+                "correction 5, compensated accumulation 7))")
     else:
-        ops = (n - 1) * (ACCEL_OPS_PER_TERM * evals + OPS_PER_TERM * 2 * n)
+        ops = (n - 1) * (ACCEL_OPS_PER_TERM * evals + (OPS_PER_TERM + DD_OPS_PER_TERM) * n)
         kname = "k_solve (shift test, double-double b, accelerated bracketed solve)"
-        odef = ("8 ops per secular term and evaluation (5 for the value, 3 for the slope) x (n-1) + the two "
-                "5-op passes per eigenvalue")
+        odef = ("(n-1) x (8 ops per secular term and evaluation (5 for the value, 3 for the slope) + per "
+                "eigenvalue the 5-op shift-test pass and the 20-op double-double pass)")
     t_solve = statistics.mean(solve_ms) * 1e-3
     achieved = ops / t_solve
     # live binary64 fma rate of this GPU at this clock (same process, after the timed region)
