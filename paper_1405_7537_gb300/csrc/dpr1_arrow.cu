@@ -99,6 +99,11 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
   const double wn = sqrt(wn2);
   const double side = (i == k) ? 1.0 : -1.0;
   double floor, E;
+  // the caller's [alo, ahi] rests on the shift test (or the 2 x 2 interlacing bounds) and is
+  // checked first where it binds; the bounds below are rigorous up to rounding
+  const double alo_in = alo, ahi_in = ahi;
+  alo = 0.0;
+  ahi = INFINITY;
   if (side > 0) {
     // largest pole of g: the nearest pole above d_i (or, for i = 0, the farthest below), or 0
     const double dmax = (i > 0) ? 1.0 / (d[i - 1] - di) : (n > 1 ? 1.0 / (d[n - 1] - di) : -INFINITY);
@@ -122,8 +127,9 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
     const double dmx = (i > 0) ? 1.0 / (d[i - 1] - di) : (n > 1 ? 1.0 / (d[n - 1] - di) : -INFINITY);
     quad_bracket(-b, -fmax(dmx, 0.0), -pmin, wn2, &alo, &ahi);
   }
-  alo = alo * (1.0 - 0x1p-48);
-  ahi = ahi * (1.0 + 0x1p-48);
+  const bool eager_lo = alo_in > alo, eager_hi = ahi_in < ahi;
+  alo = fmax(alo, alo_in) * (1.0 - 0x1p-48);
+  ahi = fmin(ahi, ahi_in) * (1.0 + 0x1p-48);
   bool ok;
   int steps;
   double nu;
@@ -148,7 +154,7 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
       return __dadd_rn(__dsub_rn(__dsub_rn(b, v), __dmul_rn(S, inv)), inv / v);
     };
     // g > 0 below the root for the rightmost eigenvalue, g < 0 for the leftmost
-    nu = bisect(phi, side, floor, alo, ahi, side > 0, cap, &ok, &steps);
+    nu = bisect(phi, side, floor, alo, ahi, side > 0, cap, &ok, &steps, eager_lo, eager_hi);
   }
   r.nu = nu;
   r.mu = 1.0 / nu;

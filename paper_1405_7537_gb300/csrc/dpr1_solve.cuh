@@ -154,58 +154,96 @@ __device__ __forceinline__ dd dd_pole_sum(const double* __restrict__ d, const do
 // Bit-pattern bisection of a secular function on |nu| for nu = side*|nu|.
 // phi(nu) has sign `below` for |nu| between `floor` and the root and the opposite sign
 // beyond it.  `floor` is a pole of phi (or 0) that is known to lie below the root and
-// is never evaluated; [alo, ahi] is an estimate of the bracket: its far end is checked
-// and pushed out while it is still below the root, its near end (when above the floor)
-// is checked and moved down towards the floor while it is above the root.  Every lane
-// of the group runs the same loop (the sums are identical in every lane).  Returns nu
-// with the smaller |phi| of the final adjacent pair; *ok = false if the cap was reached.
+// is never evaluated; [alo, ahi] is an estimate of the bracket.  Ends from a soft estimate
+// (eager_lo / eager_hi) are checked first; any other end that the bisection never moves is
+// checked when the bisection has closed on it.  A far end still below the root is pushed
+// out geometrically, a near end above the root falls back to the floor, and the bisection
+// continues (each bisection phase has the iteration cap).  Every lane of the group runs the same loop (the
+// sums are identical in every lane).  Returns nu with the smaller |phi| of the final
+// adjacent pair; *ok = false if the cap was reached.
 // ---------------------------------------------------------------------------------
 template <class Phi>
 __device__ double bisect(Phi phi, double side, double floor, double alo, double ahi, bool below_positive, int cap,
-                         bool* ok, int* steps_out) {
+                         bool* ok, int* steps_out, bool eager_lo = false, bool eager_hi = false) {
   int steps = 0;
   bool good = true;
   if (!(floor >= 0.0)) floor = 0.0;
   if (!(alo >= floor)) alo = floor;
   if (!(ahi > alo)) ahi = (alo > 0.0) ? alo * 2.0 : 1.0;
   const uint64_t fl = dbits(floor);
+  const uint64_t top = 0x7fefffffffffffffull;
   uint64_t lo = dbits(alo), hi = dbits(ahi);
+  uint64_t span = hi - lo + 64;
   double glo = 0.0, ghi = 0.0;
-  bool have_lo = false, have_hi = false;
-  // far end: pushed out geometrically (in bit space) while it is still below the root
-  for (int t = 0; t < 64; t++) {
-    double g = phi(side * dfrom(hi));
-    steps++;
-    bool below = below_positive ? (g > 0.0) : (g < 0.0);
-    if (!below) { ghi = g; have_hi = true; break; }
-    uint64_t wd = hi - lo;
-    lo = hi; glo = g; have_lo = true;
-    hi = hi + 2 * wd + 64;
-    if (hi >= 0x7ff0000000000000ull) { hi = 0x7fefffffffffffffull; }
+  bool have_lo = false, have_hi = false;    // the end point was evaluated (its side is known)
+  int it = 0, pushes = 0;
+  // ends that come from a soft estimate (eager_*) are checked before the bisection
+  if (eager_hi) {
+    for (; pushes < 64; pushes++) {
+      double g = phi(side * dfrom(hi));
+      steps++;
+      bool below = below_positive ? (g > 0.0) : (g < 0.0);
+      if (!below) { ghi = g; have_hi = true; break; }
+      lo = hi; glo = g; have_lo = true;
+      if (hi >= top) break;
+      hi = (top - hi > span) ? hi + span : top;
+      span *= 2;
+    }
   }
-  // near end (when above the floor): if the root lies below it, fall back to the floor
-  if (!have_lo && lo > fl) {
+  if (eager_lo && !have_lo && lo > fl) {
     double g = phi(side * dfrom(lo));
     steps++;
     bool below = below_positive ? (g > 0.0) : (g < 0.0);
     if (below) { glo = g; have_lo = true; }
     else { hi = lo; ghi = g; have_hi = true; lo = fl; }
   }
-  int it = 0;
-  while (hi - lo > 1) {
-    if (it >= cap) { good = false; break; }
-    uint64_t mid = lo + ((hi - lo) >> 1);
-    double g = phi(side * dfrom(mid));
-    bool below = below_positive ? (g > 0.0) : (g < 0.0);
-    if (below) { lo = mid; glo = g; have_lo = true; }
-    else { hi = mid; ghi = g; have_hi = true; }
-    it++;
+  for (;;) {
+    // bisection on the bit patterns; every evaluation moves one end and makes it known
+    int phase = 0;
+    while (hi - lo > 1) {
+      if (phase >= cap) { good = false; break; }
+      phase++;
+      uint64_t mid = lo + ((hi - lo) >> 1);
+      double g = phi(side * dfrom(mid));
+      bool below = below_positive ? (g > 0.0) : (g < 0.0);
+      if (below) { lo = mid; glo = g; have_lo = true; }
+      else { hi = mid; ghi = g; have_hi = true; }
+      it++;
+    }
+    if (!good) break;
+    // an end the bisection never moved is only an estimate: check it now (usually the root
+    // lies strictly inside and both ends have moved, so this costs nothing)
+    if (!have_hi) {
+      double g = phi(side * dfrom(hi));
+      steps++;
+      bool below = below_positive ? (g > 0.0) : (g < 0.0);
+      if (below && pushes < 64 && hi < top) {
+        // the root lies beyond the estimate: push the far end out geometrically
+        lo = hi; glo = g; have_lo = true;
+        hi = (top - hi > span) ? hi + span : top;
+        span *= 2;
+        pushes++;
+        continue;
+      }
+      ghi = g; have_hi = !below;
+      if (below) { good = false; break; }
+    }
+    if (!have_lo && lo > fl) {
+      double g = phi(side * dfrom(lo));
+      steps++;
+      bool below = below_positive ? (g > 0.0) : (g < 0.0);
+      if (!below) {
+        // the root lies below the near estimate: fall back to the floor
+        hi = lo; ghi = g; have_hi = true; lo = fl;
+        continue;
+      }
+      glo = g; have_lo = true;
+    }
+    break;
   }
   steps += it;
-  if (!have_lo && lo > fl) { glo = phi(side * dfrom(lo)); steps++; have_lo = true; }
-  if (!have_hi) { ghi = phi(side * dfrom(hi)); steps++; have_hi = true; }
   double alo_g = have_lo ? fabs(glo) : INFINITY;
-  double ahi_g = fabs(ghi);
+  double ahi_g = have_hi ? fabs(ghi) : INFINITY;
   if (isnan(alo_g)) alo_g = INFINITY;
   if (isnan(ahi_g)) ahi_g = INFINITY;
   *ok = good;
@@ -388,6 +426,11 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
   // floor: the pole of g next to the extreme eigenvalue (largest delta_j for the
   // rightmost, smallest for the leftmost), or 0 when all poles lie on the other side.
   double floor, E;   // E: the nearest pole on |nu| (the accelerated solve's model pole)
+  // [alo, ahi] from the caller (the shift test) rests on its choice of pole and is checked
+  // before the bisection where it is the binding bound; the bounds below are rigorous up to
+  // rounding and are only checked if the bisection closes on them.
+  const double alo_in = alo, ahi_in = ahi;
+  double rlo, rhi = INFINITY;
   // Corner bound: for the rightmost eigenvalue nu >= b and nu - b = sum_j w_j^2 / (nu - delta_j)
   // <= ||w||^2 / (b - max delta) when b > max delta (mirrored for the leftmost).  Next to a
   // pole b ~ 1/zeta_i^2 dominates and this bracket is narrow.
@@ -396,25 +439,28 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
     double dmax = (i > 0) ? 1.0 / (d[i - 1] - di) : (n > 1 ? 1.0 / (d[n - 1] - di) : -INFINITY);
     floor = fmax(dmax, 0.0);
     E = dmax;
-    alo = fmax(alo, b);
-    ahi = fmin(ahi, fmax(b, dmax) + wn);
-    if (b > dmax) ahi = fmin(ahi, b + wn2 / (b - dmax));
+    rlo = b;
+    rhi = fmax(b, dmax) + wn;
+    if (b > dmax) rhi = fmin(rhi, b + wn2 / (b - dmax));
     // smallest delta_j: the nearest pole below d_i, or for i = n-1 the farthest pole above
     const double dmin = (i + 1 < n) ? 1.0 / (d[i + 1] - di) : (n > 1 ? 1.0 / (d[0] - di) : -INFINITY);
-    quad_bracket(b, dmin, dmax, wn2, &alo, &ahi);
+    quad_bracket(b, dmin, dmax, wn2, &rlo, &rhi);
   } else {
     double dmin = (i + 1 < n) ? 1.0 / (d[i + 1] - di) : INFINITY;
     floor = fmax(-dmin, 0.0);
     // smallest delta_j: the nearest pole below d_i, or for i = n-1 the farthest pole above
     E = (i + 1 < n) ? -dmin : (n > 1 ? -1.0 / (d[0] - di) : -INFINITY);
-    alo = fmax(alo, -b);
-    ahi = fmin(ahi, -fmin(b, dmin) + wn);
-    if (b < dmin) ahi = fmin(ahi, -b + wn2 / (dmin - b));
+    rlo = -b;
+    rhi = -fmin(b, dmin) + wn;
+    if (b < dmin) rhi = fmin(rhi, -b + wn2 / (dmin - b));
     // on t = -nu the poles are -delta_j: the nearest is -dmin, the farthest -(largest delta_j)
     const double dmx = (i > 0) ? 1.0 / (d[i - 1] - di) : (n > 1 ? 1.0 / (d[n - 1] - di) : INFINITY);
-    quad_bracket(-b, -dmx, -dmin, wn2, &alo, &ahi);
+    quad_bracket(-b, -dmx, -dmin, wn2, &rlo, &rhi);
   }
-  // a few ulps of margin for the rounding of the bounds; bisect() checks both ends
+  alo = fmax(alo_in, rlo);
+  ahi = fmin(ahi_in, rhi);
+  const bool eager_lo = alo_in > rlo, eager_hi = ahi_in < rhi;
+  // a few ulps of margin for the rounding of the bounds
   alo = alo * (1.0 - 0x1p-48);
   ahi = ahi * (1.0 + 0x1p-48);
   bool ok;
@@ -441,7 +487,7 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
     };
     // g(nu) > 0 below the root for the rightmost; for the leftmost, |nu| below the root
     // means nu above it, where g < 0.
-    nu = bisect(phi, side, floor, alo, ahi, side > 0, cap, &ok, &steps);
+    nu = bisect(phi, side, floor, alo, ahi, side > 0, cap, &ok, &steps, eager_lo, eager_hi);
   }
   r.nu = nu;
   r.mu = 1.0 / nu;
