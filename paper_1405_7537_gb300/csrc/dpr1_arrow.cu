@@ -34,7 +34,8 @@ struct ArrowWs {
   unsigned* status;              // word 0: status; words 8..: counters (as the DPR1 header)
   unsigned* counters;
   unsigned long long* queue;     // work counter of the solve kernel
-  double* zz;                    // zeta_j^2
+  double* zz;                    // zeta_j^2 = zz + zl exactly
+  double* zl;
   double* sig;                   // pole of eigenvalue k
   double* mu;
   int* shift;
@@ -45,6 +46,7 @@ static size_t arrow_layout(int64_t n, ArrowWs* w, char* base) {
   size_t off = 0;
   size_t o_h = off; off += 256;
   size_t o_zz = off; off += a256a(8 * nn);
+  size_t o_zl = off; off += a256a(8 * nn);
   size_t o_s = off; off += a256a(8 * nn);
   size_t o_m = off; off += a256a(8 * nn);
   size_t o_sh = off; off += a256a(4 * nn);
@@ -53,6 +55,7 @@ static size_t arrow_layout(int64_t n, ArrowWs* w, char* base) {
     w->counters = (unsigned*)(base + o_h) + 8;
     w->queue = (unsigned long long*)((unsigned*)(base + o_h) + 24);
     w->zz = (double*)(base + o_zz);
+    w->zl = (double*)(base + o_zl);
     w->sig = (double*)(base + o_s);
     w->mu = (double*)(base + o_m);
     w->shift = (int*)(base + o_sh);
@@ -64,7 +67,7 @@ constexpr unsigned ST_FATAL_A = ST_NONFINITE | ST_UNSORTED | ST_BADARG;
 
 // input checks (finite, strictly decreasing d, no zero weight) and zeta^2
 __global__ void k_arrow_check(int n, const double* __restrict__ d, const double* __restrict__ z, double alpha,
-                              double* __restrict__ zz, unsigned* __restrict__ status) {
+                              double* __restrict__ zz, double* __restrict__ zl, unsigned* __restrict__ status) {
   unsigned bits = 0;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     const double dj = d[j], zj = z[j];
@@ -74,7 +77,9 @@ __global__ void k_arrow_check(int n, const double* __restrict__ d, const double*
       else if (dj == d[j + 1]) bits |= ST_BADARG;       // equal poles: reducible
     }
     if (zero_weight(zj)) bits |= ST_BADARG;               // zero weight: reducible
-    zz[j] = __dmul_rn(zj, zj);
+    const double zq = __dmul_rn(zj, zj);
+    zz[j] = zq;
+    zl[j] = __fma_rn(zj, zj, -zq);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0 && !isfinite(alpha)) bits |= ST_NONFINITE;
   bits = __reduce_or_sync(FULL, bits);
@@ -84,15 +89,15 @@ __global__ void k_arrow_check(int n, const double* __restrict__ d, const double*
 // Extreme eigenvalue nu of (A - d_i I)^{-1} on the side of eigenvalue k (rightmost when
 // i == k, leftmost when i == k - 1); [alo, ahi] an estimate of the bracket of |nu|.
 template <int L>
-__device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const double* __restrict__ z,
+__device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const double* __restrict__ zl,
                                        const double* __restrict__ zz, int n, double alpha, int k, int i, double alo,
                                        double ahi, int cap, bool fast, int lane, unsigned gm) {
   PoleResult r;
   double sq;
   const double di = d[i];
-  dd acc = dd_pole_sum<L>(d, z, n, i, di, lane, gm, &sq);
+  dd acc = dd_pole_sum<L>(d, zz, zl, n, i, di, lane, gm, &sq);
   dd B = dd_add(two_sum(di, -alpha), acc);
-  dd Zi = two_prod(z[i], z[i]);
+  const dd Zi = {zz[i], zl[i]};
   const double b = dd_to_double(dd_div(B, Zi));
   const double inv = 1.0 / zz[i];
   const double wn2 = sq / Zi.hi + inv;          // squared border: w_j (j != i) and 1/zeta_i
@@ -220,7 +225,7 @@ __global__ void __launch_bounds__(256) k_arrow_solve(int n, const double* __rest
       }
       if (!(ahi > alo)) ahi = INFINITY;
     }
-    PoleResult pr = solve_pole_arrow<L>(d, z, zz, n, alpha, k, i, alo, ahi, cap, fast, lane, gm);
+    PoleResult pr = solve_pole_arrow<L>(d, w.zl, zz, n, alpha, k, i, alo, ahi, cap, fast, lane, gm);
     if (lane == 0) {
       w.sig[k] = d[i];
       w.mu[k] = pr.mu;
@@ -342,7 +347,7 @@ dpr1_status dpr1_arrow_eig(int64_t n, const double* d, const double* z, double a
   const int sms = sm_count();
   int cg = (int)((n + 255) / 256);
   if (cg > sms * 8) cg = sms * 8;
-  k_arrow_check<<<cg, 256, 0, st>>>((int)n, d, z, alpha, w.zz, w.status);
+  k_arrow_check<<<cg, 256, 0, st>>>((int)n, d, z, alpha, w.zz, w.zl, w.status);
   const int L = o.lanes ? o.lanes : (n <= 96 ? 8 : (n <= 384 ? 16 : 32));
   if (L == 8) launch_arrow<8>((int)n, d, z, alpha, w, o, st);
   else if (L == 16) launch_arrow<16>((int)n, d, z, alpha, w, o, st);

@@ -47,6 +47,7 @@ size_t ws_layout2(int64_t total, int64_t nprob, bool batched, Ws* w, char* base)
   char* dr = take(sizeof(double) * nn);
   char* zr = take(sizeof(double) * nn);
   char* zz = take(sizeof(double) * nn);
+  char* zl = take(sizeof(double) * nn);
   char* sig = take(sizeof(double) * nn);
   char* mu = take(sizeof(double) * nn);
   char* shift = take(sizeof(int) * nn);
@@ -76,7 +77,7 @@ size_t ws_layout2(int64_t total, int64_t nprob, bool batched, Ws* w, char* base)
     w->ndefl = (int*)pd;
     w->pst = (unsigned*)ps;
     w->owner = (int*)own;
-    w->dr = (double*)dr; w->zr = (double*)zr; w->zz = (double*)zz;
+    w->dr = (double*)dr; w->zr = (double*)zr; w->zz = (double*)zz; w->zl = (double*)zl;
     w->sig = (double*)sig; w->mu = (double*)mu;
     w->shift = (int*)shift; w->flag = (int*)flag; w->list = (int*)list;
     w->lamz = (double*)lamz;
@@ -174,7 +175,9 @@ __global__ void k_scan(Prob pb, Ws w) {
     if (pbits) atomicOr(&w.pst[p], pbits);
     w.dr[g] = dj;
     w.zr[g] = zj;
-    w.zz[g] = __dmul_rn(zj, zj);
+    const double zq = __dmul_rn(zj, zj);
+    w.zz[g] = zq;
+    w.zl[g] = __fma_rn(zj, zj, -zq);
   }
   bits = __reduce_or_sync(FULL, bits);
   if ((threadIdx.x & 31) == 0 && bits) atomicOr(w.status, bits);
@@ -228,7 +231,9 @@ __global__ void k_deflate(Prob pb, Ws w) {
         }
         w.dr[base + nr] = d[j];
         w.zr[base + nr] = zs;
-        w.zz[base + nr] = __dmul_rn(zs, zs);
+        const double zq = __dmul_rn(zs, zs);
+        w.zz[base + nr] = zq;
+        w.zl[base + nr] = __fma_rn(zs, zs, -zq);
         nr++;
       }
       j = e + 1;
@@ -273,7 +278,7 @@ __global__ void __launch_bounds__(256) k_solve(Prob pb, Ws w, int cap, bool fast
     if (k >= n) continue;
     const double rho = p_rho(pb, p);
     const double* __restrict__ d = w.dr + base;
-    const double* __restrict__ z = w.zr + base;
+    const double* __restrict__ zl = w.zl + base;
     const double* __restrict__ zz = w.zz + base;
     int i;
     double alo, ahi;
@@ -307,7 +312,7 @@ __global__ void __launch_bounds__(256) k_solve(Prob pb, Ws w, int cap, bool fast
         ahi = (-1.0 - rho * sn) / (rho * zz[k - 1]);
       }
     }
-    PoleResult pr = solve_pole<L>(d, z, zz, n, rho, k, i, alo, ahi, cap, fast, lane, gm);
+    PoleResult pr = solve_pole<L>(d, zl, zz, n, rho, k, i, alo, ahi, cap, fast, lane, gm);
     if (lane == 0) {
       w.sig[g] = d[i];
       w.mu[g] = pr.mu;
@@ -406,7 +411,7 @@ __global__ void __launch_bounds__(256) k_fix(Prob pb, Ws w, double T_Knu, int ca
     const int k = (int)(g - base);
     const double rho = p_rho(pb, p);
     const double* __restrict__ d = w.dr + base;
-    const double* __restrict__ z = w.zr + base;
+    const double* __restrict__ zl = w.zl + base;
     const double* __restrict__ zz = w.zz + base;
     int i = w.shift[g];
     double di = d[i];
@@ -420,7 +425,7 @@ __global__ void __launch_bounds__(256) k_fix(Prob pb, Ws w, double T_Knu, int ca
     double best_sig = di, best_mu = mu;
     int o = (i == k) ? k - 1 : k;
     if (o >= 0 && o < n && o != i && K2 < K) {
-      PoleResult pr = solve_pole<L>(d, z, zz, n, rho, k, o, 0.0, INFINITY, cap, fast, lane, gm);
+      PoleResult pr = solve_pole<L>(d, zl, zz, n, rho, k, o, 0.0, INFINITY, cap, fast, lane, gm);
       if (!pr.ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
       if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)pr.steps);
       best_sig = d[o];
@@ -438,7 +443,7 @@ __global__ void __launch_bounds__(256) k_fix(Prob pb, Ws w, double T_Knu, int ca
       if (s > lo && s < hi) {
         bool ok;
         int st2 = 0;
-        double m2 = solve_nonpole<L>(d, z, zz, n, rho, s, k > 0 ? k - 1 : -1, k, cap, fast, lane, gm, &ok, &st2);
+        double m2 = solve_nonpole<L>(d, zl, zz, n, rho, s, k > 0 ? k - 1 : -1, k, cap, fast, lane, gm, &ok, &st2);
         if (!ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
         if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)st2);
         new_sig = s; new_mu = m2; new_shift = -1;
@@ -507,7 +512,7 @@ __global__ void k_zero_solve(Prob pb, Ws w, int cap, bool fast) {
     const int below = lo < n ? lo : -1;
     const int above = lo - 1;
     bool ok;
-    double lam0 = solve_nonpole<32>(d, w.zr + base, w.zz + base, n, p_rho(pb, p), 0.0, above, below, cap, fast, lane,
+    double lam0 = solve_nonpole<32>(d, w.zl + base, w.zz + base, n, p_rho(pb, p), 0.0, above, below, cap, fast, lane,
                                     FULL, &ok);
     if (lane == 0) {
       w.lamz[g] = lam0;

@@ -19,7 +19,7 @@ struct Ws {
   int* ndefl;          // [P]: deflated pairs of each problem
   unsigned* pst;       // [P]: PT_* bits of each problem
   int* owner;          // [total]: problem of each element (batch only)
-  double *dr, *zr, *zz;       // reduced problem: d, z, z^2
+  double *dr, *zr, *zz, *zl;  // reduced problem: d, z, z^2 = zz + zl exactly
   double *sig, *mu;           // eigenvalue pairs of the reduced problem
   int *shift, *flag, *list;   // pole index (-1: non-pole shift), remedy flag, work lists
   double* lamz;               // eigenvalue from A^{-1} (NaN: not recomputed)

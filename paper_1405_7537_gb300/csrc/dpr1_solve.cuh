@@ -118,26 +118,30 @@ __device__ __forceinline__ double shift_sum(const double* __restrict__ d, const 
 
 // sum_{j != skip} zeta_j^2 / (d_j - s) in double-double (skip = -1: all j); also returns
 // sum_{j != skip} zeta_j^2 / (d_j - s)^2 in binary64 (the squared norm of the border).
-// Each term zeta_j^2 / (d_j - s) is formed from the exact difference D = Dh + Dl (two_sum)
-// and the exact square Z = Zh + Zl (fma) as q + e_q, q = Zh / Dh rounded, with the first-order
-// correction e_q = ((Zh - q Dh) + (Zl - q Dl)) / Dh.  The q are summed by compensated
-// summation (Sum2 of Ogita, Rump and Oishi, SIAM J. Sci. Comput. 26 (2005)): two_sum keeps
-// each rounding error, and the errors and the e_q go to a second binary64 accumulator, which
+// Each term is formed from the exact difference D = Dh + Dl (FastTwoSum with the operands
+// ordered by magnitude) and the exact square zeta_j^2 = zz_j + zl_j (stored once per problem)
+// as q + e_q, q = zz_j / Dh rounded, with the first-order correction
+// e_q = ((zz_j - q Dh) + (zl_j - q Dl)) / Dh.  The q are summed by compensated summation
+// (Sum2 of Ogita, Rump and Oishi, SIAM J. Sci. Comput. 26 (2005)): two_sum keeps each
+// rounding error, and the errors and the e_q go to a second binary64 accumulator, which
 // gives the sum as accurately as accumulation in twice the working precision (Sec. 2.3).
 template <int L>
-__device__ __forceinline__ dd dd_pole_sum(const double* __restrict__ d, const double* __restrict__ z, int n,
-                                          int skip, double s, int lane, unsigned gm, double* sq,
-                                          double* cub = nullptr) {
+__device__ __forceinline__ dd dd_pole_sum(const double* __restrict__ d, const double* __restrict__ zz,
+                                          const double* __restrict__ zl, int n, int skip, double s, int lane,
+                                          unsigned gm, double* sq, double* cub = nullptr) {
   double hi = 0.0, lo = 0.0, q2 = 0.0, c3 = 0.0;
+  const double ms = -s;
   for (int j = lane; j < n; j += L) {
     if (j == skip) continue;
-    const dd D = two_sum(d[j], -s);
-    const double zj = z[j];
-    const double Zh = __dmul_rn(zj, zj);
-    const double Zl = __fma_rn(zj, zj, -Zh);
-    const double r = rcp(D.hi);
+    const double dj = d[j];
+    const bool ge = fabs(dj) >= fabs(ms);
+    const double big = ge ? dj : ms, small = ge ? ms : dj;
+    const double Dh = __dadd_rn(big, small);
+    const double Dl = __dsub_rn(small, __dsub_rn(Dh, big));
+    const double Zh = zz[j], Zl = zl[j];
+    const double r = rcp(Dh);
     const double q = __dmul_rn(Zh, r);
-    const double eq = __dmul_rn(__dadd_rn(__fma_rn(-q, D.hi, Zh), __fma_rn(-q, D.lo, Zl)), r);
+    const double eq = __dmul_rn(__dadd_rn(__fma_rn(-q, Dh, Zh), __fma_rn(-q, Dl, Zl)), r);
     const dd t = two_sum(hi, q);
     hi = t.hi;
     lo = __dadd_rn(lo, __dadd_rn(t.lo, eq));
@@ -399,24 +403,25 @@ struct PoleResult {
 // dd corner element of Eq. (b_ob): b = (1/zeta_i^2)(1/rho + sum_{j != i} zeta_j^2/(d_j - d_i)),
 // rounded to binary64 (the arrowhead is formed in working precision).
 template <int L>
-__device__ __forceinline__ double corner_b(const double* __restrict__ d, const double* __restrict__ z, int n, int i,
+__device__ __forceinline__ double corner_b(const double* __restrict__ d, const double* __restrict__ zz,
+                                           const double* __restrict__ zl, int n, int i,
                                            double rho, int lane, unsigned gm, double* wn2) {
   double sq;
-  dd acc = dd_pole_sum<L>(d, z, n, i, d[i], lane, gm, &sq);
+  dd acc = dd_pole_sum<L>(d, zz, zl, n, i, d[i], lane, gm, &sq);
   dd B = dd_add(dd_div({1.0, 0.0}, {rho, 0.0}), acc);
-  dd Zi = two_prod(z[i], z[i]);
+  const dd Zi = {zz[i], zl[i]};
   *wn2 = sq / Zi.hi;
   return dd_to_double(dd_div(B, Zi));
 }
 
 // Brackets of |nu| from the shift test (see the derivation in k_solve's comment).
 template <int L>
-__device__ PoleResult solve_pole(const double* __restrict__ d, const double* __restrict__ z,
+__device__ PoleResult solve_pole(const double* __restrict__ d, const double* __restrict__ zl,
                                  const double* __restrict__ zz, int n, double rho, int k, int i, double alo,
                                  double ahi, int cap, bool fast, int lane, unsigned gm) {
   PoleResult r;
   double wn2;
-  double b = corner_b<L>(d, z, n, i, rho, lane, gm, &wn2);
+  double b = corner_b<L>(d, zz, zl, n, i, rho, lane, gm, &wn2);
   double side = (i == k) ? 1.0 : -1.0;
   double di = d[i];
   double inv_zi2 = 1.0 / zz[i];
@@ -507,12 +512,12 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
 // (lambda = sigma + mu); f(sigma) == 0 in double-double gives mu = 0.
 // ---------------------------------------------------------------------------------
 template <int L>
-__device__ double solve_nonpole(const double* __restrict__ d, const double* __restrict__ z,
+__device__ double solve_nonpole(const double* __restrict__ d, const double* __restrict__ zl,
                                 const double* __restrict__ zz, int n, double rho, double sigma, int above, int below,
                                 int cap, bool fast, int lane, unsigned gm, bool* ok, int* steps_out = nullptr) {
   // above / below: indices of the poles next to sigma (-1: none on that side)
   double un2, cub;
-  dd acc = dd_pole_sum<L>(d, z, n, -1, sigma, lane, gm, &un2, &cub);
+  dd acc = dd_pole_sum<L>(d, zz, zl, n, -1, sigma, lane, gm, &un2, &cub);
   dd f = dd_add({1.0, 0.0}, two_prod(acc.hi, rho));
   f = dd_add(f, {__dmul_rn(acc.lo, rho), 0.0});
   *ok = true;
