@@ -27,6 +27,14 @@
 #include "dpr1_internal.cuh"
 #include "dpr1_solve.cuh"
 
+// launch shape of the remedies kernel: one block-wide group per flagged eigenvalue
+#ifndef DPR1_FIX_THREADS
+#define DPR1_FIX_THREADS 256
+#endif
+#ifndef DPR1_FIX_BLOCKS_PER_SM
+#define DPR1_FIX_BLOCKS_PER_SM 2
+#endif
+
 namespace dpr1 {
 
 // ---------------------------------------------------------------------------------
@@ -385,7 +393,7 @@ __global__ void k_classify(Prob pb, Ws w, double T_Knu) {
 //       the open interval (d_k, d_{k-1}) if it falls on a pole, and solve_nonpole.
 // ---------------------------------------------------------------------------------
 template <int L>
-__global__ void __launch_bounds__(256) k_fix(Prob pb, Ws w, double T_Knu, int cap, bool fast) {
+__global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double T_Knu, int cap, bool fast) {
   if (*w.status & ST_FATAL) return;
   const int nfix = (int)w.counters[C_FIX_N];
   const int lane = threadIdx.x & (L - 1);
@@ -784,7 +792,8 @@ static void launch_solve_fix(const Prob& pb, const Ws& w, const Options& o, int 
   if (cg > sm_count() * 8) cg = sm_count() * 8;
   k_classify<<<cg > 0 ? (int)cg : 1, 256, 0, st>>>(pb, w, o.T_Knu);
   // the flagged eigenvalues are few: one block of 256 threads each keeps the GPU busy
-  k_fix<256><<<sm_count() * 2, 256, 0, st>>>(pb, w, o.T_Knu, o.cap, o.fast);
+  k_fix<DPR1_FIX_THREADS><<<sm_count() * DPR1_FIX_BLOCKS_PER_SM, DPR1_FIX_THREADS, 0, st>>>(pb, w, o.T_Knu, o.cap,
+                                                                                          o.fast);
   record(o, 2, st);
 }
 
