@@ -192,7 +192,7 @@ __global__ void k_scan(Prob pb, Ws w) {
 }
 
 // ---------------------------------------------------------------------------------
-// k_deflate: exact deflation of Sec. 1, one thread per problem that needs it.  Ties: the
+// k_deflate: exact deflation of Sec. 1 for the problems that need it.  Ties: the
 // non-zero weights of a group of equal poles are rotated into its first non-zero member
 // by a chain of Givens rotations; the survivor keeps zeta = +-||group||, every other
 // member becomes an eigenpair (d_group, Q^T e_m).  Writes the reduced problem at the
@@ -201,54 +201,108 @@ __global__ void k_scan(Prob pb, Ws w) {
 // (dlist, local indices) and for tie members the prefix norms rprev (before) and rcur
 // (including) them.
 // ---------------------------------------------------------------------------------
+// One group of equal poles, from position j to its end e (serial; lane 0).
+__device__ int deflate_group(const Ws& w, int64_t base, const double* d, const double* z, int n, int j, int* nr,
+                             int* nd) {
+  int e = j;
+  while (e + 1 < n && d[e + 1] == d[j]) e++;
+  int first = -1;
+  double r = 0.0;
+  for (int q = j; q <= e; q++) {
+    w.gst[base + q] = j;
+    if (zero_weight(z[q])) {
+      w.src[base + q] = -1; w.coef[base + q] = 0.0; w.rprev[base + q] = 0.0; w.rcur[base + q] = 0.0;
+      w.dlist[base + (*nd)++] = q;
+      continue;
+    }
+    double rp = r;
+    r = hypot(r, z[q]);
+    w.rprev[base + q] = rp; w.rcur[base + q] = r;
+    if (first < 0) first = q;
+    else w.dlist[base + (*nd)++] = q;
+  }
+  if (first >= 0) {
+    double zs = (z[first] > 0.0) ? r : -r;
+    for (int q = j; q <= e; q++) {
+      if (zero_weight(z[q])) continue;
+      w.src[base + q] = *nr;
+      w.coef[base + q] = z[q] / zs;
+    }
+    w.dr[base + *nr] = d[j];
+    w.zr[base + *nr] = zs;
+    const double zq = __dmul_rn(zs, zs);
+    w.zz[base + *nr] = zq;
+    w.zl[base + *nr] = __fma_rn(zs, zs, -zq);
+    (*nr)++;
+  }
+  return e + 1;
+}
+
+// One warp per problem: chunks of 32 positions.  A chunk in which no pole equals a
+// neighbour holds only single-member groups (a survivor with coef 1, or a zero weight),
+// placed with ballot prefix counts; a chunk that a group of equal poles touches is done
+// serially by lane 0, group by group, to the end of the last group it starts.  The
+// outputs are those of the serial scan (same order of survivors and deflated positions).
 __global__ void k_deflate(Prob pb, Ws w) {
   if (*w.status & ST_FATAL) return;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < pb.P; p += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int p = wid; p < pb.P; p += nw) {
     unsigned ps = w.pst[p];
     if (!(ps & PT_DEFLATE) || (ps & PT_TRIVIAL)) continue;
     const int64_t base = p_base(pb, p);
     const int n = p_size(pb, p);
     const double* d = pb.d + base;
     const double* z = pb.z + base;
-    int nr = 0, nd = 0;
-    int j = 0;
-    while (j < n) {
-      int e = j;
-      while (e + 1 < n && d[e + 1] == d[j]) e++;
-      int first = -1;
-      double r = 0.0;
-      for (int q = j; q <= e; q++) {
-        w.gst[base + q] = j;
-        if (zero_weight(z[q])) {
-          w.src[base + q] = -1; w.coef[base + q] = 0.0; w.rprev[base + q] = 0.0; w.rcur[base + q] = 0.0;
-          w.dlist[base + nd++] = q;
-          continue;
+    int nr = 0, nd = 0, q0 = 0;
+    while (q0 < n) {
+      const int q = q0 + lane;
+      const bool in = q < n;
+      const double dq = in ? d[q] : 0.0, zq = in ? z[q] : 0.0;
+      const bool tie = in && ((q > 0 && d[q - 1] == dq) || (q + 1 < n && d[q + 1] == dq));
+      if (__ballot_sync(FULL, tie) == 0u) {
+        const bool zw = in && zero_weight(zq);
+        const bool keep = in && !zw;
+        const unsigned km = __ballot_sync(FULL, keep), dm = __ballot_sync(FULL, zw);
+        const unsigned below = (1u << lane) - 1u;
+        if (in) {
+          w.gst[base + q] = q;
+          if (zw) {
+            w.src[base + q] = -1; w.coef[base + q] = 0.0; w.rprev[base + q] = 0.0; w.rcur[base + q] = 0.0;
+            w.dlist[base + nd + __popc(dm & below)] = q;
+          } else {
+            const int r = nr + __popc(km & below);
+            w.src[base + q] = r;
+            w.coef[base + q] = 1.0;                       // zeta_q / zeta_q
+            w.rprev[base + q] = 0.0;
+            w.rcur[base + q] = fabs(zq);                  // hypot(0, zeta_q)
+            w.dr[base + r] = dq;
+            w.zr[base + r] = zq;
+            const double zz = __dmul_rn(zq, zq);
+            w.zz[base + r] = zz;
+            w.zl[base + r] = __fma_rn(zq, zq, -zz);
+          }
         }
-        double rp = r;
-        r = hypot(r, z[q]);
-        w.rprev[base + q] = rp; w.rcur[base + q] = r;
-        if (first < 0) first = q;
-        else w.dlist[base + nd++] = q;
-      }
-      if (first >= 0) {
-        double zs = (z[first] > 0.0) ? r : -r;
-        for (int q = j; q <= e; q++) {
-          if (zero_weight(z[q])) continue;
-          w.src[base + q] = nr;
-          w.coef[base + q] = z[q] / zs;
+        nr += __popc(km);
+        nd += __popc(dm);
+        q0 += 32;
+      } else {
+        int j = q0;
+        if (lane == 0) {
+          while (j < q0 + 32 && j < n) j = deflate_group(w, base, d, z, n, j, &nr, &nd);
         }
-        w.dr[base + nr] = d[j];
-        w.zr[base + nr] = zs;
-        const double zq = __dmul_rn(zs, zs);
-        w.zz[base + nr] = zq;
-        w.zl[base + nr] = __fma_rn(zs, zs, -zq);
-        nr++;
+        __syncwarp();
+        nr = __shfl_sync(FULL, nr, 0);
+        nd = __shfl_sync(FULL, nd, 0);
+        q0 = __shfl_sync(FULL, j, 0);
       }
-      j = e + 1;
     }
-    w.nred[p] = nr;
-    w.ndefl[p] = nd;
-    atomicAdd(&w.counters[C_DEFL], (unsigned)nd);
+    if (lane == 0) {
+      w.nred[p] = nr;
+      w.ndefl[p] = nd;
+      atomicAdd(&w.counters[C_DEFL], (unsigned)nd);
+    }
   }
 }
 
@@ -816,7 +870,8 @@ static dpr1_status run_table(const Prob& pb, void* workspace, const Options& o, 
   if (sg < 1) sg = 1;
   const int sgrid = (int)sg;
   k_scan<<<sgrid, 256, 0, st>>>(pb, w);
-  int dg = (pb.P + 127) / 128;
+  int dg = (pb.P + 3) / 4;                              // a warp per problem
+  if (dg > sms * 8) dg = sms * 8;
   k_deflate<<<dg > 0 ? dg : 1, 128, 0, st>>>(pb, w);
   int L = o.lanes ? o.lanes : (avg_n <= 96 ? 8 : (avg_n <= 384 ? 16 : 32));
   int groups_per_block = (32 * o.warps) / L;
