@@ -230,7 +230,8 @@ def bench_batched(B, dev, steps):
         ms.append(e0.elapsed_time(e1))
     batched_ms = statistics.mean(ms)
     # the same graph-captured launch with the accelerated bracketed solve
-    opts_a = B.default_options(lanes=shape[0], warps_per_block=shape[1], blocks_per_sm=shape[2],
+    shape_a = tune.tune(sizes, device=dev, zero_finder=B.ACCELERATED)
+    opts_a = B.default_options(lanes=shape_a[0], warps_per_block=shape_a[1], blocks_per_sm=shape_a[2],
                                zero_finder=B.ACCELERATED)
     with torch.cuda.stream(side):
         bt.solve(dt, zt, rt, options=opts_a)
@@ -283,7 +284,8 @@ def bench_batched(B, dev, steps):
             "speedup_vs_loop": loop_ms / batched_ms, "unit": "eigenpairs/s",
             "accelerated_ms": accel_ms, "accelerated_value": total / (accel_ms * 1e-3),
             "launch": "one CUDA-graph replay of dpr1_eig_batched vs 4096 dpr1_eig calls from Python",
-            "tuned_shape": {"lanes": shape[0], "warps_per_block": shape[1], "blocks_per_sm": shape[2]}}
+            "tuned_shape": {"lanes": shape[0], "warps_per_block": shape[1], "blocks_per_sm": shape[2]},
+            "tuned_shape_accelerated": {"lanes": shape_a[0], "warps_per_block": shape_a[1], "blocks_per_sm": shape_a[2]}}
 
 
 def bench_fwd_bwd(B, dev, n, seed, steps, with_w):

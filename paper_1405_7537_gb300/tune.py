@@ -21,14 +21,14 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "tune_c
 CANDIDATES = [(l, w, b) for l in (8, 16, 32) for w in (4, 8) for b in (1, 2, 4)]
 
 
-def size_key(sizes):
+def size_key(sizes, zero_finder=0):
     sizes = np.asarray(sizes, dtype=np.int64)
     sizes = sizes[sizes > 0]
     if sizes.size == 0:
         return "empty"
     h = np.bincount(np.minimum(np.log2(sizes).astype(int), 20), minlength=21)
     frac = np.round(h / h.sum(), 1)
-    return "%s|%s" % (torch.cuda.get_device_name(), ",".join("%g" % f for f in frac))
+    return "%s|zf%d|%s" % (torch.cuda.get_device_name(), zero_finder, ",".join("%g" % f for f in frac))
 
 
 def _load():
@@ -70,9 +70,10 @@ def _sample_batch(sizes, max_total, rng):
     return pick, np.concatenate(ds), np.concatenate(zs), rng.uniform(0.1, 10, pick.size)
 
 
-def tune(sizes, device="cuda", max_total=200_000, reps=2, force=False, verbose=False):
-    """Returns (lanes, warps_per_block, blocks_per_sm) for this size distribution."""
-    key = size_key(sizes)
+def tune(sizes, device="cuda", max_total=200_000, reps=2, force=False, verbose=False, zero_finder=0):
+    """Returns (lanes, warps_per_block, blocks_per_sm) for this size distribution and zero finder
+    (the accelerated solve does a few evaluations per eigenvalue and prefers other shapes)."""
+    key = size_key(sizes, zero_finder)
     cache = _load()
     if not force and key in cache:
         return tuple(cache[key]["shape"])
@@ -84,7 +85,8 @@ def tune(sizes, device="cuda", max_total=200_000, reps=2, force=False, verbose=F
     rt = torch.tensor(rho, device=device)
     best, best_ms, results = None, float("inf"), {}
     for shape in CANDIDATES:
-        o = B.default_options(lanes=shape[0], warps_per_block=shape[1], blocks_per_sm=shape[2])
+        o = B.default_options(lanes=shape[0], warps_per_block=shape[1], blocks_per_sm=shape[2],
+                              zero_finder=zero_finder)
         bt.solve(dt, zt, rt, options=o)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -106,7 +108,7 @@ def tune(sizes, device="cuda", max_total=200_000, reps=2, force=False, verbose=F
     return best
 
 
-def options_for(sizes, device="cuda", **kw):
-    """dpr1_options with the tuned launch shape for this size distribution."""
-    l, w, b = tune(sizes, device=device, **kw)
-    return B.default_options(lanes=l, warps_per_block=w, blocks_per_sm=b)
+def options_for(sizes, device="cuda", zero_finder=0, **kw):
+    """dpr1_options with the tuned launch shape for this size distribution and zero finder."""
+    l, w, b = tune(sizes, device=device, zero_finder=zero_finder, **kw)
+    return B.default_options(lanes=l, warps_per_block=w, blocks_per_sm=b, zero_finder=zero_finder)

@@ -149,3 +149,27 @@ def test_batch_argument_errors(B):
     with pytest.raises(B.DPR1Error) as e:
         bt.solve(cu(d), cu(z), cu([1.0, 2.0]), check=True)
     assert e.value.code == 1
+
+
+def test_autotuner_per_zero_finder(B, tmp_path, monkeypatch):
+    """The tuner times every candidate shape on a sample of the size mix, caches the winner
+    under a key of the size histogram, the GPU and the zero finder, and the tuned options
+    solve the batch to the same results as the default shape."""
+    from paper_1405_7537_gb300 import tune
+    monkeypatch.setattr(tune, "CACHE", str(tmp_path / "tune_cache.json"))
+    offs, d, z, rho = W.batch(P=64, seed=4, nmin=16, nmax=300)
+    sizes = np.diff(offs)
+    shapes = {}
+    for zf in (0, 1):
+        shapes[zf] = tune.tune(sizes, max_total=20_000, reps=1, zero_finder=zf)
+        assert shapes[zf] in tune.CANDIDATES
+        assert tune.tune(sizes, zero_finder=zf) == shapes[zf]          # cached
+    import json
+    keys = list(json.load(open(tune.CACHE)).keys())
+    assert len(keys) == 2 and any("|zf0|" in k for k in keys) and any("|zf1|" in k for k in keys)
+    bt = B.Batch(sizes)
+    dt, zt, rt = cu(d), cu(z), cu(rho)
+    bt.solve(dt, zt, rt, options=tune.options_for(sizes, zero_finder=1), check=True)
+    lam1 = bt.lam.clone()
+    bt.solve(dt, zt, rt, check=True)
+    assert torch.max(torch.abs(lam1 - bt.lam) / torch.abs(bt.lam)).item() <= tol(int(sizes.max()))
