@@ -34,6 +34,10 @@
 #ifndef DPR1_FIX_BLOCKS_PER_SM
 #define DPR1_FIX_BLOCKS_PER_SM 2
 #endif
+// batches of 64 or more problems up to this mean size run the remedies one warp per item
+#ifndef DPR1_FIX_WARP_MAX_N
+#define DPR1_FIX_WARP_MAX_N 2048
+#endif
 
 namespace dpr1 {
 
@@ -838,16 +842,27 @@ static void record(const Options& o, int t, cudaStream_t st) {
 }
 
 template <int L>
-static void launch_solve_fix(const Prob& pb, const Ws& w, const Options& o, int grid, cudaStream_t st) {
+static void launch_solve_fix(const Prob& pb, const Ws& w, const Options& o, int grid, double avg_n,
+                             cudaStream_t st) {
   record(o, 0, st);
   k_solve<L><<<grid, 32 * o.warps, 0, st>>>(pb, w, o.cap, o.fast);
   record(o, 1, st);
   int64_t cg = (pb.total + 255) / 256;
   if (cg > sm_count() * 8) cg = sm_count() * 8;
   k_classify<<<cg > 0 ? (int)cg : 1, 256, 0, st>>>(pb, w, o.T_Knu);
-  // the flagged eigenvalues are few: one block of 256 threads each keeps the GPU busy
-  k_fix<DPR1_FIX_THREADS><<<sm_count() * DPR1_FIX_BLOCKS_PER_SM, DPR1_FIX_THREADS, 0, st>>>(pb, w, o.T_Knu, o.cap,
-                                                                                          o.fast);
+  if (pb.P < 64 || avg_n > DPR1_FIX_WARP_MAX_N) {
+    // few flagged eigenvalues (one or a few problems, or large ones): a block-wide group
+    // each finishes every item soonest
+    int64_t fg = pb.total;                            // at most one block per eigenpair
+    if (fg > sm_count() * DPR1_FIX_BLOCKS_PER_SM) fg = sm_count() * DPR1_FIX_BLOCKS_PER_SM;
+    k_fix<DPR1_FIX_THREADS><<<fg > 0 ? (int)fg : 1, DPR1_FIX_THREADS, 0, st>>>(pb, w, o.T_Knu, o.cap, o.fast);
+  } else {
+    // many small problems, many flagged items: one warp each (a block-wide group would
+    // leave most of its threads idle and pay a barrier per evaluation)
+    int64_t fg = (pb.total + 7) / 8;                  // at most one warp per eigenpair
+    if (fg > sm_count() * 4) fg = sm_count() * 4;
+    k_fix<32><<<fg > 0 ? (int)fg : 1, 256, 0, st>>>(pb, w, o.T_Knu, o.cap, o.fast);
+  }
   record(o, 2, st);
 }
 
@@ -878,9 +893,9 @@ static dpr1_status run_table(const Prob& pb, void* workspace, const Options& o, 
   int64_t want_blocks = (pb.total + groups_per_block - 1) / groups_per_block;
   int grid = sms * o.bps;
   if (want_blocks < grid) grid = want_blocks > 0 ? (int)want_blocks : 1;
-  if (L == 8) launch_solve_fix<8>(pb, w, o, grid, st);
-  else if (L == 16) launch_solve_fix<16>(pb, w, o, grid, st);
-  else launch_solve_fix<32>(pb, w, o, grid, st);
+  if (L == 8) launch_solve_fix<8>(pb, w, o, grid, avg_n, st);
+  else if (L == 16) launch_solve_fix<16>(pb, w, o, grid, avg_n, st);
+  else launch_solve_fix<32>(pb, w, o, grid, avg_n, st);
   k_zero_detect<<<sgrid, 256, 0, st>>>(pb, w, o.T_zero);
   k_zero_solve<<<4, 128, 0, st>>>(pb, w, o.cap, o.fast);
   k_defl_positions<<<sgrid, 256, 0, st>>>(pb, w);
