@@ -11,8 +11,19 @@ is all eigenpairs of all ranks divided by the slowest rank's time.
 One JSON line is printed by rank 0.  Timing: W untimed warm-up steps, then K steps, each
 a full dpr1_eig call timed with CUDA events on the launching stream, L2 flushed (256 MiB
 write) before every step outside the timed events; nvidia-smi clocks are sampled during
-the timed region.  ``--impl reference`` times the CPU oracle (Algorithm 1 in binary64 on
-the host cores) on bounded samples of the same workload.
+the timed region.  The line carries the roofline of the solve kernel (algorithmic binary64
+operations over its event-timed duration, against the nominal peak; DRAM traffic from the
+committed ncu record while the kernel sources are unchanged), the CPU oracle on a bounded
+sample, the end-to-end rate through the binding from pinned host buffers (double-buffered
+outputs), and extra measurements (--extras; --only runs one alone at size --n):
+  fwd_bwd    forward and adjoint at n = 4096 (and n = 32768 with --large)
+  batched    4096 uneven problems in one graph replay against a per-problem loop
+  accel      the same workload with the accelerated bracketed solve
+  hermitian  the complex Hermitian problem (hard spectrum with random phases)
+  tridiag    divide and conquer for a random tridiagonal matrix, n = 4096
+  arrow      the arrowhead eigenproblem, n = 16384 poles
+``--impl reference`` times the CPU oracle (Algorithm 1 in binary64 on the host cores) on
+bounded samples of the same workload.
 """
 import argparse
 import hashlib
