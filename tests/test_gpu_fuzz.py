@@ -1,0 +1,110 @@
+"""Seeded randomized parity of dpr1_eig (both zero finders) on small problems of many shapes:
+uniform, clustered and graded poles, exact ties, zero and tiny weights, rho over twelve
+decades.  Irreducible problems are compared eigenvalue by eigenvalue and component by
+component with the oracle and binary128; deflated ones by eigenvalues, residual and
+orthogonality (eigenvectors of repeated eigenvalues are a basis choice)."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import run_gpu, tol
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1405_7537_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def random_problem(rng):
+    n = int(rng.integers(1, 81))
+    kind = rng.integers(0, 4)
+    if kind == 0:                                   # uniform
+        d = rng.uniform(-1, 1, n)
+    elif kind == 1:                                 # clusters of close poles
+        c = rng.uniform(-1, 1, max(1, n // 6))
+        d = rng.choice(c, n) + rng.choice([1.0, -1.0], n) * 10.0 ** rng.uniform(-12, -3, n)
+    elif kind == 2:                                 # graded over many decades
+        d = np.sign(rng.uniform(-1, 1, n)) * 10.0 ** rng.uniform(-10, 0, n)
+    else:                                           # exact ties
+        d = rng.choice(rng.uniform(-1, 1, max(1, n // 3)), n)
+    d = np.sort(d)[::-1].copy()
+    zk = rng.integers(0, 3)
+    if zk == 0:
+        z = rng.uniform(-1, 1, n)
+    elif zk == 1:
+        z = rng.choice([1.0, -1.0], n) * 10.0 ** rng.uniform(-12, 0, n)
+    else:
+        z = rng.uniform(-1, 1, n)
+        z[rng.random(n) < 0.2] = 0.0
+    rho = float(10.0 ** rng.uniform(-6, 6))
+    return d, z, rho
+
+
+def irreducible(d, z, rho):
+    return rho > 0 and not np.any(oracle.zero_weight(z)) and np.all(d[:-1] > d[1:])
+
+
+@pytest.mark.parametrize("zf", [0, 1])
+def test_fuzz_small_problems(B, zf):
+    rng = np.random.default_rng(20261203 + zf)
+    n_irr = 0
+    for case in range(160):
+        d, z, rho = random_problem(rng)
+        n = d.size
+        g = run_gpu(B, d, z, rho, zero_finder=zf)
+        lam = g["lam"]
+        if irreducible(d, z, rho):
+            n_irr += 1
+            r = oracle.eig_all(d, z, rho)
+            q = oracle.quad_all(d, z, rho)
+            lq = q["hi"] + q["lo"]
+            scale = np.maximum(np.abs(lq), 1e-300)
+            assert np.max(np.abs(lam - lq) / scale) <= tol(n), (case, "lambda vs binary128")
+            assert np.max(np.abs(lam - r["lam"]) / scale) <= tol(n), (case, "lambda vs oracle")
+            Vq = q["Vt"]
+            err = np.abs(g["Vt"] - Vq) / np.maximum(np.abs(Vq), 1e-300)
+            assert err.max() <= tol(n), (case, "vector vs binary128", float(err.max()))
+        else:
+            r = oracle.eig_full(d, z, rho)
+            A = np.diag(d) + rho * np.outer(z, z)
+            nA = max(np.linalg.norm(A, 2), 1e-300)
+            assert np.max(np.abs(lam - r["lam"])) <= tol(n) * nA, (case, "lambda (deflated)")
+            V = g["Vt"].T
+            assert np.max(np.abs(A @ V - V * lam[None, :])) <= 64 * n * 2.0 ** -53 * nA, (case, "residual")
+            assert np.max(np.abs(V.T @ V - np.eye(n))) <= 64 * n * 2.0 ** -53, (case, "orthogonality")
+    assert n_irr >= 40
+
+
+@pytest.mark.parametrize("zf", [0, 1])
+def test_fuzz_larger_irreducible(B, zf):
+    """Irreducible problems of 100 to 600 poles with clustered or graded poles and weights over
+    twelve decades: every eigenvalue and component against binary128."""
+    rng = np.random.default_rng(4242 + zf)
+    done = 0
+    while done < 12:
+        d, z, rho = random_problem(rng)
+        n = int(rng.integers(100, 601))
+        kind = rng.integers(0, 2)
+        if kind == 0:
+            c = rng.uniform(-1, 1, n // 8)
+            d = rng.choice(c, n) + rng.choice([1.0, -1.0], n) * 10.0 ** rng.uniform(-12, -3, n)
+        else:
+            d = np.sign(rng.uniform(-1, 1, n)) * 10.0 ** rng.uniform(-10, 0, n)
+        d = np.sort(d)[::-1].copy()
+        z = rng.choice([1.0, -1.0], n) * 10.0 ** rng.uniform(-12, 0, n)
+        if not irreducible(d, z, rho):
+            continue
+        done += 1
+        g = run_gpu(B, d, z, rho, zero_finder=zf)
+        q = oracle.quad_all(d, z, rho, threads=16)
+        lq = q["hi"] + q["lo"]
+        assert np.max(np.abs(g["lam"] - lq) / np.abs(lq)) <= tol(n), (done, n, rho)
+        err = np.abs(g["Vt"] - q["Vt"]) / np.maximum(np.abs(q["Vt"]), 1e-300)
+        assert err.max() <= tol(n), (done, n, rho, float(err.max()))
