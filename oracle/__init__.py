@@ -72,8 +72,8 @@ def lib():
         for name in ("oracle_dd_add", "oracle_dd_mul", "oracle_dd_div"):
             getattr(L, name).argtypes = [ctypes.c_double] * 4 + [_dp]
         L.oracle_default_opts.argtypes = [ctypes.POINTER(Opts)]
-        L.oracle_arroweig.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp, _dp,
-                                      _ip, _ip]
+        L.oracle_arroweig.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(Opts),
+                                      _dp, _dp, _dp, _dp, _ip, _ip, _dp]
         L.quad_arrow_eigpair.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp]
         _LIB = L
     return _LIB
@@ -447,27 +447,33 @@ def _split_run(run, m, threads):
             list(ex.map(run, np.array_split(np.arange(m), threads)))
 
 
-def arrow_eig_all(d, z, alpha, ks=None, threads=1):
+def arrow_eig_all(d, z, alpha, ks=None, threads=1, opts=None):
     """Eigenpairs of the arrowhead [diag(d) z; z^T alpha] (order n + 1, irreducible) by the
-    steps of Algorithm 1 on its shifted inverse (``oracle_arroweig``): dict(lam, sigma, mu,
-    shift, Vt) with rows of length n + 1, for k in ks (default 0..n)."""
+    steps of Algorithm 1 on its shifted inverse, with the remedies of Sec. 2 for large K_nu
+    and the near-zero recompute (``oracle_arroweig``; opts as for ``dpr1eig``): dict(lam,
+    sigma, mu, shift, flags, K_nu, Vt) with rows of length n + 1, for k in ks (default 0..n).
+    flags: 1 R1, 2 R2, | 4 recomputed from A^{-1}; shift -1 for a non-pole shift; K_nu of the
+    first shift."""
     d, z = _f64(d), _f64(z)
     n = d.size
     ks = np.arange(n + 1) if ks is None else np.asarray(ks, dtype=np.int64)
     m = ks.size
+    o = default_opts() if opts is None else opts
     out = dict(lam=np.empty(m), sigma=np.empty(m), mu=np.empty(m), shift=np.empty(m, dtype=np.int32),
-               Vt=np.empty((m, n + 1)))
+               flags=np.empty(m, dtype=np.int32), K_nu=np.empty(m), Vt=np.empty((m, n + 1)))
 
     def run(idx):
         v = np.empty(n + 1)
-        lam, sig, mu = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
-        sh, st = ctypes.c_int(), ctypes.c_int()
+        lam, sig, mu, K = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        sh, fl = ctypes.c_int(), ctypes.c_int()
         for p in idx:
-            rc = lib().oracle_arroweig(n, _ptr(d), _ptr(z), float(alpha), int(ks[p]), ctypes.byref(lam), _ptr(v),
-                                       ctypes.byref(sig), ctypes.byref(mu), ctypes.byref(sh), ctypes.byref(st))
+            rc = lib().oracle_arroweig(n, _ptr(d), _ptr(z), float(alpha), int(ks[p]), ctypes.byref(o),
+                                       ctypes.byref(lam), _ptr(v), ctypes.byref(sig), ctypes.byref(mu),
+                                       ctypes.byref(sh), ctypes.byref(fl), ctypes.byref(K))
             if rc:
                 raise ValueError("oracle_arroweig failed with code %d" % rc)
             out["lam"][p], out["sigma"][p], out["mu"][p], out["shift"][p] = lam.value, sig.value, mu.value, sh.value
+            out["flags"][p], out["K_nu"][p] = fl.value, K.value
             out["Vt"][p] = v
 
     _split_run(run, m, threads)

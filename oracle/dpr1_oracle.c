@@ -179,7 +179,9 @@ typedef double (*o_secular_fn)(const void* ctx, double nu);
 static double o_bisect(o_secular_fn phi, const void* ctx, double s, double a_lo, double a_hi,
                        int below_sign, int* steps_out) {
   int steps = 0;
-  if (a_lo < 0.0) a_lo = 0.0;
+  /* the bracket is on |nu| >= 0; -0.0 (and NaN) become +0.0 so that the bit patterns of the
+     two ends are ordered like their values */
+  if (!(a_lo > 0.0)) a_lo = 0.0;
   if (!(a_hi > a_lo)) a_hi = (a_lo > 0.0) ? a_lo * 2.0 : 1.0;
   /* make sure the far end is past the root */
   for (int t = 0; t < 2100; t++) {
@@ -642,14 +644,14 @@ int oracle_backward_rows(int n, const double* d, const double* z, double rho, in
   return 0;
 }
 
-/* ------------------------------------------------------------------------- */
 /* Real symmetric arrowhead matrices A = [D z; z^T alpha] of order n + 1      */
 /* (the companion problem the paper relates its method to, Sec. 1).  The same */
 /* steps as Algorithm 1: shift to the nearer pole d_i, form the inverse of    */
 /* A - d_i I, which is again an arrowhead, bisect its secular equation for    */
 /* the extreme eigenvalue nu, lambda = d_i + 1/nu, v = [x; -1] / ||.||,       */
-/* x = (D - lambda I)^{-1} z.  Irreducible input only (d strictly decreasing, */
-/* no zero weight); no remedies.                                              */
+/* x = (D - lambda I)^{-1} z; then the remedies of Sec. 2 when K_nu is large  */
+/* and the near-zero recompute.  Irreducible input only (d strictly           */
+/* decreasing, no zero weight).                                               */
 /*                                                                            */
 /* (A - d_i I)^{-1}: with Delta_j = d_j - d_i (j != i) it has the diagonal    */
 /* delta_j = 1/Delta_j, b at position i and 0 at position n, and the border   */
@@ -658,6 +660,14 @@ int oracle_backward_rows(int n, const double* d, const double* z, double rho, in
 /* (the DPR1 corner of Eq. (b_ob) with 1/rho replaced by d_i - alpha).  Its   */
 /* secular function has one more pole, at 0, of weight 1/zeta_i^2:            */
 /*   g(nu) = b - nu - sum_{j != i} w_j^2/(delta_j - nu) + (1/zeta_i^2)/nu.    */
+/*                                                                            */
+/* (A - sigma I)^{-1} for sigma not a pole (R2, and sigma = 0 for the         */
+/* near-zero recompute): with the Schur complement                            */
+/*   f(sigma) = alpha - sigma - sum_j zeta_j^2 / (d_j - sigma)                */
+/* of D - sigma I it equals diag(e, 0) + gamma u u^T, e_j = 1/(d_j - sigma),  */
+/* u = [zeta_j/(d_j - sigma); -1], gamma = 1/f(sigma): a DPR1 matrix of order */
+/* n + 1 whose extreme eigenvalue is 1/(lambda - sigma) for the eigenvalue    */
+/* lambda next to sigma (the arrowhead form of Eq. (gamma)).                  */
 /* ------------------------------------------------------------------------- */
 typedef struct {
   int n, i;
@@ -676,9 +686,132 @@ static double o_g_ah(const void* vctx, double nu) {
   return ((c->b - nu) - s) + c->wz2 / nu;
 }
 
-/* eigenvalue k (0-based, 0..n) of the arrowhead; v has n + 1 entries */
-int oracle_arroweig(int n, const double* d, const double* z, double alpha, int k, double* lambda_out,
-                    double* v, double* sigma_out, double* mu_out, int* shift_out, int* steps_out) {
+/* Forms the arrowhead inverse of A - d_i I: delta, w and the corner b (double-double). */
+static void o_ah_form(int n, const double* d, const double* z, double alpha, int i, double* delta, double* w,
+                      o_ah_ctx* c) {
+  odd_t acc = o_two_sum(d[i], -alpha);
+  for (int j = 0; j < n; j++) {
+    if (j == i) { delta[j] = 0.0; w[j] = 0.0; continue; }
+    delta[j] = 1.0 / (d[j] - d[i]);
+    w[j] = -(delta[j] * z[j]) / z[i];
+    acc = o_add(acc, o_div(o_two_prod(z[j], z[j]), o_two_sum(d[j], -d[i])));
+  }
+  odd_t bb = o_div(acc, o_two_prod(z[i], z[i]));
+  double wz = 1.0 / z[i];
+  c->n = n; c->i = i; c->delta = delta; c->w = w;
+  c->b = bb.hi + bb.lo;
+  c->wz2 = wz * wz;
+}
+
+/* Extreme eigenvalue of the arrowhead inverse, side = +1 rightmost, -1 leftmost.  Weyl
+   bracket: within ||border|| of max(b, max delta, 0) (rightmost) or min(b, min delta, 0)
+   (leftmost); the poles of g are the delta_j and 0. */
+static double o_ah_extreme(const o_ah_ctx* c, int side, int* steps) {
+  double wn2 = c->wz2, dmax = 0.0, dmin = 0.0;
+  for (int j = 0; j < c->n; j++) {
+    if (j == c->i) continue;
+    wn2 += c->w[j] * c->w[j];
+    if (c->delta[j] > dmax) dmax = c->delta[j];
+    if (c->delta[j] < dmin) dmin = c->delta[j];
+  }
+  double wn = sqrt(wn2);
+  if (side > 0) {
+    double lo = c->b > dmax ? c->b : dmax;
+    return o_bisect(o_g_ah, c, 1.0, lo, lo + wn, +1, steps);
+  }
+  double up = c->b < dmin ? c->b : dmin;
+  return o_bisect(o_g_ah, c, -1.0, -up, -up + wn, -1, steps);
+}
+
+typedef struct {
+  double nu, mu, K_nu;
+  int steps;
+} o_ah_pole;
+
+/* Solve at pole i for eigenvalue k: the extreme eigenvalue of (A - d_i I)^{-1} on the side
+   of lambda_k (rightmost when i == k, lambda_k > d_i; leftmost when i == k - 1) and
+   K_nu = ||(A - d_i I)^{-1}||_2 / |nu| (Eq. (K0)), the norm being the larger of the
+   |extreme eigenvalues|, both by bisection. */
+static void o_ah_solve_at_pole(int n, const double* d, const double* z, double alpha, int k, int i,
+                               double* delta, double* w, o_ah_pole* r) {
+  o_ah_ctx c;
+  o_ah_form(n, d, z, alpha, i, delta, w, &c);
+  int side = (i == k) ? +1 : -1;
+  int steps = 0;
+  double nu = o_ah_extreme(&c, side, &steps);
+  double other = o_ah_extreme(&c, -side, NULL);
+  double nrm = fabs(nu) > fabs(other) ? fabs(nu) : fabs(other);
+  r->nu = nu; r->mu = 1.0 / nu; r->K_nu = nrm / fabs(nu); r->steps = steps;
+}
+
+typedef struct {
+  int n;
+  const double* e;   /* 1/(d_j - sigma) */
+  const double* u;   /* zeta_j/(d_j - sigma) */
+  double gamma;
+} o_ahinv_ctx;
+
+/* h(nu) = 1 + gamma (sum_j u_j^2/(e_j - nu) + 1/(0 - nu)), the secular function of
+   diag(e, 0) + gamma u u^T with u_n = -1. */
+static double o_h_ahinv(const void* vctx, double nu) {
+  const o_ahinv_ctx* c = (const o_ahinv_ctx*)vctx;
+  double s = 0.0;
+  for (int j = 0; j < c->n; j++) s += c->u[j] * c->u[j] / (c->e[j] - nu);
+  return 1.0 + c->gamma * (s - 1.0 / nu);
+}
+
+/* Non-pole shift sigma: returns 1 and mu (lambda = sigma + mu), or 0 when f(sigma) is zero
+   in double-double (lambda = sigma, mu = 0). */
+static int o_ah_solve_nonpole(int n, const double* d, const double* z, double alpha, double sigma, double* e,
+                              double* u, double* mu_out, int* steps) {
+  odd_t f = o_two_sum(alpha, -sigma);
+  for (int j = 0; j < n; j++)
+    f = o_add(f, o_neg(o_div(o_two_prod(z[j], z[j]), o_two_sum(d[j], -sigma))));
+  if (f.hi == 0.0 && f.lo == 0.0) { *mu_out = 0.0; if (steps) *steps = 0; return 0; }
+  odd_t gdd = o_div(o_from(1.0), f);
+  double gamma = gdd.hi + gdd.lo;
+  double emax = 0.0, emin = 0.0, un2 = 1.0;   /* the pole at 0 and u_n^2 = 1 */
+  for (int j = 0; j < n; j++) {
+    double dj = d[j] - sigma;
+    e[j] = 1.0 / dj;
+    u[j] = z[j] / dj;
+    un2 += u[j] * u[j];
+    if (e[j] > emax) emax = e[j];
+    if (e[j] < emin) emin = e[j];
+  }
+  o_ahinv_ctx c = {n, e, u, gamma};
+  double nu;
+  /* gamma > 0: rightmost eigenvalue in [max(e, 0), max(e, 0) + gamma ||u||^2];
+     gamma < 0: leftmost, mirrored; h < 0 on the pole side in both cases */
+  if (gamma > 0) nu = o_bisect(o_h_ahinv, &c, 1.0, emax, emax + gamma * un2, -1, steps);
+  else nu = o_bisect(o_h_ahinv, &c, -1.0, -emin, -emin - gamma * un2, -1, steps);
+  *mu_out = 1.0 / nu;
+  return 1;
+}
+
+/* Eigenvector [x; -1] / ||.||, x_j = zeta_j / ((d_j - sigma) - mu), scaled 2-norm. */
+static void o_ah_vector(int n, const double* d, const double* z, double sigma, double mu, double* v) {
+  double m = 1.0;
+  for (int j = 0; j < n; j++) {
+    double x = z[j] / ((d[j] - sigma) - mu);
+    v[j] = x;
+    if (fabs(x) > m) m = fabs(x);
+  }
+  v[n] = -1.0;
+  double s = 0.0;
+  for (int j = 0; j <= n; j++) { double t = v[j] / m; s += t * t; }
+  double r = sqrt(s);
+  for (int j = 0; j <= n; j++) v[j] = (v[j] / m) / r;
+}
+
+/* Eigenvalue k (0-based, 0..n) of the arrowhead; v has n + 1 entries.  opt: T_Knu, T_zero
+   and remedies as for oracle_dpr1eig (NULL: defaults).  flags_out: remedy (1 R1, 2 R2) |
+   4 when lambda was recomputed from A^{-1}.  shift_out: final pole, -1 for a non-pole shift. */
+int oracle_arroweig(int n, const double* d, const double* z, double alpha, int k, const oracle_opts* opt_in,
+                    double* lambda_out, double* v, double* sigma_out, double* mu_out, int* shift_out,
+                    int* flags_out, double* K_out) {
+  oracle_opts opt;
+  if (opt_in) opt = *opt_in; else oracle_default_opts(&opt);
   if (n < 1 || k < 0 || k > n) return 1;
   for (int j = 0; j < n; j++) {
     if (z[j] == 0.0 || (j + 1 < n && !(d[j] > d[j + 1]))) return 3;   /* reducible */
@@ -689,66 +822,72 @@ int oracle_arroweig(int n, const double* d, const double* z, double alpha, int k
   /* shift: lambda_0 > d_0 (pole 0), lambda_n < d_{n-1} (pole n-1); otherwise
      lambda_k lies in (d_k, d_{k-1}) and f(lambda) = alpha - lambda - sum z_j^2/(d_j - lambda),
      decreasing there, is evaluated at the midpoint: f < 0 puts lambda in the lower half */
-  int i, side;
-  if (k == 0) { i = 0; side = 1; }
-  else if (k == n) { i = n - 1; side = -1; }
+  int i;
+  if (k == 0) i = 0;
+  else if (k == n) i = n - 1;
   else {
     double tau = (d[k - 1] - d[k]) / 2.0;
     double s = 0.0;
     for (int j = 0; j < n; j++) s += z[j] * z[j] / ((d[j] - d[k]) - tau);
     double F = (alpha - d[k]) - tau - s;
-    if (F < 0.0) { i = k; side = 1; } else { i = k - 1; side = -1; }
+    i = (F < 0.0) ? k : k - 1;
   }
-  /* the arrowhead inverse of A - d_i I */
-  odd_t acc = o_two_sum(d[i], -alpha);
-  for (int j = 0; j < n; j++) {
-    if (j == i) { delta[j] = 0.0; w[j] = 0.0; continue; }
-    delta[j] = 1.0 / (d[j] - d[i]);
-    w[j] = -(delta[j] * z[j]) / z[i];
-    acc = o_add(acc, o_div(o_two_prod(z[j], z[j]), o_two_sum(d[j], -d[i])));
+  o_ah_pole ps;
+  o_ah_solve_at_pole(n, d, z, alpha, k, i, delta, w, &ps);
+  double sigma = d[i], mu = ps.mu, K = ps.K_nu;
+  int shift = i, flags = 0;
+  if (K_out) *K_out = K;
+
+  if ((opt.remedies & 1) && K > opt.T_Knu) {
+    /* (R1) the neighbouring pole on the other side of lambda_k, when there is one (none for
+       the exterior eigenvalues), under the same acceptance rule as oracle_dpr1eig */
+    int other = (i == k) ? k - 1 : k;
+    double best_sigma = sigma, best_mu = mu, best_K = K;
+    if (other >= 0 && other < n && other != i) {
+      o_ah_pole p2;
+      o_ah_solve_at_pole(n, d, z, alpha, k, other, delta, w, &p2);
+      double ratio = fabs((d[i] - d[other]) + mu) / fabs(mu);
+      if (p2.K_nu < K && p2.K_nu <= opt.T_Knu && ratio <= opt.T_Knu) {
+        shift = other; sigma = d[other]; mu = p2.mu; K = p2.K_nu; flags = 1;
+      }
+      if (p2.K_nu < best_K) { best_sigma = d[other]; best_mu = p2.mu; best_K = p2.K_nu; }
+    }
+    if (K > opt.T_Knu) {
+      /* (R2) sigma = fl(lambda) of the better pole solution, inside (d_k, d_{k-1}) */
+      double lo = (k < n) ? d[k] : -INFINITY, hi = (k > 0) ? d[k - 1] : INFINITY;
+      double s2 = best_sigma + best_mu;
+      if (s2 <= lo) s2 = nextafter(lo, INFINITY);
+      if (s2 >= hi) s2 = nextafter(hi, -INFINITY);
+      if (s2 > lo && s2 < hi) {
+        double mu2;
+        o_ah_solve_nonpole(n, d, z, alpha, s2, delta, w, &mu2, NULL);
+        shift = -1; sigma = s2; mu = mu2; flags = 2;
+      }
+    }
   }
-  odd_t bb = o_div(acc, o_two_prod(z[i], z[i]));
-  double b = bb.hi + bb.lo;
-  double wz = 1.0 / z[i];
-  o_ah_ctx c = {n, i, delta, w, b, wz * wz};
-  /* Weyl bracket of the extreme eigenvalue of the order-(n+1) arrowhead (diagonal delta,
-     b, 0; border w, 1/zeta_i): within ||border|| of max(b, max delta, 0) (rightmost) or
-     min(b, min delta, 0) (leftmost) */
-  double wn2 = wz * wz, dmax = 0.0, dmin = 0.0;
-  for (int j = 0; j < n; j++) {
-    if (j == i) continue;
-    wn2 += w[j] * w[j];
-    if (delta[j] > dmax) dmax = delta[j];
-    if (delta[j] < dmin) dmin = delta[j];
+  o_ah_vector(n, d, z, sigma, mu, v);
+  double lambda = sigma + mu;
+
+  /* lambda much closer to zero than to its neighbouring poles: lambda = 1/nu, nu the extreme
+     eigenvalue of A^{-1} (sigma = 0) */
+  if (opt.remedies & 2) {
+    int allnz = 1;
+    for (int j = 0; j < n; j++) if (d[j] == 0.0) { allnz = 0; break; }
+    double m1 = INFINITY;
+    if (k < n) m1 = fabs(lambda - d[k]);
+    if (k > 0) { double m2 = fabs(lambda - d[k - 1]); if (m2 < m1) m1 = m2; }
+    if (allnz && opt.T_zero * fabs(lambda) < m1) {
+      double mu0;
+      int ok = o_ah_solve_nonpole(n, d, z, alpha, 0.0, delta, w, &mu0, NULL);
+      lambda = ok ? mu0 : 0.0;
+      flags |= 4;
+    }
   }
-  double wn = sqrt(wn2);
-  double nu;
-  int steps = 0;
-  if (side > 0) {
-    double lo = b > dmax ? b : dmax;
-    nu = o_bisect(o_g_ah, &c, 1.0, lo, lo + wn, +1, &steps);
-  } else {
-    double up = b < dmin ? b : dmin;
-    nu = o_bisect(o_g_ah, &c, -1.0, -up, -up + wn, -1, &steps);
-  }
-  double mu = 1.0 / nu;
-  /* eigenvector [x; -1] / ||.||, x_j = zeta_j / ((d_j - d_i) - mu), scaled 2-norm */
-  double m = 1.0;
-  for (int j = 0; j < n; j++) {
-    double x = (j == i) ? -z[i] / mu : z[j] / ((d[j] - d[i]) - mu);
-    v[j] = x;
-    if (fabs(x) > m) m = fabs(x);
-  }
-  v[n] = -1.0;
-  double s = 0.0;
-  for (int j = 0; j <= n; j++) { double t = v[j] / m; s += t * t; }
-  double r = sqrt(s);
-  for (int j = 0; j <= n; j++) v[j] = (v[j] / m) / r;
-  *lambda_out = d[i] + mu;
-  if (sigma_out) *sigma_out = d[i];
+  *lambda_out = lambda;
+  if (sigma_out) *sigma_out = sigma;
   if (mu_out) *mu_out = mu;
-  if (shift_out) *shift_out = i;
-  if (steps_out) *steps_out = steps;
+  if (shift_out) *shift_out = shift;
+  if (flags_out) *flags_out = flags;
   free(delta); free(w);
   return 0;
 }

@@ -53,6 +53,28 @@ static q_t q_f(int n, const double* d, const double* z, double rho, q_t lam) {
 }
 
 /*
+ * An arrowhead eigenvalue closer to zero than to its nearest pole (|lambda| < |mu|): d_i + mu
+ * then carries an absolute error of about 2^-113 |d_i|, large next to |lambda|.  Instead lambda
+ * is found by bisection of the secular function on lambda itself over [a, b] (an interlacing
+ * interval); every d_j - lambda is then formed to 2^-113 relative, since no pole is nearer to
+ * lambda than zero is, and the root carries 2^-113 (|alpha| + sum_j |zeta_j^2/(d_j - lambda)|)
+ * divided by |f'| >= 1.  (For D + rho z z^T the same evaluation gains nothing: its secular
+ * function 1 + rho sum_j ... cancels O(1) terms near such an eigenvalue.)  sgn_below is the
+ * sign of the function between a and the root.
+ */
+typedef q_t (*q_secular_fn)(const void* ctx, q_t lam);
+
+static q_t q_bisect_value(q_secular_fn fn, const void* ctx, q_t a, q_t b, int sgn_below) {
+  for (int steps = 0; steps < 20000; steps++) {
+    q_t mid = a + (b - a) / 2;
+    if (!(mid > a && mid < b)) break;
+    q_t f = fn(ctx, mid);
+    if ((f > 0) == (sgn_below > 0) && f != 0) a = mid; else b = mid;
+  }
+  return a + (b - a) / 2;
+}
+
+/*
  * Bisection is done on mu = lambda - d_i in coordinates shifted by the nearer end
  * pole d_i of the interlacing interval, so that mu keeps 113 significant bits even
  * when lambda is within a few binary64 ulps of a pole: f(d_i + mu) is evaluated
@@ -200,7 +222,8 @@ double quad_secular(int n, const double* d, const double* z, double rho, double 
  * for k = n; v_k = [x; -1] / ||.||, x = (D - lambda_k I)^{-1} z.  Bisection in binary128 on
  * mu = lambda - d_i, with the pole differences d_j - d_i formed in binary128, i the nearer end
  * pole of the interval (from the sign of f at its midpoint; the exterior intervals use the
- * pole they touch).  Returns the number of steps, or -1.
+ * pole they touch); an eigenvalue closer to zero than to that pole is then found by bisection
+ * on lambda itself (q_bisect_value).  Returns the number of steps, or -1.
  */
 static q_t q_fa(int n, const q_t* D, const double* z, q_t a, q_t mu) {
   q_t s = 0;
@@ -209,6 +232,19 @@ static q_t q_fa(int n, const q_t* D, const double* z, q_t a, q_t mu) {
     s += zj * zj / (D[j] - mu);
   }
   return (a - mu) - s;
+}
+
+typedef struct { int n; const double* d; const double* z; double alpha; } q_arrow_ctx;
+
+/* f(lambda) = alpha - lambda - sum_j zeta_j^2 / (d_j - lambda), unshifted */
+static q_t q_fa_ctx(const void* vc, q_t lam) {
+  const q_arrow_ctx* c = (const q_arrow_ctx*)vc;
+  q_t s = 0;
+  for (int j = 0; j < c->n; j++) {
+    q_t zj = (q_t)c->z[j];
+    s += zj * zj / ((q_t)c->d[j] - lam);
+  }
+  return ((q_t)c->alpha - lam) - s;
 }
 
 int quad_arrow_eigpair(int n, const double* d, const double* z, double alpha, int k,
@@ -249,6 +285,14 @@ int quad_arrow_eigpair(int n, const double* d, const double* z, double alpha, in
   }
   q_t mu = lo + (hi - lo) / 2;
   q_t lam = (q_t)d[i] + mu;
+  if (q_abs(lam) < q_abs(mu)) {
+    q_arrow_ctx c = {n, d, z, alpha};
+    q_t zn2 = 0;
+    for (int j = 0; j < n; j++) zn2 += (q_t)z[j] * (q_t)z[j];
+    q_t U = q_abs((q_t)alpha) + q_abs((q_t)d[0]) + q_abs((q_t)d[n - 1]) + q_sqrt(zn2 + 1) + 1;
+    q_t a = (k < n) ? (q_t)d[k] : -U, b = (k > 0) ? (q_t)d[k - 1] : U;
+    lam = q_bisect_value(q_fa_ctx, &c, a, b, +1);   /* f decreasing: f > 0 below the root */
+  }
   double h = (double)lam;
   *lam_hi = h;
   *lam_lo = (double)(lam - (q_t)h);

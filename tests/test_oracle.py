@@ -322,6 +322,36 @@ def test_near_zero_eigenvalue_path():
     assert fr_rel([lam0], [h, l]) > 1e-6          # sigma + mu cancels without it
 
 
+def test_near_zero_eigenvalue_by_determinant():
+    """An eigenvalue of about 4e-26 between poles of size 1: with dyadic data
+    1 + rho sum_j zeta_j^2 / d_j = -2^-80 exactly, and the product of the eigenvalues is
+    det(D + rho z z^T) = prod_j d_j (1 + rho sum_j zeta_j^2 / d_j) (exact in rationals), which
+    fixes the small one without any secular solve.  The oracle's recompute from A^{-1}
+    (Eq. (gamma): at sigma = 0 every term of f is exact here) reaches it to the bound; binary128
+    cannot (f cancels O(1) terms near lambda: 2^-113 absolute, about 3e-10 of lambda), so the
+    reference is held to that absolute accuracy only."""
+    from fractions import Fraction as Fr
+    d = np.array([1.0, 0.5, -0.25, -1.0])
+    z = np.array([1.0, 1.0, 1.0, 2.0 ** -40])
+    rho = 1.0
+    n = d.size
+    q = oracle.quad_all(d, z, rho)
+    k0 = int(np.argmin(np.abs(q["hi"])))
+    det = 1 + Fr(rho) * sum(Fr(float(zj)) ** 2 / Fr(float(dj)) for dj, zj in zip(d, z))
+    for dj in d:
+        det *= Fr(float(dj))
+    others = Fr(1)
+    for k in range(n):
+        if k != k0:
+            others *= Fr(float(q["hi"][k])) + Fr(float(q["lo"][k]))
+    lam_det = det / others
+    assert 1e-27 < abs(float(lam_det)) < 1e-24
+    assert abs(Fr(float(q["hi"][k0])) + Fr(float(q["lo"][k0])) - lam_det) <= Fr(2.0 ** -110)
+    lam, _, info = oracle.dpr1eig(d, z, rho, k0)
+    assert info["zero_path"] == 1
+    assert abs(Fr(float(lam)) - lam_det) <= Fr(tol(n)) * abs(lam_det)
+
+
 # ---------------------------------------------------------------- invariants
 @pytest.mark.parametrize("gen,n,seed", [("uniform", 200, 3), ("hard", 300, 2)])
 def test_interlacing_trace_orthogonality(gen, n, seed):

@@ -74,3 +74,149 @@ def test_hard_spectrum_without_remedies(alpha):
     tol = 16 * 301 * EPS
     assert np.max(np.abs(r["lam"] - lq) / np.abs(lq)) <= tol
     assert np.max(np.abs(r["Vt"] - q["Vt"]) / np.maximum(np.abs(q["Vt"]), 1e-300)) <= tol
+
+
+def _clustered(n, seed):
+    """Poles in tight clusters (spreads 1e-12 to 1e-3), weights over twelve decades, small
+    alpha: eigenvalues next to a cluster see K_nu >> 1 at the nearer pole."""
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(-1, 1, max(1, n // 6))
+    d = rng.choice(c, n) + rng.choice([1.0, -1.0], n) * 10.0 ** rng.uniform(-12, -3, n)
+    d = np.sort(d)[::-1].copy()
+    z = rng.choice([1.0, -1.0], n) * 10.0 ** rng.uniform(-12, 0, n)
+    assert np.all(d[:-1] > d[1:])
+    return d, z, float(10.0 ** rng.uniform(-10, -3))
+
+
+def _errors(r, q):
+    lq = q["hi"] + q["lo"]
+    e = np.max(np.abs(r["lam"] - lq) / np.abs(lq))
+    ev = np.max(np.abs(r["Vt"] - q["Vt"]) / np.maximum(np.abs(q["Vt"]), 1e-300))
+    return e, ev
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_remedies_restore_accuracy_on_clustered_poles(seed):
+    """K_nu >> 1 (Eq. (K0)): the plain pole solves miss the bound on clustered poles; R1 (the
+    other neighbouring pole) and R2 (a non-pole shift, the arrowhead form of Eq. (gamma)) bring
+    every eigenvalue and component back within 16(n+1)2^-53 of binary128."""
+    d, z, alpha = _clustered(240, seed)
+    n = d.size
+    tol = 16 * (n + 1) * EPS
+    q = oracle.quad_arrow_all(d, z, alpha, threads=8)
+    plain = oracle.arrow_eig_all(d, z, alpha, threads=8, opts=oracle.default_opts(remedies=0))
+    full = oracle.arrow_eig_all(d, z, alpha, threads=8)
+    assert max(_errors(plain, q)) > tol
+    e, ev = _errors(full, q)
+    assert e <= tol and ev <= tol, (e, ev)
+    flags = full["flags"] & 3
+    assert np.any(flags == 1) and np.any(flags == 2)
+    assert np.all((flags != 0) == (full["K_nu"] > 16.0))
+    assert np.all(full["shift"][flags == 2] == -1)
+
+
+def _near_singular(seed):
+    # few poles with O(1) weights keep K_nu small, so the pole solve is taken as it stands and
+    # only d_i + mu cancels
+    rng = np.random.default_rng(seed)
+    n = 3
+    d = np.concatenate([rng.uniform(0.5, 1, 2), -rng.uniform(0.5, 1, 1)])
+    d = np.sort(d)[::-1].copy()
+    z = rng.choice([1.0, -1.0], n) * rng.uniform(0.3, 1.0, n)
+    alpha = float(np.sum(z * z / d)) * (1 + 1e-13)
+    return d, z, alpha
+
+
+def _det_times_inverse_f(d, z, alpha):
+    """det(A) = prod_j d_j * f(0), f(0) = alpha - sum_j zeta_j^2 / d_j (Schur complement of D),
+    exact in rationals."""
+    from fractions import Fraction as Fr
+    f0 = Fr(alpha) - sum(Fr(float(zj)) ** 2 / Fr(float(dj)) for dj, zj in zip(d, z))
+    det = f0
+    for dj in d:
+        det *= Fr(float(dj))
+    return det
+
+
+@pytest.mark.parametrize("seed", [1, 2, 4])
+def test_near_zero_eigenvalue(seed):
+    """An arrowhead with alpha next to sum zeta_j^2/d_j is nearly singular: one eigenvalue,
+    between the positive and the negative poles, is far smaller than its distance to them.  The
+    product of the eigenvalues is det(A) = prod_j d_j f(0) (exact in rationals), which pins that
+    eigenvalue independently of any secular solve; the oracle reaches it only with the
+    recompute from A^{-1} (sigma = 0), and the binary128 reference agrees."""
+    from fractions import Fraction as Fr
+    d, z, alpha = _near_singular(seed)
+    n = d.size
+    tol = 16 * (n + 1) * EPS
+    q = oracle.quad_arrow_all(d, z, alpha)
+    lq = q["hi"] + q["lo"]
+    kz = int(np.argmin(np.abs(lq)))
+    assert 0 < kz < n and d[kz] < 0 < d[kz - 1]
+    others = Fr(1)
+    for k in range(n + 1):
+        if k != kz:
+            others *= Fr(float(q["hi"][k])) + Fr(float(q["lo"][k]))
+    lam_det = float(_det_times_inverse_f(d, z, alpha) / others)
+    assert abs(lq[kz] - lam_det) <= 4 * EPS * abs(lam_det)
+    assert abs(lam_det) < 1e-6 * min(d[kz - 1], -d[kz])
+    r = oracle.arrow_eig_all(d, z, alpha)
+    assert r["flags"][kz] & 4
+    assert abs(r["lam"][kz] - lam_det) <= tol * abs(lam_det)
+    no_zero = oracle.arrow_eig_all(d, z, alpha, opts=oracle.default_opts(remedies=1))
+    assert abs(no_zero["lam"][kz] - lam_det) > tol * abs(lam_det)
+
+
+def test_random_arrowheads_against_binary128():
+    """Seeded random arrowheads of many shapes (uniform, clustered, graded, nearly singular;
+    alpha over fourteen decades, both signs), all remedies on: every eigenvalue and component
+    within 16(n+1)2^-53 of binary128."""
+    rng = np.random.default_rng(2026)
+    done = 0
+    while done < 60:
+        n = int(rng.integers(1, 60))
+        kind = rng.integers(0, 4)
+        if kind == 0:
+            d = rng.uniform(-1, 1, n)
+        elif kind == 1:
+            c = rng.uniform(-1, 1, max(1, n // 6))
+            d = rng.choice(c, n) + rng.choice([1.0, -1.0], n) * 10.0 ** rng.uniform(-12, -3, n)
+        elif kind == 2:
+            d = np.sign(rng.uniform(-1, 1, n)) * 10.0 ** rng.uniform(-10, 0, n)
+        else:
+            d = np.concatenate([rng.uniform(0.5, 1, n - n // 2), -rng.uniform(0.5, 1, n // 2)])
+        d = np.sort(d)[::-1].copy()
+        z = rng.choice([1.0, -1.0], n) * 10.0 ** rng.uniform(-12 if rng.random() < 0.5 else -2, 0, n)
+        if kind == 3:
+            alpha = float(np.sum(z * z / d)) * (1 + 10.0 ** rng.uniform(-14, -2))
+        else:
+            alpha = float(rng.choice([1.0, -1.0]) * 10.0 ** rng.uniform(-12, 2))
+        if not (np.all(d[:-1] > d[1:]) and not np.any(oracle.zero_weight(z))):
+            continue
+        done += 1
+        r = oracle.arrow_eig_all(d, z, alpha, threads=4)
+        q = oracle.quad_arrow_all(d, z, alpha, threads=4)
+        e, ev = _errors(r, q)
+        tol = 16 * (n + 1) * EPS
+        assert e <= tol and ev <= tol, (done, n, kind, alpha, e, ev)
+
+
+def test_near_zero_eigenvalue_with_tiny_weights():
+    """Weights 4e-5 and 2.5e-9 against poles of size 0.9: the middle eigenvalue is about
+    2.4e-22.  det(A) = prod_j d_j f(0) (exact in rationals) fixes it; the binary128 reference
+    (bisection on lambda itself: d_i + mu would carry 2^-113 |d_i|, about 4e-13 of lambda) and
+    the oracle both reach it."""
+    from fractions import Fraction as Fr
+    d = np.array([float.fromhex("0x1.bf656f89b0670p-1"), float.fromhex("-0x1.c35f000a6603ap-1")])
+    z = np.array([float.fromhex("0x1.4c82cd5918a9ap-15"), float.fromhex("0x1.5cb9c1af8ca60p-29")])
+    alpha = float.fromhex("0x1.ee40d73254cdfp-30")
+    q = oracle.quad_arrow_all(d, z, alpha)
+    others = (Fr(float(q["hi"][0])) + Fr(float(q["lo"][0]))) * (Fr(float(q["hi"][2])) + Fr(float(q["lo"][2])))
+    lam_det = _det_times_inverse_f(d, z, alpha) / others
+    assert 1e-23 < abs(float(lam_det)) < 1e-21
+    # attainable in binary128 here: 2^-113 (|alpha| + sum_j |zeta_j^2/d_j|) / |f'|, about 1e-21 of
+    # lambda; the shifted d_i + mu would be about 4e-13 off
+    assert abs(Fr(float(q["hi"][1])) + Fr(float(q["lo"][1])) - lam_det) <= Fr(2.0 ** -60) * abs(lam_det)
+    r = oracle.arrow_eig_all(d, z, alpha)
+    assert r["flags"][1] & 4
+    assert abs(Fr(float(r["lam"][1])) - lam_det) <= Fr(16 * 3 * EPS) * abs(lam_det)
