@@ -472,7 +472,9 @@ def bench_tridiag(B, dev, n, seed, steps):
 
 def bench_arrow(B, dev, n, seed, steps, flush):
     """The real symmetric arrowhead [D z; z^T alpha] of order n + 1 (d, z ~ U(-1, 1)): all
-    eigenvalues and the (n+1)^2 eigenvector matrix, both zero finders."""
+    eigenvalues and the (n+1)^2 eigenvector matrix with the K_nu remedies and the near-zero
+    recompute, both zero finders; the counters of the last call show how many eigenvalues
+    took which remedy."""
     import torch
     from paper_1405_7537_gb300 import workloads as W
     d, z, alpha = W.arrowhead(n, seed)
@@ -497,8 +499,10 @@ def bench_arrow(B, dev, n, seed, steps, flush):
         st = B.stream_status(ws)
         if st != 0:
             raise B.DPR1Error(st, "arrow")
+        c = B.workspace_stats(ws)
         t = statistics.mean(ms)
-        res[name] = {"value": (n + 1) / (t * 1e-3), "ms_per_step": t}
+        res[name] = {"value": (n + 1) / (t * 1e-3), "ms_per_step": t,
+                     "remedies": {k: c[k] for k in ("flagged", "r1", "r2", "zero_path")}}
     return res
 
 

@@ -251,8 +251,13 @@ DPR1_API size_t dpr1_arrow_workspace_size(int64_t n);
  * arrowhead, with the corner b = (1/zeta_i^2)(sum_{j != i} zeta_j^2/(d_j - d_i) - (alpha - d_i))
  * formed in double-double and one more pole, at 0, of weight 1/zeta_i^2; lambda = d_i + 1/nu
  * for its extreme eigenvalue nu (bisection, or the accelerated solve with opt->zero_finder),
- * v = [x; -1] / ||.||, x = (D - lambda I)^{-1} z.  The K_nu remedies of dpr1_eig are not
- * applied to this problem.
+ * v = [x; -1] / ||.||, x = (D - lambda I)^{-1} z.  As in dpr1_eig, an eigenvalue whose K_nu
+ * (Eq. (K0)) exceeds opt->T_Knu is recomputed at the other neighbouring pole (R1) or at a
+ * non-pole shift sigma next to it (R2, Sec. 2), where (A - sigma I)^{-1} =
+ * diag((D - sigma I)^{-1}, 0) + u u^T / f(sigma), u = [(D - sigma I)^{-1} z; -1],
+ * f(sigma) = alpha - sigma - z^T (D - sigma I)^{-1} z in double-double, is a DPR1 matrix of
+ * order n + 1; and an eigenvalue much closer to zero than to its neighbouring poles
+ * (T_zero |lambda| < distance) is recomputed from A^{-1} (sigma = 0) when no pole is zero.
  *
  *   n          number of poles (n >= 0; the matrix has order n + 1)
  *   d, z       device double[n]: d strictly decreasing, every |z_j| >= 2^-511 (the matrix is
@@ -260,9 +265,12 @@ DPR1_API size_t dpr1_arrow_workspace_size(int64_t n);
  *   alpha      the corner entry
  *   lambda     device double[n+1], out: eigenvalues, non-increasing; they interlace d
  *   Vt         device double[(n+1)*ldv] or NULL, out: row k = v_k (n + 1 entries, ldv >= n + 1)
- *   sigma, mu  device double[n+1] or NULL, out: lambda_k = sigma_k + mu_k, sigma_k the pole
+ *   sigma, mu  device double[n+1] or NULL, out: the shift sigma_k (a pole, or the R2 shift)
+ *              and mu_k = 1/nu; lambda_k = sigma_k + mu_k except for an eigenvalue
+ *              recomputed from A^{-1}, and v_k is formed from (sigma_k, mu_k)
  *   xnorm      device double[n+1] or NULL, out: ||[x; -1]||
- *   workspace  dpr1_arrow_workspace_size(n) bytes, 256-byte aligned
+ *   workspace  dpr1_arrow_workspace_size(n) bytes, 256-byte aligned; dpr1_workspace_stats
+ *              reads its counters like those of dpr1_eig
  * Errors: DPR1_ERR_ARG, DPR1_ERR_WORKSPACE, DPR1_ERR_CUDA synchronously; through
  * dpr1_stream_status: DPR1_ERR_ARG (equal poles or a zero weight), DPR1_ERR_UNSORTED,
  * DPR1_ERR_NONFINITE, DPR1_ERR_NOT_CONVERGED.
@@ -308,7 +316,8 @@ DPR1_API dpr1_status dpr1_eig_noalloc(int64_t n, const double* d, const double* 
 
 /*
  * Instrumentation (no counterpart in the paper): synchronises `stream` and copies the
- * counters of the last dpr1_eig / dpr1_eig_batched call on `workspace` into out[0..7]:
+ * counters of the last dpr1_eig / dpr1_eig_batched / dpr1_arrow_eig call on `workspace` into
+ * out[0..7]:
  *   0 eigenvalues solved by the bisection kernel, 1 eigenvalues flagged by K_nu,
  *   2 remedies taken with R1, 3 with R2, 4 secular-function evaluations in the bisection
  *   kernel, 5 evaluations in the remedy kernel, 6 eigenvalues recomputed from A^{-1},

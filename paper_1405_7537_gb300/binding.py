@@ -238,7 +238,9 @@ def arrow_workspace(n, device="cuda"):
 
 def eig_arrowhead(d, z, alpha, want_vectors=True, options=None, ws=None, check=True, stream=None):
     """All n + 1 eigenpairs of the arrowhead [diag(d) z; z^T alpha] (d strictly decreasing, no
-    zero weight).  Returns dict(lam, Vt, sigma, mu, xnorm); Vt is (n+1) x (n+1), row k = v_k."""
+    zero weight), with the K_nu remedies and the near-zero recompute.  Returns dict(lam, Vt,
+    sigma, mu, xnorm); Vt is (n+1) x (n+1), row k = v_k.  ``workspace_stats(ws)`` gives the
+    counters of the call."""
     dev = d.device if isinstance(d, torch.Tensor) and d.is_cuda else torch.device("cuda", torch.cuda.current_device())
     d = _dev_f64(d, dev)
     z = _dev_f64(z, dev)
@@ -273,7 +275,8 @@ STAT_NAMES = ("solved", "flagged", "r1", "r2", "evals_solve", "evals_fix", "zero
 
 
 def workspace_stats(ws, stream=None):
-    """Counters of the last dpr1_eig call on ``ws`` (synchronises the stream)."""
+    """Counters of the last dpr1_eig / dpr1_eig_batched / dpr1_arrow_eig call on ``ws``
+    (synchronises the stream)."""
     buf = (ctypes.c_int64 * 8)()
     _check(lib().dpr1_workspace_stats(_ptr(ws), buf, _stream(stream)), "dpr1_workspace_stats")
     return dict(zip(STAT_NAMES, list(buf)))

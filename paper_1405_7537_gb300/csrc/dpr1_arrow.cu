@@ -15,7 +15,16 @@
 //   g(nu) = b - nu - (1/zeta_i^2) sum_{j != i} zeta_j^2 / (Delta_j (1 - nu Delta_j))
 //           + (1/zeta_i^2) / nu,
 // and lambda = d_i + 1/nu for its extreme eigenvalue nu (bisection or the accelerated solve).
-// The eigenvector is v = [x; -1] / ||.||, x_j = zeta_j / ((d_j - d_i) - mu).
+// The eigenvector is v = [x; -1] / ||.||, x_j = zeta_j / ((d_j - sigma) - mu).
+//
+// Then, as for D + rho z z^T (Sec. 2): where K_nu of Eq. (K0) is large the other neighbouring
+// pole (R1) or a non-pole shift sigma next to lambda (R2) is taken.  For sigma not a pole,
+// with f(sigma) the Schur complement of D - sigma I,
+//   (A - sigma I)^{-1} = diag(e, 0) + gamma u u^T,  e_j = 1/(d_j - sigma),
+//   u = [zeta_j/(d_j - sigma); -1],  gamma = 1/f(sigma),
+// a DPR1 matrix of order n + 1 with a pole at 0 of weight gamma (the arrowhead form of
+// Eq. (gamma)); its extreme eigenvalue is 1/(lambda - sigma).  sigma = 0 recomputes an
+// eigenvalue much closer to zero than to its neighbouring poles.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -36,9 +45,13 @@ struct ArrowWs {
   unsigned long long* queue;     // work counter of the solve kernel
   double* zz;                    // zeta_j^2 = zz + zl exactly
   double* zl;
-  double* sig;                   // pole of eigenvalue k
+  double* sig;                   // shift of eigenvalue k (a pole, or sigma of R2)
   double* mu;
-  int* shift;
+  int* shift;                    // pole index, -1 for a non-pole shift
+  int* list;                     // eigenvalues flagged by K_nu
+  double* fixinfo;               // per flagged slot: K_nu, K_nu at the other pole, distance ratio
+  int* zlist;                    // near-zero candidates
+  double* lamz;                  // lambda recomputed from A^{-1} (NaN: not recomputed)
 };
 
 static size_t arrow_layout(int64_t n, ArrowWs* w, char* base) {
@@ -50,6 +63,10 @@ static size_t arrow_layout(int64_t n, ArrowWs* w, char* base) {
   size_t o_s = off; off += a256a(8 * nn);
   size_t o_m = off; off += a256a(8 * nn);
   size_t o_sh = off; off += a256a(4 * nn);
+  size_t o_l = off; off += a256a(4 * nn);
+  size_t o_fi = off; off += a256a(24 * nn);
+  size_t o_zl2 = off; off += a256a(4 * nn);
+  size_t o_lz = off; off += a256a(8 * nn);
   if (w && base) {
     w->status = (unsigned*)(base + o_h);
     w->counters = (unsigned*)(base + o_h) + 8;
@@ -59,19 +76,28 @@ static size_t arrow_layout(int64_t n, ArrowWs* w, char* base) {
     w->sig = (double*)(base + o_s);
     w->mu = (double*)(base + o_m);
     w->shift = (int*)(base + o_sh);
+    w->list = (int*)(base + o_l);
+    w->fixinfo = (double*)(base + o_fi);
+    w->zlist = (int*)(base + o_zl2);
+    w->lamz = (double*)(base + o_lz);
   }
   return off;
 }
 
 constexpr unsigned ST_FATAL_A = ST_NONFINITE | ST_UNSORTED | ST_BADARG;
+constexpr unsigned AH_ZERO_POLE = 1u;   // header word 1: some d_j == 0 (no near-zero recompute)
+// remedies kernel: block-wide lane groups, two blocks per SM (as for D + rho z z^T)
+constexpr int AH_FIX_THREADS = 256;
+constexpr int AH_FIX_BLOCKS_PER_SM = 2;
 
 // input checks (finite, strictly decreasing d, no zero weight) and zeta^2
 __global__ void k_arrow_check(int n, const double* __restrict__ d, const double* __restrict__ z, double alpha,
                               double* __restrict__ zz, double* __restrict__ zl, unsigned* __restrict__ status) {
-  unsigned bits = 0;
+  unsigned bits = 0, zp = 0;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     const double dj = d[j], zj = z[j];
     if (!isfinite(dj) || !isfinite(zj)) bits |= ST_NONFINITE;
+    if (dj == 0.0) zp = AH_ZERO_POLE;
     if (j + 1 < n) {
       if (dj < d[j + 1]) bits |= ST_UNSORTED;
       else if (dj == d[j + 1]) bits |= ST_BADARG;       // equal poles: reducible
@@ -83,7 +109,9 @@ __global__ void k_arrow_check(int n, const double* __restrict__ d, const double*
   }
   if (blockIdx.x == 0 && threadIdx.x == 0 && !isfinite(alpha)) bits |= ST_NONFINITE;
   bits = __reduce_or_sync(FULL, bits);
+  zp = __reduce_or_sync(FULL, zp);
   if ((threadIdx.x & 31) == 0 && bits) atomicOr(status, bits);
+  if ((threadIdx.x & 31) == 0 && zp) atomicOr(status + 1, zp);
 }
 
 // Extreme eigenvalue nu of (A - d_i I)^{-1} on the side of eigenvalue k (rightmost when
@@ -237,6 +265,230 @@ __global__ void __launch_bounds__(256) k_arrow_solve(int n, const double* __rest
   }
 }
 
+// Non-pole shift sigma (R2, and sigma = 0 for the near-zero recompute): mu = 1/nu for the
+// extreme eigenvalue nu of (A - sigma I)^{-1} = diag(e, 0) + gamma u u^T (see the top of the
+// file), whose secular function is h(nu) = 1 + gamma (S(nu) - 1/nu), S(nu) = sum_j u_j^2/(e_j - nu)
+// the shift sum.  f(sigma) = alpha - sigma - sum_j zeta_j^2/(d_j - sigma) is formed in
+// double-double; f(sigma) = 0 gives mu = 0 (lambda = sigma).  above / below: the poles next to
+// sigma (-1: none on that side).  The poles of h on |nu| are the e_j and 0, so the largest
+// of them is max(e_above, 0) (gamma > 0, nu the rightmost) or max(-e_below, 0) (gamma < 0).
+template <int L>
+__device__ double solve_nonpole_arrow(const double* __restrict__ d, const double* __restrict__ zl,
+                                      const double* __restrict__ zz, int n, double alpha, double sigma, int above,
+                                      int below, int cap, bool fast, int lane, unsigned gm, bool* ok,
+                                      int* steps_out) {
+  double un2, cub;
+  const dd acc = dd_pole_sum<L>(d, zz, zl, n, -1, sigma, lane, gm, &un2, &cub);
+  const dd f = dd_add(two_sum(alpha, -sigma), {-acc.hi, -acc.lo});
+  *ok = true;
+  *steps_out = 0;
+  if (f.hi == 0.0 && f.lo == 0.0) return 0.0;
+  const double gamma = dd_to_double(dd_div({1.0, 0.0}, f));
+  const double uu = un2 + 1.0;                  // ||u||^2, u_n = -1
+  const double emax = above >= 0 ? 1.0 / __dsub_rn(d[above], sigma) : -INFINITY;
+  const double emin = below >= 0 ? 1.0 / __dsub_rn(d[below], sigma) : INFINITY;
+  // Rayleigh quotient of u (the pole at 0 adds nothing to u^T diag(e, 0) u): a lower bound of
+  // the rightmost and an upper bound of the leftmost eigenvalue; Weyl bounds the other side
+  const double rq = cub / uu + gamma * uu;
+  double side, floor, alo, ahi;
+  if (gamma > 0.0) {
+    side = 1.0;
+    floor = fmax(emax, 0.0);
+    alo = fmax(floor, rq * (1.0 - 0x1p-48));
+    ahi = floor + gamma * uu;
+  } else {
+    side = -1.0;
+    floor = fmax(-emin, 0.0);
+    alo = fmax(floor, -rq * (1.0 - 0x1p-48));
+    ahi = floor - gamma * uu;
+  }
+  ahi *= (1.0 + 0x1p-48);
+  int steps;
+  double nu;
+  if (fast) {
+    // F(t) = -h(side t) = |gamma| (-1/|gamma| + Psi(t)), Psi(t) = -side S(side t) + 1/t; every
+    // pole of Psi lies at or below floor, the model pole
+    const double ag = fabs(gamma);
+    auto ev = [&](double t, bool want, double* psi, double* dpsi) {
+      const double v = side * t;
+      double dS = 0.0;
+      const double S = want ? arrow_sum_d<L>(d, zz, n, -1, sigma, v, lane, gm, &dS)
+                            : arrow_sum<L>(d, zz, n, -1, sigma, v, lane, gm);
+      const double it = 1.0 / t;
+      *psi = -side * S + it;
+      *dpsi = -dS - it * it;
+      return -__fma_rn(gamma, __dsub_rn(S, 1.0 / v), 1.0);
+    };
+    nu = side * accel_solve(ev, floor, alo, ahi, floor, -1.0 / ag, 0.0, ag, cap, ok, &steps);
+  } else {
+    auto phi = [&](double v) {
+      return __fma_rn(gamma, __dsub_rn(shift_sum<L>(d, zz, n, sigma, v, lane, gm), 1.0 / v), 1.0);
+    };
+    // h < 0 between the floor and the root in both cases
+    nu = bisect(phi, side, floor, alo, ahi, false, cap, ok, &steps);
+  }
+  *steps_out = steps;
+  return 1.0 / nu;
+}
+
+// |lambda_m - p| = |(sigma_m - p) + mu_m|
+__device__ __forceinline__ double arrow_dist(const ArrowWs& w, int m, double p) {
+  return fabs(__dadd_rn(__dsub_rn(w.sig[m], p), w.mu[m]));
+}
+
+// K_nu = ||(A - d_i I)^{-1}||_2 / |nu| (Eq. (K0)).  The eigenvalues next to pole d_i are
+// lambda_i (above) and lambda_{i+1} (below), one of them lambda_k, and the norm is the
+// reciprocal distance from d_i to the spectrum, so K_nu = max(1, |mu_k| / |lambda_m - d_i|) with
+// lambda_m the other one.  For K_nu > T_Knu the eigenvalue goes to k_arrow_fix with the other
+// neighbouring pole o of lambda_k (none for the exterior eigenvalues):
+//   K'  = max(1, |lambda_k - d_o| / |lambda_m' - d_o|),  ratio = |lambda_k - d_o| / |lambda_k - d_i|.
+__global__ void k_arrow_classify(int n, const double* __restrict__ d, ArrowWs w, double T_Knu) {
+  if (*w.status & ST_FATAL_A) return;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= n; k += gridDim.x * blockDim.x) {
+    const int i = w.shift[k];
+    const double di = d[i], mu = w.mu[k];
+    const double mk = fabs(mu);
+    const int m = (i == k) ? k + 1 : k - 1;
+    const double K = fmax(1.0, mk / arrow_dist(w, m, di));
+    if (K > T_Knu) {
+      const int o = (i == k) ? k - 1 : k;
+      double K2 = INFINITY, ratio = INFINITY;
+      if (o >= 0 && o < n) {
+        const double dko = fabs(__dadd_rn(__dsub_rn(di, d[o]), mu));
+        const int m2 = (o == k) ? k + 1 : k - 1;
+        K2 = fmax(1.0, dko / arrow_dist(w, m2, d[o]));
+        ratio = dko / mk;
+      }
+      const unsigned slot = atomicAdd(&w.counters[C_FIX_N], 1u);
+      w.list[slot] = k;
+      w.fixinfo[3 * (size_t)slot] = K;
+      w.fixinfo[3 * (size_t)slot + 1] = K2;
+      w.fixinfo[3 * (size_t)slot + 2] = ratio;
+    }
+  }
+}
+
+// Remedies for the flagged eigenvalues, one lane group each (work counter):
+//  (R1) solve at the other neighbouring pole o when K' < K; accept when K' <= T_Knu and
+//       ratio <= T_Knu (beyond that the eigenvector formula at d_o cancels);
+//  (R2) otherwise sigma = fl(lambda) of the better pole solution, moved into the open interval
+//       (d_k, d_{k-1}) (d_n = -inf, d_{-1} = +inf) if it falls on a pole, and the non-pole solve.
+template <int L>
+__global__ void __launch_bounds__(L > 256 ? L : 256) k_arrow_fix(int n, const double* __restrict__ d, double alpha,
+                                                                   ArrowWs w, double T_Knu, int cap, bool fast) {
+  if (*w.status & ST_FATAL_A) return;
+  const int nfix = (int)w.counters[C_FIX_N];
+  const int lane = threadIdx.x & (L - 1);
+  const unsigned gm = group_mask<L>();
+  const int leader = (threadIdx.x & 31) & ~(L - 1);
+  __shared__ int item;
+  for (;;) {
+    int t = 0;
+    if constexpr (L > 32) {
+      if (threadIdx.x == 0) item = (int)atomicAdd(&w.counters[C_FIX_Q], 1u);
+      __syncthreads();
+      t = item;
+      __syncthreads();
+    } else {
+      if (lane == 0) t = (int)atomicAdd(&w.counters[C_FIX_Q], 1u);
+      t = __shfl_sync(gm, t, leader, 32);
+    }
+    if (t >= nfix) break;
+    const int k = w.list[t];
+    const int i = w.shift[k];
+    const double di = d[i], mu = w.mu[k];
+    const double K = w.fixinfo[3 * (size_t)t];
+    const double K2 = w.fixinfo[3 * (size_t)t + 1];
+    const double ratio = w.fixinfo[3 * (size_t)t + 2];
+    double new_sig = di, new_mu = mu, best_sig = di, best_mu = mu;
+    int new_shift = i;
+    bool done = false;
+    const int o = (i == k) ? k - 1 : k;
+    if (o >= 0 && o < n && K2 < K) {
+      const PoleResult pr = solve_pole_arrow<L>(d, w.zl, w.zz, n, alpha, k, o, 0.0, INFINITY, cap, fast, lane, gm);
+      if (!pr.ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
+      if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)pr.steps);
+      best_sig = d[o];
+      best_mu = pr.mu;
+      if (K2 <= T_Knu && ratio <= T_Knu) {
+        new_sig = d[o]; new_mu = pr.mu; new_shift = o; done = true;
+      }
+    }
+    if (!done) {
+      double sg = __dadd_rn(best_sig, best_mu);
+      const double lo = (k < n) ? d[k] : -INFINITY;
+      const double hi = (k > 0) ? d[k - 1] : INFINITY;
+      if (k < n && sg <= lo) sg = dnext_up(lo);
+      if (k > 0 && sg >= hi) sg = dnext_down(hi);
+      if (sg > lo && sg < hi) {
+        bool ok;
+        int st2;
+        const double m2 = solve_nonpole_arrow<L>(d, w.zl, w.zz, n, alpha, sg, k > 0 ? k - 1 : -1, k < n ? k : -1,
+                                                 cap, fast, lane, gm, &ok, &st2);
+        if (!ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
+        if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)st2);
+        new_sig = sg; new_mu = m2; new_shift = -1;
+      }
+    }
+    if (lane == 0) {
+      w.sig[k] = new_sig;
+      w.mu[k] = new_mu;
+      w.shift[k] = new_shift;
+      if (new_shift == -1) atomicAdd(&w.counters[C_R2], 1u);
+      else if (new_shift != i) atomicAdd(&w.counters[C_R1], 1u);
+    }
+  }
+}
+
+// Eigenvalues much closer to zero than to their neighbouring poles,
+// T_zero |lambda| < min(|lambda - d_k|, |lambda - d_{k-1}|) (the poles that exist), when no pole
+// is zero: lambda = 1/nu, nu the extreme eigenvalue of A^{-1} (the non-pole solve at sigma = 0).
+__global__ void k_arrow_zero_detect(int n, const double* __restrict__ d, ArrowWs w, double T_zero) {
+  if (*w.status & ST_FATAL_A) return;
+  const bool zero_pole = (w.status[1] & AH_ZERO_POLE) != 0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= n; k += gridDim.x * blockDim.x) {
+    w.lamz[k] = __longlong_as_double(0x7ff8000000000000ll);
+    if (zero_pole) continue;
+    const double sg = w.sig[k], m = w.mu[k];
+    const double lam = __dadd_rn(sg, m);
+    double m1 = INFINITY;
+    if (k < n) m1 = fabs(__dadd_rn(__dsub_rn(sg, d[k]), m));
+    if (k > 0) m1 = fmin(m1, fabs(__dadd_rn(__dsub_rn(sg, d[k - 1]), m)));
+    if (T_zero * fabs(lam) < m1) {
+      const unsigned slot = atomicAdd(&w.counters[C_ZERO_N], 1u);
+      w.zlist[slot] = k;
+    }
+  }
+}
+
+__global__ void k_arrow_zero_solve(int n, const double* __restrict__ d, double alpha, ArrowWs w, int cap,
+                                   bool fast) {
+  if (*w.status & ST_FATAL_A) return;
+  const int nz = (int)w.counters[C_ZERO_N];
+  const int lane = threadIdx.x & 31;
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int t = wid; t < nz; t += nw) {
+    const int k = w.zlist[t];
+    // the poles next to 0: the first negative pole and the one before it (no pole is zero)
+    int lo = 0, hi = n;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (d[mid] > 0.0) lo = mid + 1;
+      else hi = mid;
+    }
+    bool ok;
+    int st;
+    const double lam0 = solve_nonpole_arrow<32>(d, w.zl, w.zz, n, alpha, 0.0, lo - 1, lo < n ? lo : -1, cap, fast,
+                                                lane, FULL, &ok, &st);
+    if (lane == 0) {
+      w.lamz[k] = lam0;
+      atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)st);
+      if (!ok) atomicOr(w.status, ST_NOT_CONVERGED);
+    }
+  }
+}
+
 // Rows v_k = [x; -1] / ||.|| (one warp per row), lambda, sigma, mu, ||[x; -1]||.
 __global__ void __launch_bounds__(256) k_arrow_vectors(int n, const double* __restrict__ d,
                                                        const double* __restrict__ z, ArrowWs w,
@@ -281,7 +533,8 @@ __global__ void __launch_bounds__(256) k_arrow_vectors(int n, const double* __re
     const double nrm = sqrt(q);
     const double c = scale / nrm;
     if (lane == 0) {
-      lambda[k] = __dadd_rn(s, m);
+      const double lz = w.lamz[k];
+      lambda[k] = isnan(lz) ? __dadd_rn(s, m) : lz;
       if (sigma) sigma[k] = s;
       if (mu) mu[k] = m;
       if (xnorm) xnorm[k] = nrm / scale;
@@ -352,6 +605,15 @@ dpr1_status dpr1_arrow_eig(int64_t n, const double* d, const double* z, double a
   if (L == 8) launch_arrow<8>((int)n, d, z, alpha, w, o, st);
   else if (L == 16) launch_arrow<16>((int)n, d, z, alpha, w, o, st);
   else launch_arrow<32>((int)n, d, z, alpha, w, o, st);
+  int kg = (int)((n + 1 + 255) / 256);
+  if (kg > sms * 8) kg = sms * 8;
+  k_arrow_classify<<<kg, 256, 0, st>>>((int)n, d, w, o.T_Knu);
+  // one block-wide group per flagged eigenvalue: they are few (a few percent on graded or
+  // clustered spectra) and each solve spans all n poles
+  const int fg = (int)(n + 1 < (int64_t)sms * AH_FIX_BLOCKS_PER_SM ? n + 1 : (int64_t)sms * AH_FIX_BLOCKS_PER_SM);
+  k_arrow_fix<AH_FIX_THREADS><<<fg, AH_FIX_THREADS, 0, st>>>((int)n, d, alpha, w, o.T_Knu, o.cap, o.fast);
+  k_arrow_zero_detect<<<kg, 256, 0, st>>>((int)n, d, w, o.T_zero);
+  k_arrow_zero_solve<<<1, 128, 0, st>>>((int)n, d, alpha, w, o.cap, o.fast);
   int64_t vg = (n + 1 + 7) / 8;
   if (vg > sms * 16) vg = sms * 16;
   k_arrow_vectors<<<(int)vg, 256, 0, st>>>((int)n, d, z, w, lambda, Vt, ldv, sigma, mu, xnorm);

@@ -119,3 +119,81 @@ def test_hard_spectrum(B, alpha):
     d, z, _ = W.hard(1000, 2)
     for zf in (0, 1):
         check(B, d, z, alpha, zero_finder=zf)
+
+
+def _clustered(n, seed):
+    # the recipe of the oracle's remedy pin: tight pole clusters, weights over twelve decades
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(-1, 1, max(1, n // 6))
+    d = rng.choice(c, n) + rng.choice([1.0, -1.0], n) * 10.0 ** rng.uniform(-12, -3, n)
+    d = np.sort(d)[::-1].copy()
+    z = rng.choice([1.0, -1.0], n) * 10.0 ** rng.uniform(-12, 0, n)
+    return d, z, float(10.0 ** rng.uniform(-10, -3))
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+@pytest.mark.parametrize("zf", [0, 1])
+def test_clustered_poles_use_remedies(B, seed, zf):
+    """K_nu >> 1 next to pole clusters: R1 and R2 on the GPU give every eigenvalue and
+    component within the bound of the oracle and of binary128; the counters show both
+    remedies and the flagged count matches the oracle's K_nu > 16 count (up to the rounding of
+    the two K_nu estimates)."""
+    d, z, alpha = _clustered(240, seed)
+    check(B, d, z, alpha, zero_finder=zf)
+    ws = B.arrow_workspace(d.size, torch.device("cuda"))
+    B.eig_arrowhead(cu(d), cu(z), alpha, options=B.default_options(zero_finder=zf), ws=ws)
+    st = B.workspace_stats(ws)
+    r = oracle.arrow_eig_all(d, z, alpha, threads=16)
+    assert st["solved"] == d.size + 1
+    assert st["r1"] > 0 and st["r2"] > 0
+    assert abs(st["flagged"] - int(np.sum(r["K_nu"] > 16.0))) <= 2
+    assert st["r1"] + st["r2"] <= st["flagged"]
+
+
+def _near_singular(seed):
+    rng = np.random.default_rng(seed)
+    n = 3
+    d = np.concatenate([rng.uniform(0.5, 1, 2), -rng.uniform(0.5, 1, 1)])
+    d = np.sort(d)[::-1].copy()
+    z = rng.choice([1.0, -1.0], n) * rng.uniform(0.3, 1.0, n)
+    return d, z, float(np.sum(z * z / d)) * (1 + 1e-13)
+
+
+def _lam_small_by_det(d, z, alpha, q):
+    """The eigenvalue nearest zero from det(A) = prod_j d_j f(0) and the other eigenvalues
+    (binary128), in exact rationals."""
+    from fractions import Fraction as Fr
+    lq = q["hi"] + q["lo"]
+    k0 = int(np.argmin(np.abs(lq)))
+    det = Fr(alpha) - sum(Fr(float(zj)) ** 2 / Fr(float(dj)) for dj, zj in zip(d, z))
+    for dj in d:
+        det *= Fr(float(dj))
+    others = Fr(1)
+    for k in range(d.size + 1):
+        if k != k0:
+            others *= Fr(float(q["hi"][k])) + Fr(float(q["lo"][k]))
+    return k0, float(det / others)
+
+
+@pytest.mark.parametrize("case", ["s1", "s2", "s4", "tiny"])
+@pytest.mark.parametrize("zf", [0, 1])
+def test_near_zero_recompute(B, case, zf):
+    """Nearly singular arrowheads: the eigenvalue between the positive and the negative poles
+    is far smaller than its distance to them; the GPU recomputes it from A^{-1} (sigma = 0) and
+    meets the bound against det(A) = prod_j d_j f(0) in exact rationals."""
+    if case == "tiny":
+        d = np.array([float.fromhex("0x1.bf656f89b0670p-1"), float.fromhex("-0x1.c35f000a6603ap-1")])
+        z = np.array([float.fromhex("0x1.4c82cd5918a9ap-15"), float.fromhex("0x1.5cb9c1af8ca60p-29")])
+        alpha = float.fromhex("0x1.ee40d73254cdfp-30")
+    else:
+        d, z, alpha = _near_singular(int(case[1:]))
+    n = d.size
+    q = oracle.quad_arrow_all(d, z, alpha)
+    k0, lam = _lam_small_by_det(d, z, alpha, q)
+    ws = B.arrow_workspace(n, torch.device("cuda"))
+    r = B.eig_arrowhead(cu(d), cu(z), alpha, options=B.default_options(zero_finder=zf), ws=ws)
+    g = r["lam"].cpu().numpy()
+    assert B.workspace_stats(ws)["zero_path"] >= 1
+    tol = 16 * (n + 1) * EPS
+    assert abs(g[k0] - lam) <= tol * abs(lam)
+    check(B, d, z, alpha, zero_finder=zf)

@@ -1,8 +1,10 @@
-"""Seeded randomized parity of dpr1_eig (both zero finders) on small problems of many shapes:
-uniform, clustered and graded poles, exact ties, zero and tiny weights, rho over twelve
-decades.  Irreducible problems are compared eigenvalue by eigenvalue and component by
-component with the oracle and binary128; deflated ones by eigenvalues, residual and
-orthogonality (eigenvectors of repeated eigenvalues are a basis choice)."""
+"""Seeded randomized parity on problems of many shapes.  dpr1_eig (both zero finders): uniform,
+clustered and graded poles, exact ties, zero and tiny weights, rho over twelve decades;
+irreducible problems are compared eigenvalue by eigenvalue and component by component with
+the oracle and binary128, deflated ones by eigenvalues, residual and orthogonality
+(eigenvectors of repeated eigenvalues are a basis choice).  dpr1_arrow_eig: random
+arrowheads against binary128.  dpr1_tridiag_eig: random tridiagonal matrices against LAPACK.
+dpr1_eig_batched: a batch of fuzz problems against the single calls."""
 import numpy as np
 import pytest
 
@@ -108,3 +110,86 @@ def test_fuzz_larger_irreducible(B, zf):
         assert np.max(np.abs(g["lam"] - lq) / np.abs(lq)) <= tol(n), (done, n, rho)
         err = np.abs(g["Vt"] - q["Vt"]) / np.maximum(np.abs(q["Vt"]), 1e-300)
         assert err.max() <= tol(n), (done, n, rho, float(err.max()))
+
+
+@pytest.mark.parametrize("zf", [0, 1])
+def test_fuzz_arrowhead(B, zf):
+    """Random irreducible arrowheads: clustered or graded poles, weights over twelve decades,
+    alpha over many decades and both signs, against binary128."""
+    rng = np.random.default_rng(777 + zf)
+    done = 0
+    while done < 40:
+        n = int(rng.integers(1, 300))
+        kind = rng.integers(0, 3)
+        if kind == 0:
+            d = rng.uniform(-1, 1, n)
+        elif kind == 1:
+            c = rng.uniform(-1, 1, max(1, n // 6))
+            d = rng.choice(c, n) + rng.choice([1.0, -1.0], n) * 10.0 ** rng.uniform(-12, -3, n)
+        else:
+            d = np.sign(rng.uniform(-1, 1, n)) * 10.0 ** rng.uniform(-10, 0, n)
+        d = np.sort(d)[::-1].copy()
+        z = rng.choice([1.0, -1.0], n) * 10.0 ** rng.uniform(-12 if rng.random() < 0.5 else -2, 0, n)
+        alpha = float(rng.choice([1.0, -1.0]) * 10.0 ** rng.uniform(-12, 2))
+        if not (np.all(d[:-1] > d[1:]) and not np.any(oracle.zero_weight(z))):
+            continue
+        done += 1
+        r = B.eig_arrowhead(torch.tensor(d, device="cuda"), torch.tensor(z, device="cuda"), alpha,
+                            options=B.default_options(zero_finder=zf))
+        lam, Vt = r["lam"].cpu().numpy(), r["Vt"].cpu().numpy()
+        q = oracle.quad_arrow_all(d, z, alpha, threads=16)
+        lq = q["hi"] + q["lo"]
+        t = 16 * (n + 1) * 2.0 ** -53
+        assert np.max(np.abs(lam - lq) / np.abs(lq)) <= t, (done, n, alpha)
+        err = np.abs(Vt - q["Vt"]) / np.maximum(np.abs(q["Vt"]), 1e-300)
+        assert err.max() <= t, (done, n, alpha, float(err.max()))
+
+
+def test_fuzz_tridiagonal(B):
+    """Random symmetric tridiagonal matrices (uniform, graded diagonals, tiny and zero couplings)
+    by divide and conquer: eigenvalues against LAPACK, residual and orthogonality."""
+    import scipy.linalg
+    rng = np.random.default_rng(99)
+    for case in range(30):
+        n = int(rng.integers(1, 400))
+        a = rng.uniform(-1, 1, n) * (10.0 ** rng.uniform(-6, 0, n) if rng.random() < 0.3 else 1.0)
+        b = rng.uniform(-1, 1, max(n - 1, 0))
+        if rng.random() < 0.3 and n > 1:
+            b *= 10.0 ** rng.uniform(-14, 0, n - 1)
+        if rng.random() < 0.2 and n > 2:
+            b[rng.integers(0, n - 1)] = 0.0
+        lam, Qt = B.eigh_tridiagonal(torch.tensor(a, device="cuda"), torch.tensor(b, device="cuda"),
+                                     options=B.default_options(zero_finder=int(rng.integers(0, 2))))
+        lam, Qt = lam.cpu().numpy(), Qt.cpu().numpy()
+        nT = np.max(np.abs(a)) + 2 * (np.max(np.abs(b)) if n > 1 else 0.0)
+        if n > 1:
+            ref = np.sort(scipy.linalg.eigh_tridiagonal(a, b, eigvals_only=True))[::-1]
+        else:
+            ref = a.copy()
+        assert np.max(np.abs(lam - ref)) <= 16 * n * 2.0 ** -53 * nT, case
+        T = np.diag(a) + (np.diag(b, 1) + np.diag(b, -1) if n > 1 else 0.0)
+        Q = Qt.T
+        assert np.max(np.abs(T @ Q - Q * lam[None, :])) <= 16 * n * 2.0 ** -53 * nT, case
+        assert np.max(np.abs(Q.T @ Q - np.eye(n))) <= 16 * n * 2.0 ** -53, case
+
+
+def test_fuzz_batched_against_single(B):
+    """A batch of random problems of the fuzz shapes solved in one call equals the single
+    calls (both zero finders)."""
+    rng = np.random.default_rng(31)
+    probs = [random_problem(rng) for _ in range(96)]
+    sizes = [p[0].size for p in probs]
+    d = np.concatenate([p[0] for p in probs])
+    z = np.concatenate([p[1] for p in probs])
+    rho = np.array([p[2] for p in probs])
+    bt = B.Batch(sizes)
+    for zf in (0, 1):
+        bt.solve(torch.tensor(d, device="cuda"), torch.tensor(z, device="cuda"), torch.tensor(rho, device="cuda"),
+                 options=B.default_options(zero_finder=zf), check=True)
+        torch.cuda.synchronize()
+        for p, (dp, zp, rp) in enumerate(probs):
+            n = dp.size
+            lam = bt.block(p)[0].cpu().numpy()
+            g = run_gpu(B, dp, zp, rp, zero_finder=zf)
+            scale = np.maximum(np.abs(g["lam"]), np.max(np.abs(g["lam"])) * 2.0 ** -52)
+            assert np.max(np.abs(lam - g["lam"]) / scale) <= tol(n), (zf, p)
