@@ -75,6 +75,9 @@ def lib():
         L.oracle_arroweig.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(Opts),
                                       _dp, _dp, _dp, _dp, _ip, _ip, _dp]
         L.quad_arrow_eigpair.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp]
+        for name in ("oracle_dpr1_r2", "oracle_arrow_r2"):
+            getattr(L, name).argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                         _dp, _dp, _dp]
         _LIB = L
     return _LIB
 
@@ -478,6 +481,19 @@ def arrow_eig_all(d, z, alpha, ks=None, threads=1, opts=None):
 
     _split_run(run, m, threads)
     return out
+
+
+def r2(d, z, rho_or_alpha, k, lam_est, arrow=False):
+    """Remedy R2 alone from an estimate lam_est of eigenvalue k (0-based) of D + rho z z^T, or of
+    the arrowhead [D z; z^T alpha] with arrow=True: dict(lam, sigma, mu, rounds)."""
+    d, z = _f64(d), _f64(z)
+    lam, sig, mu = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    fn = lib().oracle_arrow_r2 if arrow else lib().oracle_dpr1_r2
+    rc = fn(d.size, _ptr(d), _ptr(z), float(rho_or_alpha), int(k), float(lam_est), ctypes.byref(lam),
+            ctypes.byref(sig), ctypes.byref(mu))
+    if rc < 0:
+        raise ValueError("r2: bad arguments")
+    return dict(lam=lam.value, sigma=sig.value, mu=mu.value, rounds=rc)
 
 
 def quad_arrow_all(d, z, alpha, ks=None, threads=1):

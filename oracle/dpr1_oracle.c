@@ -429,6 +429,59 @@ static int o_solve_nonpole(int n, const double* d, const double* z, double rho, 
   return 1;
 }
 
+/*
+ * (R2) from an estimate lam_est of lambda_k.  The shift is fl(lam_est) moved into the
+ * interlacing interval of lambda_k: (d_k, d_{k-1}), or (d_0, d_0 + rho ||z||^2] for k = 0.
+ * Any sigma inside gives lambda_k: f(sigma) < 0 exactly when sigma < lambda_k, and the
+ * exterior eigenvalue on that side of (A - sigma I)^{-1} is 1/(lambda_k - sigma).  It is
+ * computed to high relative accuracy when lambda_k is the eigenvalue nearest to sigma, which
+ * holds when |mu| < (distance from sigma to the nearer pole end of the interval) / 2, since
+ * every other eigenvalue lies beyond those poles.  Otherwise (the estimate was far off: K_nu
+ * of both pole solves near 1/eps) the solve is repeated at sigma = lambda (at most 3 solves).
+ * Returns the number of solves, 0 if the interval holds no double.
+ */
+static int o_r2(int n, const double* d, const double* z, double rho, int k, double lam_est, double* e,
+                double* u, double* sigma_out, double* mu_out) {
+  double lo = d[k], hi;
+  if (k > 0) {
+    hi = d[k - 1];
+  } else {
+    double zz = 0.0;
+    for (int j = 0; j < n; j++) zz += z[j] * z[j];
+    hi = d[0] + rho * zz;
+  }
+  double s = lam_est, mu = 0.0;
+  int rounds = 0;
+  for (;;) {
+    if (!(s > lo)) s = nextafter(lo, INFINITY);           /* also a NaN estimate */
+    if (k > 0 && s >= hi) s = nextafter(hi, -INFINITY);
+    if (k == 0 && s > hi) s = hi;
+    if (!(s > lo) || (k > 0 && !(s < hi))) return 0;
+    o_solve_nonpole(n, d, z, rho, s, e, u, &mu, NULL);
+    rounds++;
+    double room = s - lo;
+    if (k > 0 && hi - s < room) room = hi - s;
+    if (rounds >= 3 || fabs(mu) < 0.5 * room) break;
+    s = s + mu;
+  }
+  *sigma_out = s;
+  *mu_out = mu;
+  return rounds;
+}
+
+/* Test entry point for o_r2: lambda_k by R2 from the estimate lam_est. */
+int oracle_dpr1_r2(int n, const double* d, const double* z, double rho, int k, double lam_est, double* lambda,
+                   double* sigma, double* mu) {
+  if (n < 1 || k < 0 || k >= n || !(rho > 0.0)) return -1;
+  double* e = (double*)malloc(sizeof(double) * n);
+  double* u = (double*)malloc(sizeof(double) * n);
+  if (!e || !u) { free(e); free(u); return -1; }
+  int r = o_r2(n, d, z, rho, k, lam_est, e, u, sigma, mu);
+  if (r) *lambda = *sigma + *mu;
+  free(e); free(u);
+  return r;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Algorithm 1: the k-th eigenpair (k is 0-based here).                      */
 /* ------------------------------------------------------------------------- */
@@ -491,19 +544,12 @@ int oracle_dpr1eig(int n, const double* d, const double* z, double rho, int k,
       if (p2.K_nu < best_K) { best_sigma = d[other]; best_mu = p2.mu; best_K = p2.K_nu; }
     }
     if (K > opt.T_Knu) {
-      /* (R2): a non-pole shift next to lambda, taken from the better of the two
-         pole solutions (the one with the smaller K_nu) */
-      double lam = best_sigma + best_mu;
-      double s2 = lam;
-      if (s2 <= d[k]) s2 = nextafter(d[k], INFINITY);
-      if (k > 0 && s2 >= d[k - 1]) s2 = nextafter(d[k - 1], -INFINITY);
-      int inside = (s2 > d[k]) && (k == 0 || s2 < d[k - 1]);
-      if (inside) {
-        double mu2;
-        int st = 0;
-        o_solve_nonpole(n, d, z, rho, s2, delta, w, &mu2, &st);
+      /* (R2): a non-pole shift next to lambda, from the better of the two pole solutions
+         (the one with the smaller K_nu) */
+      double s2, mu2;
+      if (o_r2(n, d, z, rho, k, best_sigma + best_mu, delta, w, &s2, &mu2)) {
         shift = -1; sigma = s2; mu = mu2; nu = (mu2 != 0.0) ? 1.0 / mu2 : INFINITY; K = 1.0;
-        steps = st; inf.remedy = 2; inf.used_dd = 1;
+        steps = 0; inf.remedy = 2; inf.used_dd = 1;
       }
     }
   }
@@ -789,6 +835,53 @@ static int o_ah_solve_nonpole(int n, const double* d, const double* z, double al
   return 1;
 }
 
+/* (R2) for the arrowhead from an estimate lam_est of lambda_k, as o_r2: the shift is moved
+   into the interlacing interval of lambda_k, (d_k, d_{k-1}), with the exterior ends from
+   Weyl's bounds, lambda_0 <= max(d_0, alpha) + ||z|| and lambda_n >= min(d_{n-1}, alpha) - ||z||;
+   the solve is repeated at sigma = lambda while |mu| is not below half the distance from
+   sigma to the nearer pole end (at most 3 solves).  Returns the number of solves. */
+static int o_ah_r2(int n, const double* d, const double* z, double alpha, int k, double lam_est, double* e,
+                   double* u, double* sigma_out, double* mu_out) {
+  double zn = 0.0;
+  for (int j = 0; j < n; j++) zn += z[j] * z[j];
+  zn = sqrt(zn);
+  const int lo_pole = k < n, hi_pole = k > 0;
+  double lo = lo_pole ? d[k] : (d[n - 1] < alpha ? d[n - 1] : alpha) - zn;
+  double hi = hi_pole ? d[k - 1] : (d[0] > alpha ? d[0] : alpha) + zn;
+  double s = lam_est, mu = 0.0;
+  int rounds = 0;
+  for (;;) {
+    if (lo_pole && !(s > lo)) s = nextafter(lo, INFINITY);
+    if (!lo_pole && !(s >= lo)) s = lo;                    /* also a NaN estimate */
+    if (hi_pole && s >= hi) s = nextafter(hi, -INFINITY);
+    if (!hi_pole && s > hi) s = hi;
+    if ((lo_pole && !(s > lo)) || (hi_pole && !(s < hi))) return 0;
+    o_ah_solve_nonpole(n, d, z, alpha, s, e, u, &mu, NULL);
+    rounds++;
+    double room = INFINITY;
+    if (lo_pole) room = s - lo;
+    if (hi_pole && hi - s < room) room = hi - s;
+    if (rounds >= 3 || fabs(mu) < 0.5 * room) break;
+    s = s + mu;
+  }
+  *sigma_out = s;
+  *mu_out = mu;
+  return rounds;
+}
+
+/* Test entry point for o_ah_r2: lambda_k of the arrowhead by R2 from the estimate lam_est. */
+int oracle_arrow_r2(int n, const double* d, const double* z, double alpha, int k, double lam_est, double* lambda,
+                    double* sigma, double* mu) {
+  if (n < 1 || k < 0 || k > n) return -1;
+  double* e = (double*)malloc(sizeof(double) * n);
+  double* u = (double*)malloc(sizeof(double) * n);
+  if (!e || !u) { free(e); free(u); return -1; }
+  int r = o_ah_r2(n, d, z, alpha, k, lam_est, e, u, sigma, mu);
+  if (r) *lambda = *sigma + *mu;
+  free(e); free(u);
+  return r;
+}
+
 /* Eigenvector [x; -1] / ||.||, x_j = zeta_j / ((d_j - sigma) - mu), scaled 2-norm. */
 static void o_ah_vector(int n, const double* d, const double* z, double sigma, double mu, double* v) {
   double m = 1.0;
@@ -853,14 +946,9 @@ int oracle_arroweig(int n, const double* d, const double* z, double alpha, int k
       if (p2.K_nu < best_K) { best_sigma = d[other]; best_mu = p2.mu; best_K = p2.K_nu; }
     }
     if (K > opt.T_Knu) {
-      /* (R2) sigma = fl(lambda) of the better pole solution, inside (d_k, d_{k-1}) */
-      double lo = (k < n) ? d[k] : -INFINITY, hi = (k > 0) ? d[k - 1] : INFINITY;
-      double s2 = best_sigma + best_mu;
-      if (s2 <= lo) s2 = nextafter(lo, INFINITY);
-      if (s2 >= hi) s2 = nextafter(hi, -INFINITY);
-      if (s2 > lo && s2 < hi) {
-        double mu2;
-        o_ah_solve_nonpole(n, d, z, alpha, s2, delta, w, &mu2, NULL);
+      /* (R2) from the better pole solution */
+      double s2, mu2;
+      if (o_ah_r2(n, d, z, alpha, k, best_sigma + best_mu, delta, w, &s2, &mu2)) {
         shift = -1; sigma = s2; mu = mu2; flags = 2;
       }
     }

@@ -507,3 +507,47 @@ def test_tiny_weights_are_zero_weights():
     q = oracle.quad_all(d[keep], z[keep], rho)
     lk = np.sort(np.concatenate([q["hi"] + q["lo"], d[~keep]]))[::-1]
     assert np.max(np.abs(r["lam"] - lk) / np.abs(lk)) <= 16 * 64 * 2.0 ** -53
+
+
+def _r2_estimates(rng, lo, hi, true):
+    """Estimates an R2 shift may start from: absurd values, the interval ends, random points
+    inside it (uniform and next to either end), and the eigenvalue itself."""
+    est = [1e293, -1e293, float("nan"), 0.0, lo, hi, true]
+    if np.isfinite(hi):
+        w = hi - lo
+        est += list(lo + w * rng.random(3)) + [lo + w * 1e-9, hi - w * 1e-9]
+    else:
+        est += list(lo + abs(true - lo) * 10.0 ** rng.uniform(-3, 3, 4))
+    return est
+
+
+def test_r2_from_any_estimate():
+    """Remedy R2 (Sec. 2) from any starting estimate: the shift is moved into the interlacing
+    interval of lambda_k, where the sign of f picks the side whose exterior eigenvalue of
+    (A - sigma I)^{-1} is 1/(lambda_k - sigma); the solve repeats while sigma is not nearer to
+    lambda_k than to the interval's poles.  Every estimate, absurd ones included, gives
+    lambda_k within 16 n 2^-53 of binary128 on clustered, graded and uniform problems."""
+    rng = np.random.default_rng(77)
+    for case in range(12):
+        n = int(rng.integers(2, 40))
+        kind = case % 3
+        if kind == 0:
+            d = rng.uniform(-1, 1, n)
+        elif kind == 1:
+            c = rng.uniform(-1, 1, max(1, n // 5))
+            d = rng.choice(c, n) + rng.choice([1.0, -1.0], n) * 10.0 ** rng.uniform(-12, -3, n)
+        else:
+            d = np.sign(rng.uniform(-1, 1, n)) * 10.0 ** rng.uniform(-10, 0, n)
+        d = np.sort(d)[::-1].copy()
+        if not np.all(d[:-1] > d[1:]):
+            continue
+        z = rng.choice([1.0, -1.0], n) * 10.0 ** rng.uniform(-6, 0, n)
+        rho = float(10.0 ** rng.uniform(-3, 6))
+        q = oracle.quad_all(d, z, rho, want_vectors=False)
+        lq = q["hi"] + q["lo"]
+        for k in rng.choice(n, size=min(n, 4), replace=False):
+            hi = d[k - 1] if k > 0 else d[0] + rho * float(np.sum(z * z))
+            for est in _r2_estimates(rng, d[k], hi, lq[k]):
+                r = oracle.r2(d, z, rho, k, est)
+                assert 1 <= r["rounds"] <= 3
+                assert abs(r["lam"] - lq[k]) <= tol(n) * abs(lq[k]), (case, k, est, r, lq[k])

@@ -220,3 +220,33 @@ def test_near_zero_eigenvalue_with_tiny_weights():
     r = oracle.arrow_eig_all(d, z, alpha)
     assert r["flags"][1] & 4
     assert abs(Fr(float(r["lam"][1])) - lam_det) <= Fr(16 * 3 * EPS) * abs(lam_det)
+
+
+def test_r2_from_any_estimate():
+    """R2 for the arrowhead from any starting estimate (absurd values, the interval ends,
+    random points inside; the exterior intervals end at Weyl's bounds): lambda_k within
+    16(n+1)2^-53 of binary128."""
+    rng = np.random.default_rng(78)
+    for case in range(12):
+        n = int(rng.integers(1, 40))
+        if case % 2:
+            c = rng.uniform(-1, 1, max(1, n // 5))
+            d = rng.choice(c, n) + rng.choice([1.0, -1.0], n) * 10.0 ** rng.uniform(-12, -3, n)
+        else:
+            d = rng.uniform(-1, 1, n)
+        d = np.sort(d)[::-1].copy()
+        if not np.all(d[:-1] > d[1:]):
+            continue
+        z = rng.choice([1.0, -1.0], n) * 10.0 ** rng.uniform(-6, 0, n)
+        alpha = float(rng.choice([1.0, -1.0]) * 10.0 ** rng.uniform(-8, 2))
+        q = oracle.quad_arrow_all(d, z, alpha)
+        lq = q["hi"] + q["lo"]
+        zn = float(np.sqrt(np.sum(z * z)))
+        for k in rng.choice(n + 1, size=min(n + 1, 4), replace=False):
+            lo = d[k] if k < n else min(d[-1], alpha) - zn
+            hi = d[k - 1] if k > 0 else max(d[0], alpha) + zn
+            ests = [1e293, -1e293, float("nan"), 0.0, lo, hi, lq[k]] + list(lo + (hi - lo) * rng.random(3))
+            for est in ests:
+                r = oracle.r2(d, z, alpha, k, est, arrow=True)
+                assert 1 <= r["rounds"] <= 3
+                assert abs(r["lam"] - lq[k]) <= 16 * (n + 1) * EPS * abs(lq[k]), (case, k, est, r, lq[k])
