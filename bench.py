@@ -14,7 +14,7 @@ write) before every step outside the timed events; nvidia-smi clocks are sampled
 the timed region.  The line carries the roofline of the solve kernel (algorithmic binary64
 operations over its event-timed duration, against the nominal peak; DRAM traffic from the
 committed ncu record while the kernel sources are unchanged), the CPU oracle on a bounded
-sample, the end-to-end rate through the binding from pinned host buffers (double-buffered
+sample (all host cores, and one thread on a smaller sample), the end-to-end rate through the binding from pinned host buffers (double-buffered
 outputs), and extra measurements (--extras; --only runs one alone at size --n):
   fwd_bwd    forward and adjoint at n = 4096 (and n = 32768 with --large)
   batched    4096 uneven problems in one graph replay against a per-problem loop
@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--cpu-sample", type=int, default=4096)
+    ap.add_argument("--cpu-sample", type=int, default=8192)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-vs-loop and forward+backward measurements")
@@ -720,9 +720,12 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, threads, m, dtc = cpu_oracle_rate(d, z, rho, args.cpu_sample)
+        rate1, _, m1, dt1 = cpu_oracle_rate(d, z, rho, max(16, args.cpu_sample // 32), seed=8, threads=1)
         cpu = {"value": rate, "unit": "eigenpairs/s", "cores": threads, "kind": "oracle",
                "sample": "%d random eigenpairs of the same n=%d workload (%.1f s wall on %d threads)"
-                         % (m, n, dtc, threads)}
+                         % (m, n, dtc, threads),
+               "single_thread": {"value": rate1, "unit": "eigenpairs/s", "cores": 1,
+                                 "sample": "%d random eigenpairs of the same workload (%.1f s wall)" % (m1, dt1)}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": world, "steps": args.steps,

@@ -332,16 +332,33 @@ def eig_full(d, z, rho, opts=None, threads=1):
                 mu=np.array(mu_all)[order])
 
 
+def hermitian_abs(z):
+    """|z_j| of complex z as one fixed sequence of correctly rounded binary64 operations:
+    sqrt(x'^2 + y'^2) / s with x' = s Re z_j, y' = s Im z_j and s = 2^-600 (max(|Re|, |Im|) >
+    2^500), 2^600 (below 2^-500) or 1 (separate numpy operations, so no contraction).  This is
+    the reading the Hermitian reduction fixes for its real weights."""
+    z = np.ascontiguousarray(z, dtype=np.complex128)
+    re, im = z.real.copy(), z.imag.copy()
+    m = np.maximum(np.abs(re), np.abs(im))
+    s = np.where(m > 2.0 ** 500, 2.0 ** -600, np.where(m < 2.0 ** -500, 2.0 ** 600, 1.0))
+    inv = np.where(m > 2.0 ** 500, 2.0 ** 600, np.where(m < 2.0 ** -500, 2.0 ** -600, 1.0))
+    x = re * s
+    y = im * s
+    xx = x * x
+    yy = y * y
+    return np.sqrt(xx + yy) * inv
+
+
 def eig_hermitian(d, z, rho, opts=None, threads=1, ks=None):
     """Eigenpairs of the complex Hermitian D + rho z z^* (d real, non-increasing).
 
-    With phi_j = z_j / |z_j| (phi_j = 1 for z_j = 0) and Phi = diag(phi),
+    With phi_j = z_j / |z_j| (phi_j = 1 for z_j = 0; |z_j| from ``hermitian_abs``) and Phi = diag(phi),
     Phi^* (D + rho z z^*) Phi = D + rho |z| |z|^T: the eigenvalues are those of the real
     problem with weights |z_j| (Algorithm 1 through ``eig_all``, or ``eig_full`` when it
     deflates) and v_k = Phi u_k.  Returns dict(lam, Vt, sigma, mu) with complex Vt[k] = v_k."""
     d = _f64(d)
     z = np.ascontiguousarray(z, dtype=np.complex128)
-    a = np.abs(z)
+    a = hermitian_abs(z)
     phi = np.ones(z.size, dtype=np.complex128)
     nz = a > 0
     phi[nz] = z.real[nz] / a[nz] + 1j * (z.imag[nz] / a[nz])   # each part correctly rounded

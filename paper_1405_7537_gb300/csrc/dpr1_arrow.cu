@@ -371,8 +371,10 @@ __global__ void k_arrow_classify(int n, const double* __restrict__ d, ArrowWs w,
 // Remedies for the flagged eigenvalues, one lane group each (work counter):
 //  (R1) solve at the other neighbouring pole o when K' < K; accept when K' <= T_Knu and
 //       ratio <= T_Knu (beyond that the eigenvector formula at d_o cancels);
-//  (R2) otherwise sigma = fl(lambda) of the better pole solution, moved into the open interval
-//       (d_k, d_{k-1}) (d_n = -inf, d_{-1} = +inf) if it falls on a pole, and the non-pole solve.
+//  (R2) otherwise sigma = fl(lambda) of the better pole solution, moved into the interlacing
+//       interval of lambda_k (exterior ends from Weyl's bounds), and the non-pole solve,
+//       repeated at the new lambda while sigma is not nearer to lambda_k than to the
+//       interval's poles (at most 3 solves), as for D + rho z z^T.
 template <int L>
 __global__ void __launch_bounds__(L > 256 ? L : 256) k_arrow_fix(int n, const double* __restrict__ d, double alpha,
                                                                    ArrowWs w, double T_Knu, int cap, bool fast) {
@@ -415,12 +417,24 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_arrow_fix(int n, const do
       }
     }
     if (!done) {
+      // the interlacing interval of lambda_k; the exterior ends from Weyl's bounds,
+      // lambda_0 <= max(d_0, alpha) + ||z||, lambda_n >= min(d_{n-1}, alpha) - ||z||
+      const bool lo_pole = k < n, hi_pole = k > 0;
+      double zn = 0.0;
+      if (!lo_pole || !hi_pole) {
+        double zs = 0.0;
+        for (int j = lane; j < n; j += L) zs = __dadd_rn(zs, w.zz[j]);
+        zn = sqrt(group_sum<L>(zs, gm));
+      }
+      const double lo = lo_pole ? d[k] : fmin(d[n - 1], alpha) - zn;
+      const double hi = hi_pole ? d[k - 1] : fmax(d[0], alpha) + zn;
       double sg = __dadd_rn(best_sig, best_mu);
-      const double lo = (k < n) ? d[k] : -INFINITY;
-      const double hi = (k > 0) ? d[k - 1] : INFINITY;
-      if (k < n && sg <= lo) sg = dnext_up(lo);
-      if (k > 0 && sg >= hi) sg = dnext_down(hi);
-      if (sg > lo && sg < hi) {
+      for (int round = 0; round < 3; round++) {
+        if (lo_pole && !(sg > lo)) sg = dnext_up(lo);
+        if (!lo_pole && !(sg >= lo)) sg = lo;
+        if (hi_pole && sg >= hi) sg = dnext_down(hi);
+        if (!hi_pole && sg > hi) sg = hi;
+        if ((lo_pole && !(sg > lo)) || (hi_pole && !(sg < hi))) break;
         bool ok;
         int st2;
         const double m2 = solve_nonpole_arrow<L>(d, w.zl, w.zz, n, alpha, sg, k > 0 ? k - 1 : -1, k < n ? k : -1,
@@ -428,6 +442,12 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_arrow_fix(int n, const do
         if (!ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
         if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)st2);
         new_sig = sg; new_mu = m2; new_shift = -1;
+        // repeat while sigma is not nearer to lambda_k than to the interval's poles
+        double room = INFINITY;
+        if (lo_pole) room = sg - lo;
+        if (hi_pole) room = fmin(room, hi - sg);
+        if (fabs(m2) < 0.5 * room) break;
+        sg = __dadd_rn(sg, m2);
       }
     }
     if (lane == 0) {

@@ -447,8 +447,12 @@ __global__ void k_classify(Prob pb, Ws w, double T_Knu) {
 // k_fix: remedies for the flagged eigenvalues, one lane group each.
 //  (R1) solve at the other neighbouring pole o; accept when K' < K, K' <= T_Knu and
 //       ratio <= T_Knu (beyond that ratio the eigenvector formula at d_o cancels).
-//  (R2) otherwise shift to sigma = fl(lambda) from the better pole solution, moved into
-//       the open interval (d_k, d_{k-1}) if it falls on a pole, and solve_nonpole.
+//  (R2) otherwise shift to sigma = fl(lambda) from the better pole solution, moved into the
+//       interlacing interval of lambda_k ((d_k, d_{k-1}); (d_0, d_0 + rho ||z||^2] for k = 0),
+//       and solve_nonpole.  Any sigma there yields lambda_k (the sign of f(sigma) picks the
+//       side), accurately once lambda_k is the eigenvalue nearest to sigma; while |mu| is not
+//       below half the distance to the nearer pole end the solve repeats at the new lambda
+//       (at most 3 solves: a first estimate with K_nu near 1/eps is noise).
 // ---------------------------------------------------------------------------------
 template <int L>
 __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double T_Knu, int cap, bool fast) {
@@ -501,18 +505,34 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double
       }
     }
     if (!done) {
+      // the interlacing interval of lambda_k, (d_k, d_{k-1}), or (d_0, d_0 + rho ||z||^2] (Weyl)
+      const double lo = d[k];
+      double hi;
+      if (k > 0) {
+        hi = d[k - 1];
+      } else {
+        double zs = 0.0;
+        for (int j = lane; j < n; j += L) zs = __dadd_rn(zs, zz[j]);
+        hi = __fma_rn(rho, group_sum<L>(zs, gm), d[0]);
+      }
       double s = __dadd_rn(best_sig, best_mu);
-      double lo = d[k];
-      double hi = (k > 0) ? d[k - 1] : INFINITY;
-      if (s <= lo) s = dnext_up(lo);
-      if (s >= hi) s = dnext_down(hi);
-      if (s > lo && s < hi) {
+      for (int round = 0; round < 3; round++) {
+        if (!(s > lo)) s = dnext_up(lo);
+        if (k > 0 && s >= hi) s = dnext_down(hi);
+        if (k == 0 && s > hi) s = hi;
+        if (!(s > lo) || (k > 0 && !(s < hi))) break;
         bool ok;
         int st2 = 0;
-        double m2 = solve_nonpole<L>(d, zl, zz, n, rho, s, k > 0 ? k - 1 : -1, k, cap, fast, lane, gm, &ok, &st2);
+        const double m2 =
+            solve_nonpole<L>(d, zl, zz, n, rho, s, k > 0 ? k - 1 : -1, k, cap, fast, lane, gm, &ok, &st2);
         if (!ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
         if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)st2);
         new_sig = s; new_mu = m2; new_shift = -1;
+        // accurate when lambda_k is the eigenvalue nearest to sigma: every other eigenvalue lies
+        // beyond the interval's poles; otherwise solve again at the new lambda
+        const double room = (k > 0) ? fmin(s - lo, hi - s) : s - lo;
+        if (fabs(m2) < 0.5 * room) break;
+        s = __dadd_rn(s, m2);
       }
     }
     if (lane == 0) {

@@ -48,16 +48,31 @@ static size_t herm_layout(int64_t n, HermWs* w, char* base) {
   return off;
 }
 
-// |z_j| (hypot, within one ulp) and phi_j = z_j / |z_j| (phi_j = 1 for z_j = 0, a deflated
-// component whose eigenvector is e_j).  Non-finite entries give a non-finite |z_j|, which the
-// real path reports as DPR1_ERR_NONFINITE.
+// |x + iy| as one fixed sequence of correctly rounded binary64 operations,
+// sqrt(x'^2 + y'^2) / s with x' = s x, y' = s y and s = 2^-600 (max(|x|, |y|) > 2^500),
+// 2^600 (below 2^-500) or 1, so that every IEEE binary64 implementation of the same steps
+// gives the same bits (within 1.5 ulps of the true modulus).  The real problem then has
+// exactly the same weights wherever it is formed.
+__device__ __forceinline__ double abs_binary64(double x, double y) {
+  const double m = fmax(fabs(x), fabs(y));
+  double s = 1.0, inv = 1.0;
+  if (m > 0x1p500) { s = 0x1p-600; inv = 0x1p600; }
+  else if (m < 0x1p-500) { s = 0x1p600; inv = 0x1p-600; }
+  const double xs = __dmul_rn(x, s), ys = __dmul_rn(y, s);
+  return __dmul_rn(__dsqrt_rn(__dadd_rn(__dmul_rn(xs, xs), __dmul_rn(ys, ys))), inv);
+}
+
+// |z_j| and phi_j = z_j / |z_j| (phi_j = 1 for z_j = 0, a deflated component whose eigenvector
+// is e_j).  Non-finite entries give a non-finite |z_j|, which the real path reports as
+// DPR1_ERR_NONFINITE.
 __global__ void k_herm_prep(int n, const double2* __restrict__ z, double* __restrict__ zabs,
                             double2* __restrict__ phase) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     const double2 c = z[j];
-    const double a = hypot(c.x, c.y);
+    const double a = abs_binary64(c.x, c.y);
     zabs[j] = a;
-    phase[j] = (a > 0.0 && a <= 1.7976931348623157e308) ? make_double2(c.x / a, c.y / a) : make_double2(1.0, 0.0);
+    phase[j] = (a > 0.0 && a <= 1.7976931348623157e308) ? make_double2(__ddiv_rn(c.x, a), __ddiv_rn(c.y, a))
+                                                       : make_double2(1.0, 0.0);
   }
 }
 

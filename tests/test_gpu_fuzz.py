@@ -193,3 +193,45 @@ def test_fuzz_batched_against_single(B):
             g = run_gpu(B, dp, zp, rp, zero_finder=zf)
             scale = np.maximum(np.abs(g["lam"]), np.max(np.abs(g["lam"])) * 2.0 ** -52)
             assert np.max(np.abs(lam - g["lam"]) / scale) <= tol(n), (zf, p)
+
+
+@pytest.mark.parametrize("zf", [0, 1])
+def test_fuzz_hermitian(B, zf):
+    """Complex Hermitian D + rho z z^* with the fuzz shapes and random phases (some weights
+    purely real or purely imaginary, some zero): irreducible problems against the oracle's
+    phase reduction and binary128 component by component, deflated ones by eigenvalues,
+    residual and unitarity."""
+    rng = np.random.default_rng(555 + zf)
+    n_irr = 0
+    for case in range(60):
+        d, zr, rho = random_problem(rng)
+        n = d.size
+        ph = np.exp(1j * rng.uniform(-np.pi, np.pi, n))
+        pick = rng.random(n)
+        ph[pick < 0.1] = 1.0
+        ph[(pick >= 0.1) & (pick < 0.2)] = 1j
+        z = np.abs(zr) * ph
+        z[zr == 0] = 0.0
+        r = B.eig_hermitian(torch.tensor(d, device="cuda"), torch.tensor(z, device="cuda"), rho,
+                            options=B.default_options(zero_finder=zf))
+        lam, Vt = r["lam"].cpu().numpy(), r["Vt"].cpu().numpy()
+        a = oracle.hermitian_abs(z)
+        if irreducible(d, a, rho):
+            n_irr += 1
+            o = oracle.eig_hermitian(d, z, rho)
+            scale = np.abs(o["lam"])
+            assert np.max(np.abs(lam - o["lam"]) / scale) <= tol(n), (case, "lambda vs oracle")
+            err = np.abs(Vt - o["Vt"]) / np.maximum(np.abs(o["Vt"]), 1e-300)
+            assert err.max() <= tol(n), (case, "vector vs oracle", float(err.max()))
+            q = oracle.quad_all(d, a, rho)
+            lq = q["hi"] + q["lo"]
+            assert np.max(np.abs(lam - lq) / np.abs(lq)) <= tol(n), (case, "lambda vs binary128")
+        else:
+            A = np.diag(d).astype(np.complex128) + rho * np.outer(z, z.conj())
+            nA = max(np.linalg.norm(A, 2), 1e-300)
+            ref = np.sort(np.linalg.eigvalsh(A))[::-1]
+            assert np.max(np.abs(lam - ref)) <= 64 * n * 2.0 ** -53 * nA, (case, "lambda (deflated)")
+            V = Vt.T
+            assert np.max(np.abs(A @ V - V * lam[None, :])) <= 64 * n * 2.0 ** -53 * nA, (case, "residual")
+            assert np.max(np.abs(V.conj().T @ V - np.eye(n))) <= 64 * n * 2.0 ** -53, (case, "unitarity")
+    assert n_irr >= 15

@@ -45,10 +45,10 @@ def check(B, d, z, rho, ks=None, **opt):
     assert np.max(crel(g["Vt"][rows], r["Vt"])) <= tol(n)
     # binary128: eigenvalues, and the vectors through the same phases
     kq = rows[:: max(1, rows.size // 16)]
-    q = oracle.quad_all(d, np.abs(z), rho, ks=kq, threads=16)
+    q = oracle.quad_all(d, oracle.hermitian_abs(z), rho, ks=kq, threads=16)
     lam_q = q["hi"] + q["lo"]
     assert np.max(np.abs(g["lam"][kq] - lam_q) / np.abs(lam_q)) <= tol(n)
-    a = np.abs(z)
+    a = oracle.hermitian_abs(z)
     phi = z.real / a + 1j * (z.imag / a)
     assert np.max(crel(g["Vt"][kq], q["Vt"] * phi[None, :])) <= tol(n)
     return g
