@@ -54,9 +54,9 @@ ACCEL_OPS_PER_TERM = 8    # the same with its slope (mul, mul, fma)
 # TwoProd of the square (2), quotient and its first-order correction (5), compensated
 # accumulation (7)
 DD_OPS_PER_TERM = 20
-# kernels one dpr1_eig call launches: k_scan, k_deflate, k_solve, k_classify, k_fix, k_zero_detect,
+# kernels one dpr1_eig call launches: k_norm, k_scan, k_deflate, k_solve, k_classify, k_fix, k_zero_detect,
 # k_zero_solve, k_defl_positions, k_vectors, k_defl_rows, k_trivial
-LAUNCHES_PER_CALL = 11
+LAUNCHES_PER_CALL = 12
 
 
 def workload_config(n):

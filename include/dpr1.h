@@ -34,9 +34,17 @@
  *   zeta_j / ((d_j - sigma_k) - mu_k).
  * - Deflation (Sec. 1): zeta_j == 0 gives the eigenpair (d_j, e_j); d_j == d_{j+1}
  *   gives the eigenvalue d_j after a Givens rotation in the (j, j+1) plane.  Both are
- *   exact tests.  A weight whose square is not a normal binary64 number (|zeta_j| <
- *   2^-511) counts as zero: the secular function only sees zeta_j^2, and dropping it
- *   changes A by less than 2^-510 rho ||z||.  Deflated pairs carry sigma = lambda, mu = 0.
+ *   exact tests.  A weight whose square, after the normalisation below, is not a normal
+ *   binary64 number (|zeta_j| < 2^(b - 511), max|zeta| = m 2^b with m in [1/2, 1)) counts as
+ *   zero: the secular function only sees zeta_j^2, and dropping it changes A by less than
+ *   2^-510 rho ||z||.  Deflated pairs carry sigma = lambda, mu = 0.
+ * - Normalisation: each problem is solved as A = 2^a (D' + rho' z' z'^T) with the exact
+ *   powers of two D' = 2^-a D (max|d_j| = m 2^a), z' = 2^-b z and rho' = 2^(2b - a) rho, and
+ *   the results are scaled back.  In the normal range this changes no rounding; it lets data
+ *   of any magnitude through.  An eigenpair that still needs values outside the binary64
+ *   range (mu below 2^-1022 in the normalised units: the eigenvalue closer to its pole than
+ *   binary64 can resolve with full precision; or rho' itself outside the normal range) is
+ *   reported as DPR1_ERR_RANGE, never returned silently.
  * - The functions never throw, never exit and never wait on the device except in
  *   dpr1_stream_status().
  */
@@ -66,7 +74,8 @@ typedef enum {
   DPR1_ERR_NONFINITE = 4,      /* d, z or a gradient holds Inf/NaN (device check) */
   DPR1_ERR_NOT_CONVERGED = 5,  /* a bisection did not close within its iteration cap (device) */
   DPR1_ERR_CUDA = 6,           /* a CUDA launch or runtime call failed */
-  DPR1_ERR_WORKSPACE = 7       /* workspace NULL, misaligned (256 B) or smaller than required */
+  DPR1_ERR_WORKSPACE = 7,      /* workspace NULL, misaligned (256 B) or smaller than required */
+  DPR1_ERR_RANGE = 8           /* an eigenpair needs values outside the binary64 range (device) */
 } dpr1_status;
 
 /* Tunables; pass NULL for the defaults (dpr1_default_options). */
@@ -104,7 +113,7 @@ DPR1_API size_t dpr1_workspace_size(int64_t n);
  *
  *   n        order (n >= 0; n == 0 is a no-op)
  *   d, z     device double[n]; d non-increasing, any z (zeros and ties are deflated, and so is
- *            a weight whose square is not a normal binary64 number, |z_j| < 2^-511)
+ *            a weight below 2^-511 relative to the largest, see above)
  *   rho      rho >= 0 (rho == 0 gives lambda = d, V = I)
  *   lambda   device double[n], out: eigenvalues, non-increasing
  *   Vt       device double[n*ldv] or NULL, out: row k = v_k (ldv >= n)
@@ -114,7 +123,8 @@ DPR1_API size_t dpr1_workspace_size(int64_t n);
  *   opt      NULL or tunables
  *   stream   CUDA stream
  * Errors: DPR1_ERR_ARG, DPR1_ERR_RHO, DPR1_ERR_WORKSPACE, DPR1_ERR_CUDA synchronously;
- * DPR1_ERR_UNSORTED, DPR1_ERR_NONFINITE, DPR1_ERR_NOT_CONVERGED via dpr1_stream_status.
+ * DPR1_ERR_UNSORTED, DPR1_ERR_NONFINITE, DPR1_ERR_RANGE, DPR1_ERR_NOT_CONVERGED via
+ * dpr1_stream_status.
  */
 DPR1_API dpr1_status dpr1_eig(int64_t n, const double* d, const double* z, double rho,
                      double* lambda, double* Vt, int64_t ldv,
@@ -260,8 +270,10 @@ DPR1_API size_t dpr1_arrow_workspace_size(int64_t n);
  * (T_zero |lambda| < distance) is recomputed from A^{-1} (sigma = 0) when no pole is zero.
  *
  *   n          number of poles (n >= 0; the matrix has order n + 1)
- *   d, z       device double[n]: d strictly decreasing, every |z_j| >= 2^-511 (the matrix is
- *              irreducible; deflate equal poles and zero weights before the call)
+ *   d, z       device double[n]: d strictly decreasing, every |z_j| >= 2^(a - 511) with
+ *              max(|d_j|, |z_j|, |alpha|) = m 2^a, m in [1/2, 1) (the matrix is irreducible;
+ *              deflate equal poles and zero weights before the call).  The matrix is solved
+ *              as 2^a (2^-a A), an exact normalisation, as dpr1_eig does
  *   alpha      the corner entry
  *   lambda     device double[n+1], out: eigenvalues, non-increasing; they interlace d
  *   Vt         device double[(n+1)*ldv] or NULL, out: row k = v_k (n + 1 entries, ldv >= n + 1)
@@ -273,7 +285,7 @@ DPR1_API size_t dpr1_arrow_workspace_size(int64_t n);
  *              reads its counters like those of dpr1_eig
  * Errors: DPR1_ERR_ARG, DPR1_ERR_WORKSPACE, DPR1_ERR_CUDA synchronously; through
  * dpr1_stream_status: DPR1_ERR_ARG (equal poles or a zero weight), DPR1_ERR_UNSORTED,
- * DPR1_ERR_NONFINITE, DPR1_ERR_NOT_CONVERGED.
+ * DPR1_ERR_NONFINITE, DPR1_ERR_RANGE, DPR1_ERR_NOT_CONVERGED.
  */
 DPR1_API dpr1_status dpr1_arrow_eig(int64_t n, const double* d, const double* z, double alpha,
                                     double* lambda, double* Vt, int64_t ldv,

@@ -20,6 +20,7 @@ Two references live here:
 weights |z_j| by the diagonal unitary of the phases of z.
 """
 import ctypes
+import math
 import os
 from concurrent.futures import ThreadPoolExecutor
 
@@ -45,6 +46,17 @@ class Info(ctypes.Structure):
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
+
+
+class OracleRangeError(ValueError):
+    """The eigenpair needs values outside the binary64 range of the normalised problem (the
+    oracle's code 4): mu zero, subnormal or not finite, or lambda or the vector not finite."""
+
+
+def _raise(fn, rc):
+    if rc == 4:
+        raise OracleRangeError("%s: outside the binary64 range (code 4)" % fn)
+    raise ValueError("%s failed with code %d" % (fn, rc))
 
 
 def lib():
@@ -111,7 +123,7 @@ def dpr1eig(d, z, rho, k, opts=None):
     rc = lib().oracle_dpr1eig(n, _ptr(d), _ptr(z), float(rho), int(k), ctypes.byref(o),
                               ctypes.byref(lam), _ptr(v), ctypes.byref(info))
     if rc:
-        raise ValueError("oracle_dpr1eig failed with code %d" % rc)
+        _raise("oracle_dpr1eig", rc)
     return lam.value, v, {f[0]: getattr(info, f[0]) for f in Info._fields_}
 
 
@@ -140,7 +152,7 @@ def eig_all(d, z, rho, opts=None, ks=None, threads=1, want_vectors=True):
             rc = L.oracle_dpr1eig(n, _ptr(d), _ptr(z), float(rho), int(ks[p]), ctypes.byref(o),
                                   ctypes.byref(lam), _ptr(v), ctypes.byref(info))
             if rc:
-                raise ValueError("oracle_dpr1eig failed with code %d" % rc)
+                _raise("oracle_dpr1eig", rc)
             out["lam"][p] = lam.value
             out["sigma"][p] = info.sigma
             out["mu"][p] = info.mu
@@ -257,19 +269,24 @@ def dd_op(name, a, b):
     return out[0], out[1]
 
 
-def zero_weight(z):
-    """A weight whose square is below the normal range of binary64 (|zeta| < 2^-511) counts as
-    zero: the secular function sees only zeta^2, which is not representable, and deflating it
-    changes A = D + rho z z^T by less than 2^-510 rho ||z||."""
-    return np.abs(z) < 2.0 ** -511
+def zero_weight(z, zmax=None):
+    """A weight that is below 2^-511 after the normalisation max|zeta| in [1/2, 1) counts as zero:
+    |zeta_j| < 2^(e - 511) with max|zeta| = m 2^e (m in [1/2, 1); ``zmax`` gives the maximum when
+    z is a part of the problem).  The secular function of the normalised problem sees only
+    zeta_j^2, which is then not a normal binary64 number, and deflating it changes
+    A = D + rho z z^T by less than 2^-510 rho ||z||."""
+    z = np.asarray(z)
+    m = float(np.max(np.abs(z))) if zmax is None and z.size else (0.0 if zmax is None else float(zmax))
+    e = math.frexp(m)[1] if (m > 0.0 and math.isfinite(m)) else 0
+    return np.abs(z) < math.ldexp(1.0, e - 511)
 
 
 def eig_full(d, z, rho, opts=None, threads=1):
     """Eigen-decomposition of D + rho z z^T for any d sorted non-increasingly.
 
     Handles rho == 0 (lambda = d, V = I), rho < 0 (Sec. 1: solve -D - rho z z^T),
-    zeta_j == 0 and d_j == d_{j+1} (Sec. 1 deflation, exact tests only; a weight whose square
-    is not a normal binary64 number counts as zero, see ``zero_weight``) and returns
+    zeta_j == 0 and d_j == d_{j+1} (Sec. 1 deflation, exact tests only; a weight below 2^-511
+    times the power of two above the largest weight counts as zero, see ``zero_weight``) and returns
     dict(lam, Vt, sigma, mu) with lam non-increasing and Vt[k] = v_k.  Deflated pairs
     carry sigma = lambda and mu = 0."""
     d = _f64(d).copy()
@@ -291,9 +308,10 @@ def eig_full(d, z, rho, opts=None, threads=1):
     # --- deflation (exact tests only) ---
     Q = np.eye(n)              # accumulated rotations: z_rot = Q z, A = Q^T (D + rho z_rot z_rot^T) Q
     zr = z.copy()
+    zmax = float(np.max(np.abs(z)))   # the zero-weight rule is relative to the largest weight
     defl = []                  # (position, eigenvalue) of deflated pairs in the rotated basis
     for j in range(n):
-        if zero_weight(zr[j]):
+        if zero_weight(zr[j], zmax):
             defl.append(j)
     # ties: rotate each later member of a group of equal d's into the first non-zero member
     j = 0
@@ -301,7 +319,7 @@ def eig_full(d, z, rho, opts=None, threads=1):
         g = j
         while g + 1 < n and d[g + 1] == d[j]:
             g += 1
-        members = [p for p in range(j, g + 1) if not zero_weight(zr[p])]
+        members = [p for p in range(j, g + 1) if not zero_weight(zr[p], zmax)]
         if len(members) > 1:
             a = members[0]
             for p in members[1:]:
@@ -491,7 +509,7 @@ def arrow_eig_all(d, z, alpha, ks=None, threads=1, opts=None):
                                        ctypes.byref(lam), _ptr(v), ctypes.byref(sig), ctypes.byref(mu),
                                        ctypes.byref(sh), ctypes.byref(fl), ctypes.byref(K))
             if rc:
-                raise ValueError("oracle_arroweig failed with code %d" % rc)
+                _raise("oracle_arroweig", rc)
             out["lam"][p], out["sigma"][p], out["mu"][p], out["shift"][p] = lam.value, sig.value, mu.value, sh.value
             out["flags"][p], out["K_nu"][p] = fl.value, K.value
             out["Vt"][p] = v

@@ -363,6 +363,9 @@ static void o_solve_at_pole(int n, const double* d, const double* z, double rho,
   double nrm = fabs(nu) > fabs(other) ? fabs(nu) : fabs(other);
   r->nu = nu; r->mu = 1.0 / nu; r->b = ai.b;
   r->K_nu = nrm / fabs(nu); r->kappa_nu = ai.kappa_nu;
+  /* a solve that left the binary64 range (nu infinite or NaN, mu zero) is no solution: it
+     counts as K_nu = inf, so the remedies take over */
+  if (!(r->K_nu >= 1.0) || !isfinite(nu) || r->mu == 0.0) r->K_nu = INFINITY;
   r->steps = steps; r->used_dd = ai.used_dd;
 }
 
@@ -437,7 +440,9 @@ static int o_solve_nonpole(int n, const double* d, const double* z, double rho, 
  * computed to high relative accuracy when lambda_k is the eigenvalue nearest to sigma, which
  * holds when |mu| < (distance from sigma to the nearer pole end of the interval) / 2, since
  * every other eigenvalue lies beyond those poles.  Otherwise (the estimate was far off: K_nu
- * of both pole solves near 1/eps) the solve is repeated at sigma = lambda (at most 3 solves).
+ * of both pole solves near 1/eps) the next shift is the midpoint of the interval (the Weyl
+ * bound for k = 0), from which lambda_k is at least as near as any other eigenvalue, and the
+ * one after is the lambda found there (at most 3 solves).
  * Returns the number of solves, 0 if the interval holds no double.
  */
 static int o_r2(int n, const double* d, const double* z, double rho, int k, double lam_est, double* e,
@@ -462,7 +467,11 @@ static int o_r2(int n, const double* d, const double* z, double rho, int k, doub
     double room = s - lo;
     if (k > 0 && hi - s < room) room = hi - s;
     if (rounds >= 3 || fabs(mu) < 0.5 * room) break;
-    s = s + mu;
+    /* not reliable from this shift (the estimate was far off).  Next, a shift from which
+       lambda_k is at least as near as any other eigenvalue, so that the solve there is
+       accurate: the midpoint of (d_k, d_{k-1}), or for k = 0 the Weyl bound (every other
+       eigenvalue lies below lambda_0); then, if still needed, the lambda found there */
+    s = (rounds == 1) ? (k > 0 ? lo + 0.5 * (hi - lo) : hi) : s + mu;
   }
   *sigma_out = s;
   *mu_out = mu;
@@ -485,8 +494,28 @@ int oracle_dpr1_r2(int n, const double* d, const double* z, double rho, int k, d
 /* ------------------------------------------------------------------------- */
 /* Algorithm 1: the k-th eigenpair (k is 0-based here).                      */
 /* ------------------------------------------------------------------------- */
-int oracle_dpr1eig(int n, const double* d, const double* z, double rho, int k,
-                   const oracle_opts* opt_in, double* lambda_out, double* v, oracle_info* info) {
+/* The eigenpair needs values outside the binary64 range (of the normalised problem): mu is
+   zero, subnormal or not finite (lambda lies within 2^-1022 of its shift, where mu and with it
+   the eigenvector's components lose precision), or lambda or a component of v is not finite. */
+static int o_out_of_range(int n, double mu, double lambda, const double* v) {
+  if (!(fabs(mu) >= 0x1p-1022) || !isfinite(mu) || !isfinite(lambda)) return 1;
+  if (v)
+    for (int j = 0; j < n; j++)
+      if (!isfinite(v[j])) return 1;
+  return 0;
+}
+
+/* After a non-pole shift (R2): the difference d_p - lambda = (d_p - sigma) - mu to a
+   neighbouring pole p cancels by more than a factor 16.  This is the case the paper resolves
+   with sigma in double the working precision (no double between lambda and the pole), which
+   is not implemented: the pair is reported as out of range. */
+static int o_pole_difference_cancels(double dp, double sigma, double mu) {
+  const double t = (dp - sigma) - mu;
+  return 16.0 * fabs(t) < fabs(dp - sigma) + fabs(mu);
+}
+
+static int o_dpr1eig_core(int n, const double* d, const double* z, double rho, int k,
+                          const oracle_opts* opt_in, double* lambda_out, double* v, oracle_info* info) {
   oracle_opts opt;
   if (opt_in) opt = *opt_in; else oracle_default_opts(&opt);
   if (n < 1 || k < 0 || k >= n || !(rho > 0.0)) return 1;
@@ -578,7 +607,62 @@ int oracle_dpr1eig(int n, const double* d, const double* z, double rho, int k,
   *lambda_out = lambda;
   if (info) *info = inf;
   free(delta); free(w);
-  return 0;
+  if (shift < 0 && (o_pole_difference_cancels(d[k], sigma, mu) ||
+                    (k > 0 && o_pole_difference_cancels(d[k - 1], sigma, mu))))
+    return 4;
+  return o_out_of_range(n, mu, lambda, v) ? 4 : 0;
+}
+
+/*
+ * Exact power-of-two normalisation (the paper takes the data in range).  With
+ * max|d_j| = m_d 2^e_d, max|zeta_j| = m_z 2^e_z and rho = m_r 2^e_r (m in [1/2, 1), e = 0 for
+ * a zero), a = max(e_d, e_r + 2 e_z) and b = e_z: D' = 2^-a D, z' = 2^-b z,
+ * rho' = 2^(2b - a) rho, and A = 2^a (D' + rho' z' z'^T) has the same eigenvectors and
+ * lambda = 2^a lambda'.  Multiplying by a power of two changes no rounding while everything
+ * stays in the normal range, so in range this gives the bits of the unnormalised computation;
+ * outside it the matrix scale is about 1, rho' <= 4 and max|zeta'| is in [1/2, 1), which keeps
+ * zeta_j^2, rho zeta_j^2 and the poles' differences away from overflow.
+ */
+void oracle_scale_exponents(int n, const double* d, const double* z, double rho, int* a_out, int* b_out) {
+  double md = 0.0, mz = 0.0;
+  for (int j = 0; j < n; j++) {
+    if (fabs(d[j]) > md) md = fabs(d[j]);
+    if (fabs(z[j]) > mz) mz = fabs(z[j]);
+  }
+  int ed = 0, ez = 0, er = 0;
+  if (md > 0.0 && isfinite(md)) frexp(md, &ed);
+  if (mz > 0.0 && isfinite(mz)) frexp(mz, &ez);
+  if (rho > 0.0 && isfinite(rho)) frexp(rho, &er);
+  int a = ed;
+  if (!(md > 0.0) && mz > 0.0 && rho > 0.0) a = er + 2 * ez;
+  *a_out = a;
+  *b_out = ez;
+}
+
+int oracle_dpr1eig(int n, const double* d, const double* z, double rho, int k,
+                   const oracle_opts* opt_in, double* lambda_out, double* v, oracle_info* info) {
+  if (n < 1 || k < 0 || k >= n || !(rho > 0.0)) return 1;
+  int a, b;
+  oracle_scale_exponents(n, d, z, rho, &a, &b);
+  double* ds = (double*)malloc(sizeof(double) * n);
+  double* zs = (double*)malloc(sizeof(double) * n);
+  if (!ds || !zs) { free(ds); free(zs); return 2; }
+  for (int j = 0; j < n; j++) { ds[j] = ldexp(d[j], -a); zs[j] = ldexp(z[j], -b); }
+  const double rs = ldexp(rho, 2 * b - a);
+  /* rho' = 0 (the rank-one part below 2^-1074 of the poles' scale): outside the range */
+  int rc = (rs > 0.0) ? o_dpr1eig_core(n, ds, zs, rs, k, opt_in, lambda_out, v, info) : 4;
+  free(ds); free(zs);
+  if (rc && rc != 4) return rc;
+  if (rs == 0.0) return 4;
+  *lambda_out = ldexp(*lambda_out, a);
+  if (info) {
+    info->sigma = ldexp(info->sigma, a);
+    info->mu = ldexp(info->mu, a);
+    info->lambda = ldexp(info->lambda, a);
+    info->nu = ldexp(info->nu, -a);
+    info->b = ldexp(info->b, -a);
+  }
+  return rc;
 }
 
 /* All eigenpairs k in [k0, k1): lambda[k], V row-major with row k = v_k, plus (sigma, mu). */
@@ -788,6 +872,8 @@ static void o_ah_solve_at_pole(int n, const double* d, const double* z, double a
   double other = o_ah_extreme(&c, -side, NULL);
   double nrm = fabs(nu) > fabs(other) ? fabs(nu) : fabs(other);
   r->nu = nu; r->mu = 1.0 / nu; r->K_nu = nrm / fabs(nu); r->steps = steps;
+  /* a solve that left the binary64 range counts as K_nu = inf (as for D + rho z z^T) */
+  if (!(r->K_nu >= 1.0) || !isfinite(nu) || r->mu == 0.0) r->K_nu = INFINITY;
 }
 
 typedef struct {
@@ -838,8 +924,9 @@ static int o_ah_solve_nonpole(int n, const double* d, const double* z, double al
 /* (R2) for the arrowhead from an estimate lam_est of lambda_k, as o_r2: the shift is moved
    into the interlacing interval of lambda_k, (d_k, d_{k-1}), with the exterior ends from
    Weyl's bounds, lambda_0 <= max(d_0, alpha) + ||z|| and lambda_n >= min(d_{n-1}, alpha) - ||z||;
-   the solve is repeated at sigma = lambda while |mu| is not below half the distance from
-   sigma to the nearer pole end (at most 3 solves).  Returns the number of solves. */
+   when |mu| is not below half the distance from sigma to the nearer pole end, the next shift
+   is the midpoint (the Weyl bound of an exterior eigenvalue) and then the lambda found there
+   (at most 3 solves).  Returns the number of solves. */
 static int o_ah_r2(int n, const double* d, const double* z, double alpha, int k, double lam_est, double* e,
                    double* u, double* sigma_out, double* mu_out) {
   double zn = 0.0;
@@ -862,7 +949,8 @@ static int o_ah_r2(int n, const double* d, const double* z, double alpha, int k,
     if (lo_pole) room = s - lo;
     if (hi_pole && hi - s < room) room = hi - s;
     if (rounds >= 3 || fabs(mu) < 0.5 * room) break;
-    s = s + mu;
+    /* as o_r2: next the midpoint, or the Weyl bound of an exterior eigenvalue */
+    s = (rounds == 1) ? (lo_pole && hi_pole ? lo + 0.5 * (hi - lo) : (hi_pole ? lo : hi)) : s + mu;
   }
   *sigma_out = s;
   *mu_out = mu;
@@ -900,9 +988,9 @@ static void o_ah_vector(int n, const double* d, const double* z, double sigma, d
 /* Eigenvalue k (0-based, 0..n) of the arrowhead; v has n + 1 entries.  opt: T_Knu, T_zero
    and remedies as for oracle_dpr1eig (NULL: defaults).  flags_out: remedy (1 R1, 2 R2) |
    4 when lambda was recomputed from A^{-1}.  shift_out: final pole, -1 for a non-pole shift. */
-int oracle_arroweig(int n, const double* d, const double* z, double alpha, int k, const oracle_opts* opt_in,
-                    double* lambda_out, double* v, double* sigma_out, double* mu_out, int* shift_out,
-                    int* flags_out, double* K_out) {
+static int o_arroweig_core(int n, const double* d, const double* z, double alpha, int k, const oracle_opts* opt_in,
+                           double* lambda_out, double* v, double* sigma_out, double* mu_out, int* shift_out,
+                           int* flags_out, double* K_out) {
   oracle_opts opt;
   if (opt_in) opt = *opt_in; else oracle_default_opts(&opt);
   if (n < 1 || k < 0 || k > n) return 1;
@@ -977,5 +1065,37 @@ int oracle_arroweig(int n, const double* d, const double* z, double alpha, int k
   if (shift_out) *shift_out = shift;
   if (flags_out) *flags_out = flags;
   free(delta); free(w);
-  return 0;
+  if (shift < 0 && ((k < n && o_pole_difference_cancels(d[k], sigma, mu)) ||
+                    (k > 0 && o_pole_difference_cancels(d[k - 1], sigma, mu))))
+    return 4;
+  return o_out_of_range(n + 1, mu, lambda, v) ? 4 : 0;
+}
+
+/* Exact power-of-two normalisation of the arrowhead (the whole matrix scales together):
+   a = e of max(|d_j|, |zeta_j|, |alpha|) = m 2^e, A' = 2^-a A, lambda = 2^a lambda', the same
+   eigenvectors; in range this gives the bits of the unnormalised computation. */
+int oracle_arroweig(int n, const double* d, const double* z, double alpha, int k, const oracle_opts* opt_in,
+                    double* lambda_out, double* v, double* sigma_out, double* mu_out, int* shift_out,
+                    int* flags_out, double* K_out) {
+  if (n < 1 || k < 0 || k > n) return 1;
+  double m = fabs(alpha);
+  for (int j = 0; j < n; j++) {
+    if (fabs(d[j]) > m) m = fabs(d[j]);
+    if (fabs(z[j]) > m) m = fabs(z[j]);
+  }
+  int a = 0;
+  if (m > 0.0 && isfinite(m)) frexp(m, &a);
+  double* ds = (double*)malloc(sizeof(double) * n);
+  double* zs = (double*)malloc(sizeof(double) * n);
+  if (!ds || !zs) { free(ds); free(zs); return 2; }
+  for (int j = 0; j < n; j++) { ds[j] = ldexp(d[j], -a); zs[j] = ldexp(z[j], -a); }
+  double sg = 0.0, mu = 0.0;
+  int rc = o_arroweig_core(n, ds, zs, ldexp(alpha, -a), k, opt_in, lambda_out, v, &sg, &mu, shift_out, flags_out,
+                           K_out);
+  free(ds); free(zs);
+  if (rc && rc != 4) return rc;
+  *lambda_out = ldexp(*lambda_out, a);
+  if (sigma_out) *sigma_out = ldexp(sg, a);
+  if (mu_out) *mu_out = ldexp(mu, a);
+  return rc;
 }

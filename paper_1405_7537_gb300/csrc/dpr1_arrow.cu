@@ -25,6 +25,11 @@
 // a DPR1 matrix of order n + 1 with a pole at 0 of weight gamma (the arrowhead form of
 // Eq. (gamma)); its extreme eigenvalue is 1/(lambda - sigma).  sigma = 0 recomputes an
 // eigenvalue much closer to zero than to its neighbouring poles.
+//
+// The matrix is first normalised by an exact power of two, A' = 2^-a A with
+// max(|d_j|, |zeta_j|, |alpha|) = m 2^a, m in [1/2, 1) (k_arrow_norm; the kernels then work on
+// the copies d', z', alpha'), and lambda, sigma, mu are scaled back; pairs that need values
+// outside the binary64 range are reported as DPR1_ERR_RANGE.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -52,6 +57,9 @@ struct ArrowWs {
   double* fixinfo;               // per flagged slot: K_nu, K_nu at the other pole, distance ratio
   int* zlist;                    // near-zero candidates
   double* lamz;                  // lambda recomputed from A^{-1} (NaN: not recomputed)
+  double* ds;                    // d' = 2^-a d and z' = 2^-a z (normalised copies)
+  double* zs;
+  double* scal;                  // [0]: alpha' = 2^-a alpha; [1]: a (as a double)
 };
 
 static size_t arrow_layout(int64_t n, ArrowWs* w, char* base) {
@@ -67,6 +75,9 @@ static size_t arrow_layout(int64_t n, ArrowWs* w, char* base) {
   size_t o_fi = off; off += a256a(24 * nn);
   size_t o_zl2 = off; off += a256a(4 * nn);
   size_t o_lz = off; off += a256a(8 * nn);
+  size_t o_ds = off; off += a256a(8 * nn);
+  size_t o_zs = off; off += a256a(8 * nn);
+  size_t o_sc = off; off += 256;
   if (w && base) {
     w->status = (unsigned*)(base + o_h);
     w->counters = (unsigned*)(base + o_h) + 8;
@@ -80,6 +91,9 @@ static size_t arrow_layout(int64_t n, ArrowWs* w, char* base) {
     w->fixinfo = (double*)(base + o_fi);
     w->zlist = (int*)(base + o_zl2);
     w->lamz = (double*)(base + o_lz);
+    w->ds = (double*)(base + o_ds);
+    w->zs = (double*)(base + o_zs);
+    w->scal = (double*)(base + o_sc);
   }
   return off;
 }
@@ -90,12 +104,34 @@ constexpr unsigned AH_ZERO_POLE = 1u;   // header word 1: some d_j == 0 (no near
 constexpr int AH_FIX_THREADS = 256;
 constexpr int AH_FIX_BLOCKS_PER_SM = 2;
 
-// input checks (finite, strictly decreasing d, no zero weight) and zeta^2
+// Exact power-of-two normalisation (one block): a from max(|d_j|, |zeta_j|, |alpha|) = m 2^a,
+// m in [1/2, 1); the whole matrix scales by 2^-a, so lambda = 2^a lambda' and the eigenvectors
+// are unchanged.  In the normal range this changes no rounding.
+__global__ void k_arrow_norm(int n, const double* __restrict__ d, const double* __restrict__ z, double alpha,
+                             double* __restrict__ scal) {
+  double m = fabs(alpha);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) m = fmax(m, fmax(fabs(d[j]), fabs(z[j])));
+  m = group_max<256>(m, FULL);
+  if (threadIdx.x == 0) {
+    int a = 0;
+    if (m > 0.0 && isfinite(m)) frexp(m, &a);
+    scal[0] = scalbn(alpha, -a);
+    scal[1] = (double)a;
+  }
+}
+
+// input checks (finite, strictly decreasing d, no zero weight), the normalised copies and zeta'^2
 __global__ void k_arrow_check(int n, const double* __restrict__ d, const double* __restrict__ z, double alpha,
-                              double* __restrict__ zz, double* __restrict__ zl, unsigned* __restrict__ status) {
+                              ArrowWs w) {
+  const int a = (int)w.scal[1];
+  double* __restrict__ zz = w.zz;
+  double* __restrict__ zl = w.zl;
+  unsigned* __restrict__ status = w.status;
   unsigned bits = 0, zp = 0;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    const double dj = d[j], zj = z[j];
+    const double dj = d[j], zj = scalbn(z[j], -a);
+    w.ds[j] = scalbn(dj, -a);
+    w.zs[j] = zj;
     if (!isfinite(dj) || !isfinite(zj)) bits |= ST_NONFINITE;
     if (dj == 0.0) zp = AH_ZERO_POLE;
     if (j + 1 < n) {
@@ -200,9 +236,10 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
 // One lane group per eigenvalue k = 0..n (persistent grid, work counter).
 template <int L>
 __global__ void __launch_bounds__(256) k_arrow_solve(int n, const double* __restrict__ d,
-                                                     const double* __restrict__ z, double alpha, ArrowWs w, int cap,
+                                                     const double* __restrict__ z, ArrowWs w, int cap,
                                                      bool fast) {
   if (*w.status & ST_FATAL_A) return;
+  const double alpha = w.scal[0];       // d, z and alpha are the normalised copies
   const int lane = threadIdx.x & (L - 1);
   const unsigned gm = group_mask<L>();
   const int leader = (threadIdx.x & 31) & ~(L - 1);
@@ -376,9 +413,10 @@ __global__ void k_arrow_classify(int n, const double* __restrict__ d, ArrowWs w,
 //       repeated at the new lambda while sigma is not nearer to lambda_k than to the
 //       interval's poles (at most 3 solves), as for D + rho z z^T.
 template <int L>
-__global__ void __launch_bounds__(L > 256 ? L : 256) k_arrow_fix(int n, const double* __restrict__ d, double alpha,
-                                                                   ArrowWs w, double T_Knu, int cap, bool fast) {
+__global__ void __launch_bounds__(L > 256 ? L : 256) k_arrow_fix(int n, const double* __restrict__ d, ArrowWs w,
+                                                                   double T_Knu, int cap, bool fast) {
   if (*w.status & ST_FATAL_A) return;
+  const double alpha = w.scal[0];
   const int nfix = (int)w.counters[C_FIX_N];
   const int lane = threadIdx.x & (L - 1);
   const unsigned gm = group_mask<L>();
@@ -481,9 +519,9 @@ __global__ void k_arrow_zero_detect(int n, const double* __restrict__ d, ArrowWs
   }
 }
 
-__global__ void k_arrow_zero_solve(int n, const double* __restrict__ d, double alpha, ArrowWs w, int cap,
-                                   bool fast) {
+__global__ void k_arrow_zero_solve(int n, const double* __restrict__ d, ArrowWs w, int cap, bool fast) {
   if (*w.status & ST_FATAL_A) return;
+  const double alpha = w.scal[0];
   const int nz = (int)w.counters[C_ZERO_N];
   const int lane = threadIdx.x & 31;
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -507,6 +545,11 @@ __global__ void k_arrow_zero_solve(int n, const double* __restrict__ d, double a
       if (!ok) atomicOr(w.status, ST_NOT_CONVERGED);
     }
   }
+}
+
+__device__ __forceinline__ bool ah_pole_difference_cancels(double dp, double s, double m) {
+  const double t = __dsub_rn(__dsub_rn(dp, s), m);
+  return 16.0 * fabs(t) < __dadd_rn(fabs(__dsub_rn(dp, s)), fabs(m));
 }
 
 // Rows v_k = [x; -1] / ||.|| (one warp per row), lambda, sigma, mu, ||[x; -1]||.
@@ -553,12 +596,23 @@ __global__ void __launch_bounds__(256) k_arrow_vectors(int n, const double* __re
     const double nrm = sqrt(q);
     const double c = scale / nrm;
     if (lane == 0) {
+      // outputs in the caller's units (lambda, sigma, mu times 2^a; x is scale-free)
+      const int a = (int)w.scal[1];
       const double lz = w.lamz[k];
-      lambda[k] = isnan(lz) ? __dadd_rn(s, m) : lz;
-      if (sigma) sigma[k] = s;
-      if (mu) mu[k] = m;
-      if (xnorm) xnorm[k] = nrm / scale;
+      const double lam = isnan(lz) ? __dadd_rn(s, m) : lz;
+      const double xn = nrm / scale;
+      lambda[k] = scalbn(lam, a);
+      if (sigma) sigma[k] = scalbn(s, a);
+      if (mu) mu[k] = scalbn(m, a);
+      if (xnorm) xnorm[k] = xn;
       if (vr) vr[n] = -c;
+      // outside the binary64 range of the normalised problem, or a cancelling pole difference
+      // after a non-pole shift (as for D + rho z z^T)
+      bool out = !(fabs(m) >= 0x1p-1022) || !isfinite(m) || !isfinite(lam) || !(xn > 0.0) || !isfinite(xn) ||
+                 !isfinite(c);
+      if (w.shift[k] < 0) out = out || (k < n && ah_pole_difference_cancels(d[k], s, m)) ||
+                                (k > 0 && ah_pole_difference_cancels(d[k - 1], s, m));
+      if (out) atomicOr(w.status, ST_RANGE);
     }
     if (!vr) continue;
     if (!rewrite) {
@@ -579,13 +633,13 @@ __global__ void k_arrow_one(double alpha, double* lambda, double* Vt, double* si
 }
 
 template <int L>
-static void launch_arrow(int n, const double* d, const double* z, double alpha, const ArrowWs& w, const Options& o,
+static void launch_arrow(int n, const double* d, const double* z, const ArrowWs& w, const Options& o,
                          cudaStream_t st) {
   const int groups_per_block = (32 * o.warps) / L;
   int64_t want = ((int64_t)n + 1 + groups_per_block - 1) / groups_per_block;
   int grid = sm_count() * o.bps;
   if (want < grid) grid = (int)(want > 0 ? want : 1);
-  k_arrow_solve<L><<<grid, 32 * o.warps, 0, st>>>(n, d, z, alpha, w, o.cap, o.fast);
+  k_arrow_solve<L><<<grid, 32 * o.warps, 0, st>>>(n, d, z, w, o.cap, o.fast);
 }
 
 }  // namespace dpr1
@@ -620,23 +674,27 @@ dpr1_status dpr1_arrow_eig(int64_t n, const double* d, const double* z, double a
   const int sms = sm_count();
   int cg = (int)((n + 255) / 256);
   if (cg > sms * 8) cg = sms * 8;
-  k_arrow_check<<<cg, 256, 0, st>>>((int)n, d, z, alpha, w.zz, w.zl, w.status);
+  k_arrow_norm<<<1, 256, 0, st>>>((int)n, d, z, alpha, w.scal);
+  k_arrow_check<<<cg, 256, 0, st>>>((int)n, d, z, alpha, w);
+  // from here on the kernels work on the normalised copies d' = 2^-a d, z' = 2^-a z, alpha'
+  const double* ds = w.ds;
+  const double* zs = w.zs;
   const int L = o.lanes ? o.lanes : (n <= 96 ? 8 : (n <= 384 ? 16 : 32));
-  if (L == 8) launch_arrow<8>((int)n, d, z, alpha, w, o, st);
-  else if (L == 16) launch_arrow<16>((int)n, d, z, alpha, w, o, st);
-  else launch_arrow<32>((int)n, d, z, alpha, w, o, st);
+  if (L == 8) launch_arrow<8>((int)n, ds, zs, w, o, st);
+  else if (L == 16) launch_arrow<16>((int)n, ds, zs, w, o, st);
+  else launch_arrow<32>((int)n, ds, zs, w, o, st);
   int kg = (int)((n + 1 + 255) / 256);
   if (kg > sms * 8) kg = sms * 8;
-  k_arrow_classify<<<kg, 256, 0, st>>>((int)n, d, w, o.T_Knu);
+  k_arrow_classify<<<kg, 256, 0, st>>>((int)n, ds, w, o.T_Knu);
   // one block-wide group per flagged eigenvalue: they are few (a few percent on graded or
   // clustered spectra) and each solve spans all n poles
   const int fg = (int)(n + 1 < (int64_t)sms * AH_FIX_BLOCKS_PER_SM ? n + 1 : (int64_t)sms * AH_FIX_BLOCKS_PER_SM);
-  k_arrow_fix<AH_FIX_THREADS><<<fg, AH_FIX_THREADS, 0, st>>>((int)n, d, alpha, w, o.T_Knu, o.cap, o.fast);
-  k_arrow_zero_detect<<<kg, 256, 0, st>>>((int)n, d, w, o.T_zero);
-  k_arrow_zero_solve<<<1, 128, 0, st>>>((int)n, d, alpha, w, o.cap, o.fast);
+  k_arrow_fix<AH_FIX_THREADS><<<fg, AH_FIX_THREADS, 0, st>>>((int)n, ds, w, o.T_Knu, o.cap, o.fast);
+  k_arrow_zero_detect<<<kg, 256, 0, st>>>((int)n, ds, w, o.T_zero);
+  k_arrow_zero_solve<<<1, 128, 0, st>>>((int)n, ds, w, o.cap, o.fast);
   int64_t vg = (n + 1 + 7) / 8;
   if (vg > sms * 16) vg = sms * 16;
-  k_arrow_vectors<<<(int)vg, 256, 0, st>>>((int)n, d, z, w, lambda, Vt, ldv, sigma, mu, xnorm);
+  k_arrow_vectors<<<(int)vg, 256, 0, st>>>((int)n, ds, zs, w, lambda, Vt, ldv, sigma, mu, xnorm);
   return cudaGetLastError() == cudaSuccess ? DPR1_OK : DPR1_ERR_CUDA;
 }
 

@@ -28,6 +28,7 @@ enum : unsigned {
   ST_NOT_CONVERGED = 4u,
   ST_BADARG = 8u,       // inconsistent batch offsets
   ST_RHO = 16u,         // a rho_p < 0 or not finite
+  ST_RANGE = 32u,       // an eigenpair needs values outside the binary64 range (normalised problem)
 };
 
 struct dd {

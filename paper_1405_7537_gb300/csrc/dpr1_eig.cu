@@ -6,15 +6,17 @@
 // problem is the table with one entry.  Launch sequence on the caller's stream
 // (Algorithm 1, dpr1eig, for every eigenpair of every problem at once):
 //   k_owner     batch only: element -> problem map, offset checks
-//   k_scan      input checks, copies d, z, z^2 into the workspace, deflation tests (Sec. 1)
+//   k_norm      exact power-of-two normalisation of each problem (D' = 2^-a D, z' = 2^-b z)
+//   k_scan      input checks, scaled copies of d, z, z^2 in the workspace, deflation tests (Sec. 1)
 //   k_deflate   exact deflation (zeta_j == 0, ties) for the problems that need it
 //   k_solve     per eigenvalue (one lane group): shift test, corner b in double-double,
 //               bisection for the extreme eigenvalue nu of the arrowhead inverse
 //   k_classify  K_nu of Eq. (K0) from the neighbouring eigenvalues; picks R1 / R2 candidates
 //   k_fix       R1 (the other pole) and R2 (non-pole shift, f(sigma) in double-double)
 //   k_zero_*    eigenvalues much closer to zero than to their poles: lambda from A^{-1}
-//   k_vectors   lambda, (sigma, mu), ||x|| and the rows of V^T, v = x / ||x||
-//   k_defl_*    output rows of deflated problems; k_trivial for rho == 0
+//   k_vectors   lambda, (sigma, mu), ||x|| (scaled back) and the rows of V^T, v = x / ||x||;
+//               pairs outside the binary64 range are reported (DPR1_ERR_RANGE)
+//   k_defl_*    output rows of deflated problems; k_trivial for rho == 0 (and rho' out of range)
 // All work lists are global, so the persistent kernels balance the whole batch.
 #include <cuda_runtime.h>
 
@@ -80,6 +82,8 @@ size_t ws_layout2(int64_t total, int64_t nprob, bool batched, Ws* w, char* base)
   char* pn = take(sizeof(int) * pp);
   char* pd = take(sizeof(int) * pp);
   char* ps = take(sizeof(unsigned) * pp);
+  char* pe = take(sizeof(int) * 2 * pp);
+  char* pr = take(sizeof(double) * pp);
   if (w && base) {
     w->hdr = (unsigned*)hdr;
     w->status = (unsigned*)hdr;
@@ -97,6 +101,8 @@ size_t ws_layout2(int64_t total, int64_t nprob, bool batched, Ws* w, char* base)
     w->gst = (int*)gst; w->rprev = (double*)rprev; w->rcur = (double*)rcur; w->dlist = (int*)dlist;
     w->zlist = (int*)zlist;
     w->fixinfo = (double*)fk;
+    w->pexp = (int*)pe;
+    w->prho = (double*)pr;
   }
   return off;
 }
@@ -156,7 +162,51 @@ __global__ void k_owner(Prob pb, Ws w) {
 }
 
 // ---------------------------------------------------------------------------------
-// k_scan: checks and copies; one thread per element
+// k_norm: exact power-of-two normalisation of each problem (one warp per problem).  With
+// max|d_j| = m 2^a and max|zeta_j| = m' 2^b (m, m' in [1/2, 1)): D' = 2^-a D, z' = 2^-b z,
+// rho' = 2^(2b - a) rho, so A = 2^a (D' + rho' z' z'^T) has the same eigenvectors and
+// lambda = 2^a lambda'.  Multiplying by a power of two changes no rounding in the normal range,
+// so there the results are those of the unnormalised computation; for data of any magnitude
+// it keeps the poles' differences and the weights at their own scale (zeta_j^2 cannot overflow
+// or underflow) and leaves the ratio of the rank-one part to D in rho'.  With every pole zero,
+// a comes from rho ||z||^2.  rho' outside the normal range marks the problem PT_RANGE.
+// ---------------------------------------------------------------------------------
+__global__ void k_norm(Prob pb, Ws w) {
+  if (*w.status & ST_FATAL) return;
+  const int lane = threadIdx.x & 31;
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int p = wid; p < pb.P; p += nw) {
+    const int64_t base = p_base(pb, p);
+    const int n = p_size(pb, p);
+    double md = 0.0, mz = 0.0;
+    for (int j = lane; j < n; j += 32) {
+      md = fmax(md, fabs(pb.d[base + j]));
+      mz = fmax(mz, fabs(pb.z[base + j]));
+    }
+    md = group_max<32>(md, FULL);
+    mz = group_max<32>(mz, FULL);
+    if (lane == 0) {
+      const double rho = p_rho(pb, p);
+      int ed = 0, ez = 0, er = 0;
+      if (md > 0.0 && isfinite(md)) frexp(md, &ed);
+      if (mz > 0.0 && isfinite(mz)) frexp(mz, &ez);
+      if (rho > 0.0 && isfinite(rho)) frexp(rho, &er);
+      const int a = (md > 0.0) ? ed : er + 2 * ez;
+      w.pexp[2 * p] = a;
+      w.pexp[2 * p + 1] = ez;
+      const double rs = scalbn(rho, 2 * ez - a);
+      w.prho[p] = rs;
+      if (rho > 0.0 && isfinite(rho) && mz > 0.0 && isfinite(mz) && isfinite(md) && !(rs >= 0x1p-1022 && isfinite(rs))) {
+        atomicOr(&w.pst[p], PT_RANGE | PT_TRIVIAL);
+        atomicOr(w.status, ST_RANGE);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// k_scan: checks and scaled copies (d' = 2^-a d, z' = 2^-b z); one thread per element
 // ---------------------------------------------------------------------------------
 __global__ void k_scan(Prob pb, Ws w) {
   if (*w.status & ST_FATAL) return;
@@ -168,6 +218,7 @@ __global__ void k_scan(Prob pb, Ws w) {
     int n = p_size(pb, p);
     int64_t j = g - base;
     double dj = pb.d[g], zj = pb.z[g];
+    const double djs = scalbn(dj, -w.pexp[2 * p]), zjs = scalbn(zj, -w.pexp[2 * p + 1]);
     unsigned pbits = 0;
     if (j == 0) {
       double r = p_rho(pb, p);
@@ -182,14 +233,14 @@ __global__ void k_scan(Prob pb, Ws w) {
       if (dj < dn) bits |= ST_UNSORTED;
       if (dj == dn) pbits |= PT_DEFLATE;
     }
-    if (zero_weight(zj)) pbits |= PT_DEFLATE;
+    if (zero_weight(zjs)) pbits |= PT_DEFLATE;
     if (dj == 0.0) pbits |= PT_ZERO_POLE;
     if (pbits) atomicOr(&w.pst[p], pbits);
-    w.dr[g] = dj;
-    w.zr[g] = zj;
-    const double zq = __dmul_rn(zj, zj);
+    w.dr[g] = djs;
+    w.zr[g] = zjs;
+    const double zq = __dmul_rn(zjs, zjs);
     w.zz[g] = zq;
-    w.zl[g] = __fma_rn(zj, zj, -zq);
+    w.zl[g] = __fma_rn(zjs, zjs, -zq);
   }
   bits = __reduce_or_sync(FULL, bits);
   if ((threadIdx.x & 31) == 0 && bits) atomicOr(w.status, bits);
@@ -206,21 +257,22 @@ __global__ void k_scan(Prob pb, Ws w) {
 // (including) them.
 // ---------------------------------------------------------------------------------
 // One group of equal poles, from position j to its end e (serial; lane 0).
-__device__ int deflate_group(const Ws& w, int64_t base, const double* d, const double* z, int n, int j, int* nr,
-                             int* nd) {
+__device__ int deflate_group(const Ws& w, int64_t base, const double* d, const double* z, int ea, int eb, int n,
+                             int j, int* nr, int* nd) {
   int e = j;
   while (e + 1 < n && d[e + 1] == d[j]) e++;
   int first = -1;
   double r = 0.0;
   for (int q = j; q <= e; q++) {
     w.gst[base + q] = j;
-    if (zero_weight(z[q])) {
+    const double zq = scalbn(z[q], -eb);
+    if (zero_weight(zq)) {
       w.src[base + q] = -1; w.coef[base + q] = 0.0; w.rprev[base + q] = 0.0; w.rcur[base + q] = 0.0;
       w.dlist[base + (*nd)++] = q;
       continue;
     }
     double rp = r;
-    r = hypot(r, z[q]);
+    r = hypot(r, zq);
     w.rprev[base + q] = rp; w.rcur[base + q] = r;
     if (first < 0) first = q;
     else w.dlist[base + (*nd)++] = q;
@@ -228,11 +280,12 @@ __device__ int deflate_group(const Ws& w, int64_t base, const double* d, const d
   if (first >= 0) {
     double zs = (z[first] > 0.0) ? r : -r;
     for (int q = j; q <= e; q++) {
-      if (zero_weight(z[q])) continue;
+      const double zq = scalbn(z[q], -eb);
+      if (zero_weight(zq)) continue;
       w.src[base + q] = *nr;
-      w.coef[base + q] = z[q] / zs;
+      w.coef[base + q] = zq / zs;
     }
-    w.dr[base + *nr] = d[j];
+    w.dr[base + *nr] = scalbn(d[j], -ea);
     w.zr[base + *nr] = zs;
     const double zq = __dmul_rn(zs, zs);
     w.zz[base + *nr] = zq;
@@ -259,11 +312,12 @@ __global__ void k_deflate(Prob pb, Ws w) {
     const int n = p_size(pb, p);
     const double* d = pb.d + base;
     const double* z = pb.z + base;
+    const int ea = w.pexp[2 * p], eb = w.pexp[2 * p + 1];
     int nr = 0, nd = 0, q0 = 0;
     while (q0 < n) {
       const int q = q0 + lane;
       const bool in = q < n;
-      const double dq = in ? d[q] : 0.0, zq = in ? z[q] : 0.0;
+      const double dq = in ? d[q] : 0.0, zq = in ? scalbn(z[q], -eb) : 0.0;
       const bool tie = in && ((q > 0 && d[q - 1] == dq) || (q + 1 < n && d[q + 1] == dq));
       if (__ballot_sync(FULL, tie) == 0u) {
         const bool zw = in && zero_weight(zq);
@@ -281,7 +335,7 @@ __global__ void k_deflate(Prob pb, Ws w) {
             w.coef[base + q] = 1.0;                       // zeta_q / zeta_q
             w.rprev[base + q] = 0.0;
             w.rcur[base + q] = fabs(zq);                  // hypot(0, zeta_q)
-            w.dr[base + r] = dq;
+            w.dr[base + r] = scalbn(dq, -ea);
             w.zr[base + r] = zq;
             const double zz = __dmul_rn(zq, zq);
             w.zz[base + r] = zz;
@@ -294,7 +348,7 @@ __global__ void k_deflate(Prob pb, Ws w) {
       } else {
         int j = q0;
         if (lane == 0) {
-          while (j < q0 + 32 && j < n) j = deflate_group(w, base, d, z, n, j, &nr, &nd);
+          while (j < q0 + 32 && j < n) j = deflate_group(w, base, d, z, ea, eb, n, j, &nr, &nd);
         }
         __syncwarp();
         nr = __shfl_sync(FULL, nr, 0);
@@ -342,7 +396,7 @@ __global__ void __launch_bounds__(256) k_solve(Prob pb, Ws w, int cap, bool fast
     const int n = w.nred[p];
     const int k = (int)(g - base);
     if (k >= n) continue;
-    const double rho = p_rho(pb, p);
+    const double rho = w.prho[p];   // rho' of the normalised problem
     const double* __restrict__ d = w.dr + base;
     const double* __restrict__ zl = w.zl + base;
     const double* __restrict__ zz = w.zz + base;
@@ -423,6 +477,8 @@ __global__ void k_classify(Prob pb, Ws w, double T_Knu) {
     int m = (i == k) ? k + 1 : k - 1;
     double K = 1.0;
     if (m >= 0 && m < n) K = fmax(1.0, mk / dist_to(w, base + m, di));
+    // a pole solve that left the binary64 range (mu zero or not finite) is no solution
+    if (!(mk > 0.0) || !isfinite(mk) || isnan(K)) K = INFINITY;
     if (K > T_Knu) {
       int o = (i == k) ? k - 1 : k;
       double K2 = INFINITY, ratio = INFINITY;
@@ -450,9 +506,10 @@ __global__ void k_classify(Prob pb, Ws w, double T_Knu) {
 //  (R2) otherwise shift to sigma = fl(lambda) from the better pole solution, moved into the
 //       interlacing interval of lambda_k ((d_k, d_{k-1}); (d_0, d_0 + rho ||z||^2] for k = 0),
 //       and solve_nonpole.  Any sigma there yields lambda_k (the sign of f(sigma) picks the
-//       side), accurately once lambda_k is the eigenvalue nearest to sigma; while |mu| is not
-//       below half the distance to the nearer pole end the solve repeats at the new lambda
-//       (at most 3 solves: a first estimate with K_nu near 1/eps is noise).
+//       side), accurately once lambda_k is the eigenvalue nearest to sigma; when |mu| is not
+//       below half the distance to the nearer pole end, the next shift is the midpoint (the
+//       Weyl bound for k = 0) and then the lambda found there (at most 3 solves: a first
+//       estimate with K_nu near 1/eps is noise).
 // ---------------------------------------------------------------------------------
 template <int L>
 __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double T_Knu, int cap, bool fast) {
@@ -479,7 +536,7 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double
     const int64_t base = p_base(pb, p);
     const int n = w.nred[p];
     const int k = (int)(g - base);
-    const double rho = p_rho(pb, p);
+    const double rho = w.prho[p];   // rho' of the normalised problem
     const double* __restrict__ d = w.dr + base;
     const double* __restrict__ zl = w.zl + base;
     const double* __restrict__ zz = w.zz + base;
@@ -529,10 +586,12 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double
         if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)st2);
         new_sig = s; new_mu = m2; new_shift = -1;
         // accurate when lambda_k is the eigenvalue nearest to sigma: every other eigenvalue lies
-        // beyond the interval's poles; otherwise solve again at the new lambda
+        // beyond the interval's poles.  Otherwise the next shift is one from which lambda_k is at
+        // least as near as any other eigenvalue -- the midpoint of (d_k, d_{k-1}), or for k = 0
+        // the Weyl bound -- and the one after is the lambda found there
         const double room = (k > 0) ? fmin(s - lo, hi - s) : s - lo;
         if (fabs(m2) < 0.5 * room) break;
-        s = __dadd_rn(s, m2);
+        s = (round == 0) ? (k > 0 ? __fma_rn(0.5, __dsub_rn(hi, lo), lo) : hi) : __dadd_rn(s, m2);
       }
     }
     if (lane == 0) {
@@ -598,7 +657,7 @@ __global__ void k_zero_solve(Prob pb, Ws w, int cap, bool fast) {
     const int below = lo < n ? lo : -1;
     const int above = lo - 1;
     bool ok;
-    double lam0 = solve_nonpole<32>(d, w.zl + base, w.zz + base, n, p_rho(pb, p), 0.0, above, below, cap, fast, lane,
+    double lam0 = solve_nonpole<32>(d, w.zl + base, w.zz + base, n, w.prho[p], 0.0, above, below, cap, fast, lane,
                                     FULL, &ok);
     if (lane == 0) {
       w.lamz[g] = lam0;
@@ -631,18 +690,19 @@ __global__ void k_defl_positions(Prob pb, Ws w) {
     const int n = w.nred[p];
     const int k = (int)(g - base);
     const double* dfull = pb.d + base;
+    const int ea = w.pexp[2 * p];                       // (sigma, mu) are in normalised units
     if (k < n) {
       int lo = 0, hi = nd;   // deflated values strictly above lambda_k
       while (lo < hi) {
         int mid = (lo + hi) >> 1;
-        double dq = dfull[w.dlist[base + mid]];
+        double dq = scalbn(dfull[w.dlist[base + mid]], -ea);
         if (!lam_greater_equal(w.sig[base + k], w.mu[base + k], dq)) lo = mid + 1;
         else hi = mid;
       }
       w.rpos[g] = k + lo;
     }
     if (k < nd) {
-      double dq = dfull[w.dlist[base + k]];
+      double dq = scalbn(dfull[w.dlist[base + k]], -ea);
       int lo = 0, hi = n;    // reduced eigenvalues >= d_q (non-increasing in k)
       while (lo < hi) {
         int mid = (lo + hi) >> 1;
@@ -664,6 +724,11 @@ __global__ void k_defl_positions(Prob pb, Ws w) {
 // j).  In a deflated problem the row of reduced eigenvalue k goes to output row rpos and
 // component q takes coef[q] * x_{src[q]}; deflated pairs are written by k_defl_rows.
 // ---------------------------------------------------------------------------------
+__device__ __forceinline__ bool pole_difference_cancels(double dp, double s, double m) {
+  const double t = __dsub_rn(__dsub_rn(dp, s), m);
+  return 16.0 * fabs(t) < __dadd_rn(fabs(__dsub_rn(dp, s)), fabs(m));
+}
+
 __global__ void __launch_bounds__(256) k_vectors(Prob pb, Ws w) {
   if (*w.status & ST_FATAL) return;
   const int lane = threadIdx.x & 31;
@@ -715,11 +780,25 @@ __global__ void __launch_bounds__(256) k_vectors(Prob pb, Ws w) {
     const double nrm = sqrt(q);          // ||x|| * scale
     const double c = scale / nrm;
     if (lane == 0) {
+      // outputs in the caller's units: lambda, sigma, mu times 2^a, ||x|| times 2^(b - a)
+      const int ea = w.pexp[2 * p], eb = w.pexp[2 * p + 1];
       double lz = w.lamz[g];
-      pb.lambda[base + row] = isnan(lz) ? __dadd_rn(s, m) : lz;
-      if (pb.sigma) pb.sigma[base + row] = s;
-      if (pb.mu) pb.mu[base + row] = m;
-      if (pb.xnorm) pb.xnorm[base + row] = nrm / scale;
+      const double lam = isnan(lz) ? __dadd_rn(s, m) : lz;
+      const double xn = nrm / scale;
+      pb.lambda[base + row] = scalbn(lam, ea);
+      if (pb.sigma) pb.sigma[base + row] = scalbn(s, ea);
+      if (pb.mu) pb.mu[base + row] = scalbn(m, ea);
+      if (pb.xnorm) pb.xnorm[base + row] = scalbn(xn, eb - ea);
+      // the pair needs values outside the binary64 range: mu zero, subnormal or not finite
+      // (lambda within 2^-1022 of its shift in normalised units), or lambda, ||x|| not finite
+      bool out = !(fabs(m) >= 0x1p-1022) || !isfinite(m) || !isfinite(lam) || !(xn > 0.0) || !isfinite(xn) ||
+                 !isfinite(c);
+      // after a non-pole shift (R2): d_p - lambda = (d_p - sigma) - mu to a neighbouring pole
+      // cancels by more than a factor 16 -- the case that needs sigma in double the working
+      // precision (not implemented), reported like the others
+      if (w.shift[g] < 0) out = out || pole_difference_cancels(d[k], s, m) ||
+                                (k > 0 && pole_difference_cancels(d[k - 1], s, m));
+      if (out) atomicOr(w.status, ST_RANGE);
     }
     if (!vr) continue;
     if (!defl && !rewrite) {
@@ -754,6 +833,7 @@ __global__ void k_defl_rows(Prob pb, Ws w) {
     const int nfull = p_size(pb, p);
     const double* dfull = pb.d + base;
     const double* zfull = pb.z + base;
+    const int eb = w.pexp[2 * p + 1];                   // rcur, rprev are norms of scaled weights
     const int q = w.dlist[base + qd];
     const int row = w.dpos[g];
     const double dq = dfull[q];
@@ -765,7 +845,7 @@ __global__ void k_defl_rows(Prob pb, Ws w) {
     }
     if (!pb.Vt) continue;
     double* vr = pb.Vt + p_vbase(pb, p) + (int64_t)row * p_ld(pb, p);
-    const double zq = zfull[q];
+    const double zq = scalbn(zfull[q], -eb);
     const int g0 = w.gst[base + q];
     const double rc = w.rcur[base + q], rp = w.rprev[base + q];
     for (int j = lane; j < nfull; j += 32) {
@@ -774,15 +854,17 @@ __global__ void k_defl_rows(Prob pb, Ws w) {
         v = (j == q) ? 1.0 : 0.0;
       } else if (j == q) {
         v = rp / rc;
-      } else if (j >= g0 && j < q && !zero_weight(zfull[j])) {
-        v = -(zq / rc) * (zfull[j] / rp);
+      } else if (j >= g0 && j < q) {
+        const double zj = scalbn(zfull[j], -eb);
+        if (!zero_weight(zj)) v = -(zq / rc) * (zj / rp);
       }
       vr[j] = v;
     }
   }
 }
 
-// rho_p == 0: lambda = d, V = I, sigma = d, mu = 0 (one warp per row).
+// rho_p == 0 (or rho' outside the normal range, reported): lambda = d, V = I, sigma = d,
+// mu = 0 (one warp per row).
 __global__ void k_trivial(Prob pb, Ws w) {
   if (*w.status & ST_FATAL) return;
   const int lane = threadIdx.x & 31;
@@ -900,6 +982,9 @@ static dpr1_status run_table(const Prob& pb, void* workspace, const Options& o, 
     if (og > sms * 8) og = sms * 8;
     k_owner<<<og > 0 ? og : 1, 256, 0, st>>>(pb, w);
   }
+  int ng = (pb.P + 7) / 8;                              // a warp per problem
+  if (ng > sms * 8) ng = sms * 8;
+  k_norm<<<ng > 0 ? ng : 1, 256, 0, st>>>(pb, w);
   int64_t sg = (pb.total + 255) / 256;
   if (sg > sms * 8) sg = sms * 8;
   if (sg < 1) sg = 1;
@@ -975,6 +1060,7 @@ const char* dpr1_status_string(dpr1_status s) {
     case DPR1_ERR_NOT_CONVERGED: return "bisection did not converge within its iteration cap";
     case DPR1_ERR_CUDA: return "CUDA error";
     case DPR1_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case DPR1_ERR_RANGE: return "an eigenpair needs values outside the binary64 range";
   }
   return "unknown status";
 }
@@ -1040,6 +1126,7 @@ dpr1_status dpr1_stream_status(void* workspace, dpr1_stream_t stream) {
   if (st & ST_RHO) return DPR1_ERR_RHO;
   if (st & ST_NONFINITE) return DPR1_ERR_NONFINITE;
   if (st & ST_UNSORTED) return DPR1_ERR_UNSORTED;
+  if (st & ST_RANGE) return DPR1_ERR_RANGE;
   if (st & ST_NOT_CONVERGED) return DPR1_ERR_NOT_CONVERGED;
   return DPR1_OK;
 }

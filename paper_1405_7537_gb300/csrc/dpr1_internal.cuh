@@ -31,6 +31,8 @@ struct Ws {
   int* dlist;                 // deflated positions, increasing
   int* zlist;                 // near-zero candidates
   double* fixinfo;            // per flagged slot: K_nu, K_nu at the other pole, distance ratio
+  int* pexp;                  // [2P]: exponents (a, b) of the normalisation D' = 2^-a D, z' = 2^-b z
+  double* prho;               // [P]: rho' = 2^(2b - a) rho
 };
 
 struct Options {
@@ -51,6 +53,7 @@ enum : unsigned {
   PT_TRIVIAL = 1u,     // rho == 0
   PT_DEFLATE = 2u,     // a zero weight or equal poles
   PT_ZERO_POLE = 4u,   // some d_j == 0 (the near-zero recompute is then skipped, Eq. (gamma))
+  PT_RANGE = 8u,       // rho' outside the normal range: skipped (solved as rho = 0) and reported
 };
 
 size_t ws_layout(int64_t n, Ws* w, char* base);

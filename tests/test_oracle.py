@@ -18,6 +18,8 @@ missing double-double step, a missing remedy) fails at least one of them:
 """
 from fractions import Fraction as Fr
 
+import math
+
 import numpy as np
 import pytest
 
@@ -490,9 +492,10 @@ def test_backward_against_binary128_adjoint(gen, n, seed):
 
 
 def test_tiny_weights_are_zero_weights():
-    """A weight whose square is not a normal binary64 number is deflated (the secular
-    function cannot see it): the remaining eigenvalues equal the binary128 eigenvalues of
-    the reduced problem, the deflated ones are their poles, and A V = V diag(lambda)."""
+    """A weight whose square is not a normal binary64 number after the normalisation
+    max|zeta| in [1/2, 1) is deflated (the secular function cannot see it): the remaining
+    eigenvalues equal the binary128 eigenvalues of the reduced problem, the deflated ones are
+    their poles, and A V = V diag(lambda).  The rule is relative to the largest weight."""
     d, z, rho = W.uniform(64, 3)
     z = z.copy()
     z[[5, 20, 40]] = [1e-170, 1e-200, 1e-155]
@@ -503,7 +506,10 @@ def test_tiny_weights_are_zero_weights():
     assert np.max(np.abs(A @ V - V * r["lam"])) <= 1e-14
     assert np.max(np.abs(V.T @ V - np.eye(64))) <= 1e-14
     keep = ~oracle.zero_weight(z)
-    assert keep.sum() == 59 and oracle.zero_weight(2.0 ** -512) and not oracle.zero_weight(2.0 ** -511)
+    assert keep.sum() == 59
+    assert oracle.zero_weight(2.0 ** -512, zmax=0.9) and not oracle.zero_weight(2.0 ** -511, zmax=0.9)
+    assert np.array_equal(oracle.zero_weight(z * 2.0 ** 300), ~keep)
+    assert np.array_equal(oracle.zero_weight(z * 2.0 ** -300), ~keep)
     q = oracle.quad_all(d[keep], z[keep], rho)
     lk = np.sort(np.concatenate([q["hi"] + q["lo"], d[~keep]]))[::-1]
     assert np.max(np.abs(r["lam"] - lk) / np.abs(lk)) <= 16 * 64 * 2.0 ** -53
@@ -551,3 +557,80 @@ def test_r2_from_any_estimate():
                 r = oracle.r2(d, z, rho, k, est)
                 assert 1 <= r["rounds"] <= 3
                 assert abs(r["lam"] - lq[k]) <= tol(n) * abs(lq[k]), (case, k, est, r, lq[k])
+
+
+def test_scale_invariance_is_exact():
+    """The exact power-of-two normalisation: D + rho z z^T with d -> 2^s d, z -> 2^t z and
+    rho -> 2^(s - 2t) rho is 2^s times the same matrix, and the oracle returns exactly 2^s times
+    the eigenvalues and the same eigenvectors, bit for bit, even where the unscaled data would
+    over- or underflow (s, t up to +-900)."""
+    d, z, rho = W.hard(120, 4)
+    base = oracle.eig_all(d, z, rho)
+    for s, t in ((0, 300), (600, 0), (-600, 0), (900, 400), (-900, -400), (37, -11)):
+        ds, zs, rs = np.ldexp(d, s), np.ldexp(z, t), math.ldexp(rho, s - 2 * t)
+        r = oracle.eig_all(ds, zs, rs)
+        assert np.array_equal(r["lam"], np.ldexp(base["lam"], s)), (s, t)
+        assert np.array_equal(r["Vt"], base["Vt"]), (s, t)
+
+
+def _harsh(rng, wmax=150):
+    """Data of any magnitude: poles scaled by 2^U(-700, 700), weights over up to 2^wmax within a
+    problem and scaled by 2^U(-300, 300), and a rank-one part from 2^-300 to 2^300 times the
+    poles' scale; poles uniform, clustered or graded."""
+    n = int(rng.integers(2, 40))
+    kind = rng.integers(0, 3)
+    if kind == 0:
+        d = rng.uniform(-1, 1, n)
+    elif kind == 1:
+        c = rng.uniform(-1, 1, max(1, n // 5))
+        d = rng.choice(c, n) + rng.choice([1.0, -1.0], n) * 10.0 ** rng.uniform(-12, -3, n)
+    else:
+        d = np.sign(rng.uniform(-1, 1, n)) * 10.0 ** rng.uniform(-12, 0, n)
+    d = np.sort(d)[::-1].copy()
+    z = rng.choice([1.0, -1.0], n) * 2.0 ** rng.uniform(-rng.uniform(0, wmax), 0, n)
+    rho = 2.0 ** rng.uniform(-300, 300) / float(np.sum(z * z)) * float(np.max(np.abs(d)))
+    s, t = int(rng.integers(-700, 700)), int(rng.integers(-300, 300))
+    e = math.frexp(rho)[1] + s - 2 * t
+    if not -1000 < e < 1000:          # keep rho itself a normal binary64 number
+        return _harsh(rng, wmax)
+    return np.ldexp(d, s), np.ldexp(z, t), math.ldexp(rho, s - 2 * t)
+
+
+def test_harsh_data_meets_the_bound_or_reports_range():
+    """No silent failure on data of any magnitude: every eigenpair either meets 16 n 2^-53
+    against binary128 (components compared relative to max(|v|, 2^-1022), the binary64 normal
+    range) or the oracle reports that it needs values outside the binary64 range."""
+    rng = np.random.default_rng(2718)
+    ok = rng_err = 0
+    while ok + rng_err < 150:
+        d, z, rho = _harsh(rng)
+        n = d.size
+        if not (np.all(d[:-1] > d[1:]) and np.all(np.isfinite(d)) and not np.any(oracle.zero_weight(z))
+                and rho > 0 and np.isfinite(rho)):
+            continue
+        try:
+            r = oracle.eig_all(d, z, rho, threads=4)
+        except oracle.OracleRangeError:
+            rng_err += 1
+            continue
+        q = oracle.quad_all(d, z, rho, threads=4)
+        lq = q["hi"] + q["lo"]
+        assert np.max(np.abs(r["lam"] - lq) / np.abs(lq)) <= tol(n)
+        err = np.abs(r["Vt"] - q["Vt"]) / np.maximum(np.abs(q["Vt"]), 2.0 ** -1022)
+        assert err.max() <= tol(n), float(err.max() / tol(n))
+        ok += 1
+    assert ok >= 120
+
+
+def test_out_of_range_pair_is_reported():
+    """A weight of 1e-152 next to weights of 1 (above the zero-weight cut, 2^-511 of the largest):
+    lambda_0 - d_0 is about rho zeta_0^2 ~ 1e-314, below the normal binary64 range even after
+    the normalisation, so the pair cannot be formed with full precision and the oracle reports
+    it instead of returning it."""
+    d = np.array([2.0e-3, 3.0e-4, 2.0e-12])
+    z = np.array([1e-152, 1.0, -0.5])
+    with pytest.raises(oracle.OracleRangeError):
+        oracle.dpr1eig(d, z, 4e-10, 0)
+    lam, _, _ = oracle.dpr1eig(d, z, 4e-10, 1)        # the other pairs are in range
+    q = oracle.quad_eig(d, z, 4e-10, 1, want_vector=False)
+    assert abs(lam - (q[0] + q[1])) <= tol(3) * abs(lam)
