@@ -162,7 +162,7 @@ __global__ void k_owner(Prob pb, Ws w) {
 }
 
 // ---------------------------------------------------------------------------------
-// k_norm: exact power-of-two normalisation of each problem (one warp per problem).  With
+// k_norm: exact power-of-two normalisation of each problem (one block per problem).  With
 // max|d_j| = m 2^a and max|zeta_j| = m' 2^b (m, m' in [1/2, 1)): D' = 2^-a D, z' = 2^-b z,
 // rho' = 2^(2b - a) rho, so A = 2^a (D' + rho' z' z'^T) has the same eigenvectors and
 // lambda = 2^a lambda'.  Multiplying by a power of two changes no rounding in the normal range,
@@ -171,22 +171,19 @@ __global__ void k_owner(Prob pb, Ws w) {
 // or underflow) and leaves the ratio of the rank-one part to D in rho'.  With every pole zero,
 // a comes from rho ||z||^2.  rho' outside the normal range marks the problem PT_RANGE.
 // ---------------------------------------------------------------------------------
-__global__ void k_norm(Prob pb, Ws w) {
+__global__ void __launch_bounds__(256) k_norm(Prob pb, Ws w) {
   if (*w.status & ST_FATAL) return;
-  const int lane = threadIdx.x & 31;
-  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int p = wid; p < pb.P; p += nw) {
+  for (int p = blockIdx.x; p < pb.P; p += gridDim.x) {
     const int64_t base = p_base(pb, p);
     const int n = p_size(pb, p);
     double md = 0.0, mz = 0.0;
-    for (int j = lane; j < n; j += 32) {
+    for (int j = threadIdx.x; j < n; j += 256) {
       md = fmax(md, fabs(pb.d[base + j]));
       mz = fmax(mz, fabs(pb.z[base + j]));
     }
-    md = group_max<32>(md, FULL);
-    mz = group_max<32>(mz, FULL);
-    if (lane == 0) {
+    md = group_max<256>(md, FULL);
+    mz = group_max<256>(mz, FULL);
+    if (threadIdx.x == 0) {
       const double rho = p_rho(pb, p);
       int ed = 0, ez = 0, er = 0;
       if (md > 0.0 && isfinite(md)) frexp(md, &ed);
@@ -982,7 +979,7 @@ static dpr1_status run_table(const Prob& pb, void* workspace, const Options& o, 
     if (og > sms * 8) og = sms * 8;
     k_owner<<<og > 0 ? og : 1, 256, 0, st>>>(pb, w);
   }
-  int ng = (pb.P + 7) / 8;                              // a warp per problem
+  int ng = pb.P;                                        // a block per problem
   if (ng > sms * 8) ng = sms * 8;
   k_norm<<<ng > 0 ? ng : 1, 256, 0, st>>>(pb, w);
   int64_t sg = (pb.total + 255) / 256;
