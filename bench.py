@@ -13,7 +13,8 @@ a full dpr1_eig call timed with CUDA events on the launching stream, L2 flushed 
 write) before every step outside the timed events; nvidia-smi clocks are sampled during
 the timed region.  The line carries the roofline of the solve kernel (algorithmic binary64
 operations over its event-timed duration, against the nominal peak; DRAM traffic from the
-committed ncu record while the kernel sources are unchanged), the CPU oracle on a bounded
+committed ncu record while the kernel sources are unchanged), that of the eigenvector phase
+(the n^2 write of V against the measured copy rate, and its binary64 work), the CPU oracle on a bounded
 sample (all host cores, and one thread on a smaller sample), the end-to-end rate through the binding from pinned host buffers (double-buffered
 outputs), and extra measurements (--extras; --only runs one alone at size --n):
   fwd_bwd    forward and adjoint at n = 4096 (and n = 32768 with --large)
@@ -516,6 +517,15 @@ def kernel_source_hash(files):
     return h.hexdigest()[:16]
 
 
+def measured_hbm_gbs():
+    """The measured HBM copy rate (MEASURED_PEAKS.json) and where it came from."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "of fallback (6.8 TB/s)"
+
+
 def committed_traffic(n, zero_finder=0):
     """DRAM bytes per launch of the solve kernel from the committed ncu summary, if it was
     taken on the current kernel sources (else None)."""
@@ -642,6 +652,22 @@ def run_ours(args):
             "ops_per_launch": ops, "ops_definition": odef,
             "launch_ms": 1e3 * t_solve, "bisection_evaluations": evals}
 
+    # the eigenvector phase (k_vectors and the short near-zero and deflation kernels before it):
+    # the n^2 write of V against the measured copy rate, and its binary64 work against the peak
+    t_vec = statistics.mean(vec_ms) * 1e-3
+    hbm_peak = measured_hbm_gbs()
+    v_bytes = 8.0 * n * n
+    v_ops = 6.0 * n * n
+    hbm_frac = v_bytes / t_vec / (hbm_peak[0] * 1e9)
+    alu_frac = v_ops / t_vec / NOMINAL_FP64_OPS
+    phase_roofs = {"eigenvectors": {
+        "bound": "alu" if alu_frac >= hbm_frac else "hbm", "ms": 1e3 * t_vec,
+        "hbm": {"achieved": v_bytes / t_vec / 1e9, "peak": hbm_peak[0], "unit": "GB/s", "frac": hbm_frac,
+                "peak_source": hbm_peak[1], "bytes_definition": "8 n^2 bytes of V written once"},
+        "alu": {"achieved": v_ops / t_vec / 1e12, "peak": NOMINAL_FP64_OPS / 1e12, "unit": "T binary64-op/s",
+                "frac": alu_frac, "ops_definition": "per element: 2 sub, 1 div, 1 mul, 1 fma (sum of squares), "
+                                                    "1 mul (rescale)"}}}
+
     # end to end through the public API with host buffers
     e2e = None
     if args.e2e_steps > 0:
@@ -732,7 +758,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": dict(workload_config(n), zero_finder=("bisection" if zf == 0 else "accelerated")),
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "phase_rooflines": phase_roofs, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": LAUNCHES_PER_CALL * args.steps, "clocks": clocks,
                 "phases_ms": {"bisection": statistics.mean(solve_ms), "remedies": statistics.mean(fix_ms),
                               "eigenvectors": statistics.mean(vec_ms)},
