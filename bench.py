@@ -55,6 +55,9 @@ ACCEL_OPS_PER_TERM = 8    # the same with its slope (mul, mul, fma)
 # TwoProd of the square (2), quotient and its first-order correction (5), compensated
 # accumulation (7)
 DD_OPS_PER_TERM = 20
+# the binary64 pass over the corner's terms that decides whether b needs double-double
+# (kappa_nu of Eq. (knu2)): sub, div, mul, add
+B64_OPS_PER_TERM = 4
 # kernels one dpr1_eig call launches: k_norm, k_scan, k_deflate, k_solve, k_classify, k_fix, k_zero_detect,
 # k_zero_solve, k_defl_positions, k_vectors, k_defl_rows, k_trivial
 LAUNCHES_PER_CALL = 12
@@ -367,7 +370,8 @@ def bench_accel(B, dev, d, z, rho, ws, out, flush, steps, bisection_ms):
         raise B.DPR1Error(st, "accelerated timed")
     t = statistics.mean(ms)
     solve = statistics.mean(p[0] for p in ph)
-    ops = (n - 1) * (ACCEL_OPS_PER_TERM * stats["evals_solve"] + (OPS_PER_TERM + DD_OPS_PER_TERM) * n)
+    ops = (n - 1) * (ACCEL_OPS_PER_TERM * stats["evals_solve"] + (OPS_PER_TERM + B64_OPS_PER_TERM) * n
+                     + DD_OPS_PER_TERM * stats["double_double"])
     return {"zero_finder": "accelerated bracketed solve (nearest-pole rational model, value and slope)",
             "value": n / (t * 1e-3), "unit": "eigenpairs/s", "ms_per_step": t, "steps": len(ms),
             "phases_ms": {"solve": solve, "remedies": statistics.mean(p[1] for p in ph),
@@ -378,7 +382,9 @@ def bench_accel(B, dev, d, z, rho, ws, out, flush, steps, bisection_ms):
                                   "frac": ops / (solve * 1e-3) / NOMINAL_FP64_OPS,
                                   "ops_definition": "(n-1) x (8 ops per secular term and evaluation (5 for the "
                                                     "value, 3 for the slope) + per eigenvalue the 5-op shift-test "
-                                                    "pass and the 20-op double-double pass)"}}
+                                                    "pass and the 4-op binary64 corner pass + 20 ops per "
+                                                    "double-double term where kappa_nu asks for it)"},
+            "double_double_corners": stats["double_double"]}
 
 
 def bench_hermitian(B, dev, n, seed, steps, flush):
@@ -618,17 +624,21 @@ def run_ours(args):
 
     # roofline of the dominant kernel (the bisection kernel k_solve)
     evals = stats["evals_solve"]
+    n_dd = stats["double_double"]
+    corner = B64_OPS_PER_TERM * n + DD_OPS_PER_TERM * n_dd
     if zf == 0:
-        ops = (n - 1) * (OPS_PER_TERM * (evals + n) + DD_OPS_PER_TERM * n)
-        kname = "k_solve (shift test, double-double b, bisection)"
+        ops = (n - 1) * (OPS_PER_TERM * (evals + n) + corner)
+        kname = "k_solve (shift test, corner b, bisection)"
         odef = ("(n-1) x (5 ops (sub, fma, mul, div, add) per secular term x (bisection evaluations + the "
-                "shift-test pass) + 20 ops per double-double term of b (TwoSum 6, TwoProd 2, quotient and "
-                "correction 5, compensated accumulation 7))")
+                "shift-test pass) + per eigenvalue the 4-op binary64 pass of the corner b (sub, div, mul, "
+                "add) + for the eigenvalues whose kappa_nu asks for it 20 ops per double-double term of b "
+                "(TwoSum 6, TwoProd 2, quotient and correction 5, compensated accumulation 7))")
     else:
-        ops = (n - 1) * (ACCEL_OPS_PER_TERM * evals + (OPS_PER_TERM + DD_OPS_PER_TERM) * n)
-        kname = "k_solve (shift test, double-double b, accelerated bracketed solve)"
+        ops = (n - 1) * (ACCEL_OPS_PER_TERM * evals + OPS_PER_TERM * n + corner)
+        kname = "k_solve (shift test, corner b, accelerated bracketed solve)"
         odef = ("(n-1) x (8 ops per secular term and evaluation (5 for the value, 3 for the slope) + per "
-                "eigenvalue the 5-op shift-test pass and the 20-op double-double pass)")
+                "eigenvalue the 5-op shift-test pass and the 4-op binary64 corner pass + 20 ops per "
+                "double-double term for the eigenvalues whose kappa_nu asks for it)")
     t_solve = statistics.mean(solve_ms) * 1e-3
     achieved = ops / t_solve
     # live binary64 fma rate of this GPU at this clock (same process, after the timed region)
@@ -650,7 +660,7 @@ def run_ours(args):
             "measured_fma_rate": measured_fma / 1e12,
             "frac_of_measured_fma_rate": achieved / measured_fma,
             "ops_per_launch": ops, "ops_definition": odef,
-            "launch_ms": 1e3 * t_solve, "bisection_evaluations": evals}
+            "launch_ms": 1e3 * t_solve, "bisection_evaluations": evals, "double_double_corners": n_dd}
 
     # the eigenvector phase (k_vectors and the short near-zero and deflation kernels before it):
     # the n^2 write of V against the measured copy rate, and its binary64 work against the peak

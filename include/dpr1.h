@@ -95,6 +95,10 @@ typedef struct {
                             slope, kept inside the bisection bracket; the fast zero finder
                             alternative of Sec. 2.2).  Both stop at the
                             adjacent pair of doubles across the sign change. */
+  int dd_mode;           /* the corner b of Eq. (b_ob): 1 (default) in double the working
+                            precision when kappa_nu of Eq. (knu2) exceeds T_kappa * n, as
+                            Algorithm 1 does, else in binary64; 2: always in double-double */
+  double T_kappa;        /* "kappa_nu >> O(n)": double-double when kappa_nu > T_kappa * n (1500) */
 } dpr1_options;
 
 DPR1_API void dpr1_default_options(dpr1_options* opt);
@@ -329,11 +333,12 @@ DPR1_API dpr1_status dpr1_eig_noalloc(int64_t n, const double* d, const double* 
 /*
  * Instrumentation (no counterpart in the paper): synchronises `stream` and copies the
  * counters of the last dpr1_eig / dpr1_eig_batched / dpr1_arrow_eig call on `workspace` into
- * out[0..7]:
+ * out[0..8]:
  *   0 eigenvalues solved by the bisection kernel, 1 eigenvalues flagged by K_nu,
  *   2 remedies taken with R1, 3 with R2, 4 secular-function evaluations in the bisection
  *   kernel, 5 evaluations in the remedy kernel, 6 eigenvalues recomputed from A^{-1},
- *   7 deflated pairs.
+ *   7 deflated pairs, 8 corners b formed in double-double by the bisection kernel.
+ *   `out` holds 9 values.
  */
 DPR1_API dpr1_status dpr1_workspace_stats(void* workspace, int64_t* out, dpr1_stream_t stream);
 

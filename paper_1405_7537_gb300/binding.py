@@ -20,13 +20,15 @@ _LIB = None
 class Options(ctypes.Structure):
     _fields_ = [("T_Knu", ctypes.c_double), ("T_zero", ctypes.c_double), ("lanes", ctypes.c_int),
                 ("warps_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("max_bisect", ctypes.c_int),
-                ("phase_events", ctypes.POINTER(ctypes.c_void_p)), ("zero_finder", ctypes.c_int)]
+                ("phase_events", ctypes.POINTER(ctypes.c_void_p)), ("zero_finder", ctypes.c_int),
+                ("dd_mode", ctypes.c_int), ("T_kappa", ctypes.c_double)]
 
 BISECTION, ACCELERATED = 0, 1   # dpr1_options.zero_finder
 
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "d is not sorted non-increasingly", 3: "rho must be finite and >= 0",
-          4: "non-finite input", 5: "bisection did not converge", 6: "CUDA error", 7: "workspace error"}
+          4: "non-finite input", 5: "bisection did not converge", 6: "CUDA error", 7: "workspace error",
+          8: "an eigenpair needs values outside the binary64 range"}
 
 
 class DPR1Error(RuntimeError):
@@ -271,13 +273,13 @@ def probe_reciprocal(x):
     return out
 
 
-STAT_NAMES = ("solved", "flagged", "r1", "r2", "evals_solve", "evals_fix", "zero_path", "deflated")
+STAT_NAMES = ("solved", "flagged", "r1", "r2", "evals_solve", "evals_fix", "zero_path", "deflated", "double_double")
 
 
 def workspace_stats(ws, stream=None):
     """Counters of the last dpr1_eig / dpr1_eig_batched / dpr1_arrow_eig call on ``ws``
     (synchronises the stream)."""
-    buf = (ctypes.c_int64 * 8)()
+    buf = (ctypes.c_int64 * 9)()
     _check(lib().dpr1_workspace_stats(_ptr(ws), buf, _stream(stream)), "dpr1_workspace_stats")
     return dict(zip(STAT_NAMES, list(buf)))
 

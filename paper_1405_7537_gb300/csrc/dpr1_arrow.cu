@@ -229,6 +229,7 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
   r.mu = 1.0 / nu;
   r.b = b;
   r.ok = ok;
+  r.dd = true;
   r.steps = steps;
   return r;
 }

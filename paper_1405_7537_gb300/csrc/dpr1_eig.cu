@@ -84,6 +84,7 @@ size_t ws_layout2(int64_t total, int64_t nprob, bool batched, Ws* w, char* base)
   char* ps = take(sizeof(unsigned) * pp);
   char* pe = take(sizeof(int) * 2 * pp);
   char* pr = take(sizeof(double) * pp);
+  char* pzs = take(sizeof(double) * pp);
   if (w && base) {
     w->hdr = (unsigned*)hdr;
     w->status = (unsigned*)hdr;
@@ -103,6 +104,7 @@ size_t ws_layout2(int64_t total, int64_t nprob, bool batched, Ws* w, char* base)
     w->fixinfo = (double*)fk;
     w->pexp = (int*)pe;
     w->prho = (double*)pr;
+    w->pzsum = (double*)pzs;
   }
   return off;
 }
@@ -183,7 +185,14 @@ __global__ void __launch_bounds__(256) k_norm(Prob pb, Ws w) {
     }
     md = group_max<256>(md, FULL);
     mz = group_max<256>(mz, FULL);
+    // sum_j |zeta'_j| of the normalised weights (K_z of Eq. (knu2)), in a fixed order
+    int ezb = 0;
+    if (mz > 0.0 && isfinite(mz)) frexp(mz, &ezb);
+    double zs = 0.0;
+    for (int j = threadIdx.x; j < n; j += 256) zs = __dadd_rn(zs, fabs(scalbn(pb.z[base + j], -ezb)));
+    zs = group_sum<256>(zs, FULL);
     if (threadIdx.x == 0) {
+      w.pzsum[p] = zs;
       const double rho = p_rho(pb, p);
       int ed = 0, ez = 0, er = 0;
       if (md > 0.0 && isfinite(md)) frexp(md, &ed);
@@ -376,7 +385,7 @@ __global__ void k_deflate(Prob pb, Ws w) {
 // (solve_pole checks the near end, so a wrong sign of a rounded F costs steps, not accuracy).
 // ---------------------------------------------------------------------------------
 template <int L>
-__global__ void __launch_bounds__(256) k_solve(Prob pb, Ws w, int cap, bool fast) {
+__global__ void __launch_bounds__(256) k_solve(Prob pb, Ws w, int cap, bool fast, int dd_mode, double T_kappa) {
   if (*w.status & ST_FATAL) return;
   const int lane = threadIdx.x & (L - 1);
   const unsigned gm = group_mask<L>();
@@ -429,8 +438,10 @@ __global__ void __launch_bounds__(256) k_solve(Prob pb, Ws w, int cap, bool fast
         ahi = (-1.0 - rho * sn) / (rho * zz[k - 1]);
       }
     }
-    PoleResult pr = solve_pole<L>(d, zl, zz, n, rho, k, i, alo, ahi, cap, fast, lane, gm);
+    PoleResult pr = solve_pole<L>(d, zl, zz, n, rho, k, i, alo, ahi, cap, fast, lane, gm,
+                                  CornerRule{dd_mode, T_kappa, w.pzsum[p]});
     if (lane == 0) {
+      if (pr.dd) atomicAdd(&w.counters[C_DD], 1u);
       w.sig[g] = d[i];
       w.mu[g] = pr.mu;
       w.shift[g] = i;
@@ -509,7 +520,8 @@ __global__ void k_classify(Prob pb, Ws w, double T_Knu) {
 //       estimate with K_nu near 1/eps is noise).
 // ---------------------------------------------------------------------------------
 template <int L>
-__global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double T_Knu, int cap, bool fast) {
+__global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double T_Knu, int cap, bool fast,
+                                                           int dd_mode, double T_kappa) {
   if (*w.status & ST_FATAL) return;
   const int nfix = (int)w.counters[C_FIX_N];
   const int lane = threadIdx.x & (L - 1);
@@ -549,7 +561,8 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double
     double best_sig = di, best_mu = mu;
     int o = (i == k) ? k - 1 : k;
     if (o >= 0 && o < n && o != i && K2 < K) {
-      PoleResult pr = solve_pole<L>(d, zl, zz, n, rho, k, o, 0.0, INFINITY, cap, fast, lane, gm);
+      PoleResult pr = solve_pole<L>(d, zl, zz, n, rho, k, o, 0.0, INFINITY, cap, fast, lane, gm,
+                                    CornerRule{dd_mode, T_kappa, w.pzsum[p]});
       if (!pr.ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
       if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)pr.steps);
       best_sig = d[o];
@@ -933,6 +946,8 @@ Options resolve(const dpr1_options* o) {
   r.cap = s->max_bisect >= 64 && s->max_bisect <= 4096 ? s->max_bisect : def.max_bisect;
   r.events = s->phase_events;
   r.fast = s->zero_finder == 1;
+  r.dd_mode = (s->dd_mode == 2) ? 2 : 1;
+  r.T_kappa = s->T_kappa > 0 ? s->T_kappa : def.T_kappa;
   return r;
 }
 
@@ -944,7 +959,7 @@ template <int L>
 static void launch_solve_fix(const Prob& pb, const Ws& w, const Options& o, int grid, double avg_n,
                              cudaStream_t st) {
   record(o, 0, st);
-  k_solve<L><<<grid, 32 * o.warps, 0, st>>>(pb, w, o.cap, o.fast);
+  k_solve<L><<<grid, 32 * o.warps, 0, st>>>(pb, w, o.cap, o.fast, o.dd_mode, o.T_kappa);
   record(o, 1, st);
   int64_t cg = (pb.total + 255) / 256;
   if (cg > sm_count() * 8) cg = sm_count() * 8;
@@ -954,13 +969,14 @@ static void launch_solve_fix(const Prob& pb, const Ws& w, const Options& o, int 
     // each finishes every item soonest
     int64_t fg = pb.total;                            // at most one block per eigenpair
     if (fg > sm_count() * DPR1_FIX_BLOCKS_PER_SM) fg = sm_count() * DPR1_FIX_BLOCKS_PER_SM;
-    k_fix<DPR1_FIX_THREADS><<<fg > 0 ? (int)fg : 1, DPR1_FIX_THREADS, 0, st>>>(pb, w, o.T_Knu, o.cap, o.fast);
+    k_fix<DPR1_FIX_THREADS><<<fg > 0 ? (int)fg : 1, DPR1_FIX_THREADS, 0, st>>>(pb, w, o.T_Knu, o.cap, o.fast,
+                                                                                  o.dd_mode, o.T_kappa);
   } else {
     // many small problems, many flagged items: one warp each (a block-wide group would
     // leave most of its threads idle and pay a barrier per evaluation)
     int64_t fg = (pb.total + 7) / 8;                  // at most one warp per eigenpair
     if (fg > sm_count() * 4) fg = sm_count() * 4;
-    k_fix<32><<<fg > 0 ? (int)fg : 1, 256, 0, st>>>(pb, w, o.T_Knu, o.cap, o.fast);
+    k_fix<32><<<fg > 0 ? (int)fg : 1, 256, 0, st>>>(pb, w, o.T_Knu, o.cap, o.fast, o.dd_mode, o.T_kappa);
   }
   record(o, 2, st);
 }
@@ -1045,6 +1061,8 @@ void dpr1_default_options(dpr1_options* opt) {
   opt->max_bisect = 96;
   opt->phase_events = nullptr;
   opt->zero_finder = 0;
+  opt->dd_mode = 1;
+  opt->T_kappa = 1500.0;
 }
 
 const char* dpr1_status_string(dpr1_status s) {
@@ -1143,6 +1161,7 @@ dpr1_status dpr1_workspace_stats(void* workspace, int64_t* out, dpr1_stream_t st
   out[5] = c[C_EVAL_FIX];
   out[6] = c[C_ZERO_N];
   out[7] = c[C_DEFL];
+  out[8] = c[C_DD];
   return DPR1_OK;
 }
 

@@ -33,6 +33,7 @@ struct Ws {
   double* fixinfo;            // per flagged slot: K_nu, K_nu at the other pole, distance ratio
   int* pexp;                  // [2P]: exponents (a, b) of the normalisation D' = 2^-a D, z' = 2^-b z
   double* prho;               // [P]: rho' = 2^(2b - a) rho
+  double* pzsum;              // [P]: sum_j |zeta'_j| (for K_z of Eq. (knu2))
 };
 
 struct Options {
@@ -40,12 +41,14 @@ struct Options {
   int lanes, warps, bps, cap;
   void* const* events;
   bool fast;   // accelerated solve instead of bisection
+  int dd_mode;       // corner b: 1 double-double when kappa_nu > T_kappa n, 2 always
+  double T_kappa;
 };
 
 // hdr counters (Ws::counters index)
 enum : int {
   C_FIX_N = 1, C_FIX_Q = 2, C_ZERO_N = 3, C_EVAL_SOLVE = 4, C_EVAL_FIX = 5,
-  C_R2 = 6, C_R1 = 7, C_SOLVED = 8, C_DEFL = 9
+  C_R2 = 6, C_R1 = 7, C_SOLVED = 8, C_DEFL = 9, C_DD = 10
 };
 
 // per-problem bits (Ws::pst)

@@ -397,15 +397,54 @@ __device__ __forceinline__ void quad_bracket(double B, double Efar, double Enear
 struct PoleResult {
   double mu, nu, b;
   bool ok;
+  bool dd;     // b was formed in double-double
   int steps;
 };
 
-// dd corner element of Eq. (b_ob): b = (1/zeta_i^2)(1/rho + sum_{j != i} zeta_j^2/(d_j - d_i)),
-// rounded to binary64 (the arrowhead is formed in working precision).
+// How the corner b is formed (Sec. 2.3): mode 1 in double the working precision when kappa_nu of
+// Eq. (knu2) exceeds T_kappa n, as Algorithm 1 does, mode 2 always; zsum = sum_j |zeta_j| of the
+// problem (for K_z).
+struct CornerRule {
+  int mode;
+  double T_kappa;
+  double zsum;
+};
+
+// Corner element of Eq. (b_ob): b = (1/zeta_i^2)(1/rho + sum_{j != i} zeta_j^2/(d_j - d_i)),
+// rounded to binary64 (the arrowhead is formed in working precision).  Mode 1 first sums the
+// terms in binary64, P over j < i (positive) and N over j > i (negative), and takes
+//   K_b = (1 + rho P - rho N) / |1 + rho P + rho N|,   K_z = sum_{j != i} |zeta_j| / |zeta_i|,
+//   kappa_nu = min((n + 4) sqrt(n) K_b, 3 sqrt(n) + (n + 4)(1 + 2 K_z))     (Eq. (knu2));
+// b is then recomputed in double-double only when kappa_nu > T_kappa n.
 template <int L>
 __device__ __forceinline__ double corner_b(const double* __restrict__ d, const double* __restrict__ zz,
                                            const double* __restrict__ zl, int n, int i,
-                                           double rho, int lane, unsigned gm, double* wn2) {
+                                           double rho, int lane, unsigned gm, double* wn2, CornerRule cr,
+                                           bool* used_dd) {
+  if (cr.mode != 2) {
+    const double di = d[i];
+    double p = 0.0, q = 0.0, s2 = 0.0;
+    for (int j = lane; j < n; j += L) {
+      if (j == i) continue;
+      const double r = rcp(__dsub_rn(d[j], di));
+      const double t = __dmul_rn(zz[j], r);
+      if (j < i) p = __dadd_rn(p, t);
+      else q = __dadd_rn(q, t);
+      s2 = __fma_rn(t, r, s2);
+    }
+    const double P = group_sum<L>(p, gm), N = group_sum<L>(q, gm);
+    *wn2 = group_sum<L>(s2, gm) / zz[i];
+    const double nn = (double)n, sn = sqrt(nn);
+    const double Kb = (1.0 + rho * P - rho * N) / fabs(1.0 + rho * P + rho * N);
+    const double zi = sqrt(zz[i]);
+    const double Kz = (cr.zsum - zi) / zi;
+    const double kappa = fmin((nn + 4.0) * sn * Kb, 3.0 * sn + (nn + 4.0) * (1.0 + 2.0 * Kz));
+    if (kappa <= cr.T_kappa * nn) {
+      *used_dd = false;
+      return (1.0 / zz[i]) * ((1.0 / rho + P) + N);
+    }
+  }
+  *used_dd = true;
   double sq;
   dd acc = dd_pole_sum<L>(d, zz, zl, n, i, d[i], lane, gm, &sq);
   dd B = dd_add(dd_div({1.0, 0.0}, {rho, 0.0}), acc);
@@ -418,10 +457,11 @@ __device__ __forceinline__ double corner_b(const double* __restrict__ d, const d
 template <int L>
 __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __restrict__ zl,
                                  const double* __restrict__ zz, int n, double rho, int k, int i, double alo,
-                                 double ahi, int cap, bool fast, int lane, unsigned gm) {
+                                 double ahi, int cap, bool fast, int lane, unsigned gm, CornerRule cr) {
   PoleResult r;
   double wn2;
-  double b = corner_b<L>(d, zz, zl, n, i, rho, lane, gm, &wn2);
+  bool used_dd;
+  double b = corner_b<L>(d, zz, zl, n, i, rho, lane, gm, &wn2, cr, &used_dd);
   double side = (i == k) ? 1.0 : -1.0;
   double di = d[i];
   double inv_zi2 = 1.0 / zz[i];
@@ -498,6 +538,7 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
   r.mu = 1.0 / nu;
   r.b = b;
   r.ok = ok;
+  r.dd = used_dd;
   r.steps = steps;
   return r;
 }

@@ -146,3 +146,32 @@ def test_tiny_weights_are_zero_weights(B):
     V = g["Vt"].T
     assert np.max(np.abs(A @ V - V * g["lam"])) <= 1e-14
     assert np.max(np.abs(V.T @ V - np.eye(n))) <= 1e-14
+
+
+@pytest.mark.parametrize("gen,n,seed", [("hard", 2000, 3), ("uniform", 1500, 2)])
+@pytest.mark.parametrize("zf", [0, 1])
+def test_corner_rule(B, gen, n, seed, zf):
+    """The corner b of Eq. (b_ob) in double the working precision only where kappa_nu of
+    Eq. (knu2) exceeds 1500 n, as Algorithm 1 does (dd_mode 1, the default), or always
+    (dd_mode 2): both meet the bound against binary128 and the oracle, the counter shows the
+    double-double corners (all of them in mode 2, a minority in mode 1, within a few of the
+    oracle's own kappa_nu rule on a sample)."""
+    import torch
+    d, z, rho = getattr(W, gen)(n, seed)
+    dt, zt = torch.tensor(d, device="cuda"), torch.tensor(z, device="cuda")
+    q = oracle.quad_all(d, z, rho, threads=16)
+    lq = q["hi"] + q["lo"]
+    counts = {}
+    for mode in (1, 2):
+        ws = B.workspace(n)
+        r = B.eig(dt, zt, rho, options=B.default_options(zero_finder=zf, dd_mode=mode), ws=ws)
+        torch.cuda.synchronize()
+        counts[mode] = B.workspace_stats(ws)["double_double"]
+        lam, Vt = r["lam"].cpu().numpy(), r["Vt"].cpu().numpy()
+        assert np.max(np.abs(lam - lq) / np.abs(lq)) <= tol(n), mode
+        assert np.max(np.abs(Vt - q["Vt"]) / np.maximum(np.abs(q["Vt"]), 1e-300)) <= tol(n), mode
+    assert counts[2] == n
+    assert 0 < counts[1] < n // 2
+    ks = np.arange(0, n, 10)
+    used = sum(oracle.dpr1eig(d, z, rho, int(k), oracle.default_opts(dd_mode=1))[2]["used_dd"] for k in ks)
+    assert abs(counts[1] / n - used / ks.size) <= 0.05
