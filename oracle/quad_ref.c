@@ -25,12 +25,18 @@ typedef _Float128 q_t;
 
 static q_t q_abs(q_t a) { return a < 0 ? -a : a; }
 
-/* square root by Newton's iteration from the binary64 estimate (argument in [1, 1e300]) */
+/* square root by Newton's iteration from the binary64 estimate, after an exact scaling by
+   powers of four into [1, 4) (so that the estimate is neither zero nor infinite) */
 static q_t q_sqrt(q_t a) {
-  if (a <= 0) return 0;
+  if (!(a > 0)) return 0;
+  q_t s = 1;
+  while (a >= (q_t)0x1p64) { a /= (q_t)0x1p64; s *= (q_t)0x1p32; }
+  while (a < (q_t)0x1p-64) { a *= (q_t)0x1p64; s /= (q_t)0x1p32; }
+  while (a >= 4) { a /= 4; s *= 2; }
+  while (a < 1) { a *= 4; s /= 2; }
   q_t y = (q_t)sqrt((double)a);
   for (int t = 0; t < 3; t++) y = (y + a / y) / 2;
-  return y;
+  return y * s;
 }
 
 /* f(d_i + mu) with D[j] = d_j - d_i formed in binary128 */
@@ -254,7 +260,7 @@ int quad_arrow_eigpair(int n, const double* d, const double* z, double alpha, in
   if (!D) return -1;
   q_t zn = 0;
   for (int j = 0; j < n; j++) zn += (q_t)z[j] * (q_t)z[j];
-  zn = q_sqrt(zn) + 1;
+  zn = q_sqrt(zn);
   int i;
   q_t lo, hi;
   if (k == 0 || k == n) {
@@ -289,7 +295,7 @@ int quad_arrow_eigpair(int n, const double* d, const double* z, double alpha, in
     q_arrow_ctx c = {n, d, z, alpha};
     q_t zn2 = 0;
     for (int j = 0; j < n; j++) zn2 += (q_t)z[j] * (q_t)z[j];
-    q_t U = q_abs((q_t)alpha) + q_abs((q_t)d[0]) + q_abs((q_t)d[n - 1]) + q_sqrt(zn2 + 1) + 1;
+    q_t U = 2 * (q_abs((q_t)alpha) + q_abs((q_t)d[0]) + q_abs((q_t)d[n - 1]) + q_sqrt(zn2));
     q_t a = (k < n) ? (q_t)d[k] : -U, b = (k > 0) ? (q_t)d[k - 1] : U;
     lam = q_bisect_value(q_fa_ctx, &c, a, b, +1);   /* f decreasing: f > 0 below the root */
   }

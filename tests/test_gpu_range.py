@@ -123,3 +123,32 @@ def test_arrowhead_scale_invariance_is_exact(B):
         r = B.eig_arrowhead(cu(np.ldexp(d, s)), cu(np.ldexp(z, s)), math.ldexp(alpha, s))
         assert np.array_equal(r["lam"].cpu().numpy(), np.ldexp(lam0, s)), s
         assert np.array_equal(r["Vt"].cpu().numpy(), V0), s
+
+
+def test_harsh_arrowheads(B):
+    """Arrowheads of any magnitude (the oracle's harsh generator): each call meets the bound
+    against binary128 or reports DPR1_ERR_RANGE."""
+    from test_oracle_arrow import _harsh_arrow
+    rng = np.random.default_rng(707)
+    cu = lambda a: torch.tensor(np.array(a, copy=True), device="cuda")
+    ok = seen = 0
+    while seen < 60:
+        d, z, alpha = _harsh_arrow(rng)
+        n = d.size
+        if not (np.all(d[:-1] > d[1:]) and np.all(np.isfinite(d)) and np.isfinite(alpha) and not np.any(z == 0)):
+            continue
+        seen += 1
+        for zf in (0, 1):
+            try:
+                r = B.eig_arrowhead(cu(d), cu(z), alpha, options=B.default_options(zero_finder=zf))
+            except B.DPR1Error as ex:
+                assert ex.code in (RANGE, 1), ex.code      # 1: a weight below the zero-weight cut
+                continue
+            q = oracle.quad_arrow_all(d, z, alpha, threads=8)
+            lq = q["hi"] + q["lo"]
+            t = 16 * (n + 1) * 2.0 ** -53
+            lam, Vt = r["lam"].cpu().numpy(), r["Vt"].cpu().numpy()
+            assert np.max(np.abs(lam - lq) / np.abs(lq)) <= t, (seen, zf)
+            assert np.max(np.abs(Vt - q["Vt"]) / np.maximum(np.abs(q["Vt"]), 2.0 ** -1022)) <= t, (seen, zf)
+            ok += 1
+    assert ok >= 80

@@ -250,3 +250,49 @@ def test_r2_from_any_estimate():
                 r = oracle.r2(d, z, alpha, k, est, arrow=True)
                 assert 1 <= r["rounds"] <= 3
                 assert abs(r["lam"] - lq[k]) <= 16 * (n + 1) * EPS * abs(lq[k]), (case, k, est, r, lq[k])
+
+
+def _harsh_arrow(rng, wmax=100):
+    """Arrowheads of any magnitude: the matrix scaled by 2^U(-600, 600), weights spread over up
+    to 2^wmax and scaled by 2^U(-60, 60) against the poles, alpha from 2^-200 to 2^200 times them."""
+    import math
+    n = int(rng.integers(1, 40))
+    kind = rng.integers(0, 3)
+    if kind == 0:
+        d = rng.uniform(-1, 1, n)
+    elif kind == 1:
+        c = rng.uniform(-1, 1, max(1, n // 5))
+        d = rng.choice(c, n) + rng.choice([1.0, -1.0], n) * 10.0 ** rng.uniform(-12, -3, n)
+    else:
+        d = np.sign(rng.uniform(-1, 1, n)) * 10.0 ** rng.uniform(-12, 0, n)
+    d = np.sort(d)[::-1].copy()
+    z = rng.choice([1.0, -1.0], n) * 2.0 ** rng.uniform(-rng.uniform(0, wmax), 0, n) * 2.0 ** rng.uniform(-60, 60)
+    alpha = float(rng.choice([1.0, -1.0]) * 2.0 ** rng.uniform(-200, 200))
+    s = int(rng.integers(-600, 600))
+    return np.ldexp(d, s), np.ldexp(z, s), math.ldexp(alpha, s)
+
+
+def test_harsh_arrowheads():
+    """Arrowheads of any magnitude meet 16(n+1)2^-53 against binary128 (components relative to
+    max(|v|, 2^-1022)) or are reported as out of range -- none fails silently.  This also pins
+    the binary128 reference at such scales (its square root and brackets are scale-free)."""
+    rng = np.random.default_rng(606)
+    ok = 0
+    seen = 0
+    while seen < 120:
+        d, z, alpha = _harsh_arrow(rng)
+        n = d.size
+        if not (np.all(d[:-1] > d[1:]) and np.all(np.isfinite(d)) and np.isfinite(alpha) and not np.any(z == 0)):
+            continue
+        seen += 1
+        try:
+            r = oracle.arrow_eig_all(d, z, alpha, threads=4)
+        except oracle.OracleRangeError:
+            continue
+        q = oracle.quad_arrow_all(d, z, alpha, threads=4)
+        lq = q["hi"] + q["lo"]
+        tol = 16 * (n + 1) * EPS
+        assert np.max(np.abs(r["lam"] - lq) / np.abs(lq)) <= tol, seen
+        assert np.max(np.abs(r["Vt"] - q["Vt"]) / np.maximum(np.abs(q["Vt"]), 2.0 ** -1022)) <= tol, seen
+        ok += 1
+    assert ok >= 100
