@@ -407,9 +407,9 @@ __global__ void k_arrow_classify(int n, const double* __restrict__ d, ArrowWs w,
 }
 
 // Remedies for the flagged eigenvalues, one lane group each (work counter):
-//  (R1) solve at the other neighbouring pole o when K' < K; accept when K' <= T_Knu and
-//       ratio <= T_Knu (beyond that the eigenvector formula at d_o cancels);
-//  (R2) otherwise sigma = fl(lambda) of the better pole solution, moved into the interlacing
+//  (R1) solve at the other neighbouring pole o when K' < K, K' <= T_Knu and ratio <= T_Knu
+//       (beyond that the eigenvector formula at d_o cancels);
+//  (R2) otherwise sigma = fl(lambda) of the first pole solution, moved into the interlacing
 //       interval of lambda_k (exterior ends from Weyl's bounds), and the non-pole solve,
 //       repeated at the new lambda while sigma is not nearer to lambda_k than to the
 //       interval's poles (at most 3 solves), as for D + rho z z^T.
@@ -441,19 +441,16 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_arrow_fix(int n, const do
     const double K = w.fixinfo[3 * (size_t)t];
     const double K2 = w.fixinfo[3 * (size_t)t + 1];
     const double ratio = w.fixinfo[3 * (size_t)t + 2];
-    double new_sig = di, new_mu = mu, best_sig = di, best_mu = mu;
+    double new_sig = di, new_mu = mu;
     int new_shift = i;
     bool done = false;
     const int o = (i == k) ? k - 1 : k;
-    if (o >= 0 && o < n && K2 < K) {
+    // R1 only when it will be taken (as for D + rho z z^T)
+    if (o >= 0 && o < n && K2 < K && K2 <= T_Knu && ratio <= T_Knu) {
       const PoleResult pr = solve_pole_arrow<L>(d, w.zl, w.zz, n, alpha, k, o, 0.0, INFINITY, cap, fast, lane, gm);
       if (!pr.ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
       if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)pr.steps);
-      best_sig = d[o];
-      best_mu = pr.mu;
-      if (K2 <= T_Knu && ratio <= T_Knu) {
-        new_sig = d[o]; new_mu = pr.mu; new_shift = o; done = true;
-      }
+      new_sig = d[o]; new_mu = pr.mu; new_shift = o; done = true;
     }
     if (!done) {
       // the interlacing interval of lambda_k; the exterior ends from Weyl's bounds,
@@ -467,7 +464,7 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_arrow_fix(int n, const do
       }
       const double lo = lo_pole ? d[k] : fmin(d[n - 1], alpha) - zn;
       const double hi = hi_pole ? d[k - 1] : fmax(d[0], alpha) + zn;
-      double sg = __dadd_rn(best_sig, best_mu);
+      double sg = __dadd_rn(di, mu);                    // the first solution's lambda
       for (int round = 0; round < 3; round++) {
         if (lo_pole && !(sg > lo)) sg = dnext_up(lo);
         if (!lo_pole && !(sg >= lo)) sg = lo;

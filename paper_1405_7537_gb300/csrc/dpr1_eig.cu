@@ -509,9 +509,10 @@ __global__ void k_classify(Prob pb, Ws w, double T_Knu) {
 
 // ---------------------------------------------------------------------------------
 // k_fix: remedies for the flagged eigenvalues, one lane group each.
-//  (R1) solve at the other neighbouring pole o; accept when K' < K, K' <= T_Knu and
-//       ratio <= T_Knu (beyond that ratio the eigenvector formula at d_o cancels).
-//  (R2) otherwise shift to sigma = fl(lambda) from the better pole solution, moved into the
+//  (R1) solve at the other neighbouring pole o when K' < K, K' <= T_Knu and ratio <= T_Knu
+//       (beyond that ratio the eigenvector formula at d_o cancels); K' and the ratio come
+//       from k_classify, so the solve runs only when it is taken.
+//  (R2) otherwise shift to sigma = fl(lambda) of the first pole solution, moved into the
 //       interlacing interval of lambda_k ((d_k, d_{k-1}); (d_0, d_0 + rho ||z||^2] for k = 0),
 //       and solve_nonpole.  Any sigma there yields lambda_k (the sign of f(sigma) picks the
 //       side), accurately once lambda_k is the eigenvalue nearest to sigma; when |mu| is not
@@ -558,18 +559,15 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double
     double new_sig = di, new_mu = mu;
     int new_shift = i;
     bool done = false;
-    double best_sig = di, best_mu = mu;
     int o = (i == k) ? k - 1 : k;
-    if (o >= 0 && o < n && o != i && K2 < K) {
+    // R1 is solved only when it will be taken (K' and the ratio come from k_classify); R2 starts
+    // from the first estimate otherwise, and its clamp and safe second shift cover a poor one
+    if (o >= 0 && o < n && o != i && K2 < K && K2 <= T_Knu && ratio <= T_Knu) {
       PoleResult pr = solve_pole<L>(d, zl, zz, n, rho, k, o, 0.0, INFINITY, cap, fast, lane, gm,
                                     CornerRule{dd_mode, T_kappa, w.pzsum[p]});
       if (!pr.ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
       if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)pr.steps);
-      best_sig = d[o];
-      best_mu = pr.mu;
-      if (K2 <= T_Knu && ratio <= T_Knu) {
-        new_sig = d[o]; new_mu = pr.mu; new_shift = o; done = true;
-      }
+      new_sig = d[o]; new_mu = pr.mu; new_shift = o; done = true;
     }
     if (!done) {
       // the interlacing interval of lambda_k, (d_k, d_{k-1}), or (d_0, d_0 + rho ||z||^2] (Weyl)
@@ -582,7 +580,7 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double
         for (int j = lane; j < n; j += L) zs = __dadd_rn(zs, zz[j]);
         hi = __fma_rn(rho, group_sum<L>(zs, gm), d[0]);
       }
-      double s = __dadd_rn(best_sig, best_mu);
+      double s = __dadd_rn(di, mu);                     // the first solution's lambda
       for (int round = 0; round < 3; round++) {
         if (!(s > lo)) s = dnext_up(lo);
         if (k > 0 && s >= hi) s = dnext_down(hi);
