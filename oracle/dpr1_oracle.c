@@ -37,14 +37,22 @@
  *   - R1 is taken when the other neighbouring pole gives a smaller K_nu that is within
  *     T_Knu and lambda is not more than T_Knu times farther from that pole than from
  *     the first one (otherwise the eigenvector formula at the other pole cancels);
- *     else R2.  R2 shifts to sigma = fl(lambda) of the better pole solution (moved
- *     into the open interval if it falls on a pole), computes
- *     f(sigma) in double-double and finds the exterior eigenvalue of the DPR1 matrix
+ *     else R2.  R2 shifts to sigma = fl(lambda) of the better pole solution moved into the
+ *     interlacing interval of lambda_k ((d_k, d_{k-1}), or (d_0, d_0 + rho ||z||^2] for
+ *     k = 0), computes f(sigma) in double-double and finds the exterior eigenvalue of the
+ *     DPR1 matrix
  *     (A - sigma I)^{-1} = (D - sigma I)^{-1} + gamma (D - sigma I)^{-1} z z^T (D - sigma I)^{-1},
- *     gamma = -rho / f(sigma), by bisection.
+ *     gamma = -rho / f(sigma), by bisection; when sigma was not nearer to lambda_k than to
+ *     the interval's poles, again from the midpoint (the Weyl bound for k = 0) and then
+ *     from the lambda found there (o_r2).  A pole solve that left the binary64 range
+ *     counts as K_nu = inf.
  *   - "|lambda| << min(|lambda - d_k|, |lambda - d_{k-1}|)": T_zero |lambda| < min(...).
  *     The denominator of gamma is formed in double-double; if it is zero, lambda = 0.
  *   - Shift test tie F == 0 takes the else branch (sigma = d_{k-1}), as printed.
+ *   - Data of any magnitude: each problem is solved after the exact power-of-two
+ *     normalisation D' = 2^-a D, z' = 2^-b z, rho' = 2^(2b-a) rho (oracle_dpr1eig), and a
+ *     pair that needs values outside the binary64 range (mu zero, subnormal or not finite;
+ *     lambda or v not finite; a cancelling pole difference after R2) returns code 4.
  */
 #include <math.h>
 #include <stdint.h>
