@@ -183,7 +183,9 @@ DPR1_API size_t dpr1_backward_workspace_size(int64_t n);
  *   grad_Vt, ldg     device double[n*ldg] or NULL (zero): row k = dL/dv_k
  *   grad_d, grad_z   device double[n], out (overwritten)
  *   grad_rho         device double[1], out
- * The sum over eigenpairs is done in a fixed order: results are reproducible.
+ * The sum over eigenpairs is done in a fixed order: results are reproducible.  The problem
+ * is normalised by exact powers of two as in dpr1_eig and the gradients are scaled back
+ * (in the normal range this changes no rounding).
  * Errors as dpr1_eig; a non-finite intermediate (e.g. a deflated input) is reported as
  * DPR1_ERR_NONFINITE through dpr1_stream_status on this workspace.
  */

@@ -19,6 +19,10 @@
 // Work split: warp w of a fixed set of NWB warps takes rows k = w, w + NWB, ... and keeps
 // its own partial rows of dbar and zbar in the workspace (no atomics), and a final kernel
 // sums the partials in warp order, so the result does not depend on scheduling.
+// The problem is normalised as in the forward (D' = 2^-a D, z' = 2^-b z, rho' = 2^(2b-a) rho,
+// sigma' = 2^-a sigma, mu' = 2^-a mu, dL/dlambda' = 2^a dL/dlambda) and the gradients are
+// scaled back (dL/dd = 2^-a dL/dd', dL/dz = 2^-b dL/dz', dL/drho = 2^(2b-a) dL/drho'): in the
+// normal range this changes no rounding, and it keeps data of any magnitude in range.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -39,9 +43,12 @@ static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct BwdWs {
   unsigned* status;
+  int* ex;      // status words 2, 3: the exponents a, b of the normalisation
   double* pd;   // [NWB][n]
   double* pz;   // [NWB][n]
   double* pr;   // [NWB]
+  double* ds;   // [n] d' = 2^-a d
+  double* zs;   // [n] z' = 2^-b z
 };
 
 static size_t bwd_layout(int64_t n, BwdWs* w, char* base) {
@@ -51,8 +58,13 @@ static size_t bwd_layout(int64_t n, BwdWs* w, char* base) {
   size_t o_pd = off; off += a256(sizeof(double) * nn * NWB);
   size_t o_pz = off; off += a256(sizeof(double) * nn * NWB);
   size_t o_pr = off; off += a256(sizeof(double) * NWB);
+  size_t o_ds = off; off += a256(sizeof(double) * nn);
+  size_t o_zs = off; off += a256(sizeof(double) * nn);
   if (w && base) {
     w->status = (unsigned*)(base + o_st);
+    w->ex = (int*)(base + o_st) + 2;
+    w->ds = (double*)(base + o_ds);
+    w->zs = (double*)(base + o_zs);
     w->pd = (double*)(base + o_pd);
     w->pz = (double*)(base + o_pz);
     w->pr = (double*)(base + o_pr);
@@ -60,20 +72,50 @@ static size_t bwd_layout(int64_t n, BwdWs* w, char* base) {
   return off;
 }
 
-__global__ void __launch_bounds__(256) k_bwd_rows(int n, const double* __restrict__ d, const double* __restrict__ z,
-                                                  double rho, const double* __restrict__ sig,
+// The exponents of the normalisation (one block): max|d_j| = m 2^a, max|z_j| = m' 2^b.
+__global__ void k_bwd_norm(int n, const double* __restrict__ d, const double* __restrict__ z, BwdWs w) {
+  double md = 0.0, mz = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    md = fmax(md, fabs(d[j]));
+    mz = fmax(mz, fabs(z[j]));
+  }
+  md = group_max<256>(md, FULL);
+  mz = group_max<256>(mz, FULL);
+  if (threadIdx.x == 0) {
+    int a = 0, b = 0;
+    if (md > 0.0 && isfinite(md)) frexp(md, &a);
+    if (mz > 0.0 && isfinite(mz)) frexp(mz, &b);
+    w.ex[0] = a;
+    w.ex[1] = b;
+  }
+}
+
+// the normalised copies d' and z'
+__global__ void k_bwd_scale(int n, const double* __restrict__ d, const double* __restrict__ z, BwdWs w) {
+  const int a = w.ex[0], b = w.ex[1];
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    w.ds[j] = scalbn(d[j], -a);
+    w.zs[j] = scalbn(z[j], -b);
+  }
+}
+
+__global__ void __launch_bounds__(32 * WPB, 1) k_bwd_rows(int n, double rho_in, const double* __restrict__ sig,
                                                   const double* __restrict__ mu, const double* __restrict__ gl,
                                                   const double* __restrict__ gV, int64_t ldg, BwdWs w) {
   const int lane = threadIdx.x & 31;
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (wid >= NWB) return;
+  const int ea = w.ex[0], eb = w.ex[1];
+  const double* __restrict__ d = w.ds;
+  const double* __restrict__ z = w.zs;
+  const double rho = scalbn(rho_in, 2 * eb - ea);
   double* __restrict__ pd = w.pd + (size_t)wid * n;
   double* __restrict__ pz = w.pz + (size_t)wid * n;
   double prho = 0.0;
   unsigned bad = 0;
   bool first = true;
   for (int k = wid; k < n; k += NWB) {
-    const double s = sig[k], m = mu[k];
+    const double s = scalbn(sig[k], -ea), m = scalbn(mu[k], -ea);
     // pass 1: ||x|| (scaled when the plain sum of squares leaves the safe range) and the
     // index p of the largest component (the smallest index among equal ones)
     double mx = 0.0, q = 0.0;
@@ -133,7 +175,7 @@ __global__ void __launch_bounds__(256) k_bwd_rows(int n, const double* __restric
     }
     const double c = grow ? __fma_rn(vp, gvp, P) : 0.0;
     const double gp = grow ? __fma_rn(gvp, S2, -vp * P) : 0.0;
-    const double Lam = (gl ? gl[k] : 0.0) + __fma_rn(-c, Bs, A);
+    const double Lam = (gl ? scalbn(gl[k], ea) : 0.0) + __fma_rn(-c, Bs, A);
     const double Tp = __dmul_rn(gp, vp) * rp;
     const double lb = Lam + Tp;
     // pass 3: contributions
@@ -168,19 +210,20 @@ __global__ void __launch_bounds__(256) k_bwd_rows(int n, const double* __restric
 __global__ void k_bwd_reduce(int n, BwdWs w, double* __restrict__ gd, double* __restrict__ gz,
                              double* __restrict__ grho) {
   const int nw = n < NWB ? n : NWB;
+  const int ea = w.ex[0], eb = w.ex[1];
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     double a = 0.0, b = 0.0;
     for (int t = 0; t < nw; t++) {
       a += w.pd[(size_t)t * n + j];
       b += w.pz[(size_t)t * n + j];
     }
-    gd[j] = a;
-    gz[j] = b;
+    gd[j] = scalbn(a, -ea);
+    gz[j] = scalbn(b, -eb);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     double r = 0.0;
     for (int t = 0; t < nw; t++) r += w.pr[t];
-    *grho = r;
+    *grho = scalbn(r, 2 * eb - ea);
   }
 }
 
@@ -211,9 +254,11 @@ dpr1_status dpr1_eig_backward(int64_t n, const double* d, const double* z, doubl
   BwdWs w;
   bwd_layout(n, &w, (char*)workspace);
   if (cudaMemsetAsync(w.status, 0, 256, st) != cudaSuccess) return DPR1_ERR_CUDA;
-  k_bwd_rows<<<NWB / WPB, 32 * WPB, 0, st>>>((int)n, d, z, rho, sigma, mu, grad_lambda, grad_Vt, ldg, w);
   int g = (int)((n + 255) / 256);
   if (g > 4 * sm_count()) g = 4 * sm_count();
+  k_bwd_norm<<<1, 256, 0, st>>>((int)n, d, z, w);
+  k_bwd_scale<<<g, 256, 0, st>>>((int)n, d, z, w);
+  k_bwd_rows<<<NWB / WPB, 32 * WPB, 0, st>>>((int)n, rho, sigma, mu, grad_lambda, grad_Vt, ldg, w);
   k_bwd_reduce<<<g, 256, 0, st>>>((int)n, w, grad_d, grad_z, grad_rho);
   return cudaGetLastError() == cudaSuccess ? DPR1_OK : DPR1_ERR_CUDA;
 }

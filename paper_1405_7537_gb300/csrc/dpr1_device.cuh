@@ -80,9 +80,10 @@ __device__ __forceinline__ bool rcp_in_range(double x) {
   return ex - 3u <= 2040u;
 }
 
-// A weight zeta with zeta^2 below the normal range of binary64 (|zeta| < 2^-511) is a zero
-// weight: its square, the only form in which the secular function sees it, is not
-// representable, and deflating it changes A = D + rho z z^T by less than 2^-510 rho ||z||.
+// A normalised weight zeta (max|zeta| in [1/2, 1)) with zeta^2 below the normal range of
+// binary64 (|zeta| < 2^-511) is a zero weight: its square, the only form in which the secular
+// function sees it, is not representable, and deflating it changes A = D + rho z z^T by less
+// than 2^-510 rho ||z||.
 __device__ __forceinline__ bool zero_weight(double z) { return fabs(z) < 0x1p-511; }
 
 // IEEE quotient for the rare out-of-range operands; kept out of line so that the compiler

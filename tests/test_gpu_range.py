@@ -152,3 +152,35 @@ def test_harsh_arrowheads(B):
             assert np.max(np.abs(Vt - q["Vt"]) / np.maximum(np.abs(q["Vt"]), 2.0 ** -1022)) <= t, (seen, zf)
             ok += 1
     assert ok >= 80
+
+
+def test_backward_scale_invariance_is_exact(B):
+    """The backward is normalised like the forward.  With d -> 2^s d, z -> 2^t z and
+    rho -> 2^(s - 2t) rho, lambda scales by 2^s and V is unchanged, so a loss on lambda alone
+    gives gradients scaled by (1, 2^(s - t), 2^(2t)) for (d, z, rho), and a loss on V alone by
+    (2^-s, 2^-t, 2^(2t - s)) -- bit for bit, also where the unnormalised data over- or underflow."""
+    d, z, rho = W.uniform(200, 5)
+    rng = np.random.default_rng(5)
+    gl = torch.tensor(rng.standard_normal(d.size), device="cuda")
+    gV = torch.tensor(rng.standard_normal((d.size, d.size)), device="cuda")
+
+    def grads(dd, zz, rr, lam_part):
+        dt, zt = torch.tensor(dd, device="cuda"), torch.tensor(zz, device="cuda")
+        r = B.eig(dt, zt, rr)
+        g = B.eig_backward(dt, zt, rr, r["sigma"], r["mu"], gl if lam_part else None, None if lam_part else gV)
+        torch.cuda.synchronize()
+        return [g[0].cpu().numpy(), g[1].cpu().numpy(), float(g[2])]
+
+    base = {lp: grads(d, z, rho, lp) for lp in (True, False)}
+    for s, t in ((600, 0), (-600, 0), (0, 300), (300, -300), (-37, 11)):
+        ds, zs, rs = np.ldexp(d, s), np.ldexp(z, t), math.ldexp(rho, s - 2 * t)
+        a = grads(ds, zs, rs, True)
+        b0 = base[True]
+        assert np.array_equal(a[0], b0[0]), (s, t)
+        assert np.array_equal(a[1], np.ldexp(b0[1], s - t)), (s, t)
+        assert a[2] == math.ldexp(b0[2], 2 * t), (s, t)
+        v = grads(ds, zs, rs, False)
+        b1 = base[False]
+        assert np.array_equal(v[0], np.ldexp(b1[0], -s)), (s, t)
+        assert np.array_equal(v[1], np.ldexp(b1[1], -t)), (s, t)
+        assert v[2] == math.ldexp(b1[2], 2 * t - s), (s, t)
