@@ -184,3 +184,32 @@ def test_backward_scale_invariance_is_exact(B):
         assert np.array_equal(v[0], np.ldexp(b1[0], -s)), (s, t)
         assert np.array_equal(v[1], np.ldexp(b1[1], -t)), (s, t)
         assert v[2] == math.ldexp(b1[2], 2 * t - s), (s, t)
+
+
+def test_tridiagonal_scale_invariance_is_exact(B):
+    """Divide and conquer scales with the matrix: every step (the tear, the deflation tolerance
+    relative to ||T||, the normalised DPR1 merges, the products of the eigenvector blocks) is
+    homogeneous, so T -> 2^s T gives 2^s lambda and the same Q, bit for bit."""
+    rng = np.random.default_rng(12)
+    a, b = rng.uniform(-1, 1, 700), rng.uniform(-1, 1, 699)
+    cu = lambda x: torch.tensor(np.array(x, copy=True), device="cuda")
+    lam0, Q0 = (x.cpu().numpy() for x in B.eigh_tridiagonal(cu(a), cu(b)))
+    for s in (640, -640, 17):
+        lam, Q = (x.cpu().numpy() for x in B.eigh_tridiagonal(cu(np.ldexp(a, s)), cu(np.ldexp(b, s))))
+        assert np.array_equal(lam, np.ldexp(lam0, s)), s
+        assert np.array_equal(Q, Q0), s
+
+
+def test_hermitian_scale_invariance_is_exact(B):
+    """The Hermitian reduction scales too: z -> 2^t z (its modulus is a fixed sequence of
+    correctly rounded operations with a power-of-two scaling) and d -> 2^s d, rho -> 2^(s-2t) rho
+    give 2^s lambda and the same complex V."""
+    d, z, rho = W.hermitian(150, 3, base="uniform")
+    cu = lambda x: torch.tensor(np.array(x, copy=True), device="cuda")
+    base = B.eig_hermitian(cu(d), cu(z), rho)
+    lam0, V0 = base["lam"].cpu().numpy(), base["Vt"].cpu().numpy()
+    for s, t in ((500, -200), (-500, -200), (600, 320)):      # rho * 2^(s - 2t) stays normal
+        zs = np.ldexp(z.real, t) + 1j * np.ldexp(z.imag, t)
+        r = B.eig_hermitian(cu(np.ldexp(d, s)), cu(zs), math.ldexp(rho, s - 2 * t))
+        assert np.array_equal(r["lam"].cpu().numpy(), np.ldexp(lam0, s)), (s, t)
+        assert np.array_equal(r["Vt"].cpu().numpy(), V0), (s, t)
