@@ -534,7 +534,10 @@ def measured_hbm_gbs():
 
 def committed_traffic(n, zero_finder=0):
     """DRAM bytes per launch of the solve kernel from the committed ncu summary, if it was
-    taken on the current kernel sources (else None)."""
+    taken on the current kernel sources (else None).  The bisection's figure is a capture at
+    its own order n (the stored elements of the inverse are re-read per evaluation, so the
+    traffic does not scale with the eigenpair count); the accelerated solve's is per
+    eigenpair (inputs read once, results written once) and scales with n."""
     path = os.path.join(ROOT, "profiles", "k_solve_traffic.json")
     try:
         with open(path) as f:
@@ -546,8 +549,12 @@ def committed_traffic(n, zero_finder=0):
             return None
     except OSError:
         return None
-    per_unit = rec.get("dram_bytes_per_eigenpair", {}).get("accelerated" if zero_finder else "bisection")
-    return per_unit * n if per_unit else None
+    ent = rec.get("accelerated" if zero_finder else "bisection", {})
+    if "dram_bytes_per_eigenpair" in ent:
+        return ent["dram_bytes_per_eigenpair"] * n
+    if ent.get("n") == n:
+        return ent.get("dram_bytes_per_launch")
+    return None
 
 
 def run_ours(args):

@@ -108,7 +108,14 @@ DPR1_API const char* dpr1_status_string(dpr1_status s);
 
 /*
  * Bytes of workspace for dpr1_eig on a problem of order n (the workspace must be
- * 256-byte aligned; its contents need not be initialised).
+ * 256-byte aligned; its contents need not be initialised).  The size includes, at the end,
+ * one buffer of 2n doubles per lane group of the solve kernel's default launch on the
+ * current device (16 groups per SM for n > 384): there each group stores the elements of
+ * the inverse of its shifted matrix, Delta_j = d_j - d_i and zeta_j^2 / Delta_j of Eq. (invAi),
+ * once per eigenvalue, and every bisection step reads them instead of forming them again.
+ * These buffers are optional: a smaller workspace is accepted down to the part without
+ * them (the bisection then forms the elements at every step, with the same accuracy
+ * bound); below that part the call returns DPR1_ERR_WORKSPACE.
  */
 DPR1_API size_t dpr1_workspace_size(int64_t n);
 
@@ -138,6 +145,10 @@ DPR1_API dpr1_status dpr1_eig(int64_t n, const double* d, const double* z, doubl
 
 /*
  * Bytes of workspace for dpr1_eig_batched on nprob problems with total_n eigenpairs in all.
+ * As for dpr1_workspace_size, the size ends with optional buffers for the stored elements of
+ * the inverse, here of order max(2048, 4 total_n / nprob) (at most total_n) per lane group; the
+ * call divides whatever workspace lies beyond the required part among its lane groups, and
+ * problems larger than a group's buffer form the elements at every bisection step.
  */
 DPR1_API size_t dpr1_batched_workspace_size(int64_t nprob, int64_t total_n);
 

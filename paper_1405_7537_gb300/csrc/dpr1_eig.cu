@@ -105,8 +105,35 @@ size_t ws_layout2(int64_t total, int64_t nprob, bool batched, Ws* w, char* base)
     w->pexp = (int*)pe;
     w->prho = (double*)pr;
     w->pzsum = (double*)pzs;
+    w->terms = nullptr;
+    w->term_n = 0;
+    w->term_slots = 0;
   }
   return off;
+}
+
+// Lane-group width of k_solve for an average problem order (when the options leave it open).
+static int default_lanes(double avg_n) { return avg_n <= 96 ? 8 : (avg_n <= 384 ? 16 : 32); }
+
+// Bytes of the stored-element buffers appended to the workspace: 2 term_n doubles for each
+// lane group of k_solve's default launch (8 warps per block, 2 blocks per SM), term_n = n for
+// one problem and max(2048, 4 n_avg) (at most total) for a batch; problems of larger order,
+// and groups beyond the buffers under other launch options, form the elements per evaluation.
+size_t term_bytes(int64_t total, int64_t nprob) {
+  if (total <= 0 || nprob <= 0) return 0;
+  const double avg = (double)total / (double)nprob;
+  const int64_t gpb = (32 * 8) / default_lanes(avg);
+  int64_t groups = (int64_t)sm_count() * 2 * gpb;
+  const int64_t need = (total + gpb - 1) / gpb * gpb;
+  if (groups > need) groups = need;
+  int64_t tn = total;
+  if (nprob > 1) {
+    const int64_t cap = (int64_t)(4.0 * avg) + 1;
+    tn = cap > 2048 ? cap : 2048;
+    if (tn > total) tn = total;
+  }
+  tn = (tn + 31) & ~(int64_t)31;
+  return (size_t)groups * 16u * (size_t)tn;
 }
 
 size_t ws_layout(int64_t n, Ws* w, char* base) { return ws_layout2(n, 1, false, w, base); }
@@ -372,7 +399,9 @@ __global__ void k_deflate(Prob pb, Ws w) {
 
 // ---------------------------------------------------------------------------------
 // k_solve: one lane group of L threads per eigenvalue; groups take global eigenvalue
-// indices from a counter (persistent grid) and skip deflated slots.
+// indices from a counter (persistent grid) and skip deflated slots.  A group with a buffer in
+// the workspace stores the elements of the inverse there in the corner pass and bisects with
+// stored_sum.
 //
 // Shift test (Algorithm 1): tau = (d_{k-1} - d_k)/2 and
 //   F = 1 + rho sum_j zeta_j^2 / ((d_j - d_k) - tau);  F > 0 -> sigma = d_k, else d_{k-1}.
@@ -390,6 +419,8 @@ __global__ void __launch_bounds__(256) k_solve(Prob pb, Ws w, int cap, bool fast
   const int lane = threadIdx.x & (L - 1);
   const unsigned gm = group_mask<L>();
   const int leader = (threadIdx.x & 31) & ~(L - 1);
+  const int64_t grp = (int64_t)blockIdx.x * (blockDim.x / L) + threadIdx.x / L;
+  double* const Dbuf = (w.terms && grp < w.term_slots) ? w.terms + 2 * grp * w.term_n : nullptr;
   for (;;) {
     long long gl = 0;
     if (lane == 0) gl = (long long)atomicAdd(&w.counters64[0], 1ull);
@@ -438,8 +469,10 @@ __global__ void __launch_bounds__(256) k_solve(Prob pb, Ws w, int cap, bool fast
         ahi = (-1.0 - rho * sn) / (rho * zz[k - 1]);
       }
     }
+    const bool stored = Dbuf && n <= w.term_n;
     PoleResult pr = solve_pole<L>(d, zl, zz, n, rho, k, i, alo, ahi, cap, fast, lane, gm,
-                                  CornerRule{dd_mode, T_kappa, w.pzsum[p]});
+                                  CornerRule{dd_mode, T_kappa, w.pzsum[p]}, stored ? Dbuf : nullptr,
+                                  stored ? Dbuf + w.term_n : nullptr);
     if (lane == 0) {
       if (pr.dd) atomicAdd(&w.counters[C_DD], 1u);
       w.sig[g] = d[i];
@@ -981,9 +1014,10 @@ static void launch_solve_fix(const Prob& pb, const Ws& w, const Options& o, int 
 
 // Launch sequence for a problem table; `avg_n` picks the lane-group width when the
 // options leave it open.
-static dpr1_status run_table(const Prob& pb, void* workspace, const Options& o, double avg_n, cudaStream_t st) {
+static dpr1_status run_table(const Prob& pb, void* workspace, size_t wbytes, const Options& o, double avg_n,
+                             cudaStream_t st) {
   Ws w;
-  ws_layout2(pb.total, pb.P, pb.offs != nullptr, &w, (char*)workspace);
+  const size_t base = ws_layout2(pb.total, pb.P, pb.offs != nullptr, &w, (char*)workspace);
   if (cudaMemsetAsync(w.hdr, 0, sizeof(unsigned) * 64, st) != cudaSuccess) return DPR1_ERR_CUDA;
   if (cudaMemsetAsync(w.pst, 0, sizeof(unsigned) * (size_t)(pb.P > 0 ? pb.P : 1), st) != cudaSuccess)
     return DPR1_ERR_CUDA;
@@ -1004,11 +1038,30 @@ static dpr1_status run_table(const Prob& pb, void* workspace, const Options& o, 
   int dg = (pb.P + 3) / 4;                              // a warp per problem
   if (dg > sms * 8) dg = sms * 8;
   k_deflate<<<dg > 0 ? dg : 1, 128, 0, st>>>(pb, w);
-  int L = o.lanes ? o.lanes : (avg_n <= 96 ? 8 : (avg_n <= 384 ? 16 : 32));
+  int L = o.lanes ? o.lanes : default_lanes(avg_n);
   int groups_per_block = (32 * o.warps) / L;
   int64_t want_blocks = (pb.total + groups_per_block - 1) / groups_per_block;
   int grid = sms * o.bps;
   if (want_blocks < grid) grid = want_blocks > 0 ? (int)want_blocks : 1;
+  // the rest of the workspace holds the stored elements of the inverse for the bisection:
+  // one buffer per lane group, as large as the bytes allow (one problem: the groups that
+  // fit a buffer of its order)
+  if (!o.fast && wbytes > base) {
+    const size_t tb = wbytes - base;
+    const int64_t groups = (int64_t)grid * groups_per_block;
+    int64_t tn = (int64_t)(tb / (16u * (size_t)groups)) & ~(int64_t)31;
+    int64_t slots = groups;
+    if (pb.P == 1 && tn < pb.total) {
+      tn = (pb.total + 31) & ~(int64_t)31;
+      slots = (int64_t)(tb / (16u * (size_t)tn));
+      if (slots > groups) slots = groups;
+    }
+    if (tn >= 32 && slots > 0) {
+      w.terms = (double*)((char*)workspace + base);
+      w.term_n = tn;
+      w.term_slots = slots;
+    }
+  }
   if (L == 8) launch_solve_fix<8>(pb, w, o, grid, avg_n, st);
   else if (L == 16) launch_solve_fix<16>(pb, w, o, grid, avg_n, st);
   else launch_solve_fix<32>(pb, w, o, grid, avg_n, st);
@@ -1028,7 +1081,6 @@ static dpr1_status run_table(const Prob& pb, void* workspace, const Options& o, 
 dpr1_status run_eig(int64_t n64, const double* d, const double* z, double rho, double* lambda, double* Vt,
                     int64_t ldv, double* sigma, double* mu, double* xnorm, void* workspace, size_t wbytes,
                     const dpr1_options* opt, cudaStream_t st) {
-  (void)wbytes;
   Prob pb;
   pb.P = 1;
   pb.total = n64;
@@ -1040,7 +1092,7 @@ dpr1_status run_eig(int64_t n64, const double* d, const double* z, double rho, d
   pb.d = d; pb.z = z;
   pb.lambda = lambda; pb.Vt = Vt; pb.sigma = sigma; pb.mu = mu; pb.xnorm = xnorm;
   Options o = resolve(opt);
-  return run_table(pb, workspace, o, (double)n64, st);
+  return run_table(pb, workspace, wbytes, o, (double)n64, st);
 }
 
 }  // namespace dpr1
@@ -1080,12 +1132,12 @@ const char* dpr1_status_string(dpr1_status s) {
 
 size_t dpr1_workspace_size(int64_t n) {
   if (n < 0) return 0;
-  return ws_layout(n, nullptr, nullptr);
+  return ws_layout(n, nullptr, nullptr) + term_bytes(n, 1);
 }
 
 size_t dpr1_batched_workspace_size(int64_t nprob, int64_t total_n) {
   if (nprob < 0 || total_n < 0) return 0;
-  return ws_layout2(total_n, nprob, true, nullptr, nullptr);
+  return ws_layout2(total_n, nprob, true, nullptr, nullptr) + term_bytes(total_n, nprob);
 }
 
 dpr1_status dpr1_eig(int64_t n, const double* d, const double* z, double rho, double* lambda, double* Vt, int64_t ldv,
@@ -1096,7 +1148,8 @@ dpr1_status dpr1_eig(int64_t n, const double* d, const double* z, double rho, do
   if (n == 0) return DPR1_OK;
   if (!d || !z || !lambda) return DPR1_ERR_ARG;
   if (Vt && ldv < n) return DPR1_ERR_ARG;
-  if (!workspace || ((uintptr_t)workspace & 255) || workspace_bytes < dpr1_workspace_size(n))
+  // the stored-element buffers at the end of the workspace are optional
+  if (!workspace || ((uintptr_t)workspace & 255) || workspace_bytes < ws_layout(n, nullptr, nullptr))
     return DPR1_ERR_WORKSPACE;
   return run_eig(n, d, z, rho, lambda, Vt, ldv, sigma, mu, xnorm, workspace, workspace_bytes, opt,
                  (cudaStream_t)stream);
@@ -1110,7 +1163,8 @@ dpr1_status dpr1_eig_batched(int64_t nprob, int64_t total_n, const int64_t* offs
   if (nprob == 0 || total_n == 0) return DPR1_OK;
   if (!offs || !d || !z || !rho || !lambda) return DPR1_ERR_ARG;
   if (Vt && !voffs) return DPR1_ERR_ARG;
-  if (!workspace || ((uintptr_t)workspace & 255) || workspace_bytes < dpr1_batched_workspace_size(nprob, total_n))
+  if (!workspace || ((uintptr_t)workspace & 255) ||
+      workspace_bytes < ws_layout2(total_n, nprob, true, nullptr, nullptr))
     return DPR1_ERR_WORKSPACE;
   Prob pb;
   pb.P = (int)nprob;
@@ -1123,7 +1177,7 @@ dpr1_status dpr1_eig_batched(int64_t nprob, int64_t total_n, const int64_t* offs
   pb.d = d; pb.z = z;
   pb.lambda = lambda; pb.Vt = Vt; pb.sigma = sigma; pb.mu = mu; pb.xnorm = xnorm;
   Options o = resolve(opt);
-  return run_table(pb, workspace, o, (double)total_n / (double)nprob, (cudaStream_t)stream);
+  return run_table(pb, workspace, workspace_bytes, o, (double)total_n / (double)nprob, (cudaStream_t)stream);
 }
 
 dpr1_status dpr1_stream_status(void* workspace, dpr1_stream_t stream) {

@@ -34,6 +34,12 @@ struct Ws {
   int* pexp;                  // [2P]: exponents (a, b) of the normalisation D' = 2^-a D, z' = 2^-b z
   double* prho;               // [P]: rho' = 2^(2b - a) rho
   double* pzsum;              // [P]: sum_j |zeta'_j| (for K_z of Eq. (knu2))
+  // elements of the inverse for the bisection (k_solve): lane group g < term_slots owns
+  // terms[2 g term_n, 2 (g + 1) term_n) (Delta_j, then zz_j / Delta_j) and uses it for
+  // problems of order <= term_n; nullptr: every evaluation forms them from dr and zz
+  double* terms;
+  int64_t term_n;
+  int64_t term_slots;
 };
 
 struct Options {
@@ -60,6 +66,7 @@ enum : unsigned {
 };
 
 size_t ws_layout(int64_t n, Ws* w, char* base);
+size_t term_bytes(int64_t total, int64_t nprob);
 Options resolve(const dpr1_options* o);
 int sm_count();
 

@@ -29,7 +29,9 @@ dpr1_status run_eig(int64_t n64, const double* d, const double* z, double rho, d
                     int64_t ldv, double* sigma, double* mu, double* xnorm, void* workspace, size_t wbytes,
                     const dpr1_options* opt, cudaStream_t st);
 
-constexpr size_t NOALLOC_WS_BYTES = 640u * 1024u;   // holds the workspace of n <= DPR1_NOALLOC_MAX_N
+// holds the workspace of n <= DPR1_NOALLOC_MAX_N without the bisection's stored-element buffers
+// (run_eig uses what is left over for them)
+constexpr size_t NOALLOC_WS_BYTES = 640u * 1024u;
 
 static __device__ __align__(256) unsigned char g_noalloc_ws[NOALLOC_WS_BYTES];
 
@@ -66,7 +68,7 @@ extern "C" dpr1_status dpr1_eig_noalloc(int64_t n, const double* d, const double
   if (n == 0) return DPR1_OK;
   if (!d || !z || !lambda) return DPR1_ERR_ARG;
   if (Vt && ldv < n) return DPR1_ERR_ARG;
-  size_t need = dpr1_workspace_size(n);
+  size_t need = ws_layout(n, nullptr, nullptr);   // the stored-element buffers are optional
   if (need > NOALLOC_WS_BYTES) return DPR1_ERR_WORKSPACE;
   void* ws = nullptr;
   dpr1_status s = noalloc_address(&ws);

@@ -108,6 +108,52 @@ __device__ __forceinline__ double arrow_sum_d(const double* __restrict__ d, cons
   return s;
 }
 
+// The same sum S(nu) from the elements of the inverse formed once per eigenvalue (Eq. (invAi)):
+// Ds[j] = Delta_j and us[j] = zz_j / Delta_j (both 0 at the excluded index j = i, which then
+// adds 0 / 1), so each evaluation forms only t_j = 1 - nu Delta_j (one fma) and sums
+// u_j / t_j, four terms over one reciprocal:
+//   u0/t0 + u1/t1 = (u0 t1 + u1 t0) / (t0 t1),  and two such pairs combined the same way.
+// Every u_j / t_j = zz_j / (Delta_j t_j) has the sign of the sum, so each u_a t_b of a numerator
+// has the sign of t_a t_b times that sign and no numerator cancels.  Each lane reads only the
+// entries it wrote (index j = lane mod L).  A numerator or denominator outside the fast
+// reciprocal's range (extreme data) sends the group to the range-safe sum from d and zz.
+template <int L>
+__device__ __forceinline__ double stored_sum(const double* __restrict__ Ds, const double* __restrict__ us,
+                                             const double* __restrict__ d, const double* __restrict__ zz, int n,
+                                             int i, double di, double nu, int lane, unsigned gm) {
+  double s0 = 0.0;
+  bool b = false;
+  int j = lane;
+  for (; j + 3 * L < n; j += 4 * L) {
+    const double t0 = __fma_rn(-nu, Ds[j], 1.0), t1 = __fma_rn(-nu, Ds[j + L], 1.0);
+    const double t2 = __fma_rn(-nu, Ds[j + 2 * L], 1.0), t3 = __fma_rn(-nu, Ds[j + 3 * L], 1.0);
+    const double u0 = us[j], u1 = us[j + L], u2 = us[j + 2 * L], u3 = us[j + 3 * L];
+    const double n01 = __fma_rn(u0, t1, __dmul_rn(u1, t0)), p01 = __dmul_rn(t0, t1);
+    const double n23 = __fma_rn(u2, t3, __dmul_rn(u3, t2)), p23 = __dmul_rn(t2, t3);
+    const double num = __fma_rn(n01, p23, __dmul_rn(n23, p01)), den = __dmul_rn(p01, p23);
+    b |= !rcp_in_range(den) || !rcp_in_range(num);
+    s0 = __fma_rn(num, rcp_nr(den), s0);
+  }
+  if (j + L < n) {
+    const double t0 = __fma_rn(-nu, Ds[j], 1.0), t1 = __fma_rn(-nu, Ds[j + L], 1.0);
+    const double num = __fma_rn(us[j], t1, __dmul_rn(us[j + L], t0)), den = __dmul_rn(t0, t1);
+    b |= !rcp_in_range(den) || !rcp_in_range(num);
+    s0 = __fma_rn(num, rcp_nr(den), s0);
+    j += 2 * L;
+  }
+  if (j < n) {
+    const double t0 = __fma_rn(-nu, Ds[j], 1.0), u0 = us[j];
+    b |= !rcp_in_range(t0) || (u0 != 0.0 && !rcp_in_range(u0));
+    s0 = __fma_rn(u0, rcp_nr(t0), s0);
+  }
+  const double s = group_sum<L>(s0, gm);
+  if (group_any<L>(b, gm)) {
+    bool bad;
+    return arrow_sum_pass<L, true, false>(d, zz, n, i, di, nu, lane, gm, &bad, nullptr);
+  }
+  return s;
+}
+
 // Same terms with Delta_j = d_j - sigma for a non-pole shift (no excluded index):
 // sum_j u_j^2 / (e_j - nu), e_j = 1/(d_j - sigma), u_j = zeta_j/(d_j - sigma).
 template <int L>
@@ -416,18 +462,25 @@ struct CornerRule {
 //   K_b = (1 + rho P - rho N) / |1 + rho P + rho N|,   K_z = sum_{j != i} |zeta_j| / |zeta_i|,
 //   kappa_nu = min((n + 4) sqrt(n) K_b, 3 sqrt(n) + (n + 4)(1 + 2 K_z))     (Eq. (knu2));
 // b is then recomputed in double-double only when kappa_nu > T_kappa n.
+// With Ds != nullptr the pass also stores the elements Delta_j and zz_j / Delta_j of the
+// inverse for stored_sum (a pass of its own in mode 2).
 template <int L>
 __device__ __forceinline__ double corner_b(const double* __restrict__ d, const double* __restrict__ zz,
                                            const double* __restrict__ zl, int n, int i,
                                            double rho, int lane, unsigned gm, double* wn2, CornerRule cr,
-                                           bool* used_dd) {
+                                           bool* used_dd, double* __restrict__ Ds, double* __restrict__ us) {
+  const double di = d[i];
   if (cr.mode != 2) {
-    const double di = d[i];
     double p = 0.0, q = 0.0, s2 = 0.0;
     for (int j = lane; j < n; j += L) {
-      if (j == i) continue;
-      const double r = rcp(__dsub_rn(d[j], di));
+      if (j == i) {
+        if (Ds) { Ds[j] = 0.0; us[j] = 0.0; }
+        continue;
+      }
+      const double D = __dsub_rn(d[j], di);
+      const double r = rcp(D);
       const double t = __dmul_rn(zz[j], r);
+      if (Ds) { Ds[j] = D; us[j] = t; }
       if (j < i) p = __dadd_rn(p, t);
       else q = __dadd_rn(q, t);
       s2 = __fma_rn(t, r, s2);
@@ -445,23 +498,34 @@ __device__ __forceinline__ double corner_b(const double* __restrict__ d, const d
     }
   }
   *used_dd = true;
+  if (cr.mode == 2 && Ds) {
+    for (int j = lane; j < n; j += L) {
+      const double D = (j == i) ? 0.0 : __dsub_rn(d[j], di);
+      Ds[j] = D;
+      us[j] = (j == i) ? 0.0 : __dmul_rn(zz[j], rcp(D));
+    }
+  }
   double sq;
-  dd acc = dd_pole_sum<L>(d, zz, zl, n, i, d[i], lane, gm, &sq);
+  dd acc = dd_pole_sum<L>(d, zz, zl, n, i, di, lane, gm, &sq);
   dd B = dd_add(dd_div({1.0, 0.0}, {rho, 0.0}), acc);
   const dd Zi = {zz[i], zl[i]};
   *wn2 = sq / Zi.hi;
   return dd_to_double(dd_div(B, Zi));
 }
 
-// Brackets of |nu| from the shift test (see the derivation in k_solve's comment).
+// Brackets of |nu| from the shift test (see the derivation in k_solve's comment).  Ds, us: the
+// lane group's private buffers of n doubles each for the elements of the inverse (bisection
+// with stored_sum), or nullptr (each evaluation forms them from d and zz).
 template <int L>
 __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __restrict__ zl,
                                  const double* __restrict__ zz, int n, double rho, int k, int i, double alo,
-                                 double ahi, int cap, bool fast, int lane, unsigned gm, CornerRule cr) {
+                                 double ahi, int cap, bool fast, int lane, unsigned gm, CornerRule cr,
+                                 double* __restrict__ Ds = nullptr, double* __restrict__ us = nullptr) {
   PoleResult r;
   double wn2;
   bool used_dd;
-  double b = corner_b<L>(d, zz, zl, n, i, rho, lane, gm, &wn2, cr, &used_dd);
+  if (fast) Ds = us = nullptr;
+  double b = corner_b<L>(d, zz, zl, n, i, rho, lane, gm, &wn2, cr, &used_dd, Ds, us);
   double side = (i == k) ? 1.0 : -1.0;
   double di = d[i];
   double inv_zi2 = 1.0 / zz[i];
@@ -527,7 +591,7 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
     nu = side * accel_solve(ev, floor, alo, ahi, E, side * b, 1.0, 1.0, cap, &ok, &steps);
   } else {
     auto phi = [&](double v) {
-      double S = arrow_sum<L>(d, zz, n, i, di, v, lane, gm);
+      double S = Ds ? stored_sum<L>(Ds, us, d, zz, n, i, di, v, lane, gm) : arrow_sum<L>(d, zz, n, i, di, v, lane, gm);
       return __dsub_rn(__dsub_rn(b, v), __dmul_rn(S, inv_zi2));
     };
     // g(nu) > 0 below the root for the rightmost; for the leftmost, |nu| below the root

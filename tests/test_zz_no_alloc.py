@@ -49,7 +49,13 @@ def test_noalloc_matches_dpr1_eig_twice():
         V0, V1 = ref["Vt"].cpu().numpy(), Vt.cpu().numpy()
         assert np.max(np.abs(l1 - l0) / np.abs(l0)) <= tol
         assert np.max(np.abs(V1 - V0) / np.maximum(np.abs(V0), 1e-300)) <= tol
-        assert np.array_equal(sig.cpu().numpy(), ref["sigma"].cpu().numpy())
+        # shifts: the same poles; a non-pole shift (remedy R2) is the computed eigenvalue, which
+        # may differ in its last bits because only part of the bisection's stored-element
+        # buffers fits the static array
+        s0, s1 = ref["sigma"].cpu().numpy(), sig.cpu().numpy()
+        pole0, pole1 = np.isin(s0, d), np.isin(s1, d)
+        assert np.array_equal(pole0, pole1) and np.array_equal(s0[pole0], s1[pole1])
+        assert np.max(np.abs(s1 - s0) / np.abs(s0), initial=0.0) <= tol
     # beyond the static scratch: rejected before any launch
     n = 4097
     big = torch.zeros(n, dtype=torch.float64, device="cuda")
