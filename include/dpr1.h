@@ -267,7 +267,10 @@ DPR1_API dpr1_status dpr1_tridiag_eig(int64_t n, const double* a, const double* 
                                       const dpr1_options* opt, dpr1_stream_t stream);
 
 /*
- * Bytes of workspace for dpr1_arrow_eig with n poles (256-byte aligned, uninitialised).
+ * Bytes of workspace for dpr1_arrow_eig with n poles (256-byte aligned, uninitialised).  As
+ * for dpr1_workspace_size, it ends with optional buffers in which the bisection stores the
+ * elements of the inverse of each shifted matrix once per eigenvalue; a workspace down to
+ * the part without them is accepted.
  */
 DPR1_API size_t dpr1_arrow_workspace_size(int64_t n);
 

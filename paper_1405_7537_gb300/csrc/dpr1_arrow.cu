@@ -60,6 +60,11 @@ struct ArrowWs {
   double* ds;                    // d' = 2^-a d and z' = 2^-a z (normalised copies)
   double* zs;
   double* scal;                  // [0]: alpha' = 2^-a alpha; [1]: a (as a double)
+  // elements of the inverse for the bisection (as Ws::terms): lane group g < term_slots owns
+  // terms[2 g term_n, 2 (g + 1) term_n)
+  double* terms;
+  int64_t term_n;
+  int64_t term_slots;
 };
 
 static size_t arrow_layout(int64_t n, ArrowWs* w, char* base) {
@@ -94,6 +99,9 @@ static size_t arrow_layout(int64_t n, ArrowWs* w, char* base) {
     w->ds = (double*)(base + o_ds);
     w->zs = (double*)(base + o_zs);
     w->scal = (double*)(base + o_sc);
+    w->terms = nullptr;
+    w->term_n = 0;
+    w->term_slots = 0;
   }
   return off;
 }
@@ -155,11 +163,14 @@ __global__ void k_arrow_check(int n, const double* __restrict__ d, const double*
 template <int L>
 __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const double* __restrict__ zl,
                                        const double* __restrict__ zz, int n, double alpha, int k, int i, double alo,
-                                       double ahi, int cap, bool fast, int lane, unsigned gm) {
+                                       double ahi, int cap, bool fast, int lane, unsigned gm,
+                                       double* __restrict__ Ds = nullptr, double* __restrict__ us = nullptr) {
   PoleResult r;
   double sq;
   const double di = d[i];
-  dd acc = dd_pole_sum<L>(d, zz, zl, n, i, di, lane, gm, &sq);
+  if (fast) Ds = us = nullptr;
+  // the corner's pass also stores the elements of the inverse when the group has a buffer
+  dd acc = dd_pole_sum<L>(d, zz, zl, n, i, di, lane, gm, &sq, nullptr, Ds, us);
   dd B = dd_add(two_sum(di, -alpha), acc);
   const dd Zi = {zz[i], zl[i]};
   const double b = dd_to_double(dd_div(B, Zi));
@@ -219,7 +230,7 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
     nu = side * accel_solve(ev, floor, alo, ahi, E, side * b, 1.0, 1.0, cap, &ok, &steps);
   } else {
     auto phi = [&](double v) {
-      const double S = arrow_sum<L>(d, zz, n, i, di, v, lane, gm);
+      const double S = Ds ? stored_sum<L>(Ds, us, d, zz, n, i, di, v, lane, gm) : arrow_sum<L>(d, zz, n, i, di, v, lane, gm);
       return __dadd_rn(__dsub_rn(__dsub_rn(b, v), __dmul_rn(S, inv)), inv / v);
     };
     // g > 0 below the root for the rightmost eigenvalue, g < 0 for the leftmost
@@ -245,6 +256,8 @@ __global__ void __launch_bounds__(256) k_arrow_solve(int n, const double* __rest
   const unsigned gm = group_mask<L>();
   const int leader = (threadIdx.x & 31) & ~(L - 1);
   const double* __restrict__ zz = w.zz;
+  const int64_t grp = (int64_t)blockIdx.x * (blockDim.x / L) + threadIdx.x / L;
+  double* const Dbuf = (w.terms && grp < w.term_slots && n <= w.term_n) ? w.terms + 2 * grp * w.term_n : nullptr;
   for (;;) {
     long long gl = 0;
     if (lane == 0) gl = (long long)atomicAdd(w.queue, 1ull);
@@ -291,7 +304,8 @@ __global__ void __launch_bounds__(256) k_arrow_solve(int n, const double* __rest
       }
       if (!(ahi > alo)) ahi = INFINITY;
     }
-    PoleResult pr = solve_pole_arrow<L>(d, w.zl, zz, n, alpha, k, i, alo, ahi, cap, fast, lane, gm);
+    PoleResult pr = solve_pole_arrow<L>(d, w.zl, zz, n, alpha, k, i, alo, ahi, cap, fast, lane, gm, Dbuf,
+                                        Dbuf ? Dbuf + w.term_n : nullptr);
     if (lane == 0) {
       w.sig[k] = d[i];
       w.mu[k] = pr.mu;
@@ -630,13 +644,25 @@ __global__ void k_arrow_one(double alpha, double* lambda, double* Vt, double* si
   if (Vt) Vt[0] = -1.0;
 }
 
+// tb: workspace bytes beyond the required part, for the bisection's stored elements (one
+// buffer of 2 n doubles per lane group, for as many groups as the bytes allow)
 template <int L>
-static void launch_arrow(int n, const double* d, const double* z, const ArrowWs& w, const Options& o,
-                         cudaStream_t st) {
+static void launch_arrow(int n, const double* d, const double* z, ArrowWs w, const Options& o, char* tail,
+                         size_t tb, cudaStream_t st) {
   const int groups_per_block = (32 * o.warps) / L;
   int64_t want = ((int64_t)n + 1 + groups_per_block - 1) / groups_per_block;
   int grid = sm_count() * o.bps;
   if (want < grid) grid = (int)(want > 0 ? want : 1);
+  if (!o.fast && tb > 0) {
+    const int64_t tn = ((int64_t)n + 31) & ~(int64_t)31;
+    int64_t slots = (int64_t)(tb / (16u * (size_t)tn));
+    if (slots > (int64_t)grid * groups_per_block) slots = (int64_t)grid * groups_per_block;
+    if (slots > 0) {
+      w.terms = (double*)tail;
+      w.term_n = tn;
+      w.term_slots = slots;
+    }
+  }
   k_arrow_solve<L><<<grid, 32 * o.warps, 0, st>>>(n, d, z, w, o.cap, o.fast);
 }
 
@@ -648,7 +674,7 @@ extern "C" {
 
 size_t dpr1_arrow_workspace_size(int64_t n) {
   if (n < 0) return 0;
-  return arrow_layout(n, nullptr, nullptr);
+  return arrow_layout(n, nullptr, nullptr) + term_bytes(n, 1);
 }
 
 dpr1_status dpr1_arrow_eig(int64_t n, const double* d, const double* z, double alpha, double* lambda, double* Vt,
@@ -657,11 +683,14 @@ dpr1_status dpr1_arrow_eig(int64_t n, const double* d, const double* z, double a
   if (n < 0 || n > (int64_t)0x3fffffff - 1) return DPR1_ERR_ARG;
   if (!lambda || (n > 0 && (!d || !z))) return DPR1_ERR_ARG;
   if (Vt && ldv < n + 1) return DPR1_ERR_ARG;
-  if (!workspace || ((uintptr_t)workspace & 255) || workspace_bytes < dpr1_arrow_workspace_size(n))
+  // the stored-element buffers at the end of the workspace are optional
+  if (!workspace || ((uintptr_t)workspace & 255) || workspace_bytes < arrow_layout(n, nullptr, nullptr))
     return DPR1_ERR_WORKSPACE;
   cudaStream_t st = (cudaStream_t)stream;
   ArrowWs w;
-  arrow_layout(n, &w, (char*)workspace);
+  const size_t base = arrow_layout(n, &w, (char*)workspace);
+  char* const tail = (char*)workspace + base;
+  const size_t tb = workspace_bytes - base;
   if (cudaMemsetAsync(w.status, 0, 256, st) != cudaSuccess) return DPR1_ERR_CUDA;
   if (n == 0) {
     if (!std::isfinite(alpha)) return DPR1_ERR_NONFINITE;
@@ -678,9 +707,9 @@ dpr1_status dpr1_arrow_eig(int64_t n, const double* d, const double* z, double a
   const double* ds = w.ds;
   const double* zs = w.zs;
   const int L = o.lanes ? o.lanes : (n <= 96 ? 8 : (n <= 384 ? 16 : 32));
-  if (L == 8) launch_arrow<8>((int)n, ds, zs, w, o, st);
-  else if (L == 16) launch_arrow<16>((int)n, ds, zs, w, o, st);
-  else launch_arrow<32>((int)n, ds, zs, w, o, st);
+  if (L == 8) launch_arrow<8>((int)n, ds, zs, w, o, tail, tb, st);
+  else if (L == 16) launch_arrow<16>((int)n, ds, zs, w, o, tail, tb, st);
+  else launch_arrow<32>((int)n, ds, zs, w, o, tail, tb, st);
   int kg = (int)((n + 1 + 255) / 256);
   if (kg > sms * 8) kg = sms * 8;
   k_arrow_classify<<<kg, 256, 0, st>>>((int)n, ds, w, o.T_Knu);

@@ -171,14 +171,20 @@ __device__ __forceinline__ double shift_sum(const double* __restrict__ d, const 
 // (Sum2 of Ogita, Rump and Oishi, SIAM J. Sci. Comput. 26 (2005)): two_sum keeps each
 // rounding error, and the errors and the e_q go to a second binary64 accumulator, which
 // gives the sum as accurately as accumulation in twice the working precision (Sec. 2.3).
+// With Ds != nullptr it also stores Dh = fl(d_j - s) and q = zz_j / Dh (0 and 0 at skip): the
+// elements of the inverse that stored_sum reads.
 template <int L>
 __device__ __forceinline__ dd dd_pole_sum(const double* __restrict__ d, const double* __restrict__ zz,
                                           const double* __restrict__ zl, int n, int skip, double s, int lane,
-                                          unsigned gm, double* sq, double* cub = nullptr) {
+                                          unsigned gm, double* sq, double* cub = nullptr,
+                                          double* __restrict__ Ds = nullptr, double* __restrict__ us = nullptr) {
   double hi = 0.0, lo = 0.0, q2 = 0.0, c3 = 0.0;
   const double ms = -s;
   for (int j = lane; j < n; j += L) {
-    if (j == skip) continue;
+    if (j == skip) {
+      if (Ds) { Ds[j] = 0.0; us[j] = 0.0; }
+      continue;
+    }
     const double dj = d[j];
     const bool ge = fabs(dj) >= fabs(ms);
     const double big = ge ? dj : ms, small = ge ? ms : dj;
@@ -187,6 +193,7 @@ __device__ __forceinline__ dd dd_pole_sum(const double* __restrict__ d, const do
     const double Zh = zz[j], Zl = zl[j];
     const double r = rcp(Dh);
     const double q = __dmul_rn(Zh, r);
+    if (Ds) { Ds[j] = Dh; us[j] = q; }
     const double eq = __dmul_rn(__dadd_rn(__fma_rn(-q, Dh, Zh), __fma_rn(-q, Dl, Zl)), r);
     const dd t = two_sum(hi, q);
     hi = t.hi;
