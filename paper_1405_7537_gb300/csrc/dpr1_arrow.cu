@@ -328,9 +328,12 @@ template <int L>
 __device__ double solve_nonpole_arrow(const double* __restrict__ d, const double* __restrict__ zl,
                                       const double* __restrict__ zz, int n, double alpha, double sigma, int above,
                                       int below, int cap, bool fast, int lane, unsigned gm, bool* ok,
-                                      int* steps_out) {
+                                      int* steps_out, double* __restrict__ Ds = nullptr,
+                                      double* __restrict__ us = nullptr) {
   double un2, cub;
-  const dd acc = dd_pole_sum<L>(d, zz, zl, n, -1, sigma, lane, gm, &un2, &cub);
+  if (fast) Ds = us = nullptr;
+  // the double-double pass also stores the elements for the bisection when the group has a buffer
+  const dd acc = dd_pole_sum<L>(d, zz, zl, n, -1, sigma, lane, gm, &un2, &cub, Ds, us);
   const dd f = dd_add(two_sum(alpha, -sigma), {-acc.hi, -acc.lo});
   *ok = true;
   *steps_out = 0;
@@ -374,7 +377,8 @@ __device__ double solve_nonpole_arrow(const double* __restrict__ d, const double
     nu = side * accel_solve(ev, floor, alo, ahi, floor, -1.0 / ag, 0.0, ag, cap, ok, &steps);
   } else {
     auto phi = [&](double v) {
-      return __fma_rn(gamma, __dsub_rn(shift_sum<L>(d, zz, n, sigma, v, lane, gm), 1.0 / v), 1.0);
+      const double S = Ds ? stored_sum<L>(Ds, us, d, zz, n, -1, sigma, v, lane, gm) : shift_sum<L>(d, zz, n, sigma, v, lane, gm);
+      return __fma_rn(gamma, __dsub_rn(S, 1.0 / v), 1.0);
     };
     // h < 0 between the floor and the root in both cases
     nu = bisect(phi, side, floor, alo, ahi, false, cap, ok, &steps);
@@ -436,6 +440,10 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_arrow_fix(int n, const do
   const int lane = threadIdx.x & (L - 1);
   const unsigned gm = group_mask<L>();
   const int leader = (threadIdx.x & 31) & ~(L - 1);
+  // the solve kernel has finished: its lane-group buffers are free for the remedies' bisections
+  const int64_t grp = (int64_t)blockIdx.x * (blockDim.x / L) + threadIdx.x / L;
+  double* const Ds = (w.terms && grp < w.term_slots && n <= w.term_n) ? w.terms + 2 * grp * w.term_n : nullptr;
+  double* const us = Ds ? Ds + w.term_n : nullptr;
   __shared__ int item;
   for (;;) {
     int t = 0;
@@ -461,7 +469,8 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_arrow_fix(int n, const do
     const int o = (i == k) ? k - 1 : k;
     // R1 only when it will be taken (as for D + rho z z^T)
     if (o >= 0 && o < n && K2 < K && K2 <= T_Knu && ratio <= T_Knu) {
-      const PoleResult pr = solve_pole_arrow<L>(d, w.zl, w.zz, n, alpha, k, o, 0.0, INFINITY, cap, fast, lane, gm);
+      const PoleResult pr = solve_pole_arrow<L>(d, w.zl, w.zz, n, alpha, k, o, 0.0, INFINITY, cap, fast, lane, gm,
+                                                Ds, us);
       if (!pr.ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
       if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)pr.steps);
       new_sig = d[o]; new_mu = pr.mu; new_shift = o; done = true;
@@ -488,7 +497,7 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_arrow_fix(int n, const do
         bool ok;
         int st2;
         const double m2 = solve_nonpole_arrow<L>(d, w.zl, w.zz, n, alpha, sg, k > 0 ? k - 1 : -1, k < n ? k : -1,
-                                                 cap, fast, lane, gm, &ok, &st2);
+                                                 cap, fast, lane, gm, &ok, &st2, Ds, us);
         if (!ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
         if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)st2);
         new_sig = sg; new_mu = m2; new_shift = -1;
@@ -645,9 +654,10 @@ __global__ void k_arrow_one(double alpha, double* lambda, double* Vt, double* si
 }
 
 // tb: workspace bytes beyond the required part, for the bisection's stored elements (one
-// buffer of 2 n doubles per lane group, for as many groups as the bytes allow)
+// buffer of 2 n doubles per lane group, for as many groups as the bytes allow; the remedies
+// reuse them after the solve kernel)
 template <int L>
-static void launch_arrow(int n, const double* d, const double* z, ArrowWs w, const Options& o, char* tail,
+static void launch_arrow(int n, const double* d, const double* z, ArrowWs* w, const Options& o, char* tail,
                          size_t tb, cudaStream_t st) {
   const int groups_per_block = (32 * o.warps) / L;
   int64_t want = ((int64_t)n + 1 + groups_per_block - 1) / groups_per_block;
@@ -656,14 +666,17 @@ static void launch_arrow(int n, const double* d, const double* z, ArrowWs w, con
   if (!o.fast && tb > 0) {
     const int64_t tn = ((int64_t)n + 31) & ~(int64_t)31;
     int64_t slots = (int64_t)(tb / (16u * (size_t)tn));
-    if (slots > (int64_t)grid * groups_per_block) slots = (int64_t)grid * groups_per_block;
+    const int64_t cap = (int64_t)grid * groups_per_block > (int64_t)sm_count() * AH_FIX_BLOCKS_PER_SM
+                            ? (int64_t)grid * groups_per_block
+                            : (int64_t)sm_count() * AH_FIX_BLOCKS_PER_SM;
+    if (slots > cap) slots = cap;
     if (slots > 0) {
-      w.terms = (double*)tail;
-      w.term_n = tn;
-      w.term_slots = slots;
+      w->terms = (double*)tail;
+      w->term_n = tn;
+      w->term_slots = slots;
     }
   }
-  k_arrow_solve<L><<<grid, 32 * o.warps, 0, st>>>(n, d, z, w, o.cap, o.fast);
+  k_arrow_solve<L><<<grid, 32 * o.warps, 0, st>>>(n, d, z, *w, o.cap, o.fast);
 }
 
 }  // namespace dpr1
@@ -707,9 +720,9 @@ dpr1_status dpr1_arrow_eig(int64_t n, const double* d, const double* z, double a
   const double* ds = w.ds;
   const double* zs = w.zs;
   const int L = o.lanes ? o.lanes : (n <= 96 ? 8 : (n <= 384 ? 16 : 32));
-  if (L == 8) launch_arrow<8>((int)n, ds, zs, w, o, tail, tb, st);
-  else if (L == 16) launch_arrow<16>((int)n, ds, zs, w, o, tail, tb, st);
-  else launch_arrow<32>((int)n, ds, zs, w, o, tail, tb, st);
+  if (L == 8) launch_arrow<8>((int)n, ds, zs, &w, o, tail, tb, st);
+  else if (L == 16) launch_arrow<16>((int)n, ds, zs, &w, o, tail, tb, st);
+  else launch_arrow<32>((int)n, ds, zs, &w, o, tail, tb, st);
   int kg = (int)((n + 1 + 255) / 256);
   if (kg > sms * 8) kg = sms * 8;
   k_arrow_classify<<<kg, 256, 0, st>>>((int)n, ds, w, o.T_Knu);

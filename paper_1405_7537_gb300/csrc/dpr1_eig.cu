@@ -552,6 +552,7 @@ __global__ void k_classify(Prob pb, Ws w, double T_Knu) {
 //       below half the distance to the nearer pole end, the next shift is the midpoint (the
 //       Weyl bound for k = 0) and then the lambda found there (at most 3 solves: a first
 //       estimate with K_nu near 1/eps is noise).
+// A group with one of k_solve's buffers bisects from stored elements there, as k_solve does.
 // ---------------------------------------------------------------------------------
 template <int L>
 __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double T_Knu, int cap, bool fast,
@@ -561,6 +562,9 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double
   const int lane = threadIdx.x & (L - 1);
   const unsigned gm = group_mask<L>();
   const int leader = (threadIdx.x & 31) & ~(L - 1);
+  // k_solve has finished: its lane-group buffers are free for the remedies' bisections
+  const int64_t grp = (int64_t)blockIdx.x * (blockDim.x / L) + threadIdx.x / L;
+  double* const Dbuf = (w.terms && grp < w.term_slots) ? w.terms + 2 * grp * w.term_n : nullptr;
   __shared__ int item;
   for (;;) {
     int t = 0;
@@ -593,11 +597,13 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double
     int new_shift = i;
     bool done = false;
     int o = (i == k) ? k - 1 : k;
+    double* const Ds = (Dbuf && n <= w.term_n) ? Dbuf : nullptr;
+    double* const us = Ds ? Dbuf + w.term_n : nullptr;
     // R1 is solved only when it will be taken (K' and the ratio come from k_classify); R2 starts
     // from the first estimate otherwise, and its clamp and safe second shift cover a poor one
     if (o >= 0 && o < n && o != i && K2 < K && K2 <= T_Knu && ratio <= T_Knu) {
       PoleResult pr = solve_pole<L>(d, zl, zz, n, rho, k, o, 0.0, INFINITY, cap, fast, lane, gm,
-                                    CornerRule{dd_mode, T_kappa, w.pzsum[p]});
+                                    CornerRule{dd_mode, T_kappa, w.pzsum[p]}, Ds, us);
       if (!pr.ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
       if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)pr.steps);
       new_sig = d[o]; new_mu = pr.mu; new_shift = o; done = true;
@@ -622,7 +628,7 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double
         bool ok;
         int st2 = 0;
         const double m2 =
-            solve_nonpole<L>(d, zl, zz, n, rho, s, k > 0 ? k - 1 : -1, k, cap, fast, lane, gm, &ok, &st2);
+            solve_nonpole<L>(d, zl, zz, n, rho, s, k > 0 ? k - 1 : -1, k, cap, fast, lane, gm, &ok, &st2, Ds, us);
         if (!ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
         if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)st2);
         new_sig = s; new_mu = m2; new_shift = -1;

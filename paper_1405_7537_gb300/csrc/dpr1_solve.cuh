@@ -626,10 +626,14 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
 template <int L>
 __device__ double solve_nonpole(const double* __restrict__ d, const double* __restrict__ zl,
                                 const double* __restrict__ zz, int n, double rho, double sigma, int above, int below,
-                                int cap, bool fast, int lane, unsigned gm, bool* ok, int* steps_out = nullptr) {
+                                int cap, bool fast, int lane, unsigned gm, bool* ok, int* steps_out = nullptr,
+                                double* __restrict__ Ds = nullptr, double* __restrict__ us = nullptr) {
   // above / below: indices of the poles next to sigma (-1: none on that side)
   double un2, cub;
-  dd acc = dd_pole_sum<L>(d, zz, zl, n, -1, sigma, lane, gm, &un2, &cub);
+  if (fast) Ds = us = nullptr;
+  // the double-double pass also stores the elements d_j - sigma and zeta_j^2 / (d_j - sigma)
+  // for the bisection when the group has a buffer (Ds, us as for solve_pole)
+  dd acc = dd_pole_sum<L>(d, zz, zl, n, -1, sigma, lane, gm, &un2, &cub, Ds, us);
   dd f = dd_add({1.0, 0.0}, two_prod(acc.hi, rho));
   f = dd_add(f, {__dmul_rn(acc.lo, rho), 0.0});
   *ok = true;
@@ -673,7 +677,10 @@ __device__ double solve_nonpole(const double* __restrict__ d, const double* __re
     };
     nu = side * accel_solve(ev, floor, alo, ahi, E, -1.0 / ag, 0.0, ag, cap, ok, &steps);
   } else {
-    auto phi = [&](double v) { return __fma_rn(gamma, shift_sum<L>(d, zz, n, sigma, v, lane, gm), 1.0); };
+    auto phi = [&](double v) {
+      const double S = Ds ? stored_sum<L>(Ds, us, d, zz, n, -1, sigma, v, lane, gm) : shift_sum<L>(d, zz, n, sigma, v, lane, gm);
+      return __fma_rn(gamma, S, 1.0);
+    };
     nu = bisect(phi, side, floor, alo, ahi, false, cap, ok, &steps);
   }
   if (steps_out) *steps_out = steps;
