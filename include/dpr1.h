@@ -114,7 +114,7 @@ DPR1_API const char* dpr1_status_string(dpr1_status s);
  * the inverse of its shifted matrix, Delta_j = d_j - d_i and zeta_j^2 / Delta_j of Eq. (invAi),
  * once per eigenvalue, and every bisection step reads them instead of forming them again.
  * These buffers are optional: a smaller workspace is accepted down to the part without
- * them (the bisection then forms the elements at every step, with the same accuracy
+ * them (every evaluation of the secular function then forms the elements again, with the same accuracy
  * bound); below that part the call returns DPR1_ERR_WORKSPACE.
  */
 DPR1_API size_t dpr1_workspace_size(int64_t n);
@@ -148,7 +148,7 @@ DPR1_API dpr1_status dpr1_eig(int64_t n, const double* d, const double* z, doubl
  * As for dpr1_workspace_size, the size ends with optional buffers for the stored elements of
  * the inverse, here of order max(2048, 4 total_n / nprob) (at most total_n) per lane group; the
  * call divides whatever workspace lies beyond the required part among its lane groups, and
- * problems larger than a group's buffer form the elements at every bisection step.
+ * problems larger than a group's buffer form the elements at every evaluation.
  */
 DPR1_API size_t dpr1_batched_workspace_size(int64_t nprob, int64_t total_n);
 
@@ -268,7 +268,7 @@ DPR1_API dpr1_status dpr1_tridiag_eig(int64_t n, const double* a, const double* 
 
 /*
  * Bytes of workspace for dpr1_arrow_eig with n poles (256-byte aligned, uninitialised).  As
- * for dpr1_workspace_size, it ends with optional buffers in which the bisection stores the
+ * for dpr1_workspace_size, it ends with optional buffers in which the solves store the
  * elements of the inverse of each shifted matrix once per eigenvalue; a workspace down to
  * the part without them is accepted.
  */

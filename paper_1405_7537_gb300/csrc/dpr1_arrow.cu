@@ -60,7 +60,7 @@ struct ArrowWs {
   double* ds;                    // d' = 2^-a d and z' = 2^-a z (normalised copies)
   double* zs;
   double* scal;                  // [0]: alpha' = 2^-a alpha; [1]: a (as a double)
-  // elements of the inverse for the bisection (as Ws::terms): lane group g < term_slots owns
+  // elements of the inverse for the solves (as Ws::terms): lane group g < term_slots owns
   // terms[2 g term_n, 2 (g + 1) term_n)
   double* terms;
   int64_t term_n;
@@ -168,7 +168,6 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
   PoleResult r;
   double sq;
   const double di = d[i];
-  if (fast) Ds = us = nullptr;
   // the corner's pass also stores the elements of the inverse when the group has a buffer
   dd acc = dd_pole_sum<L>(d, zz, zl, n, i, di, lane, gm, &sq, nullptr, Ds, us);
   dd B = dd_add(two_sum(di, -alpha), acc);
@@ -218,8 +217,8 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
     auto ev = [&](double t, bool want, double* psi, double* dpsi) {
       const double v = side * t;
       double dS = 0.0;
-      const double S = want ? arrow_sum_d<L>(d, zz, n, i, di, v, lane, gm, &dS)
-                            : arrow_sum<L>(d, zz, n, i, di, v, lane, gm);
+      const double S = want ? elem_sum_d<L>(Ds, us, d, zz, n, i, di, v, lane, gm, &dS)
+                            : elem_sum<L>(Ds, us, d, zz, n, i, di, v, lane, gm);
       const double Sz = __dmul_rn(S, inv);
       const double ex = inv / t;
       *psi = -side * Sz + ex;
@@ -230,7 +229,7 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
     nu = side * accel_solve(ev, floor, alo, ahi, E, side * b, 1.0, 1.0, cap, &ok, &steps);
   } else {
     auto phi = [&](double v) {
-      const double S = Ds ? stored_sum<L>(Ds, us, d, zz, n, i, di, v, lane, gm) : arrow_sum<L>(d, zz, n, i, di, v, lane, gm);
+      const double S = elem_sum<L>(Ds, us, d, zz, n, i, di, v, lane, gm);
       return __dadd_rn(__dsub_rn(__dsub_rn(b, v), __dmul_rn(S, inv)), inv / v);
     };
     // g > 0 below the root for the rightmost eigenvalue, g < 0 for the leftmost
@@ -331,8 +330,7 @@ __device__ double solve_nonpole_arrow(const double* __restrict__ d, const double
                                       int* steps_out, double* __restrict__ Ds = nullptr,
                                       double* __restrict__ us = nullptr) {
   double un2, cub;
-  if (fast) Ds = us = nullptr;
-  // the double-double pass also stores the elements for the bisection when the group has a buffer
+  // the double-double pass also stores the elements for the solve when the group has a buffer
   const dd acc = dd_pole_sum<L>(d, zz, zl, n, -1, sigma, lane, gm, &un2, &cub, Ds, us);
   const dd f = dd_add(two_sum(alpha, -sigma), {-acc.hi, -acc.lo});
   *ok = true;
@@ -367,8 +365,8 @@ __device__ double solve_nonpole_arrow(const double* __restrict__ d, const double
     auto ev = [&](double t, bool want, double* psi, double* dpsi) {
       const double v = side * t;
       double dS = 0.0;
-      const double S = want ? arrow_sum_d<L>(d, zz, n, -1, sigma, v, lane, gm, &dS)
-                            : arrow_sum<L>(d, zz, n, -1, sigma, v, lane, gm);
+      const double S = want ? elem_sum_d<L>(Ds, us, d, zz, n, -1, sigma, v, lane, gm, &dS)
+                            : elem_sum<L>(Ds, us, d, zz, n, -1, sigma, v, lane, gm);
       const double it = 1.0 / t;
       *psi = -side * S + it;
       *dpsi = -dS - it * it;
@@ -377,7 +375,7 @@ __device__ double solve_nonpole_arrow(const double* __restrict__ d, const double
     nu = side * accel_solve(ev, floor, alo, ahi, floor, -1.0 / ag, 0.0, ag, cap, ok, &steps);
   } else {
     auto phi = [&](double v) {
-      const double S = Ds ? stored_sum<L>(Ds, us, d, zz, n, -1, sigma, v, lane, gm) : shift_sum<L>(d, zz, n, sigma, v, lane, gm);
+      const double S = elem_sum<L>(Ds, us, d, zz, n, -1, sigma, v, lane, gm);
       return __fma_rn(gamma, __dsub_rn(S, 1.0 / v), 1.0);
     };
     // h < 0 between the floor and the root in both cases
@@ -440,7 +438,7 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_arrow_fix(int n, const do
   const int lane = threadIdx.x & (L - 1);
   const unsigned gm = group_mask<L>();
   const int leader = (threadIdx.x & 31) & ~(L - 1);
-  // the solve kernel has finished: its lane-group buffers are free for the remedies' bisections
+  // the solve kernel has finished: its lane-group buffers are free for the remedies' solves
   const int64_t grp = (int64_t)blockIdx.x * (blockDim.x / L) + threadIdx.x / L;
   double* const Ds = (w.terms && grp < w.term_slots && n <= w.term_n) ? w.terms + 2 * grp * w.term_n : nullptr;
   double* const us = Ds ? Ds + w.term_n : nullptr;
@@ -653,7 +651,7 @@ __global__ void k_arrow_one(double alpha, double* lambda, double* Vt, double* si
   if (Vt) Vt[0] = -1.0;
 }
 
-// tb: workspace bytes beyond the required part, for the bisection's stored elements (one
+// tb: workspace bytes beyond the required part, for the solves' stored elements (one
 // buffer of 2 n doubles per lane group, for as many groups as the bytes allow; the remedies
 // reuse them after the solve kernel)
 template <int L>
@@ -663,7 +661,7 @@ static void launch_arrow(int n, const double* d, const double* z, ArrowWs* w, co
   int64_t want = ((int64_t)n + 1 + groups_per_block - 1) / groups_per_block;
   int grid = sm_count() * o.bps;
   if (want < grid) grid = (int)(want > 0 ? want : 1);
-  if (!o.fast && tb > 0) {
+  if (tb > 0) {
     const int64_t tn = ((int64_t)n + 31) & ~(int64_t)31;
     int64_t slots = (int64_t)(tb / (16u * (size_t)tn));
     const int64_t cap = (int64_t)grid * groups_per_block > (int64_t)sm_count() * AH_FIX_BLOCKS_PER_SM

@@ -400,8 +400,8 @@ __global__ void k_deflate(Prob pb, Ws w) {
 // ---------------------------------------------------------------------------------
 // k_solve: one lane group of L threads per eigenvalue; groups take global eigenvalue
 // indices from a counter (persistent grid) and skip deflated slots.  A group with a buffer in
-// the workspace stores the elements of the inverse there in the corner pass and bisects with
-// stored_sum.
+// the workspace stores the elements of the inverse there in the corner pass and evaluates the
+// secular function from them (stored_sum, stored_sum_d).
 //
 // Shift test (Algorithm 1): tau = (d_{k-1} - d_k)/2 and
 //   F = 1 + rho sum_j zeta_j^2 / ((d_j - d_k) - tau);  F > 0 -> sigma = d_k, else d_{k-1}.
@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double
   const int lane = threadIdx.x & (L - 1);
   const unsigned gm = group_mask<L>();
   const int leader = (threadIdx.x & 31) & ~(L - 1);
-  // k_solve has finished: its lane-group buffers are free for the remedies' bisections
+  // k_solve has finished: its lane-group buffers are free for the remedies' solves
   const int64_t grp = (int64_t)blockIdx.x * (blockDim.x / L) + threadIdx.x / L;
   double* const Dbuf = (w.terms && grp < w.term_slots) ? w.terms + 2 * grp * w.term_n : nullptr;
   __shared__ int item;
@@ -1049,10 +1049,10 @@ static dpr1_status run_table(const Prob& pb, void* workspace, size_t wbytes, con
   int64_t want_blocks = (pb.total + groups_per_block - 1) / groups_per_block;
   int grid = sms * o.bps;
   if (want_blocks < grid) grid = want_blocks > 0 ? (int)want_blocks : 1;
-  // the rest of the workspace holds the stored elements of the inverse for the bisection:
+  // the rest of the workspace holds the stored elements of the inverse for the solves:
   // one buffer per lane group, as large as the bytes allow (one problem: the groups that
   // fit a buffer of its order)
-  if (!o.fast && wbytes > base) {
+  if (wbytes > base) {
     const size_t tb = wbytes - base;
     const int64_t groups = (int64_t)grid * groups_per_block;
     int64_t tn = (int64_t)(tb / (16u * (size_t)groups)) & ~(int64_t)31;

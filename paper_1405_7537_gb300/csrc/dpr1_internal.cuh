@@ -34,7 +34,7 @@ struct Ws {
   int* pexp;                  // [2P]: exponents (a, b) of the normalisation D' = 2^-a D, z' = 2^-b z
   double* prho;               // [P]: rho' = 2^(2b - a) rho
   double* pzsum;              // [P]: sum_j |zeta'_j| (for K_z of Eq. (knu2))
-  // elements of the inverse for the bisection (k_solve): lane group g < term_slots owns
+  // elements of the inverse for the secular evaluations (k_solve, k_fix): lane group g < term_slots owns
   // terms[2 g term_n, 2 (g + 1) term_n) (Delta_j, then zz_j / Delta_j) and uses it for
   // problems of order <= term_n; nullptr: every evaluation forms them from dr and zz
   double* terms;

@@ -29,7 +29,7 @@ dpr1_status run_eig(int64_t n64, const double* d, const double* z, double rho, d
                     int64_t ldv, double* sigma, double* mu, double* xnorm, void* workspace, size_t wbytes,
                     const dpr1_options* opt, cudaStream_t st);
 
-// holds the workspace of n <= DPR1_NOALLOC_MAX_N without the bisection's stored-element buffers
+// holds the workspace of n <= DPR1_NOALLOC_MAX_N without the solves' stored-element buffers
 // (run_eig uses what is left over for them)
 constexpr size_t NOALLOC_WS_BYTES = 640u * 1024u;
 
