@@ -1,6 +1,6 @@
 """GPU parity of dpr1_eig (through the C ABI) against the CPU oracle and the binary128 reference.
 
-Bound (BASELINE the benchmark spec): every eigenvalue and every eigenvector component within
+Bound: every eigenvalue and every eigenvector component within
 relative 16 n 2^-53 of the binary128 reference, and of the oracle.
 """
 import numpy as np
