@@ -524,7 +524,7 @@ def kernel_source_hash(files):
 
 
 def measured_hbm_gbs():
-    """The measured HBM copy rate (MEASURED_PEAKS.json) and where it came from."""
+    """The measured HBM copy rate of this GPU type (MEASURED_PEAKS.json) and where it came from."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return float(json.load(f)["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs)"
