@@ -99,6 +99,10 @@ typedef struct {
                             precision when kappa_nu of Eq. (knu2) exceeds T_kappa * n, as
                             Algorithm 1 does, else in binary64; 2: always in double-double */
   double T_kappa;        /* "kappa_nu >> O(n)": double-double when kappa_nu > T_kappa * n (1500) */
+  int screen;            /* 1 (default): a bisection step whose sign a binary32 evaluation of the
+                            stored elements settles with a rigorous error bound -- the sign the
+                            binary64 evaluation would give -- skips the binary64 evaluation, so
+                            the results are the same bits as with 0 (every step in binary64) */
 } dpr1_options;
 
 DPR1_API void dpr1_default_options(dpr1_options* opt);
@@ -353,8 +357,9 @@ DPR1_API dpr1_status dpr1_eig_noalloc(int64_t n, const double* d, const double* 
  *   0 eigenvalues solved by the bisection kernel, 1 eigenvalues flagged by K_nu,
  *   2 remedies taken with R1, 3 with R2, 4 secular-function evaluations in the bisection
  *   kernel, 5 evaluations in the remedy kernel, 6 eigenvalues recomputed from A^{-1},
- *   7 deflated pairs, 8 corners b formed in double-double by the bisection kernel.
- *   `out` holds 9 values.
+ *   7 deflated pairs, 8 corners b formed in double-double by the bisection kernel,
+ *   9 bisection steps (of those counted in 4 and 5) settled by the binary32 screen.
+ *   `out` holds 10 values.
  */
 DPR1_API dpr1_status dpr1_workspace_stats(void* workspace, int64_t* out, dpr1_stream_t stream);
 

@@ -21,7 +21,7 @@ class Options(ctypes.Structure):
     _fields_ = [("T_Knu", ctypes.c_double), ("T_zero", ctypes.c_double), ("lanes", ctypes.c_int),
                 ("warps_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("max_bisect", ctypes.c_int),
                 ("phase_events", ctypes.POINTER(ctypes.c_void_p)), ("zero_finder", ctypes.c_int),
-                ("dd_mode", ctypes.c_int), ("T_kappa", ctypes.c_double)]
+                ("dd_mode", ctypes.c_int), ("T_kappa", ctypes.c_double), ("screen", ctypes.c_int)]
 
 BISECTION, ACCELERATED = 0, 1   # dpr1_options.zero_finder
 
@@ -273,13 +273,14 @@ def probe_reciprocal(x):
     return out
 
 
-STAT_NAMES = ("solved", "flagged", "r1", "r2", "evals_solve", "evals_fix", "zero_path", "deflated", "double_double")
+STAT_NAMES = ("solved", "flagged", "r1", "r2", "evals_solve", "evals_fix", "zero_path", "deflated", "double_double",
+              "screened")
 
 
 def workspace_stats(ws, stream=None):
     """Counters of the last dpr1_eig / dpr1_eig_batched / dpr1_arrow_eig call on ``ws``
     (synchronises the stream)."""
-    buf = (ctypes.c_int64 * 9)()
+    buf = (ctypes.c_int64 * len(STAT_NAMES))()
     _check(lib().dpr1_workspace_stats(_ptr(ws), buf, _stream(stream)), "dpr1_workspace_stats")
     return dict(zip(STAT_NAMES, list(buf)))
 

@@ -60,8 +60,7 @@ struct ArrowWs {
   double* ds;                    // d' = 2^-a d and z' = 2^-a z (normalised copies)
   double* zs;
   double* scal;                  // [0]: alpha' = 2^-a alpha; [1]: a (as a double)
-  // elements of the inverse for the solves (as Ws::terms): lane group g < term_slots owns
-  // terms[2 g term_n, 2 (g + 1) term_n)
+  // elements of the inverse for the solves, laid out as Ws::terms (the binary32 copies unused)
   double* terms;
   int64_t term_n;
   int64_t term_slots;
@@ -256,7 +255,7 @@ __global__ void __launch_bounds__(256) k_arrow_solve(int n, const double* __rest
   const int leader = (threadIdx.x & 31) & ~(L - 1);
   const double* __restrict__ zz = w.zz;
   const int64_t grp = (int64_t)blockIdx.x * (blockDim.x / L) + threadIdx.x / L;
-  double* const Dbuf = (w.terms && grp < w.term_slots && n <= w.term_n) ? w.terms + 2 * grp * w.term_n : nullptr;
+  double* const Dbuf = (w.terms && grp < w.term_slots && n <= w.term_n) ? w.terms + 3 * grp * w.term_n : nullptr;
   for (;;) {
     long long gl = 0;
     if (lane == 0) gl = (long long)atomicAdd(w.queue, 1ull);
@@ -304,7 +303,7 @@ __global__ void __launch_bounds__(256) k_arrow_solve(int n, const double* __rest
       if (!(ahi > alo)) ahi = INFINITY;
     }
     PoleResult pr = solve_pole_arrow<L>(d, w.zl, zz, n, alpha, k, i, alo, ahi, cap, fast, lane, gm, Dbuf,
-                                        Dbuf ? Dbuf + w.term_n : nullptr);
+                                        Dbuf ? Dbuf + n : nullptr);
     if (lane == 0) {
       w.sig[k] = d[i];
       w.mu[k] = pr.mu;
@@ -440,8 +439,8 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_arrow_fix(int n, const do
   const int leader = (threadIdx.x & 31) & ~(L - 1);
   // the solve kernel has finished: its lane-group buffers are free for the remedies' solves
   const int64_t grp = (int64_t)blockIdx.x * (blockDim.x / L) + threadIdx.x / L;
-  double* const Ds = (w.terms && grp < w.term_slots && n <= w.term_n) ? w.terms + 2 * grp * w.term_n : nullptr;
-  double* const us = Ds ? Ds + w.term_n : nullptr;
+  double* const Ds = (w.terms && grp < w.term_slots && n <= w.term_n) ? w.terms + 3 * grp * w.term_n : nullptr;
+  double* const us = Ds ? Ds + n : nullptr;
   __shared__ int item;
   for (;;) {
     int t = 0;
@@ -651,6 +650,27 @@ __global__ void k_arrow_one(double alpha, double* lambda, double* Vt, double* si
   if (Vt) Vt[0] = -1.0;
 }
 
+// lane groups of the solve kernel's default launch and of the remedies kernel
+static int arrow_lanes(int64_t n) { return n <= 96 ? 8 : (n <= 384 ? 16 : 32); }
+
+static int64_t arrow_groups(int64_t n, int L, int warps, int bps) {
+  const int groups_per_block = (32 * warps) / L;
+  int64_t want = (n + 1 + groups_per_block - 1) / groups_per_block;
+  int64_t grid = (int64_t)sm_count() * bps;
+  if (want < grid) grid = want > 0 ? want : 1;
+  int64_t need = grid * groups_per_block;
+  const int64_t fixg = (n + 1 < (int64_t)sm_count() * AH_FIX_BLOCKS_PER_SM) ? n + 1
+                                                                           : (int64_t)sm_count() * AH_FIX_BLOCKS_PER_SM;
+  return fixg > need ? fixg : need;
+}
+
+// bytes of the stored-element buffers for the default launch (8 warps per block, 2 blocks per SM)
+static size_t arrow_term_bytes(int64_t n) {
+  if (n <= 0) return 0;
+  const int64_t tn = (n + 31) & ~(int64_t)31;
+  return (size_t)arrow_groups(n, arrow_lanes(n), 8, 2) * TERM_BYTES * (size_t)tn;
+}
+
 // tb: workspace bytes beyond the required part, for the solves' stored elements (one
 // buffer of 2 n doubles per lane group, for as many groups as the bytes allow; the remedies
 // reuse them after the solve kernel)
@@ -662,16 +682,15 @@ static void launch_arrow(int n, const double* d, const double* z, ArrowWs* w, co
   int grid = sm_count() * o.bps;
   if (want < grid) grid = (int)(want > 0 ? want : 1);
   if (tb > 0) {
+    // a buffer for every group of the solve and the remedies kernels, or none (so the sums are
+    // formed the same way whichever group takes an eigenvalue)
     const int64_t tn = ((int64_t)n + 31) & ~(int64_t)31;
-    int64_t slots = (int64_t)(tb / (16u * (size_t)tn));
-    const int64_t cap = (int64_t)grid * groups_per_block > (int64_t)sm_count() * AH_FIX_BLOCKS_PER_SM
-                            ? (int64_t)grid * groups_per_block
-                            : (int64_t)sm_count() * AH_FIX_BLOCKS_PER_SM;
-    if (slots > cap) slots = cap;
-    if (slots > 0) {
+    const int64_t slots = (int64_t)(tb / (TERM_BYTES * (size_t)tn));
+    const int64_t need = arrow_groups(n, L, o.warps, o.bps);
+    if (slots >= need) {
       w->terms = (double*)tail;
       w->term_n = tn;
-      w->term_slots = slots;
+      w->term_slots = need;
     }
   }
   k_arrow_solve<L><<<grid, 32 * o.warps, 0, st>>>(n, d, z, *w, o.cap, o.fast);
@@ -685,7 +704,7 @@ extern "C" {
 
 size_t dpr1_arrow_workspace_size(int64_t n) {
   if (n < 0) return 0;
-  return arrow_layout(n, nullptr, nullptr) + term_bytes(n, 1);
+  return arrow_layout(n, nullptr, nullptr) + arrow_term_bytes(n);
 }
 
 dpr1_status dpr1_arrow_eig(int64_t n, const double* d, const double* z, double alpha, double* lambda, double* Vt,
@@ -717,7 +736,7 @@ dpr1_status dpr1_arrow_eig(int64_t n, const double* d, const double* z, double a
   // from here on the kernels work on the normalised copies d' = 2^-a d, z' = 2^-a z, alpha'
   const double* ds = w.ds;
   const double* zs = w.zs;
-  const int L = o.lanes ? o.lanes : (n <= 96 ? 8 : (n <= 384 ? 16 : 32));
+  const int L = o.lanes ? o.lanes : arrow_lanes(n);
   if (L == 8) launch_arrow<8>((int)n, ds, zs, &w, o, tail, tb, st);
   else if (L == 16) launch_arrow<16>((int)n, ds, zs, &w, o, tail, tb, st);
   else launch_arrow<32>((int)n, ds, zs, &w, o, tail, tb, st);

@@ -66,6 +66,14 @@ __device__ __forceinline__ double rcp_approx(double x) {
   return r;
 }
 
+// binary32 approximate reciprocal (flushes subnormal inputs and results to zero); the screen
+// of the bisection allows it 2^-22 relative error
+__device__ __forceinline__ float rcp_approx_f32(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // 1/x within one ulp for |x| in [2^-1020, 2^1021) (see the file comment); no range handling.
 __device__ __forceinline__ double rcp_nr(double x) {
   double r0 = rcp_approx(x);

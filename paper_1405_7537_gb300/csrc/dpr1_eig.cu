@@ -115,8 +115,8 @@ size_t ws_layout2(int64_t total, int64_t nprob, bool batched, Ws* w, char* base)
 // Lane-group width of k_solve for an average problem order (when the options leave it open).
 static int default_lanes(double avg_n) { return avg_n <= 96 ? 8 : (avg_n <= 384 ? 16 : 32); }
 
-// Bytes of the stored-element buffers appended to the workspace: 2 term_n doubles for each
-// lane group of k_solve's default launch (8 warps per block, 2 blocks per SM), term_n = n for
+// Bytes of the stored-element buffers appended to the workspace: TERM_BYTES term_n bytes for
+// each lane group of k_solve's default launch (8 warps per block, 2 blocks per SM), term_n = n for
 // one problem and max(2048, 4 n_avg) (at most total) for a batch; problems of larger order,
 // and groups beyond the buffers under other launch options, form the elements per evaluation.
 size_t term_bytes(int64_t total, int64_t nprob) {
@@ -133,7 +133,7 @@ size_t term_bytes(int64_t total, int64_t nprob) {
     if (tn > total) tn = total;
   }
   tn = (tn + 31) & ~(int64_t)31;
-  return (size_t)groups * 16u * (size_t)tn;
+  return (size_t)groups * TERM_BYTES * (size_t)tn;
 }
 
 size_t ws_layout(int64_t n, Ws* w, char* base) { return ws_layout2(n, 1, false, w, base); }
@@ -414,13 +414,14 @@ __global__ void k_deflate(Prob pb, Ws w) {
 // (solve_pole checks the near end, so a wrong sign of a rounded F costs steps, not accuracy).
 // ---------------------------------------------------------------------------------
 template <int L>
-__global__ void __launch_bounds__(256) k_solve(Prob pb, Ws w, int cap, bool fast, int dd_mode, double T_kappa) {
+__global__ void __launch_bounds__(256) k_solve(Prob pb, Ws w, int cap, bool fast, int dd_mode, double T_kappa,
+                                               bool screen) {
   if (*w.status & ST_FATAL) return;
   const int lane = threadIdx.x & (L - 1);
   const unsigned gm = group_mask<L>();
   const int leader = (threadIdx.x & 31) & ~(L - 1);
   const int64_t grp = (int64_t)blockIdx.x * (blockDim.x / L) + threadIdx.x / L;
-  double* const Dbuf = (w.terms && grp < w.term_slots) ? w.terms + 2 * grp * w.term_n : nullptr;
+  double* const Dbuf = (w.terms && grp < w.term_slots) ? w.terms + 3 * grp * w.term_n : nullptr;
   for (;;) {
     long long gl = 0;
     if (lane == 0) gl = (long long)atomicAdd(&w.counters64[0], 1ull);
@@ -472,9 +473,10 @@ __global__ void __launch_bounds__(256) k_solve(Prob pb, Ws w, int cap, bool fast
     const bool stored = Dbuf && n <= w.term_n;
     PoleResult pr = solve_pole<L>(d, zl, zz, n, rho, k, i, alo, ahi, cap, fast, lane, gm,
                                   CornerRule{dd_mode, T_kappa, w.pzsum[p]}, stored ? Dbuf : nullptr,
-                                  stored ? Dbuf + w.term_n : nullptr);
+                                  stored ? Dbuf + n : nullptr, screen);
     if (lane == 0) {
       if (pr.dd) atomicAdd(&w.counters[C_DD], 1u);
+      if (pr.screened) atomicAdd(&w.counters[C_SCREEN], (unsigned)pr.screened);
       w.sig[g] = d[i];
       w.mu[g] = pr.mu;
       w.shift[g] = i;
@@ -556,7 +558,7 @@ __global__ void k_classify(Prob pb, Ws w, double T_Knu) {
 // ---------------------------------------------------------------------------------
 template <int L>
 __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double T_Knu, int cap, bool fast,
-                                                           int dd_mode, double T_kappa) {
+                                                           int dd_mode, double T_kappa, bool screen) {
   if (*w.status & ST_FATAL) return;
   const int nfix = (int)w.counters[C_FIX_N];
   const int lane = threadIdx.x & (L - 1);
@@ -564,7 +566,7 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double
   const int leader = (threadIdx.x & 31) & ~(L - 1);
   // k_solve has finished: its lane-group buffers are free for the remedies' solves
   const int64_t grp = (int64_t)blockIdx.x * (blockDim.x / L) + threadIdx.x / L;
-  double* const Dbuf = (w.terms && grp < w.term_slots) ? w.terms + 2 * grp * w.term_n : nullptr;
+  double* const Dbuf = (w.terms && grp < w.term_slots) ? w.terms + 3 * grp * w.term_n : nullptr;
   __shared__ int item;
   for (;;) {
     int t = 0;
@@ -598,14 +600,15 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double
     bool done = false;
     int o = (i == k) ? k - 1 : k;
     double* const Ds = (Dbuf && n <= w.term_n) ? Dbuf : nullptr;
-    double* const us = Ds ? Dbuf + w.term_n : nullptr;
+    double* const us = Ds ? Dbuf + n : nullptr;
     // R1 is solved only when it will be taken (K' and the ratio come from k_classify); R2 starts
     // from the first estimate otherwise, and its clamp and safe second shift cover a poor one
     if (o >= 0 && o < n && o != i && K2 < K && K2 <= T_Knu && ratio <= T_Knu) {
       PoleResult pr = solve_pole<L>(d, zl, zz, n, rho, k, o, 0.0, INFINITY, cap, fast, lane, gm,
-                                    CornerRule{dd_mode, T_kappa, w.pzsum[p]}, Ds, us);
+                                    CornerRule{dd_mode, T_kappa, w.pzsum[p]}, Ds, us, screen);
       if (!pr.ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
       if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)pr.steps);
+      if (lane == 0 && pr.screened) atomicAdd(&w.counters[C_SCREEN], (unsigned)pr.screened);
       new_sig = d[o]; new_mu = pr.mu; new_shift = o; done = true;
     }
     if (!done) {
@@ -985,6 +988,7 @@ Options resolve(const dpr1_options* o) {
   r.fast = s->zero_finder == 1;
   r.dd_mode = (s->dd_mode == 2) ? 2 : 1;
   r.T_kappa = s->T_kappa > 0 ? s->T_kappa : def.T_kappa;
+  r.screen = s->screen != 0;
   return r;
 }
 
@@ -996,7 +1000,7 @@ template <int L>
 static void launch_solve_fix(const Prob& pb, const Ws& w, const Options& o, int grid, double avg_n,
                              cudaStream_t st) {
   record(o, 0, st);
-  k_solve<L><<<grid, 32 * o.warps, 0, st>>>(pb, w, o.cap, o.fast, o.dd_mode, o.T_kappa);
+  k_solve<L><<<grid, 32 * o.warps, 0, st>>>(pb, w, o.cap, o.fast, o.dd_mode, o.T_kappa, o.screen);
   record(o, 1, st);
   int64_t cg = (pb.total + 255) / 256;
   if (cg > sm_count() * 8) cg = sm_count() * 8;
@@ -1006,14 +1010,16 @@ static void launch_solve_fix(const Prob& pb, const Ws& w, const Options& o, int 
     // each finishes every item soonest
     int64_t fg = pb.total;                            // at most one block per eigenpair
     if (fg > sm_count() * DPR1_FIX_BLOCKS_PER_SM) fg = sm_count() * DPR1_FIX_BLOCKS_PER_SM;
+    if (w.terms && fg > w.term_slots) fg = w.term_slots;   // every group with a buffer
     k_fix<DPR1_FIX_THREADS><<<fg > 0 ? (int)fg : 1, DPR1_FIX_THREADS, 0, st>>>(pb, w, o.T_Knu, o.cap, o.fast,
-                                                                                  o.dd_mode, o.T_kappa);
+                                                                                  o.dd_mode, o.T_kappa, o.screen);
   } else {
     // many small problems, many flagged items: one warp each (a block-wide group would
     // leave most of its threads idle and pay a barrier per evaluation)
     int64_t fg = (pb.total + 7) / 8;                  // at most one warp per eigenpair
     if (fg > sm_count() * 4) fg = sm_count() * 4;
-    k_fix<32><<<fg > 0 ? (int)fg : 1, 256, 0, st>>>(pb, w, o.T_Knu, o.cap, o.fast, o.dd_mode, o.T_kappa);
+    if (w.terms && fg * 8 > w.term_slots) fg = w.term_slots / 8 > 0 ? w.term_slots / 8 : 1;
+    k_fix<32><<<fg > 0 ? (int)fg : 1, 256, 0, st>>>(pb, w, o.T_Knu, o.cap, o.fast, o.dd_mode, o.T_kappa, o.screen);
   }
   record(o, 2, st);
 }
@@ -1049,23 +1055,19 @@ static dpr1_status run_table(const Prob& pb, void* workspace, size_t wbytes, con
   int64_t want_blocks = (pb.total + groups_per_block - 1) / groups_per_block;
   int grid = sms * o.bps;
   if (want_blocks < grid) grid = want_blocks > 0 ? (int)want_blocks : 1;
-  // the rest of the workspace holds the stored elements of the inverse for the solves:
-  // one buffer per lane group, as large as the bytes allow (one problem: the groups that
-  // fit a buffer of its order)
+  // the rest of the workspace holds the stored elements of the inverse for the solves: one
+  // buffer for every lane group of the launch (for one problem, of its order), or none at all.
+  // Every group then forms the secular sums the same way, so the results do not depend on
+  // which group takes which eigenvalue.
   if (wbytes > base) {
     const size_t tb = wbytes - base;
     const int64_t groups = (int64_t)grid * groups_per_block;
-    int64_t tn = (int64_t)(tb / (16u * (size_t)groups)) & ~(int64_t)31;
-    int64_t slots = groups;
-    if (pb.P == 1 && tn < pb.total) {
-      tn = (pb.total + 31) & ~(int64_t)31;
-      slots = (int64_t)(tb / (16u * (size_t)tn));
-      if (slots > groups) slots = groups;
-    }
-    if (tn >= 32 && slots > 0) {
+    int64_t tn = (int64_t)(tb / (TERM_BYTES * (size_t)groups)) & ~(int64_t)31;
+    if (pb.P == 1 && tn < pb.total) tn = (pb.total + 31) & ~(int64_t)31;
+    if (tn >= 32 && (size_t)groups * TERM_BYTES * (size_t)tn <= tb) {
       w.terms = (double*)((char*)workspace + base);
       w.term_n = tn;
-      w.term_slots = slots;
+      w.term_slots = groups;
     }
   }
   if (L == 8) launch_solve_fix<8>(pb, w, o, grid, avg_n, st);
@@ -1119,6 +1121,7 @@ void dpr1_default_options(dpr1_options* opt) {
   opt->zero_finder = 0;
   opt->dd_mode = 1;
   opt->T_kappa = 1500.0;
+  opt->screen = 1;
 }
 
 const char* dpr1_status_string(dpr1_status s) {
@@ -1220,6 +1223,7 @@ dpr1_status dpr1_workspace_stats(void* workspace, int64_t* out, dpr1_stream_t st
   out[6] = c[C_ZERO_N];
   out[7] = c[C_DEFL];
   out[8] = c[C_DD];
+  out[9] = c[C_SCREEN];
   return DPR1_OK;
 }
 

@@ -35,8 +35,9 @@ struct Ws {
   double* prho;               // [P]: rho' = 2^(2b - a) rho
   double* pzsum;              // [P]: sum_j |zeta'_j| (for K_z of Eq. (knu2))
   // elements of the inverse for the secular evaluations (k_solve, k_fix): lane group g < term_slots owns
-  // terms[2 g term_n, 2 (g + 1) term_n) (Delta_j, then zz_j / Delta_j) and uses it for
-  // problems of order <= term_n; nullptr: every evaluation forms them from dr and zz
+  // TERM_BYTES term_n bytes at terms + 3 g term_n and uses them for problems of order n <= term_n:
+  // n doubles Delta_j, n doubles zz_j / Delta_j, then their binary32 copies (n floats each);
+  // nullptr: every evaluation forms them from dr and zz
   double* terms;
   int64_t term_n;
   int64_t term_slots;
@@ -49,12 +50,13 @@ struct Options {
   bool fast;   // accelerated solve instead of bisection
   int dd_mode;       // corner b: 1 double-double when kappa_nu > T_kappa n, 2 always
   double T_kappa;
+  bool screen;       // binary32 screen of the bisection steps (same results)
 };
 
 // hdr counters (Ws::counters index)
 enum : int {
   C_FIX_N = 1, C_FIX_Q = 2, C_ZERO_N = 3, C_EVAL_SOLVE = 4, C_EVAL_FIX = 5,
-  C_R2 = 6, C_R1 = 7, C_SOLVED = 8, C_DEFL = 9, C_DD = 10
+  C_R2 = 6, C_R1 = 7, C_SOLVED = 8, C_DEFL = 9, C_DD = 10, C_SCREEN = 11
 };
 
 // per-problem bits (Ws::pst)
@@ -64,6 +66,10 @@ enum : unsigned {
   PT_ZERO_POLE = 4u,   // some d_j == 0 (the near-zero recompute is then skipped, Eq. (gamma))
   PT_RANGE = 8u,       // rho' outside the normal range: skipped (solved as rho = 0) and reported
 };
+
+// bytes per element of a lane group's buffer: Delta_j, zz_j / Delta_j (binary64) and their
+// binary32 copies (the screen's)
+constexpr size_t TERM_BYTES = 24;
 
 size_t ws_layout(int64_t n, Ws* w, char* base);
 size_t term_bytes(int64_t total, int64_t nprob);

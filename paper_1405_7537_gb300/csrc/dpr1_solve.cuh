@@ -154,6 +154,61 @@ __device__ __forceinline__ double stored_sum(const double* __restrict__ Ds, cons
   return s;
 }
 
+// Binary32 screen of a bisection step.  From the binary32 copies Df_j = fl32(Delta_j) and
+// uf_j = fl32(u_j) and vf = fl32(nu) each lane forms t = fl(1 - vf Df) (one fma),
+// a = fl(uf rcp(t)) and sums the a_j with Sum2 (TwoSum, Ogita-Rump-Oishi 2005); with the
+// exact product p = vf Df and the exact term T_j = u_j / (1 - nu Delta_j),
+//   |t - (1 - nu Delta_j)| <= 2^-24 |t| + 2.01 2^-24 |p|,
+// so for rho = 2^-24 (1.01 + 2.02 |p| / |t|) <= 1/4 the relative error of a_j is at most
+// 2^-24 + 2^-24 + 2^-22 (the two roundings and the reciprocal) + 2.5 rho, and
+//   |a_j - T_j| <= e_j = |a_j| (19 + 6 |p r|) 2^-24  (r = rcp(t), ratio |p/t| <= 1.01 |p r|).
+// The returned bound E = 1.25 sum_j e_j (the 1.25 covers the roundings of the bound itself,
+// of Sum2 and of the reduction) + 8 n 2^-126 (terms below the binary32 normal range) holds
+// for |S - sum_j T_j|, and A = 1.02 sum_j e_j / 19 + E >= sum_j |T_j|; the copies and nu must
+// lie in the ranges checked by store_elem and here (|nu| in [2^-60, 2^60], so |p| <= 2^100 and
+// no a_j overflows unseen).  Returns false when the screen does not apply (a range, or a
+// non-finite sum or bound).
+template <int L>
+__device__ __forceinline__ bool screen_sum(const float* __restrict__ Df, const float* __restrict__ uf, int n,
+                                           double nu, int lane, unsigned gm, double* S, double* E, double* A) {
+  const float vf = __double2float_rn(nu);
+  const float av = fabsf(vf);
+  float sh = 0.0f, sl = 0.0f, e = 0.0f;
+  for (int j = lane; j < n; j += L) {
+    const float D = Df[j], u = uf[j];
+    const float t = __fmaf_rn(-vf, D, 1.0f);
+    const float r = rcp_approx_f32(t);
+    const float a = __fmul_rn(u, r);
+    const float w = fabsf(__fmul_rn(__fmul_rn(vf, D), r));
+    const float sn = __fadd_rn(sh, a);
+    const float bb = __fsub_rn(sn, sh);
+    sl = __fadd_rn(sl, __fadd_rn(__fsub_rn(sh, __fsub_rn(sn, bb)), __fsub_rn(a, bb)));
+    sh = sn;
+    e = __fmaf_rn(fabsf(a), __fmaf_rn(6.0f, w, 19.0f), e);
+  }
+  const double sum = group_sum<L>(__dadd_rn((double)sh, (double)sl), gm);
+  const double es = group_sum<L>((double)e, gm);
+  *S = sum;
+  *E = 1.25 * 0x1p-24 * es + 8.0 * (double)n * 0x1p-126;
+  *A = (1.02 / 19.0) * es + *E;
+  return av >= 0x1p-60f && av <= 0x1p60f && isfinite(sum) && isfinite(es);
+}
+
+// Stores the elements of the inverse at j: Delta_j and u_j = zz_j / Delta_j, and with Df their
+// binary32 copies.  Returns false when a copy is not a normal binary32 number in the screen's
+// range (|Delta| in [2^-80, 2^40), |u| in [2^-80, 2^60), or zero), which turns the screen off.
+__device__ __forceinline__ bool store_elem(double* __restrict__ Ds, double* __restrict__ us, float* __restrict__ Df,
+                                           float* __restrict__ uf, int j, double D, double u) {
+  Ds[j] = D;
+  us[j] = u;
+  if (!Df) return true;
+  Df[j] = __double2float_rn(D);
+  uf[j] = __double2float_rn(u);
+  const unsigned eD = (unsigned)(__double_as_longlong(D) >> 52) & 0x7ffu;
+  const unsigned eu = (unsigned)(__double_as_longlong(u) >> 52) & 0x7ffu;
+  return (D == 0.0 || (eD >= 943u && eD <= 1062u)) && (u == 0.0 || (eu >= 943u && eu <= 1082u));
+}
+
 // The sum and its derivative dS/dnu = sum_j zz_j / t_j^2 = sum_j (u_j / t_j)(Delta_j / t_j) from
 // the stored elements (the accelerated solve): one reciprocal of t_j per term, 8 binary64
 // instructions against 10 when Delta_j and Delta_j t_j are formed at every evaluation.
@@ -275,9 +330,20 @@ __device__ __forceinline__ dd dd_pole_sum(const double* __restrict__ d, const do
 // sums are identical in every lane).  Returns nu with the smaller |phi| of the final
 // adjacent pair; *ok = false if the cap was reached.
 // ---------------------------------------------------------------------------------
-template <class Phi>
+// No screen: every step evaluates phi.
+struct NoScreen {
+  __device__ bool operator()(double, double*) const { return false; }
+};
+
+// screen(nu, &g) may settle a step without phi: it returns true with g of the sign phi(nu)
+// would have (the bisection then takes the same decision).  Once it fails, the remaining steps
+// (closer to the root) use phi only; an end whose value came from the screen is evaluated by phi
+// before the final choice, so the result is the one of phi alone.  *screened counts the steps
+// the screen settled.
+template <class Phi, class Scr = NoScreen>
 __device__ double bisect(Phi phi, double side, double floor, double alo, double ahi, bool below_positive, int cap,
-                         bool* ok, int* steps_out, bool eager_lo = false, bool eager_hi = false) {
+                         bool* ok, int* steps_out, bool eager_lo = false, bool eager_hi = false, Scr screen = Scr(),
+                         int* screened = nullptr) {
   int steps = 0;
   bool good = true;
   if (!(floor >= 0.0)) floor = 0.0;
@@ -289,7 +355,9 @@ __device__ double bisect(Phi phi, double side, double floor, double alo, double 
   uint64_t span = hi - lo + 64;
   double glo = 0.0, ghi = 0.0;
   bool have_lo = false, have_hi = false;    // the end point was evaluated (its side is known)
-  int it = 0, pushes = 0;
+  bool scr_lo = false, scr_hi = false;      // its value came from the screen
+  bool scr_on = true;
+  int it = 0, pushes = 0, nscr = 0;
   // ends that come from a soft estimate (eager_*) are checked before the bisection
   if (eager_hi) {
     for (; pushes < 64; pushes++) {
@@ -317,10 +385,17 @@ __device__ double bisect(Phi phi, double side, double floor, double alo, double 
       if (phase >= cap) { good = false; break; }
       phase++;
       uint64_t mid = lo + ((hi - lo) >> 1);
-      double g = phi(side * dfrom(mid));
+      double g;
+      bool sc = false;
+      if (scr_on) {
+        sc = screen(side * dfrom(mid), &g);
+        scr_on = sc;
+      }
+      if (!sc) g = phi(side * dfrom(mid));
+      else nscr++;
       bool below = below_positive ? (g > 0.0) : (g < 0.0);
-      if (below) { lo = mid; glo = g; have_lo = true; }
-      else { hi = mid; ghi = g; have_hi = true; }
+      if (below) { lo = mid; glo = g; have_lo = true; scr_lo = sc; }
+      else { hi = mid; ghi = g; have_hi = true; scr_hi = sc; }
       it++;
     }
     if (!good) break;
@@ -332,13 +407,13 @@ __device__ double bisect(Phi phi, double side, double floor, double alo, double 
       bool below = below_positive ? (g > 0.0) : (g < 0.0);
       if (below && pushes < 64 && hi < top) {
         // the root lies beyond the estimate: push the far end out geometrically
-        lo = hi; glo = g; have_lo = true;
+        lo = hi; glo = g; have_lo = true; scr_lo = false;
         hi = (top - hi > span) ? hi + span : top;
         span *= 2;
         pushes++;
         continue;
       }
-      ghi = g; have_hi = !below;
+      ghi = g; have_hi = !below; scr_hi = false;
       if (below) { good = false; break; }
     }
     if (!have_lo && lo > fl) {
@@ -347,14 +422,18 @@ __device__ double bisect(Phi phi, double side, double floor, double alo, double 
       bool below = below_positive ? (g > 0.0) : (g < 0.0);
       if (!below) {
         // the root lies below the near estimate: fall back to the floor
-        hi = lo; ghi = g; have_hi = true; lo = fl;
+        hi = lo; ghi = g; have_hi = true; scr_hi = false; lo = fl;
         continue;
       }
-      glo = g; have_lo = true;
+      glo = g; have_lo = true; scr_lo = false;
     }
     break;
   }
+  // the final choice compares the values of phi at the two ends
+  if (have_lo && scr_lo) { glo = phi(side * dfrom(lo)); steps++; }
+  if (have_hi && scr_hi) { ghi = phi(side * dfrom(hi)); steps++; }
   steps += it;
+  if (screened) *screened = nscr;
   double alo_g = have_lo ? fabs(glo) : INFINITY;
   double ahi_g = have_hi ? fabs(ghi) : INFINITY;
   if (isnan(alo_g)) alo_g = INFINITY;
@@ -508,6 +587,7 @@ struct PoleResult {
   bool ok;
   bool dd;     // b was formed in double-double
   int steps;
+  int screened;   // bisection steps settled by the binary32 screen
 };
 
 // How the corner b is formed (Sec. 2.3): mode 1 in double the working precision when kappa_nu of
@@ -531,19 +611,21 @@ template <int L>
 __device__ __forceinline__ double corner_b(const double* __restrict__ d, const double* __restrict__ zz,
                                            const double* __restrict__ zl, int n, int i,
                                            double rho, int lane, unsigned gm, double* wn2, CornerRule cr,
-                                           bool* used_dd, double* __restrict__ Ds, double* __restrict__ us) {
+                                           bool* used_dd, double* __restrict__ Ds, double* __restrict__ us,
+                                           float* __restrict__ Df, float* __restrict__ uf, bool* scr_ok) {
   const double di = d[i];
+  bool ok = Df != nullptr;
   if (cr.mode != 2) {
     double p = 0.0, q = 0.0, s2 = 0.0;
     for (int j = lane; j < n; j += L) {
       if (j == i) {
-        if (Ds) { Ds[j] = 0.0; us[j] = 0.0; }
+        if (Ds) ok &= store_elem(Ds, us, Df, uf, j, 0.0, 0.0);
         continue;
       }
       const double D = __dsub_rn(d[j], di);
       const double r = rcp(D);
       const double t = __dmul_rn(zz[j], r);
-      if (Ds) { Ds[j] = D; us[j] = t; }
+      if (Ds) ok &= store_elem(Ds, us, Df, uf, j, D, t);
       if (j < i) p = __dadd_rn(p, t);
       else q = __dadd_rn(q, t);
       s2 = __fma_rn(t, r, s2);
@@ -555,18 +637,21 @@ __device__ __forceinline__ double corner_b(const double* __restrict__ d, const d
     const double zi = sqrt(zz[i]);
     const double Kz = (cr.zsum - zi) / zi;
     const double kappa = fmin((nn + 4.0) * sn * Kb, 3.0 * sn + (nn + 4.0) * (1.0 + 2.0 * Kz));
+    *scr_ok = !group_any<L>(!ok, gm);
     if (kappa <= cr.T_kappa * nn) {
       *used_dd = false;
       return (1.0 / zz[i]) * ((1.0 / rho + P) + N);
     }
   }
   *used_dd = true;
-  if (cr.mode == 2 && Ds) {
-    for (int j = lane; j < n; j += L) {
-      const double D = (j == i) ? 0.0 : __dsub_rn(d[j], di);
-      Ds[j] = D;
-      us[j] = (j == i) ? 0.0 : __dmul_rn(zz[j], rcp(D));
+  if (cr.mode == 2) {
+    if (Ds) {
+      for (int j = lane; j < n; j += L) {
+        const double D = (j == i) ? 0.0 : __dsub_rn(d[j], di);
+        ok &= store_elem(Ds, us, Df, uf, j, D, (j == i) ? 0.0 : __dmul_rn(zz[j], rcp(D)));
+      }
     }
+    *scr_ok = !group_any<L>(!ok, gm);
   }
   double sq;
   dd acc = dd_pole_sum<L>(d, zz, zl, n, i, di, lane, gm, &sq);
@@ -583,11 +668,16 @@ template <int L>
 __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __restrict__ zl,
                                  const double* __restrict__ zz, int n, double rho, int k, int i, double alo,
                                  double ahi, int cap, bool fast, int lane, unsigned gm, CornerRule cr,
-                                 double* __restrict__ Ds = nullptr, double* __restrict__ us = nullptr) {
+                                 double* __restrict__ Ds = nullptr, double* __restrict__ us = nullptr,
+                                 bool screen = false) {
   PoleResult r;
+  r.screened = 0;
   double wn2;
-  bool used_dd;
-  double b = corner_b<L>(d, zz, zl, n, i, rho, lane, gm, &wn2, cr, &used_dd, Ds, us);
+  bool used_dd, scr_ok = false;
+  // the binary32 copies follow the two binary64 arrays (us = Ds + n)
+  float* const Df = (Ds && screen && !fast) ? (float*)(us + n) : nullptr;
+  float* const uf = Df ? Df + n : nullptr;
+  double b = corner_b<L>(d, zz, zl, n, i, rho, lane, gm, &wn2, cr, &used_dd, Ds, us, Df, uf, &scr_ok);
   double side = (i == k) ? 1.0 : -1.0;
   double di = d[i];
   double inv_zi2 = 1.0 / zz[i];
@@ -656,9 +746,26 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
       double S = elem_sum<L>(Ds, us, d, zz, n, i, di, v, lane, gm);
       return __dsub_rn(__dsub_rn(b, v), __dmul_rn(S, inv_zi2));
     };
+    // The screen settles a step when its g = fl(fl(b - v) - fl(S32 inv_zi2)) exceeds every
+    // way the decision could differ from phi's: |S32 - S| <= E32 (screen_sum), |S64 - S| <= E64
+    // for phi's binary64 sum (at most (m + 64) 2^-52 of sum_j |T_j| <= A, m = ceil(n / L) terms
+    // per lane: twice the count of its roundings), and the roundings of the two products.
+    // fl(x - y) has the sign of x - y, so phi's sign then equals the sign of g.
+    const double mlane = (double)((n + L - 1) / L);
+    auto scr = [&](double v, double* g) -> bool {
+      if (!scr_ok) return false;
+      double S32, E32, aS;
+      if (!screen_sum<L>(Df, uf, n, v, lane, gm, &S32, &E32, &aS)) return false;
+      const double E64 = (mlane + 64.0) * 0x1p-52 * aS;
+      const double tol = 1.01 * inv_zi2 * (E32 + E64 + 0x1p-51 * aS);
+      const double G = __dsub_rn(__dsub_rn(b, v), __dmul_rn(S32, inv_zi2));
+      if (!(fabs(G) > tol)) return false;
+      *g = G;
+      return true;
+    };
     // g(nu) > 0 below the root for the rightmost; for the leftmost, |nu| below the root
     // means nu above it, where g < 0.
-    nu = bisect(phi, side, floor, alo, ahi, side > 0, cap, &ok, &steps, eager_lo, eager_hi);
+    nu = bisect(phi, side, floor, alo, ahi, side > 0, cap, &ok, &steps, eager_lo, eager_hi, scr, &r.screened);
   }
   r.nu = nu;
   r.mu = 1.0 / nu;

@@ -1,0 +1,105 @@
+"""The binary32 screen of the bisection steps changes no result.
+
+A step is settled in binary32 only when the sign of the secular function there is certain
+from a rigorous error bound, and is then the sign the binary64 evaluation gives; the ends
+of the final bracket are evaluated in binary64.  So with the screen on (the default) and
+off, every eigenvalue, shift pair and eigenvector component must be the same bits, on
+every workload kind, while the screen settles part of the steps where brackets are wide."""
+import numpy as np
+import pytest
+
+from paper_1405_7537_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1405_7537_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def cu(x):
+    return torch.tensor(np.array(x, dtype=np.float64, copy=True), device="cuda")
+
+
+def solve(B, d, z, rho, screen, **opt):
+    n = d.size
+    # twice the default size: buffers for every lane group under any of the launch shapes used
+    ws = torch.empty(2 * B.workspace_size(n), dtype=torch.uint8, device="cuda")
+    r = B.eig(cu(d), cu(z), rho, options=B.default_options(screen=screen, **opt), ws=ws)
+    st = B.workspace_stats(ws)
+    return {k: v.cpu().numpy() for k, v in r.items() if v is not None}, st
+
+
+def same_bits(a, b):
+    for k in ("lam", "sigma", "mu", "xnorm", "Vt"):
+        assert np.array_equal(a[k].view(np.int64), b[k].view(np.int64)), k
+
+
+@pytest.mark.parametrize("case", ["uniform2048", "hard4096", "diff4096", "graded300", "lanes16", "lanes8",
+                                  "always_dd"])
+def test_screen_changes_no_bit(B, case):
+    opt = {}
+    if case == "uniform2048":
+        d, z, rho = W.uniform(2048, 21)
+    elif case == "hard4096":
+        d, z, rho = W.hard(4096, 22)
+    elif case == "diff4096":
+        d, z, rho = W.diff(4096, 2)[:3]
+    elif case == "graded300":
+        n = 300
+        d = np.sort(10.0 ** -np.linspace(0, 14, n))[::-1].copy()
+        z = np.sqrt(d) * np.random.default_rng(23).uniform(0.5, 1.0, n)
+        rho = 1e-6
+    elif case == "lanes16":
+        d, z, rho = W.uniform(700, 24)
+        opt = dict(lanes=16)
+    elif case == "lanes8":
+        d, z, rho = W.uniform(300, 25)
+        opt = dict(lanes=8)
+    else:
+        d, z, rho = W.hard(1500, 26)
+        opt = dict(dd_mode=2)
+    on, st_on = solve(B, d, z, rho, 1, **opt)
+    off, st_off = solve(B, d, z, rho, 0, **opt)
+    same_bits(on, off)
+    assert st_off["screened"] == 0
+    assert (st_on["r1"], st_on["r2"], st_on["flagged"]) == (st_off["r1"], st_off["r2"], st_off["flagged"])
+    # binary64 evaluations with the screen: all steps less the settled ones (plus at most two
+    # end re-evaluations per solve)
+    if case in ("uniform2048", "diff4096"):
+        assert st_on["screened"] > 0.15 * st_off["evals_solve"], (st_on, st_off)
+        assert st_on["evals_solve"] - st_on["screened"] < 0.9 * st_off["evals_solve"], (st_on, st_off)
+
+
+def test_screen_in_a_batch(B):
+    offs, d, z, rho = W.batch(P=48, seed=27, nmin=16, nmax=600)
+    sizes = np.diff(offs)
+    res = []
+    for screen in (1, 0):
+        bt = B.Batch(sizes)
+        bt.solve(cu(d), cu(z), cu(rho), options=B.default_options(screen=screen), check=True)
+        torch.cuda.synchronize()
+        res.append((bt.lam.cpu().numpy(), bt.Vt.cpu().numpy()))
+    assert np.array_equal(res[0][0].view(np.int64), res[1][0].view(np.int64))
+    assert np.array_equal(res[0][1].view(np.int64), res[1][1].view(np.int64))
+
+
+@pytest.mark.parametrize("lanes,bps", [(8, 2), (16, 1), (32, 3), (0, 4)])
+def test_repeatable_under_launch_shapes(B, lanes, bps):
+    """Every lane group of a launch has a buffer of stored elements or none does, so which
+    group takes which eigenvalue (a work counter decides) never changes a result: two runs
+    give the same bits, with the default workspace and launch shapes it was not sized for."""
+    d, z, rho = W.hard(1200, 28)
+    runs = [solve_default(B, d, z, rho, lanes=lanes, blocks_per_sm=bps) for _ in range(2)]
+    same_bits(runs[0], runs[1])
+
+
+def solve_default(B, d, z, rho, **opt):
+    r = B.eig(cu(d), cu(z), rho, options=B.default_options(**opt))
+    return {k: v.cpu().numpy() for k, v in r.items() if v is not None}
