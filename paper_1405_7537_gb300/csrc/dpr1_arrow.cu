@@ -60,7 +60,7 @@ struct ArrowWs {
   double* ds;                    // d' = 2^-a d and z' = 2^-a z (normalised copies)
   double* zs;
   double* scal;                  // [0]: alpha' = 2^-a alpha; [1]: a (as a double)
-  // elements of the inverse for the solves, laid out as Ws::terms (the binary32 copies unused)
+  // elements of the inverse for the solves and their binary32 copies, laid out as Ws::terms
   double* terms;
   int64_t term_n;
   int64_t term_slots;
@@ -163,12 +163,18 @@ template <int L>
 __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const double* __restrict__ zl,
                                        const double* __restrict__ zz, int n, double alpha, int k, int i, double alo,
                                        double ahi, int cap, bool fast, int lane, unsigned gm,
-                                       double* __restrict__ Ds = nullptr, double* __restrict__ us = nullptr) {
+                                       double* __restrict__ Ds = nullptr, double* __restrict__ us = nullptr,
+                                       bool screen = false) {
   PoleResult r;
+  r.screened = 0;
   double sq;
   const double di = d[i];
-  // the corner's pass also stores the elements of the inverse when the group has a buffer
-  dd acc = dd_pole_sum<L>(d, zz, zl, n, i, di, lane, gm, &sq, nullptr, Ds, us);
+  // the corner's pass also stores the elements of the inverse when the group has a buffer (and
+  // their binary32 copies for the screen, after the two binary64 arrays: us = Ds + n)
+  float* const Df = (Ds && screen && !fast) ? (float*)(us + n) : nullptr;
+  float* const uf = Df ? Df + n : nullptr;
+  bool scr_ok = false;
+  dd acc = dd_pole_sum<L>(d, zz, zl, n, i, di, lane, gm, &sq, nullptr, Ds, us, Df, uf, &scr_ok);
   dd B = dd_add(two_sum(di, -alpha), acc);
   const dd Zi = {zz[i], zl[i]};
   const double b = dd_to_double(dd_div(B, Zi));
@@ -231,8 +237,23 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
       const double S = elem_sum<L>(Ds, us, d, zz, n, i, di, v, lane, gm);
       return __dadd_rn(__dsub_rn(__dsub_rn(b, v), __dmul_rn(S, inv)), inv / v);
     };
+    // binary32 screen as in solve_pole; the extra pole's term fl(inv / v) is the same in both
+    // evaluations, and the bound also covers the rounding of the intermediate difference X
+    const double mlane = (double)((n + L - 1) / L);
+    auto scr = [&](double v, double* g) -> bool {
+      if (!scr_ok) return false;
+      double S32, E32, aS;
+      if (!screen_sum<L>(Df, uf, n, v, lane, gm, &S32, &E32, &aS)) return false;
+      const double E64 = (mlane + 64.0) * 0x1p-52 * aS;
+      const double X = __dsub_rn(__dsub_rn(b, v), __dmul_rn(S32, inv));
+      const double G = __dadd_rn(X, inv / v);
+      const double tol = 1.01 * (inv * (E32 + E64 + 0x1p-51 * aS) + 0x1p-51 * fabs(X));
+      if (!(fabs(G) > tol)) return false;
+      *g = G;
+      return true;
+    };
     // g > 0 below the root for the rightmost eigenvalue, g < 0 for the leftmost
-    nu = bisect(phi, side, floor, alo, ahi, side > 0, cap, &ok, &steps, eager_lo, eager_hi);
+    nu = bisect(phi, side, floor, alo, ahi, side > 0, cap, &ok, &steps, eager_lo, eager_hi, scr, &r.screened);
   }
   r.nu = nu;
   r.mu = 1.0 / nu;
@@ -247,7 +268,7 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
 template <int L>
 __global__ void __launch_bounds__(256) k_arrow_solve(int n, const double* __restrict__ d,
                                                      const double* __restrict__ z, ArrowWs w, int cap,
-                                                     bool fast) {
+                                                     bool fast, bool screen) {
   if (*w.status & ST_FATAL_A) return;
   const double alpha = w.scal[0];       // d, z and alpha are the normalised copies
   const int lane = threadIdx.x & (L - 1);
@@ -303,8 +324,9 @@ __global__ void __launch_bounds__(256) k_arrow_solve(int n, const double* __rest
       if (!(ahi > alo)) ahi = INFINITY;
     }
     PoleResult pr = solve_pole_arrow<L>(d, w.zl, zz, n, alpha, k, i, alo, ahi, cap, fast, lane, gm, Dbuf,
-                                        Dbuf ? Dbuf + n : nullptr);
+                                        Dbuf ? Dbuf + n : nullptr, screen);
     if (lane == 0) {
+      if (pr.screened) atomicAdd(&w.counters[C_SCREEN], (unsigned)pr.screened);
       w.sig[k] = d[i];
       w.mu[k] = pr.mu;
       w.shift[k] = i;
@@ -430,7 +452,7 @@ __global__ void k_arrow_classify(int n, const double* __restrict__ d, ArrowWs w,
 //       interval's poles (at most 3 solves), as for D + rho z z^T.
 template <int L>
 __global__ void __launch_bounds__(L > 256 ? L : 256) k_arrow_fix(int n, const double* __restrict__ d, ArrowWs w,
-                                                                   double T_Knu, int cap, bool fast) {
+                                                                   double T_Knu, int cap, bool fast, bool screen) {
   if (*w.status & ST_FATAL_A) return;
   const double alpha = w.scal[0];
   const int nfix = (int)w.counters[C_FIX_N];
@@ -467,9 +489,10 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_arrow_fix(int n, const do
     // R1 only when it will be taken (as for D + rho z z^T)
     if (o >= 0 && o < n && K2 < K && K2 <= T_Knu && ratio <= T_Knu) {
       const PoleResult pr = solve_pole_arrow<L>(d, w.zl, w.zz, n, alpha, k, o, 0.0, INFINITY, cap, fast, lane, gm,
-                                                Ds, us);
+                                                Ds, us, screen);
       if (!pr.ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
       if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)pr.steps);
+      if (lane == 0 && pr.screened) atomicAdd(&w.counters[C_SCREEN], (unsigned)pr.screened);
       new_sig = d[o]; new_mu = pr.mu; new_shift = o; done = true;
     }
     if (!done) {
@@ -693,7 +716,7 @@ static void launch_arrow(int n, const double* d, const double* z, ArrowWs* w, co
       w->term_slots = need;
     }
   }
-  k_arrow_solve<L><<<grid, 32 * o.warps, 0, st>>>(n, d, z, *w, o.cap, o.fast);
+  k_arrow_solve<L><<<grid, 32 * o.warps, 0, st>>>(n, d, z, *w, o.cap, o.fast, o.screen);
 }
 
 }  // namespace dpr1
@@ -746,7 +769,7 @@ dpr1_status dpr1_arrow_eig(int64_t n, const double* d, const double* z, double a
   // one block-wide group per flagged eigenvalue: they are few (a few percent on graded or
   // clustered spectra) and each solve spans all n poles
   const int fg = (int)(n + 1 < (int64_t)sms * AH_FIX_BLOCKS_PER_SM ? n + 1 : (int64_t)sms * AH_FIX_BLOCKS_PER_SM);
-  k_arrow_fix<AH_FIX_THREADS><<<fg, AH_FIX_THREADS, 0, st>>>((int)n, ds, w, o.T_Knu, o.cap, o.fast);
+  k_arrow_fix<AH_FIX_THREADS><<<fg, AH_FIX_THREADS, 0, st>>>((int)n, ds, w, o.T_Knu, o.cap, o.fast, o.screen);
   k_arrow_zero_detect<<<kg, 256, 0, st>>>((int)n, ds, w, o.T_zero);
   k_arrow_zero_solve<<<1, 128, 0, st>>>((int)n, ds, w, o.cap, o.fast);
   int64_t vg = (n + 1 + 7) / 8;

@@ -283,17 +283,21 @@ __device__ __forceinline__ double shift_sum(const double* __restrict__ d, const 
 // rounding error, and the errors and the e_q go to a second binary64 accumulator, which
 // gives the sum as accurately as accumulation in twice the working precision (Sec. 2.3).
 // With Ds != nullptr it also stores Dh = fl(d_j - s) and q = zz_j / Dh (0 and 0 at skip): the
-// elements of the inverse that stored_sum reads.
+// elements of the inverse that stored_sum reads; with Df their binary32 copies (store_elem),
+// and *scr_ok tells whether the binary32 screen applies to them.
 template <int L>
 __device__ __forceinline__ dd dd_pole_sum(const double* __restrict__ d, const double* __restrict__ zz,
                                           const double* __restrict__ zl, int n, int skip, double s, int lane,
                                           unsigned gm, double* sq, double* cub = nullptr,
-                                          double* __restrict__ Ds = nullptr, double* __restrict__ us = nullptr) {
+                                          double* __restrict__ Ds = nullptr, double* __restrict__ us = nullptr,
+                                          float* __restrict__ Df = nullptr, float* __restrict__ uf = nullptr,
+                                          bool* scr_ok = nullptr) {
   double hi = 0.0, lo = 0.0, q2 = 0.0, c3 = 0.0;
   const double ms = -s;
+  bool ok = Df != nullptr;
   for (int j = lane; j < n; j += L) {
     if (j == skip) {
-      if (Ds) { Ds[j] = 0.0; us[j] = 0.0; }
+      if (Ds) ok &= store_elem(Ds, us, Df, uf, j, 0.0, 0.0);
       continue;
     }
     const double dj = d[j];
@@ -304,7 +308,7 @@ __device__ __forceinline__ dd dd_pole_sum(const double* __restrict__ d, const do
     const double Zh = zz[j], Zl = zl[j];
     const double r = rcp(Dh);
     const double q = __dmul_rn(Zh, r);
-    if (Ds) { Ds[j] = Dh; us[j] = q; }
+    if (Ds) ok &= store_elem(Ds, us, Df, uf, j, Dh, q);
     const double eq = __dmul_rn(__dadd_rn(__fma_rn(-q, Dh, Zh), __fma_rn(-q, Dl, Zl)), r);
     const dd t = two_sum(hi, q);
     hi = t.hi;
@@ -315,6 +319,7 @@ __device__ __forceinline__ dd dd_pole_sum(const double* __restrict__ d, const do
   }
   *sq = group_sum<L>(q2, gm);
   if (cub) *cub = group_sum<L>(c3, gm);
+  if (scr_ok) *scr_ok = !group_any<L>(!ok, gm);
   return group_sum_dd<L>(two_sum(hi, lo), gm);
 }
 

@@ -103,3 +103,27 @@ def test_repeatable_under_launch_shapes(B, lanes, bps):
 def solve_default(B, d, z, rho, **opt):
     r = B.eig(cu(d), cu(z), rho, options=B.default_options(**opt))
     return {k: v.cpu().numpy() for k, v in r.items() if v is not None}
+
+
+@pytest.mark.parametrize("kind", ["uniform", "clustered"])
+def test_arrowhead_screen_changes_no_bit(B, kind):
+    """The same for the arrowhead solves (the extra pole at 0 adds a term both evaluations
+    form the same way)."""
+    if kind == "uniform":
+        d, z, alpha = W.arrowhead(1200, 29)
+    else:
+        rng = np.random.default_rng(30)
+        c = rng.uniform(-1, 1, 40)
+        d = np.sort(rng.choice(c, 240) + rng.choice([1.0, -1.0], 240) * 10.0 ** rng.uniform(-12, -3, 240))[::-1].copy()
+        z = rng.choice([1.0, -1.0], 240) * 10.0 ** rng.uniform(-12, 0, 240)
+        alpha = 1e-5
+    res, st = [], []
+    for screen in (1, 0):
+        ws = torch.empty(2 * int(B.lib().dpr1_arrow_workspace_size(d.size)), dtype=torch.uint8, device="cuda")
+        r = B.eig_arrowhead(cu(d), cu(z), alpha, options=B.default_options(screen=screen), ws=ws)
+        res.append({k: v.cpu().numpy() for k, v in r.items() if v is not None})
+        st.append(B.workspace_stats(ws))
+    same_bits(res[0], res[1])
+    assert st[1]["screened"] == 0
+    if kind == "uniform":
+        assert st[0]["screened"] > 0.1 * st[1]["evals_solve"], st
