@@ -127,3 +127,43 @@ def test_arrowhead_screen_changes_no_bit(B, kind):
     assert st[1]["screened"] == 0
     if kind == "uniform":
         assert st[0]["screened"] > 0.1 * st[1]["evals_solve"], st
+
+
+def _fuzz_problem(rng, t):
+    n = int(np.exp(rng.uniform(np.log(2), np.log(3000))))
+    kind = t % 5
+    if kind == 0:
+        d = rng.uniform(-1, 1, n); z = rng.uniform(-1, 1, n)
+    elif kind == 1:                               # graded poles, weights over twelve decades
+        d = rng.choice([1, -1], n) * 10.0 ** rng.uniform(-14, 0, n)
+        z = rng.choice([1, -1], n) * 10.0 ** rng.uniform(-12, 0, n)
+    elif kind == 2:                               # tight pole clusters
+        c = rng.uniform(-1, 1, max(1, n // 5))
+        d = rng.choice(c, n) + rng.choice([1, -1], n) * 10.0 ** rng.uniform(-13, -2, n)
+        z = rng.choice([1, -1], n) * 10.0 ** rng.uniform(-15, 0, n)
+    elif kind == 3:                               # far from 1 in magnitude
+        d = rng.uniform(-1, 1, n) * 2.0 ** rng.integers(-300, 300)
+        z = rng.uniform(-1, 1, n) * 2.0 ** rng.integers(-300, 300)
+    else:
+        d = rng.standard_normal(n); z = rng.standard_normal(n) * 1e-3
+    d = np.unique(d)[::-1].copy()
+    return d, z[:d.size]
+
+
+def test_screen_fuzz(B):
+    """60 random problems (uniform, graded, clustered, far-scaled, small-weight), every third
+    an arrowhead: the same bits with the screen on and off."""
+    rng = np.random.default_rng(2024)
+    for t in range(60):
+        d, z = _fuzz_problem(rng, t)
+        arrow = t % 3 == 0
+        rho = float(rng.uniform(-1, 1)) if arrow else float(10.0 ** rng.uniform(-6, 6))
+        out = []
+        for screen in (1, 0):
+            o = B.default_options(screen=screen)
+            if arrow:
+                r = B.eig_arrowhead(cu(d), cu(z), rho, options=o, check=False)
+            else:
+                r = B.eig(cu(d), cu(z), rho, options=o, check=False)
+            out.append({k: v.cpu().numpy() for k, v in r.items() if v is not None})
+        same_bits(out[0], out[1])
