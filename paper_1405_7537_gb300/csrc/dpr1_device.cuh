@@ -67,7 +67,8 @@ __device__ __forceinline__ double rcp_approx(double x) {
 }
 
 // binary32 approximate reciprocal (flushes subnormal inputs and results to zero); the screen
-// of the bisection allows it 2^-22 relative error
+// of the bisection refines it by one Newton step, after which any seed within 2^-14 relative
+// gives the reciprocal within 1.07 2^-24
 __device__ __forceinline__ float rcp_approx_f32(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));

@@ -155,43 +155,51 @@ __device__ __forceinline__ double stored_sum(const double* __restrict__ Ds, cons
 }
 
 // Binary32 screen of a bisection step.  From the binary32 copies Df_j = fl32(Delta_j) and
-// uf_j = fl32(u_j) and vf = fl32(nu) each lane forms t = fl(1 - vf Df) (one fma),
-// a = fl(uf rcp(t)) and sums the a_j with Sum2 (TwoSum, Ogita-Rump-Oishi 2005); with the
-// exact product p = vf Df and the exact term T_j = u_j / (1 - nu Delta_j),
-//   |t - (1 - nu Delta_j)| <= 2^-24 |t| + 2.01 2^-24 |p|,
-// so for rho = 2^-24 (1.01 + 2.02 |p| / |t|) <= 1/4 the relative error of a_j is at most
-// 2^-24 + 2^-24 + 2^-22 (the two roundings and the reciprocal) + 2.5 rho, and
-//   |a_j - T_j| <= e_j = |a_j| (19 + 6 |p r|) 2^-24  (r = rcp(t), ratio |p/t| <= 1.01 |p r|).
-// The returned bound E = 1.25 sum_j e_j (the 1.25 covers the roundings of the bound itself,
-// of Sum2 and of the reduction) + 8 n 2^-126 (terms below the binary32 normal range) holds
-// for |S - sum_j T_j|, and A = 1.02 sum_j e_j / 19 + E >= sum_j |T_j|; the copies and nu must
-// lie in the ranges checked by store_elem and here (|nu| in [2^-60, 2^60], so |p| <= 2^100 and
-// no a_j overflows unseen).  Returns false when the screen does not apply (a range, or a
-// non-finite sum or bound).
+// uf_j = fl32(u_j) and vf = fl32(nu) (each within eps = 2^-24 relative) each lane forms
+// t = fl(1 - vf Df) (one fma), r = 1/t (approximate reciprocal and one Newton step: within
+// 1.07 eps for any seed within 2^-14, 1.0001 eps for the hardware's), a = fl(uf r), and sums the
+// a_j with Sum2 (TwoSum, Ogita-Rump-Oishi 2005).
+// With p = vf Df exactly and the exact term T_j = u_j / (1 - nu Delta_j):
+//   |t - (1 - nu Delta_j)| <= eps (1.0001 |t| + 2.0002 |p|),
+// so the relative error of a_j is at most eps (4.07 + 2.0005 |p / t|) and, with w = |fl(fl(p) r)|
+// (|p / t| <= w (1 + 3.01 eps)) and Sum2's own eps per term,
+//   |a_j - T_j| + (Sum2's share) <= e_j = |a_j| (6 + 2.5 w) eps,
+// valid while w <= 2^20 (then t and 1 - nu Delta_j have one sign and the relative error
+// stays below 1/8; a lane with a larger w turns the screen off for the step).  The returned
+// bound E = 1.05 (1 + 2 (m + 2) eps) sum_j e_j + 8 n 2^-126 (m terms per lane: the roundings of
+// the bound's own sum; the last term for results below the binary32 normal range) holds for
+// |S - sum_j T_j|, and A = 1.02 sum_j e_j / (6 eps) + E >= sum_j |T_j|.  The copies and nu
+// must lie in the ranges checked by store_elem and here (|nu| in [2^-60, 2^60], so |p| <= 2^100).
+// Returns false when the screen does not apply (a range, w, or a non-finite sum or bound).
 template <int L>
 __device__ __forceinline__ bool screen_sum(const float* __restrict__ Df, const float* __restrict__ uf, int n,
                                            double nu, int lane, unsigned gm, double* S, double* E, double* A) {
   const float vf = __double2float_rn(nu);
   const float av = fabsf(vf);
   float sh = 0.0f, sl = 0.0f, e = 0.0f;
+  bool bad = !(av >= 0x1p-60f && av <= 0x1p60f);
   for (int j = lane; j < n; j += L) {
     const float D = Df[j], u = uf[j];
     const float t = __fmaf_rn(-vf, D, 1.0f);
-    const float r = rcp_approx_f32(t);
+    const float r0 = rcp_approx_f32(t);
+    const float r = __fmaf_rn(r0, __fmaf_rn(-t, r0, 1.0f), r0);
     const float a = __fmul_rn(u, r);
     const float w = fabsf(__fmul_rn(__fmul_rn(vf, D), r));
+    bad |= !(w <= 0x1p20f);
     const float sn = __fadd_rn(sh, a);
     const float bb = __fsub_rn(sn, sh);
     sl = __fadd_rn(sl, __fadd_rn(__fsub_rn(sh, __fsub_rn(sn, bb)), __fsub_rn(a, bb)));
     sh = sn;
-    e = __fmaf_rn(fabsf(a), __fmaf_rn(6.0f, w, 19.0f), e);
+    e = __fmaf_rn(fabsf(a), __fmaf_rn(2.5f, w, 6.0f), e);
   }
   const double sum = group_sum<L>(__dadd_rn((double)sh, (double)sl), gm);
   const double es = group_sum<L>((double)e, gm);
+  bad = group_any<L>(bad, gm);
+  const double m = (double)((n + L - 1) / L);
   *S = sum;
-  *E = 1.25 * 0x1p-24 * es + 8.0 * (double)n * 0x1p-126;
-  *A = (1.02 / 19.0) * es + *E;
-  return av >= 0x1p-60f && av <= 0x1p60f && isfinite(sum) && isfinite(es);
+  *E = 1.05 * (1.0 + 2.0 * (m + 2.0) * 0x1p-24) * 0x1p-24 * es + 8.0 * (double)n * 0x1p-126;
+  *A = (1.02 / 6.0) * es + *E;
+  return !bad && m * 0x1p-24 < 0.25 && isfinite(sum) && isfinite(es);
 }
 
 // Stores the elements of the inverse at j: Delta_j and u_j = zz_j / Delta_j, and with Df their
