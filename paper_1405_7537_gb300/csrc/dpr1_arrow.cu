@@ -349,15 +349,10 @@ __device__ double solve_nonpole_arrow(const double* __restrict__ d, const double
                                       const double* __restrict__ zz, int n, double alpha, double sigma, int above,
                                       int below, int cap, bool fast, int lane, unsigned gm, bool* ok,
                                       int* steps_out, double* __restrict__ Ds = nullptr,
-                                      double* __restrict__ us = nullptr, bool screen = false,
-                                      int* screened = nullptr) {
+                                      double* __restrict__ us = nullptr) {
   double un2, cub;
-  // the double-double pass also stores the elements for the solve when the group has a buffer,
-  // and their binary32 copies for the screen
-  float* const Df = (Ds && screen && !fast) ? (float*)(us + n) : nullptr;
-  float* const uf = Df ? Df + n : nullptr;
-  bool scr_ok = false;
-  const dd acc = dd_pole_sum<L>(d, zz, zl, n, -1, sigma, lane, gm, &un2, &cub, Ds, us, Df, uf, &scr_ok);
+  // the double-double pass also stores the elements for the solve when the group has a buffer
+  const dd acc = dd_pole_sum<L>(d, zz, zl, n, -1, sigma, lane, gm, &un2, &cub, Ds, us);
   const dd f = dd_add(two_sum(alpha, -sigma), {-acc.hi, -acc.lo});
   *ok = true;
   *steps_out = 0;
@@ -404,21 +399,8 @@ __device__ double solve_nonpole_arrow(const double* __restrict__ d, const double
       const double S = elem_sum<L>(Ds, us, d, zz, n, -1, sigma, v, lane, gm);
       return __fma_rn(gamma, __dsub_rn(S, 1.0 / v), 1.0);
     };
-    // binary32 screen (as in solve_pole): the bound also covers the rounding of S - 1/v
-    const double mlane = (double)((n + L - 1) / L);
-    auto scr = [&](double v, double* g) -> bool {
-      if (!scr_ok) return false;
-      double S32, E32, aS;
-      if (!screen_sum<L>(Df, uf, n, v, lane, gm, &S32, &E32, &aS)) return false;
-      const double E64 = (mlane + 64.0) * 0x1p-52 * aS;
-      const double X = __dsub_rn(S32, 1.0 / v);
-      const double G = __fma_rn(gamma, X, 1.0);
-      if (!(fabs(G) > 1.01 * fabs(gamma) * (E32 + E64 + 0x1p-51 * fabs(X)))) return false;
-      *g = G;
-      return true;
-    };
     // h < 0 between the floor and the root in both cases
-    nu = bisect(phi, side, floor, alo, ahi, false, cap, ok, &steps, false, false, scr, screened);
+    nu = bisect(phi, side, floor, alo, ahi, false, cap, ok, &steps);
   }
   *steps_out = steps;
   return 1.0 / nu;
@@ -533,12 +515,11 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_arrow_fix(int n, const do
         if (!hi_pole && sg > hi) sg = hi;
         if ((lo_pole && !(sg > lo)) || (hi_pole && !(sg < hi))) break;
         bool ok;
-        int st2, sc2 = 0;
+        int st2;
         const double m2 = solve_nonpole_arrow<L>(d, w.zl, w.zz, n, alpha, sg, k > 0 ? k - 1 : -1, k < n ? k : -1,
-                                                 cap, fast, lane, gm, &ok, &st2, Ds, us, screen, &sc2);
+                                                 cap, fast, lane, gm, &ok, &st2, Ds, us);
         if (!ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
         if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)st2);
-        if (lane == 0 && sc2) atomicAdd(&w.counters[C_SCREEN], (unsigned)sc2);
         new_sig = sg; new_mu = m2; new_shift = -1;
         // repeat while sigma is not nearer to lambda_k than to the interval's poles
         double room = INFINITY;

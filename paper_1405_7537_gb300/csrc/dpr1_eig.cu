@@ -629,12 +629,11 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double
         if (k == 0 && s > hi) s = hi;
         if (!(s > lo) || (k > 0 && !(s < hi))) break;
         bool ok;
-        int st2 = 0, sc2 = 0;
-        const double m2 = solve_nonpole<L>(d, zl, zz, n, rho, s, k > 0 ? k - 1 : -1, k, cap, fast, lane, gm, &ok,
-                                           &st2, Ds, us, screen, &sc2);
+        int st2 = 0;
+        const double m2 =
+            solve_nonpole<L>(d, zl, zz, n, rho, s, k > 0 ? k - 1 : -1, k, cap, fast, lane, gm, &ok, &st2, Ds, us);
         if (!ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
         if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)st2);
-        if (lane == 0 && sc2) atomicAdd(&w.counters[C_SCREEN], (unsigned)sc2);
         new_sig = s; new_mu = m2; new_shift = -1;
         // accurate when lambda_k is the eigenvalue nearest to sigma: every other eigenvalue lies
         // beyond the interval's poles.  Otherwise the next shift is one from which lambda_k is at

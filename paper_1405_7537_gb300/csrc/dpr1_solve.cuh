@@ -802,17 +802,12 @@ template <int L>
 __device__ double solve_nonpole(const double* __restrict__ d, const double* __restrict__ zl,
                                 const double* __restrict__ zz, int n, double rho, double sigma, int above, int below,
                                 int cap, bool fast, int lane, unsigned gm, bool* ok, int* steps_out = nullptr,
-                                double* __restrict__ Ds = nullptr, double* __restrict__ us = nullptr,
-                                bool screen = false, int* screened = nullptr) {
+                                double* __restrict__ Ds = nullptr, double* __restrict__ us = nullptr) {
   // above / below: indices of the poles next to sigma (-1: none on that side)
   double un2, cub;
   // the double-double pass also stores the elements d_j - sigma and zeta_j^2 / (d_j - sigma)
-  // for the solve when the group has a buffer (Ds, us as for solve_pole), and their binary32
-  // copies for the screen
-  float* const Df = (Ds && screen && !fast) ? (float*)(us + n) : nullptr;
-  float* const uf = Df ? Df + n : nullptr;
-  bool scr_ok = false;
-  dd acc = dd_pole_sum<L>(d, zz, zl, n, -1, sigma, lane, gm, &un2, &cub, Ds, us, Df, uf, &scr_ok);
+  // for the solve when the group has a buffer (Ds, us as for solve_pole)
+  dd acc = dd_pole_sum<L>(d, zz, zl, n, -1, sigma, lane, gm, &un2, &cub, Ds, us);
   dd f = dd_add({1.0, 0.0}, two_prod(acc.hi, rho));
   f = dd_add(f, {__dmul_rn(acc.lo, rho), 0.0});
   *ok = true;
@@ -860,20 +855,7 @@ __device__ double solve_nonpole(const double* __restrict__ d, const double* __re
       const double S = elem_sum<L>(Ds, us, d, zz, n, -1, sigma, v, lane, gm);
       return __fma_rn(gamma, S, 1.0);
     };
-    // binary32 screen (as in solve_pole): fma(gamma, S, 1) has the sign of gamma S + 1, and the
-    // two evaluations differ by |gamma| |S32 - S64| <= |gamma| (E32 + E64)
-    const double mlane = (double)((n + L - 1) / L);
-    auto scr = [&](double v, double* g) -> bool {
-      if (!scr_ok) return false;
-      double S32, E32, aS;
-      if (!screen_sum<L>(Df, uf, n, v, lane, gm, &S32, &E32, &aS)) return false;
-      const double E64 = (mlane + 64.0) * 0x1p-52 * aS;
-      const double G = __fma_rn(gamma, S32, 1.0);
-      if (!(fabs(G) > 1.01 * fabs(gamma) * (E32 + E64))) return false;
-      *g = G;
-      return true;
-    };
-    nu = bisect(phi, side, floor, alo, ahi, false, cap, ok, &steps, false, false, scr, screened);
+    nu = bisect(phi, side, floor, alo, ahi, false, cap, ok, &steps);
   }
   if (steps_out) *steps_out = steps;
   return 1.0 / nu;
