@@ -248,10 +248,8 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
       const double X = __dsub_rn(__dsub_rn(b, v), __dmul_rn(S32, inv));
       const double G = __dadd_rn(X, inv / v);
       const double tol = 1.01 * (inv * (E32 + E64 + 0x1p-51 * aS) + 0x1p-51 * fabs(X));
-      // |phi| >= |G| (1 - 2^-50) - tol: returned as g, with the sign of G
-      const double low = __dsub_rn(fabs(G) * (1.0 - 0x1p-50), tol);
-      if (!(low > 0.0)) return false;
-      *g = copysign(low, G);
+      if (!(fabs(G) > tol)) return false;
+      *g = G;
       return true;
     };
     // g > 0 below the root for the rightmost eigenvalue, g < 0 for the leftmost

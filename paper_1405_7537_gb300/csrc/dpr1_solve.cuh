@@ -349,11 +349,10 @@ struct NoScreen {
 };
 
 // screen(nu, &g) may settle a step without phi: it returns true with g of the sign phi(nu)
-// would have and |g| <= |phi(nu)| (the bisection then takes the same decision).  Once it fails,
-// the remaining steps (closer to the root) use phi only.  The final choice needs phi at an end
-// whose value came from the screen only when the other end's |phi| is not already below that
-// lower bound, so the result is the one of phi alone.  *screened counts the steps the screen
-// settled.
+// would have (the bisection then takes the same decision).  Once it fails, the remaining steps
+// (closer to the root) use phi only; an end whose value came from the screen is evaluated by phi
+// before the final choice, so the result is the one of phi alone.  *screened counts the steps
+// the screen settled.
 template <class Phi, class Scr = NoScreen>
 __device__ double bisect(Phi phi, double side, double floor, double alo, double ahi, bool below_positive, int cap,
                          bool* ok, int* steps_out, bool eager_lo = false, bool eager_hi = false, Scr screen = Scr(),
@@ -443,16 +442,9 @@ __device__ double bisect(Phi phi, double side, double floor, double alo, double 
     }
     break;
   }
-  // the final choice compares |phi| at the two ends; a screened end's |g| is a lower bound of its
-  // |phi|, which decides the comparison when the other end's |phi| lies below it
-  if (have_lo && scr_lo && have_hi && !scr_hi) {
-    if (!(fabs(ghi) < fabs(glo))) { glo = phi(side * dfrom(lo)); steps++; }
-  } else if (have_hi && scr_hi && have_lo && !scr_lo) {
-    if (!(fabs(glo) < fabs(ghi))) { ghi = phi(side * dfrom(hi)); steps++; }
-  } else {
-    if (have_lo && scr_lo) { glo = phi(side * dfrom(lo)); steps++; }
-    if (have_hi && scr_hi) { ghi = phi(side * dfrom(hi)); steps++; }
-  }
+  // the final choice compares the values of phi at the two ends
+  if (have_lo && scr_lo) { glo = phi(side * dfrom(lo)); steps++; }
+  if (have_hi && scr_hi) { ghi = phi(side * dfrom(hi)); steps++; }
   steps += it;
   if (screened) *screened = nscr;
   double alo_g = have_lo ? fabs(glo) : INFINITY;
@@ -780,10 +772,8 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
       const double E64 = (mlane + 64.0) * 0x1p-52 * aS;
       const double tol = 1.01 * inv_zi2 * (E32 + E64 + 0x1p-51 * aS);
       const double G = __dsub_rn(__dsub_rn(b, v), __dmul_rn(S32, inv_zi2));
-      // |phi| >= |G| (1 - 2^-50) - tol: returned as g, with the sign of G
-      const double low = __dsub_rn(fabs(G) * (1.0 - 0x1p-50), tol);
-      if (!(low > 0.0)) return false;
-      *g = copysign(low, G);
+      if (!(fabs(G) > tol)) return false;
+      *g = G;
       return true;
     };
     // g(nu) > 0 below the root for the rightmost; for the leftmost, |nu| below the root
