@@ -17,12 +17,14 @@ committed ncu record while the kernel sources are unchanged), that of the eigenv
 (the n^2 write of V against the measured copy rate, and its binary64 work), the CPU oracle on a bounded
 sample (all host cores, and one thread on a smaller sample), the end-to-end rate through the binding from pinned host buffers (double-buffered
 outputs), and extra measurements (--extras; --only runs one alone at size --n):
-  fwd_bwd    forward and adjoint at n = 4096 (and n = 32768 with --large)
-  batched    4096 uneven problems in one graph replay against a per-problem loop
-  accel      the same workload with the accelerated bracketed solve
-  hermitian  the complex Hermitian problem (hard spectrum with random phases)
-  tridiag    divide and conquer for a random tridiagonal matrix, n = 4096
-  arrow      the arrowhead eigenproblem, n = 16384 poles
+  small          the n = 512 forward, direct calls and a CUDA-graph replay
+  fwd_bwd        forward and adjoint at n = 4096
+  fwd_bwd_large  forward and adjoint with recompute at n = 32768 (W drawn on the device)
+  batched        4096 uneven problems in one graph replay against a per-problem loop
+  accel          the same workload with the accelerated bracketed solve
+  hermitian      the complex Hermitian problem (hard spectrum with random phases)
+  tridiag        divide and conquer for a random tridiagonal matrix, n = 4096
+  arrow          the arrowhead eigenproblem, n = 16384 poles
 ``--impl reference`` times the CPU oracle (Algorithm 1 in binary64 on the host cores) on
 bounded samples of the same workload.
 """
@@ -83,9 +85,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-vs-loop and forward+backward measurements")
-    ap.add_argument("--extras", default="fwd_bwd,batched,accel,hermitian,tridiag,arrow",
-                    help="comma list of extra measurements: fwd_bwd, batched, accel, hermitian, tridiag, arrow")
-    ap.add_argument("--large", action="store_true", help="also time the n=32768 forward+backward workload")
+    ap.add_argument("--extras", default="small,fwd_bwd,fwd_bwd_large,batched,accel,hermitian,tridiag,arrow",
+                    help="comma list of extra measurements: small, fwd_bwd, fwd_bwd_large, batched, accel, "
+                         "hermitian, tridiag, arrow")
     ap.add_argument("--only", choices=["tridiag", "hermitian", "fwd_bwd", "arrow"], default=None,
                     help="run one extra measurement alone at size --n (a small case for profiling) and print it")
     ap.add_argument("--zero-finder", type=int, choices=[0, 1], default=0,
@@ -167,7 +169,9 @@ def run_reference(args):
         return 0
     from paper_1405_7537_gb300 import workloads as W
     d, z, rho = W.hard(args.n, SEED)
-    per_step = 48
+    # a sample large enough that thread start-up on the host cores is negligible (about a third of
+    # a second of oracle work per step on 16 cores)
+    per_step = 2048
     for _ in range(args.warmup):
         cpu_oracle_rate(d, z, rho, per_step, seed=99)
     times = []
@@ -309,14 +313,19 @@ def bench_fwd_bwd(B, dev, n, seed, steps, with_w):
     from paper_1405_7537_gb300 import workloads as W
     if with_w:
         d, z, rho, w, Wm = W.diff(n, seed)
+        gVt = torch.tensor(Wm.T.copy(), device=dev)        # dL/dVt = W^T for V[:, k] = v_k
+        del Wm
     else:
-        d, z, rho, Wm = W.large(n, seed)
+        # n = 32768: W ~ N(0, 1) (8.6 GB) is drawn on the device from a seeded generator; the
+        # backward reads it once like any dL/dVt
+        d, z, rho, _ = W.large(n, seed, with_W=False)
         w = None
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(seed)
+        gVt = torch.randn((n, n), dtype=torch.float64, device=dev, generator=gen)
     dt = torch.tensor(np.array(d), device=dev)
     zt = torch.tensor(np.array(z), device=dev)
     wt = torch.tensor(w, device=dev) if w is not None else None
-    gVt = torch.tensor(Wm.T.copy(), device=dev)            # dL/dVt = W^T for V[:, k] = v_k
-    del Wm
     ws = B.workspace(n, dev)
     bws = B.backward_workspace(n, dev)
     out = B.eig(dt, zt, rho, ws=ws)
@@ -336,9 +345,67 @@ def bench_fwd_bwd(B, dev, n, seed, steps, with_w):
         fw.append(e0.elapsed_time(e1))
         bw.append(e2.elapsed_time(e3))
     f, b = statistics.mean(fw), statistics.mean(bw)
+    del gVt
     return {"n": n, "seed": seed, "fwd_ms": f, "bwd_ms": b, "fwd_plus_bwd_over_fwd": (f + b) / f,
-            "loss": ("w . lambda + " if with_w else "") + "sum W o V, W ~ N(0,1)",
+            "value": n / ((f + b) * 1e-3), "unit": "eigenpairs/s (forward + backward)", "steps": max(1, steps),
+            "loss": ("w . lambda + " if with_w else "") + "sum W o V, W ~ N(0,1)"
+                    + ("" if with_w else " (drawn on the device, torch generator seed %d)" % seed),
             "note": "the backward recomputes the eigenvector columns from (sigma, mu); V is not saved"}
+
+
+def bench_small(B, dev, steps):
+    """The n = 512 forward (d, z ~ U(-1, 1), rho = 1, seed 0; eigenvalues and V): back-to-back
+    dpr1_eig calls, and the same call captured once in a CUDA graph and replayed.  At this size a
+    call is a dozen short launches, so the graph shows what launch overhead costs."""
+    import torch
+    from paper_1405_7537_gb300 import workloads as W
+    d, z, rho = W.uniform(512, 0)
+    n = d.size
+    dt = torch.tensor(d, device=dev)
+    zt = torch.tensor(z, device=dev)
+    ws = B.workspace(n, dev)
+    out = B.eig(dt, zt, rho, ws=ws)
+    torch.cuda.synchronize()
+    reps = 200
+    res = {"workload": "n=512, d, z ~ U(-1,1) (|z| > 1e-3), rho = 1, seed 0; eigenvalues and V", "n": n,
+           "unit": "eigenpairs/s", "calls_per_step": reps}
+    ms = []
+    for _ in range(max(1, steps)):
+        e0, e1 = _events()
+        e0.record()
+        for _ in range(reps):
+            B.eig(dt, zt, rho, ws=ws, out=out, check=False)
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1) / reps)
+    t = statistics.mean(ms)
+    res["direct"] = {"value": n / (t * 1e-3), "ms_per_call": t}
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        B.eig(dt, zt, rho, ws=ws, out=out, check=False)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        B.eig(dt, zt, rho, ws=ws, out=out, check=False)
+    g.replay()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(max(1, steps)):
+        e0, e1 = _events()
+        e0.record()
+        for _ in range(reps):
+            g.replay()
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1) / reps)
+    st = B.stream_status(ws)
+    if st != 0:
+        raise B.DPR1Error(st, "small")
+    t = statistics.mean(ms)
+    res["graph"] = {"value": n / (t * 1e-3), "ms_per_call": t}
+    return res
 
 
 def bench_accel(B, dev, d, z, rho, ws, out, flush, steps, bisection_ms):
@@ -749,10 +816,12 @@ def run_ours(args):
 
     extras = {}
     which = set() if args.no_extras else set(x.strip() for x in args.extras.split(",") if x.strip())
+    if "small" in which:
+        extras["small"] = bench_small(B, dev, 3)
     if "fwd_bwd" in which:
         extras["fwd_bwd"] = bench_fwd_bwd(B, dev, 4096, 2, 3, True)
-        if args.large:
-            extras["fwd_bwd_large"] = bench_fwd_bwd(B, dev, 32768, 4, 1, False)
+    if "fwd_bwd_large" in which:
+        extras["fwd_bwd_large"] = bench_fwd_bwd(B, dev, 32768, 4, 2, False)
     if "batched" in which:
         extras["batched"] = bench_batched(B, dev, 2)
     if "arrow" in which:

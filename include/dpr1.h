@@ -85,7 +85,11 @@ typedef struct {
   int lanes;             /* threads per eigenvalue in the solve kernels: 0 = auto, else 8, 16 or 32 */
   int warps_per_block;   /* 0 = auto */
   int blocks_per_sm;     /* 0 = auto */
-  int max_bisect;        /* iteration cap per bisection (default 96; >= 64 needed in general) */
+  int max_bisect;        /* iteration cap per bisection (default 96; 1..4096 accepted, other values
+                            give the default).  A bisection phase that reaches it stops and the
+                            call reports DPR1_ERR_NOT_CONVERGED; bisection to adjacent doubles
+                            needs up to 64 steps, so caps below 64 serve to test that path.  The
+                            accelerated solve may take cap + cap/3 evaluations. */
   void* const* phase_events; /* instrumentation: NULL, or 4 cudaEvent_t recorded on `stream`
                                 before the bisection kernel, after it, after the remedies and
                                 after the eigenvector kernel */
@@ -338,8 +342,12 @@ DPR1_API dpr1_status dpr1_stream_status(void* workspace, dpr1_stream_t stream);
  *                 reported); non-zero: synchronise `stream` at the end and return the
  *                 device-detected status as dpr1_stream_status would
  *
- * The first call on a device looks up the device address of the static array (with
- * that device current); make that first call before any stream capture.  All calls
+ * The first call in each CUDA context of a device looks up the device address of the
+ * static array (with that device current) and caches it under the context's unique ID;
+ * make that first call before any stream capture.  If the context is destroyed and
+ * rebuilt (cudaDeviceReset by the caller or by another library), the array's address
+ * may change: the next call notices the new context and looks it up again, so a reset
+ * invalidates nothing the caller holds for this entry point.  All calls
  * share the one array and it keeps the last call's contents (the call clears what must
  * start at zero).  Calls that overlap on the GPU -- on different streams or from
  * host threads without ordering -- race on it and give wrong results.

@@ -983,7 +983,7 @@ Options resolve(const dpr1_options* o) {
   r.lanes = (s->lanes == 8 || s->lanes == 16 || s->lanes == 32) ? s->lanes : 0;
   r.warps = s->warps_per_block > 0 && s->warps_per_block <= 8 ? s->warps_per_block : 8;
   r.bps = s->blocks_per_sm > 0 && s->blocks_per_sm <= 8 ? s->blocks_per_sm : 2;
-  r.cap = s->max_bisect >= 64 && s->max_bisect <= 4096 ? s->max_bisect : def.max_bisect;
+  r.cap = s->max_bisect >= 1 && s->max_bisect <= 4096 ? s->max_bisect : def.max_bisect;
   r.events = s->phase_events;
   r.fast = s->zero_finder == 1;
   r.dd_mode = (s->dd_mode == 2) ? 2 : 1;

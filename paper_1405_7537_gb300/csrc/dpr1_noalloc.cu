@@ -13,6 +13,7 @@
 // start of each call.  Two calls whose work overlaps on the GPU (different streams, or
 // different host threads without ordering) race on the shared array and give wrong
 // results: order them on one stream.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -35,23 +36,63 @@ constexpr size_t NOALLOC_WS_BYTES = 640u * 1024u;
 
 static __device__ __align__(256) unsigned char g_noalloc_ws[NOALLOC_WS_BYTES];
 
-// Device address of g_noalloc_ws, looked up once per device with that device current.
-// In host code the name g_noalloc_ws is only a host-side stand-in for the symbol.
+// Device address of g_noalloc_ws.  In host code the name g_noalloc_ws is only a host-side
+// stand-in for the symbol; its device address is looked up with cudaGetSymbolAddress, with the
+// device current, at the first call in each CUDA context of a device, and cached under that
+// context's unique ID (cuCtxGetId, reached through the runtime's driver entry points so the
+// library needs no link against the driver).  A context that is destroyed and rebuilt (for
+// example after cudaDeviceReset by the caller or another library) reloads the module, and the
+// array may then sit at another address: the new context has a new ID, so the next call looks
+// the address up again instead of using a stale one.  Where the context ID cannot be read, the
+// address is looked up at every call.
+typedef CUresult (*ctx_get_current_fn)(CUcontext*);
+typedef CUresult (*ctx_get_id_fn)(CUcontext, unsigned long long*);
+
 static std::mutex g_mu;
 static void* g_addr[64];
-static bool g_done[64];
+static unsigned long long g_ctx[64];      // context ID the cached address belongs to (0: none)
+static ctx_get_current_fn g_get_current = nullptr;
+static ctx_get_id_fn g_get_id = nullptr;
+static bool g_entry_tried = false;
+
+// ID of the context current on this thread, 0 if there is none or it cannot be read.
+static unsigned long long current_ctx_id() {
+  if (!g_entry_tried) {
+    g_entry_tried = true;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q2 == cudaDriverEntryPointSuccess) {
+      g_get_current = (ctx_get_current_fn)f1;
+      g_get_id = (ctx_get_id_fn)f2;
+    }
+  }
+  if (!g_get_current || !g_get_id) return 0;
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (g_get_current(&c) != CUDA_SUCCESS || c == nullptr) return 0;
+  if (g_get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 static dpr1_status noalloc_address(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DPR1_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_done[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_ws) != cudaSuccess || p == nullptr) return DPR1_ERR_CUDA;
-    g_addr[dev] = p;
-    g_done[dev] = true;
+  const unsigned long long id = current_ctx_id();
+  if (id != 0 && g_ctx[dev] == id) {
+    *out = g_addr[dev];
+    return DPR1_OK;
   }
-  *out = g_addr[dev];
+  // first call in this context (the lookup also makes the device's primary context current)
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_ws) != cudaSuccess || p == nullptr) return DPR1_ERR_CUDA;
+  g_addr[dev] = p;
+  g_ctx[dev] = current_ctx_id();
+  *out = p;
   return DPR1_OK;
 }
 

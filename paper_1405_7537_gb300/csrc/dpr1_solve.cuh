@@ -516,7 +516,9 @@ __device__ double accel_solve(Ev ev, double floor, double alo, double ahi, doubl
   uint64_t back = 1, back_lo = 1, wref = 0;
   int steps = 0, model_steps = 0, since = 0;
   bool want = true, from_lo = false;
-  const int limit = cap + 32;
+  // the bracket halves at least every second step once both ends are known: a third more
+  // evaluations than the bisection's cap (128 for the default cap of 96)
+  const int limit = cap + (cap + 2) / 3;
   for (;;) {
     if (steps >= limit) { good = false; break; }
     const double tv = dfrom(t);

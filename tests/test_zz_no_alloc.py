@@ -49,9 +49,10 @@ def test_noalloc_matches_dpr1_eig_twice():
         V0, V1 = ref["Vt"].cpu().numpy(), Vt.cpu().numpy()
         assert np.max(np.abs(l1 - l0) / np.abs(l0)) <= tol
         assert np.max(np.abs(V1 - V0) / np.maximum(np.abs(V0), 1e-300)) <= tol
-        # shifts: the same poles; a non-pole shift (remedy R2) is the computed eigenvalue, which
-        # may differ in its last bits because only part of the bisection's stored-element
-        # buffers fits the static array
+        # shifts: the same poles; a non-pole shift (remedy R2) is the computed eigenvalue.  The
+        # static array leaves no room for the bisection's stored-element buffers, so this call
+        # forms the secular sums at every evaluation -- a different grouping of the terms from
+        # dpr1_eig with a full workspace -- and a non-pole shift may differ in its last bits
         s0, s1 = ref["sigma"].cpu().numpy(), sig.cpu().numpy()
         pole0, pole1 = np.isin(s0, d), np.isin(s1, d)
         assert np.array_equal(pole0, pole1) and np.array_equal(s0[pole0], s1[pole1])
