@@ -41,7 +41,7 @@ class Info(ctypes.Structure):
                 ("remedy", ctypes.c_int), ("zero_path", ctypes.c_int), ("steps", ctypes.c_int),
                 ("sigma", ctypes.c_double), ("mu", ctypes.c_double), ("nu", ctypes.c_double),
                 ("lam", ctypes.c_double), ("b", ctypes.c_double), ("K_nu", ctypes.c_double),
-                ("K_nu_final", ctypes.c_double), ("kappa_nu", ctypes.c_double)]
+                ("K_nu_final", ctypes.c_double), ("kappa_nu", ctypes.c_double), ("r2_dd", ctypes.c_int)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -131,7 +131,8 @@ def eig_all(d, z, rho, opts=None, ks=None, threads=1, want_vectors=True):
     """All (or the listed) eigenpairs of an irreducible, strictly ordered problem.
 
     Returns dict(lam, Vt, sigma, mu, shift, flags) indexed by the position in ks.
-    flags: bit0-1 remedy (1 = R1, 2 = R2), bit2 near-zero recompute, bit3 double-double used.
+    flags: bit0-1 remedy (1 = R1, 2 = R2), bit2 near-zero recompute, bit3 double-double used,
+    bit4 the R2 shift formed in double the working precision.
     The eigenpairs are independent; ``threads`` > 1 splits them over host threads
     (the C calls release the interpreter lock)."""
     d, z = _f64(d), _f64(z)
@@ -157,7 +158,7 @@ def eig_all(d, z, rho, opts=None, ks=None, threads=1, want_vectors=True):
             out["sigma"][p] = info.sigma
             out["mu"][p] = info.mu
             out["shift"][p] = info.shift
-            out["flags"][p] = info.remedy | (info.zero_path << 2) | (info.used_dd << 3)
+            out["flags"][p] = info.remedy | (info.zero_path << 2) | (info.used_dd << 3) | (info.r2_dd << 4)
             if want_vectors:
                 out["Vt"][p] = v
 
@@ -490,7 +491,8 @@ def arrow_eig_all(d, z, alpha, ks=None, threads=1, opts=None):
     steps of Algorithm 1 on its shifted inverse, with the remedies of Sec. 2 for large K_nu
     and the near-zero recompute (``oracle_arroweig``; opts as for ``dpr1eig``): dict(lam,
     sigma, mu, shift, flags, K_nu, Vt) with rows of length n + 1, for k in ks (default 0..n).
-    flags: 1 R1, 2 R2, | 4 recomputed from A^{-1}; shift -1 for a non-pole shift; K_nu of the
+    flags: 1 R1, 2 R2, | 4 recomputed from A^{-1}, | 8 the R2 shift formed in double the working
+    precision; shift -1 for a non-pole shift; K_nu of the
     first shift."""
     d, z = _f64(d), _f64(z)
     n = d.size

@@ -44,15 +44,19 @@
  *     (A - sigma I)^{-1} = (D - sigma I)^{-1} + gamma (D - sigma I)^{-1} z z^T (D - sigma I)^{-1},
  *     gamma = -rho / f(sigma), by bisection; when sigma was not nearer to lambda_k than to
  *     the interval's poles, again from the midpoint (the Weyl bound for k = 0) and then
- *     from the lambda found there (o_r2).  A pole solve that left the binary64 range
- *     counts as K_nu = inf.
+ *     from the lambda found there (o_r2).  When no binary64 number lies between lambda_k and
+ *     a neighbouring pole (the interval holds none, or the binary64 result's difference to a
+ *     pole cancels by more than 16), the shift is formed in double the working precision:
+ *     sigma = d_k + t, the DPR1 matrix from the double-double differences d_j - sigma, and the
+ *     result is returned against the nearer pole (o_r2_dd).  A pole solve that left the
+ *     binary64 range counts as K_nu = inf.
  *   - "|lambda| << min(|lambda - d_k|, |lambda - d_{k-1}|)": T_zero |lambda| < min(...).
  *     The denominator of gamma is formed in double-double; if it is zero, lambda = 0.
  *   - Shift test tie F == 0 takes the else branch (sigma = d_{k-1}), as printed.
  *   - Data of any magnitude: each problem is solved after the exact power-of-two
  *     normalisation D' = 2^-a D, z' = 2^-b z, rho' = 2^(2b-a) rho (oracle_dpr1eig), and a
  *     pair that needs values outside the binary64 range (mu zero, subnormal or not finite;
- *     lambda or v not finite; a cancelling pole difference after R2) returns code 4.
+ *     lambda or v not finite) returns code 4.
  */
 #include <math.h>
 #include <stdint.h>
@@ -161,6 +165,7 @@ typedef struct {
   double K_nu;        /* K_nu of the first shift */
   double K_nu_final;  /* K_nu of the final shift (1 for R2) */
   double kappa_nu;    /* Eq. (knu2) of the first shift */
+  int r2_dd;          /* R2 took its shift in double the working precision */
 } oracle_info;
 
 void oracle_default_opts(oracle_opts* o) {
@@ -396,11 +401,18 @@ static double o_h_dpr1(const void* vctx, double nu) {
   return 1.0 + c->gamma * s;
 }
 
-/* f(sigma) = 1 + rho sum zeta_j^2/(d_j - sigma) in double-double, Eq. (Pick). */
-static odd_t o_f_dd(int n, const double* d, const double* z, double rho, double sigma) {
+/* d_j - sigma in double-double for a shift sigma = s + t (s, t binary64; t = 0 for a shift
+   in working precision, when this is the exact difference of two binary64 numbers). */
+static odd_t o_diff(double dj, double s, double t) {
+  odd_t r = o_two_sum(dj, -s);
+  return (t != 0.0) ? o_add(r, o_from(-t)) : r;
+}
+
+/* f(sigma) = 1 + rho sum zeta_j^2/(d_j - sigma) in double-double, Eq. (Pick), sigma = s + t. */
+static odd_t o_f_dd(int n, const double* d, const double* z, double rho, double s, double t) {
   odd_t acc = o_from(0.0);
   for (int j = 0; j < n; j++) {
-    odd_t dj = o_two_sum(d[j], -sigma);
+    odd_t dj = o_diff(d[j], s, t);
     odd_t zz = o_two_prod(z[j], z[j]);
     acc = o_add(acc, o_div(zz, dj));
   }
@@ -408,18 +420,22 @@ static odd_t o_f_dd(int n, const double* d, const double* z, double rho, double 
 }
 
 /*
+ * Exterior eigenvalue of (A - sigma I)^{-1} for the shift sigma = s + t.  The elements of the
+ * DPR1 matrix are formed from the differences d_j - sigma rounded to binary64 (for t = 0 the
+ * plain binary64 difference d_j - s; for t != 0 the double-double difference, the shift in
+ * double the working precision of remedy R2); f(sigma) is formed in double-double.
  * Returns 1 and mu (lambda = sigma + mu) on success, 0 if f(sigma) is zero in
  * double-double (lambda = sigma, mu = 0).
  */
-static int o_solve_nonpole(int n, const double* d, const double* z, double rho, double sigma,
+static int o_solve_nonpole(int n, const double* d, const double* z, double rho, double s, double t,
                            double* e, double* u, double* mu_out, int* steps) {
-  odd_t f = o_f_dd(n, d, z, rho, sigma);
+  odd_t f = o_f_dd(n, d, z, rho, s, t);
   if (f.hi == 0.0 && f.lo == 0.0) { *mu_out = 0.0; if (steps) *steps = 0; return 0; }
   odd_t gdd = o_div(o_from(-rho), f);
   double gamma = gdd.hi + gdd.lo;
   double emax = -INFINITY, emin = INFINITY, un2 = 0.0;
   for (int j = 0; j < n; j++) {
-    double dj = d[j] - sigma;
+    double dj = o_diff(d[j], s, t).hi;
     e[j] = 1.0 / dj;
     u[j] = z[j] / dj;
     un2 += u[j] * u[j];
@@ -440,9 +456,68 @@ static int o_solve_nonpole(int n, const double* d, const double* z, double rho, 
   return 1;
 }
 
+/* After a non-pole shift (R2): the difference d_p - lambda = (d_p - sigma) - mu to a
+   neighbouring pole p cancels by more than a factor 16.  Then lambda lies much nearer to the
+   pole than any binary64 shift can: no floating-point number lies between lambda and the pole,
+   and the shift must be formed in double the working precision (o_r2_dd). */
+static int o_pole_difference_cancels(double dp, double sigma, double mu) {
+  const double t = (dp - sigma) - mu;
+  return 16.0 * fabs(t) < fabs(dp - sigma) + fabs(mu);
+}
+
 /*
- * (R2) from an estimate lam_est of lambda_k.  The shift is fl(lam_est) moved into the
- * interlacing interval of lambda_k: (d_k, d_{k-1}), or (d_0, d_0 + rho ||z||^2] for k = 0.
+ * (R2) with the shift in double the working precision (Sec. 2, the last sentence of remedy
+ * (R2)): sigma = d_k + t, the binary64 offset t inside the interlacing interval of lambda_k
+ * measured from its lower pole: t in (0, g), g = d_{k-1} - d_k (exact in double-double), or for
+ * k = 0 t in (0, rho ||z||^2] (Weyl).  The DPR1 matrix (A - sigma I)^{-1} is formed from the
+ * double-double differences d_j - sigma (o_solve_nonpole).  The rounds follow o_r2: first the
+ * estimate est_s + est_m (an unevaluated pair), then the midpoint of the interval (the Weyl end
+ * for k = 0), then the lambda found there, until |mu| is below half the distance from sigma to
+ * the nearer pole end.  lambda - d_k = t + mu is then returned against the nearer pole:
+ * sigma_out = d_k, mu_out = fl(t + mu), or sigma_out = d_{k-1}, mu_out = fl((t - g) + mu), so
+ * that every pole difference (d_j - sigma_out) - mu_out keeps its relative accuracy.
+ */
+static int o_r2_dd(int n, const double* d, const double* z, double rho, int k, double est_s, double est_m,
+                   double* e, double* u, double* sigma_out, double* mu_out) {
+  const double base = d[k];
+  odd_t g;
+  if (k > 0) {
+    g = o_two_sum(d[k - 1], -base);
+  } else {
+    double zz = 0.0;
+    for (int j = 0; j < n; j++) zz += z[j] * z[j];
+    g = o_from(rho * zz);
+  }
+  const double gw = g.hi + g.lo;
+  odd_t te = o_add(o_two_sum(est_s, -base), o_from(est_m));
+  double t = te.hi + te.lo, mu = 0.0;
+  const double mid = (k > 0) ? 0.5 * gw : gw;
+  int rounds = 0;
+  for (;;) {
+    if (!(t > 0.0) || (k > 0 && !(t < gw)) || (k == 0 && t > gw)) t = mid;   /* also a NaN estimate */
+    o_solve_nonpole(n, d, z, rho, base, t, e, u, &mu, NULL);
+    rounds++;
+    double room = t;
+    if (k > 0 && gw - t < room) room = gw - t;
+    if (rounds >= 3 || fabs(mu) < 0.5 * room) break;
+    t = (rounds == 1) ? mid : t + mu;
+  }
+  odd_t lm = o_two_sum(t, mu);                  /* lambda - d_k */
+  if (k > 0 && lm.hi > 0.5 * gw) {
+    odd_t up = o_add(lm, o_neg(g));             /* lambda - d_{k-1} */
+    *sigma_out = d[k - 1];
+    *mu_out = up.hi + up.lo;
+  } else {
+    *sigma_out = base;
+    *mu_out = lm.hi + lm.lo;
+  }
+  return rounds;
+}
+
+/*
+ * (R2) from an estimate est_s + est_m of lambda_k (an unevaluated pair, e.g. a pole and its mu).
+ * The shift is fl(est_s + est_m) moved into the interlacing interval of lambda_k: (d_k, d_{k-1}),
+ * or (d_0, d_0 + rho ||z||^2] for k = 0.
  * Any sigma inside gives lambda_k: f(sigma) < 0 exactly when sigma < lambda_k, and the
  * exterior eigenvalue on that side of (A - sigma I)^{-1} is 1/(lambda_k - sigma).  It is
  * computed to high relative accuracy when lambda_k is the eigenvalue nearest to sigma, which
@@ -451,10 +526,13 @@ static int o_solve_nonpole(int n, const double* d, const double* z, double rho, 
  * of both pole solves near 1/eps) the next shift is the midpoint of the interval (the Weyl
  * bound for k = 0), from which lambda_k is at least as near as any other eigenvalue, and the
  * one after is the lambda found there (at most 3 solves).
- * Returns the number of solves, 0 if the interval holds no double.
+ * When the interval holds no binary64 number, or the result's difference to a neighbouring pole
+ * cancels (no binary64 number lies between lambda_k and that pole), the shift is formed in
+ * double the working precision instead (o_r2_dd; *dd_out = 1).
+ * Returns the number of solves.
  */
-static int o_r2(int n, const double* d, const double* z, double rho, int k, double lam_est, double* e,
-                double* u, double* sigma_out, double* mu_out) {
+static int o_r2(int n, const double* d, const double* z, double rho, int k, double est_s, double est_m, double* e,
+                double* u, double* sigma_out, double* mu_out, int* dd_out) {
   double lo = d[k], hi;
   if (k > 0) {
     hi = d[k - 1];
@@ -463,14 +541,19 @@ static int o_r2(int n, const double* d, const double* z, double rho, int k, doub
     for (int j = 0; j < n; j++) zz += z[j] * z[j];
     hi = d[0] + rho * zz;
   }
-  double s = lam_est, mu = 0.0;
+  double s = est_s + est_m, mu = 0.0;
   int rounds = 0;
+  *dd_out = 0;
   for (;;) {
     if (!(s > lo)) s = nextafter(lo, INFINITY);           /* also a NaN estimate */
     if (k > 0 && s >= hi) s = nextafter(hi, -INFINITY);
     if (k == 0 && s > hi) s = hi;
-    if (!(s > lo) || (k > 0 && !(s < hi))) return 0;
-    o_solve_nonpole(n, d, z, rho, s, e, u, &mu, NULL);
+    if (!(s > lo) || (k > 0 && !(s < hi))) {
+      /* no binary64 number inside the interval */
+      *dd_out = 1;
+      return rounds + o_r2_dd(n, d, z, rho, k, est_s, est_m, e, u, sigma_out, mu_out);
+    }
+    o_solve_nonpole(n, d, z, rho, s, 0.0, e, u, &mu, NULL);
     rounds++;
     double room = s - lo;
     if (k > 0 && hi - s < room) room = hi - s;
@@ -480,6 +563,10 @@ static int o_r2(int n, const double* d, const double* z, double rho, int k, doub
        accurate: the midpoint of (d_k, d_{k-1}), or for k = 0 the Weyl bound (every other
        eigenvalue lies below lambda_0); then, if still needed, the lambda found there */
     s = (rounds == 1) ? (k > 0 ? lo + 0.5 * (hi - lo) : hi) : s + mu;
+  }
+  if (o_pole_difference_cancels(d[k], s, mu) || (k > 0 && o_pole_difference_cancels(d[k - 1], s, mu))) {
+    *dd_out = 1;
+    return rounds + o_r2_dd(n, d, z, rho, k, s, mu, e, u, sigma_out, mu_out);
   }
   *sigma_out = s;
   *mu_out = mu;
@@ -493,7 +580,8 @@ int oracle_dpr1_r2(int n, const double* d, const double* z, double rho, int k, d
   double* e = (double*)malloc(sizeof(double) * n);
   double* u = (double*)malloc(sizeof(double) * n);
   if (!e || !u) { free(e); free(u); return -1; }
-  int r = o_r2(n, d, z, rho, k, lam_est, e, u, sigma, mu);
+  int dd;
+  int r = o_r2(n, d, z, rho, k, lam_est, 0.0, e, u, sigma, mu, &dd);
   if (r) *lambda = *sigma + *mu;
   free(e); free(u);
   return r;
@@ -511,15 +599,6 @@ static int o_out_of_range(int n, double mu, double lambda, const double* v) {
     for (int j = 0; j < n; j++)
       if (!isfinite(v[j])) return 1;
   return 0;
-}
-
-/* After a non-pole shift (R2): the difference d_p - lambda = (d_p - sigma) - mu to a
-   neighbouring pole p cancels by more than a factor 16.  This is the case the paper resolves
-   with sigma in double the working precision (no double between lambda and the pole), which
-   is not implemented: the pair is reported as out of range. */
-static int o_pole_difference_cancels(double dp, double sigma, double mu) {
-  const double t = (dp - sigma) - mu;
-  return 16.0 * fabs(t) < fabs(dp - sigma) + fabs(mu);
 }
 
 static int o_dpr1eig_core(int n, const double* d, const double* z, double rho, int k,
@@ -584,9 +663,10 @@ static int o_dpr1eig_core(int n, const double* d, const double* z, double rho, i
       /* (R2): a non-pole shift next to lambda, from the better of the two pole solutions
          (the one with the smaller K_nu) */
       double s2, mu2;
-      if (o_r2(n, d, z, rho, k, best_sigma + best_mu, delta, w, &s2, &mu2)) {
+      int dd2;
+      if (o_r2(n, d, z, rho, k, best_sigma, best_mu, delta, w, &s2, &mu2, &dd2)) {
         shift = -1; sigma = s2; mu = mu2; nu = (mu2 != 0.0) ? 1.0 / mu2 : INFINITY; K = 1.0;
-        steps = 0; inf.remedy = 2; inf.used_dd = 1;
+        steps = 0; inf.remedy = 2; inf.used_dd = 1; inf.r2_dd = dd2;
       }
     }
   }
@@ -604,7 +684,7 @@ static int o_dpr1eig_core(int n, const double* d, const double* z, double rho, i
     if (k > 0) { double m2 = fabs(lambda - d[k - 1]); if (m2 < m1) m1 = m2; }
     if (allnz && opt.T_zero * fabs(lambda) < m1) {
       double mu0;
-      int ok = o_solve_nonpole(n, d, z, rho, 0.0, delta, w, &mu0, NULL);
+      int ok = o_solve_nonpole(n, d, z, rho, 0.0, 0.0, delta, w, &mu0, NULL);
       lambda = ok ? mu0 : 0.0;
       inf.zero_path = 1;
     }
@@ -900,19 +980,21 @@ static double o_h_ahinv(const void* vctx, double nu) {
   return 1.0 + c->gamma * (s - 1.0 / nu);
 }
 
-/* Non-pole shift sigma: returns 1 and mu (lambda = sigma + mu), or 0 when f(sigma) is zero
-   in double-double (lambda = sigma, mu = 0). */
-static int o_ah_solve_nonpole(int n, const double* d, const double* z, double alpha, double sigma, double* e,
+/* Non-pole shift sigma = s + t (t = 0: a binary64 shift; t != 0: the shift in double the working
+   precision, the elements from the double-double differences d_j - sigma rounded to binary64, as
+   o_solve_nonpole): returns 1 and mu (lambda = sigma + mu), or 0 when f(sigma) is zero in
+   double-double (lambda = sigma, mu = 0). */
+static int o_ah_solve_nonpole(int n, const double* d, const double* z, double alpha, double s, double t, double* e,
                               double* u, double* mu_out, int* steps) {
-  odd_t f = o_two_sum(alpha, -sigma);
+  odd_t f = o_diff(alpha, s, t);
   for (int j = 0; j < n; j++)
-    f = o_add(f, o_neg(o_div(o_two_prod(z[j], z[j]), o_two_sum(d[j], -sigma))));
+    f = o_add(f, o_neg(o_div(o_two_prod(z[j], z[j]), o_diff(d[j], s, t))));
   if (f.hi == 0.0 && f.lo == 0.0) { *mu_out = 0.0; if (steps) *steps = 0; return 0; }
   odd_t gdd = o_div(o_from(1.0), f);
   double gamma = gdd.hi + gdd.lo;
   double emax = 0.0, emin = 0.0, un2 = 1.0;   /* the pole at 0 and u_n^2 = 1 */
   for (int j = 0; j < n; j++) {
-    double dj = d[j] - sigma;
+    double dj = o_diff(d[j], s, t).hi;
     e[j] = 1.0 / dj;
     u[j] = z[j] / dj;
     un2 += u[j] * u[j];
@@ -929,29 +1011,73 @@ static int o_ah_solve_nonpole(int n, const double* d, const double* z, double al
   return 1;
 }
 
-/* (R2) for the arrowhead from an estimate lam_est of lambda_k, as o_r2: the shift is moved
+/* (R2) for the arrowhead with the shift in double the working precision, as o_r2_dd: sigma =
+   base + t with base the pole end of the interlacing interval nearer the lower end (d_k; d_{n-1}
+   for k = n, whose interval lies below it), tau = |t| in (0, g) between two poles, or up to the
+   Weyl end for an exterior eigenvalue; the result is returned against the nearer pole. */
+static int o_ah_r2_dd(int n, const double* d, const double* z, double alpha, int k, double wlo, double whi,
+                      double est_s, double est_m, double* e, double* u, double* sigma_out, double* mu_out) {
+  const int lo_pole = k < n, hi_pole = k > 0;
+  const double sgn = lo_pole ? 1.0 : -1.0;
+  const double base = lo_pole ? d[k] : d[n - 1];
+  odd_t g;
+  if (lo_pole && hi_pole) g = o_two_sum(d[k - 1], -base);
+  else g = o_from(lo_pole ? whi - base : base - wlo);   /* to the Weyl end */
+  const double gw = g.hi + g.lo;
+  const double mid = (lo_pole && hi_pole) ? 0.5 * gw : gw;
+  odd_t te = o_add(o_two_sum(est_s, -base), o_from(est_m));
+  double tau = sgn * (te.hi + te.lo), mu = 0.0;
+  int rounds = 0;
+  for (;;) {
+    if (!(tau > 0.0) || !(tau <= gw) || (hi_pole && lo_pole && !(tau < gw))) tau = mid;
+    o_ah_solve_nonpole(n, d, z, alpha, base, sgn * tau, e, u, &mu, NULL);
+    rounds++;
+    double room = tau;
+    if (lo_pole && hi_pole && gw - tau < room) room = gw - tau;
+    if (rounds >= 3 || fabs(mu) < 0.5 * room) break;
+    tau = (rounds == 1) ? mid : tau + sgn * mu;
+  }
+  odd_t lm = o_two_sum(sgn * tau, mu);          /* lambda - base */
+  if (lo_pole && hi_pole && lm.hi > 0.5 * gw) {
+    odd_t up = o_add(lm, o_neg(g));             /* lambda - d_{k-1} */
+    *sigma_out = d[k - 1];
+    *mu_out = up.hi + up.lo;
+  } else {
+    *sigma_out = base;
+    *mu_out = lm.hi + lm.lo;
+  }
+  return rounds;
+}
+
+/* (R2) for the arrowhead from an estimate est_s + est_m of lambda_k, as o_r2: the shift is moved
    into the interlacing interval of lambda_k, (d_k, d_{k-1}), with the exterior ends from
    Weyl's bounds, lambda_0 <= max(d_0, alpha) + ||z|| and lambda_n >= min(d_{n-1}, alpha) - ||z||;
    when |mu| is not below half the distance from sigma to the nearer pole end, the next shift
    is the midpoint (the Weyl bound of an exterior eigenvalue) and then the lambda found there
-   (at most 3 solves).  Returns the number of solves. */
-static int o_ah_r2(int n, const double* d, const double* z, double alpha, int k, double lam_est, double* e,
-                   double* u, double* sigma_out, double* mu_out) {
+   (at most 3 solves).  When no binary64 shift lies between lambda_k and a neighbouring pole the
+   shift is formed in double the working precision (o_ah_r2_dd; *dd_out = 1).  Returns the
+   number of solves. */
+static int o_ah_r2(int n, const double* d, const double* z, double alpha, int k, double est_s, double est_m,
+                   double* e, double* u, double* sigma_out, double* mu_out, int* dd_out) {
   double zn = 0.0;
   for (int j = 0; j < n; j++) zn += z[j] * z[j];
   zn = sqrt(zn);
   const int lo_pole = k < n, hi_pole = k > 0;
   double lo = lo_pole ? d[k] : (d[n - 1] < alpha ? d[n - 1] : alpha) - zn;
   double hi = hi_pole ? d[k - 1] : (d[0] > alpha ? d[0] : alpha) + zn;
-  double s = lam_est, mu = 0.0;
+  double s = est_s + est_m, mu = 0.0;
   int rounds = 0;
+  *dd_out = 0;
   for (;;) {
     if (lo_pole && !(s > lo)) s = nextafter(lo, INFINITY);
     if (!lo_pole && !(s >= lo)) s = lo;                    /* also a NaN estimate */
     if (hi_pole && s >= hi) s = nextafter(hi, -INFINITY);
     if (!hi_pole && s > hi) s = hi;
-    if ((lo_pole && !(s > lo)) || (hi_pole && !(s < hi))) return 0;
-    o_ah_solve_nonpole(n, d, z, alpha, s, e, u, &mu, NULL);
+    if ((lo_pole && !(s > lo)) || (hi_pole && !(s < hi))) {
+      *dd_out = 1;
+      return rounds + o_ah_r2_dd(n, d, z, alpha, k, lo, hi, est_s, est_m, e, u, sigma_out, mu_out);
+    }
+    o_ah_solve_nonpole(n, d, z, alpha, s, 0.0, e, u, &mu, NULL);
     rounds++;
     double room = INFINITY;
     if (lo_pole) room = s - lo;
@@ -959,6 +1085,10 @@ static int o_ah_r2(int n, const double* d, const double* z, double alpha, int k,
     if (rounds >= 3 || fabs(mu) < 0.5 * room) break;
     /* as o_r2: next the midpoint, or the Weyl bound of an exterior eigenvalue */
     s = (rounds == 1) ? (lo_pole && hi_pole ? lo + 0.5 * (hi - lo) : (hi_pole ? lo : hi)) : s + mu;
+  }
+  if ((lo_pole && o_pole_difference_cancels(d[k], s, mu)) || (hi_pole && o_pole_difference_cancels(d[k - 1], s, mu))) {
+    *dd_out = 1;
+    return rounds + o_ah_r2_dd(n, d, z, alpha, k, lo, hi, s, mu, e, u, sigma_out, mu_out);
   }
   *sigma_out = s;
   *mu_out = mu;
@@ -972,7 +1102,8 @@ int oracle_arrow_r2(int n, const double* d, const double* z, double alpha, int k
   double* e = (double*)malloc(sizeof(double) * n);
   double* u = (double*)malloc(sizeof(double) * n);
   if (!e || !u) { free(e); free(u); return -1; }
-  int r = o_ah_r2(n, d, z, alpha, k, lam_est, e, u, sigma, mu);
+  int dd;
+  int r = o_ah_r2(n, d, z, alpha, k, lam_est, 0.0, e, u, sigma, mu, &dd);
   if (r) *lambda = *sigma + *mu;
   free(e); free(u);
   return r;
@@ -995,7 +1126,8 @@ static void o_ah_vector(int n, const double* d, const double* z, double sigma, d
 
 /* Eigenvalue k (0-based, 0..n) of the arrowhead; v has n + 1 entries.  opt: T_Knu, T_zero
    and remedies as for oracle_dpr1eig (NULL: defaults).  flags_out: remedy (1 R1, 2 R2) |
-   4 when lambda was recomputed from A^{-1}.  shift_out: final pole, -1 for a non-pole shift. */
+   4 when lambda was recomputed from A^{-1} | 8 when the R2 shift was formed in double the
+   working precision.  shift_out: final pole, -1 for a non-pole shift. */
 static int o_arroweig_core(int n, const double* d, const double* z, double alpha, int k, const oracle_opts* opt_in,
                            double* lambda_out, double* v, double* sigma_out, double* mu_out, int* shift_out,
                            int* flags_out, double* K_out) {
@@ -1044,8 +1176,9 @@ static int o_arroweig_core(int n, const double* d, const double* z, double alpha
     if (K > opt.T_Knu) {
       /* (R2) from the better pole solution */
       double s2, mu2;
-      if (o_ah_r2(n, d, z, alpha, k, best_sigma + best_mu, delta, w, &s2, &mu2)) {
-        shift = -1; sigma = s2; mu = mu2; flags = 2;
+      int dd2;
+      if (o_ah_r2(n, d, z, alpha, k, best_sigma, best_mu, delta, w, &s2, &mu2, &dd2)) {
+        shift = -1; sigma = s2; mu = mu2; flags = 2 | (dd2 << 3);
       }
     }
   }
@@ -1062,7 +1195,7 @@ static int o_arroweig_core(int n, const double* d, const double* z, double alpha
     if (k > 0) { double m2 = fabs(lambda - d[k - 1]); if (m2 < m1) m1 = m2; }
     if (allnz && opt.T_zero * fabs(lambda) < m1) {
       double mu0;
-      int ok = o_ah_solve_nonpole(n, d, z, alpha, 0.0, delta, w, &mu0, NULL);
+      int ok = o_ah_solve_nonpole(n, d, z, alpha, 0.0, 0.0, delta, w, &mu0, NULL);
       lambda = ok ? mu0 : 0.0;
       flags |= 4;
     }

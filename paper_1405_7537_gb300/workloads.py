@@ -185,6 +185,29 @@ def glued_wilkinson(n=21, copies=4, glue=1e-10):
     return a, b
 
 
+def adjacent_poles(seed):
+    """Poles at consecutive binary64 numbers: a cluster of 3 to 5 of them in [0.5, 1) with weights
+    +-10^U(-30, -15), except one of size sqrt(c 2^-52), c ~ U(0.2, 4), which puts the zero of the
+    rest of the secular function inside the cluster; 1 to 3 poles U(-1, 0.4) and as many
+    U(1.2, 2) with weights +-U(0.1, 1); rho = 10^U(-1, 1).  Eigenvalues then lie within a fraction
+    of an ulp of a pole, and their neighbours hug the poles more closely still (K_nu >> 1 at
+    both poles), so that no binary64 number lies between such an eigenvalue and its pole."""
+    rng = np.random.default_rng(seed)
+    eps = 2.0 ** -52
+    m = int(rng.integers(3, 6))
+    q = [float(rng.uniform(0.5, 1.0))]
+    for _ in range(m - 1):
+        q.append(float(np.nextafter(q[-1], 2.0)))
+    nfar = int(rng.integers(1, 4))
+    far = list(rng.uniform(-1.0, 0.4, nfar)) + list(rng.uniform(1.2, 2.0, nfar))
+    d = np.array(sorted(q + far, reverse=True))
+    inq = np.isin(d, q)
+    z = np.where(inq, 10.0 ** rng.uniform(-30.0, -15.0, d.size), rng.uniform(0.1, 1.0, d.size))
+    z *= np.where(rng.random(d.size) < 0.5, 1.0, -1.0)
+    z[np.flatnonzero(inq)[rng.integers(0, m)]] = np.sqrt(eps * rng.uniform(0.2, 4.0))
+    return d, z, float(10.0 ** rng.uniform(-1.0, 1.0))
+
+
 def arrowhead(n=16384, seed=6):
     """A real symmetric arrowhead [diag(d) z; z^T alpha] of order n + 1: d ~ U(-1, 1) sorted
     decreasing and distinct, z ~ U(-1, 1) redrawn while |z| <= 1e-3, alpha ~ U(-1, 1)."""
