@@ -36,6 +36,10 @@
 #ifndef DPR1_FIX_BLOCKS_PER_SM
 #define DPR1_FIX_BLOCKS_PER_SM 2
 #endif
+// resident blocks per SM that the solve kernel's register budget is compiled for
+#ifndef DPR1_SOLVE_MIN_BLOCKS
+#define DPR1_SOLVE_MIN_BLOCKS 1
+#endif
 // batches of 64 or more problems up to this mean size run the remedies one warp per item
 #ifndef DPR1_FIX_WARP_MAX_N
 #define DPR1_FIX_WARP_MAX_N 2048
@@ -414,8 +418,8 @@ __global__ void k_deflate(Prob pb, Ws w) {
 // (solve_pole checks the near end, so a wrong sign of a rounded F costs steps, not accuracy).
 // ---------------------------------------------------------------------------------
 template <int L>
-__global__ void __launch_bounds__(256) k_solve(Prob pb, Ws w, int cap, bool fast, int dd_mode, double T_kappa,
-                                               bool screen) {
+__global__ void __launch_bounds__(256, DPR1_SOLVE_MIN_BLOCKS)
+    k_solve(Prob pb, Ws w, int cap, bool fast, int dd_mode, double T_kappa, bool screen) {
   if (*w.status & ST_FATAL) return;
   const int lane = threadIdx.x & (L - 1);
   const unsigned gm = group_mask<L>();

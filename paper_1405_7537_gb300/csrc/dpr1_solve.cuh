@@ -13,7 +13,14 @@
 
 #include "dpr1_device.cuh"
 
+// unrolling of the evaluation loop over the stored elements
+#ifndef DPR1_STORED_UNROLL
+#define DPR1_STORED_UNROLL 2
+#endif
+
 namespace dpr1 {
+
+constexpr int kStoredUnroll = DPR1_STORED_UNROLL;
 
 // ---------------------------------------------------------------------------------
 // Secular sums
@@ -124,6 +131,7 @@ __device__ __forceinline__ double stored_sum(const double* __restrict__ Ds, cons
   double s0 = 0.0;
   bool b = false;
   int j = lane;
+#pragma unroll kStoredUnroll
   for (; j + 3 * L < n; j += 4 * L) {
     const double t0 = __fma_rn(-nu, Ds[j], 1.0), t1 = __fma_rn(-nu, Ds[j + L], 1.0);
     const double t2 = __fma_rn(-nu, Ds[j + 2 * L], 1.0), t3 = __fma_rn(-nu, Ds[j + 3 * L], 1.0);
