@@ -366,8 +366,9 @@ DPR1_API dpr1_status dpr1_eig_noalloc(int64_t n, const double* d, const double* 
  *   2 remedies taken with R1, 3 with R2, 4 secular-function evaluations in the bisection
  *   kernel, 5 evaluations in the remedy kernel, 6 eigenvalues recomputed from A^{-1},
  *   7 deflated pairs, 8 corners b formed in double-double by the bisection kernel,
- *   9 bisection steps (of those counted in 4 and 5) settled by the binary32 screen.
- *   `out` holds 10 values.
+ *   9 bisection steps (of those counted in 4 and 5) settled by the binary32 screen,
+ *   10 R2 remedies that formed their shift in double the working precision (of those in 3).
+ *   `out` holds 11 values.
  */
 DPR1_API dpr1_status dpr1_workspace_stats(void* workspace, int64_t* out, dpr1_stream_t stream);
 

@@ -344,23 +344,25 @@ __global__ void __launch_bounds__(256) k_arrow_solve(int n, const double* __rest
 // double-double; f(sigma) = 0 gives mu = 0 (lambda = sigma).  above / below: the poles next to
 // sigma (-1: none on that side).  The poles of h on |nu| are the e_j and 0, so the largest
 // of them is max(e_above, 0) (gamma > 0, nu the rightmost) or max(-e_below, 0) (gamma < 0).
-template <int L>
+// With OFS the shift is sigma + sigma_lo in double the working precision (as solve_nonpole).
+template <int L, bool OFS = false>
 __device__ double solve_nonpole_arrow(const double* __restrict__ d, const double* __restrict__ zl,
                                       const double* __restrict__ zz, int n, double alpha, double sigma, int above,
                                       int below, int cap, bool fast, int lane, unsigned gm, bool* ok,
                                       int* steps_out, double* __restrict__ Ds = nullptr,
-                                      double* __restrict__ us = nullptr) {
+                                      double* __restrict__ us = nullptr, double sigma_lo = 0.0) {
   double un2, cub;
   // the double-double pass also stores the elements for the solve when the group has a buffer
-  const dd acc = dd_pole_sum<L>(d, zz, zl, n, -1, sigma, lane, gm, &un2, &cub, Ds, us);
-  const dd f = dd_add(two_sum(alpha, -sigma), {-acc.hi, -acc.lo});
+  const dd acc = dd_pole_sum<L, OFS>(d, zz, zl, n, -1, sigma, lane, gm, &un2, &cub, Ds, us, nullptr, nullptr,
+                                     nullptr, sigma_lo);
+  const dd f = dd_add(OFS ? shift_diff(alpha, sigma, sigma_lo) : two_sum(alpha, -sigma), {-acc.hi, -acc.lo});
   *ok = true;
   *steps_out = 0;
   if (f.hi == 0.0 && f.lo == 0.0) return 0.0;
   const double gamma = dd_to_double(dd_div({1.0, 0.0}, f));
   const double uu = un2 + 1.0;                  // ||u||^2, u_n = -1
-  const double emax = above >= 0 ? 1.0 / __dsub_rn(d[above], sigma) : -INFINITY;
-  const double emin = below >= 0 ? 1.0 / __dsub_rn(d[below], sigma) : INFINITY;
+  const double emax = above >= 0 ? 1.0 / elem_diff<OFS>(d[above], sigma, sigma_lo) : -INFINITY;
+  const double emin = below >= 0 ? 1.0 / elem_diff<OFS>(d[below], sigma, sigma_lo) : INFINITY;
   // Rayleigh quotient of u (the pole at 0 adds nothing to u^T diag(e, 0) u): a lower bound of
   // the rightmost and an upper bound of the leftmost eigenvalue; Weyl bounds the other side
   const double rq = cub / uu + gamma * uu;
@@ -386,8 +388,8 @@ __device__ double solve_nonpole_arrow(const double* __restrict__ d, const double
     auto ev = [&](double t, bool want, double* psi, double* dpsi) {
       const double v = side * t;
       double dS = 0.0;
-      const double S = want ? elem_sum_d<L>(Ds, us, d, zz, n, -1, sigma, v, lane, gm, &dS)
-                            : elem_sum<L>(Ds, us, d, zz, n, -1, sigma, v, lane, gm);
+      const double S = want ? elem_sum_d<L, OFS>(Ds, us, d, zz, n, -1, sigma, v, lane, gm, &dS, sigma_lo)
+                            : elem_sum<L, OFS>(Ds, us, d, zz, n, -1, sigma, v, lane, gm, sigma_lo);
       const double it = 1.0 / t;
       *psi = -side * S + it;
       *dpsi = -dS - it * it;
@@ -396,7 +398,7 @@ __device__ double solve_nonpole_arrow(const double* __restrict__ d, const double
     nu = side * accel_solve(ev, floor, alo, ahi, floor, -1.0 / ag, 0.0, ag, cap, ok, &steps);
   } else {
     auto phi = [&](double v) {
-      const double S = elem_sum<L>(Ds, us, d, zz, n, -1, sigma, v, lane, gm);
+      const double S = elem_sum<L, OFS>(Ds, us, d, zz, n, -1, sigma, v, lane, gm, sigma_lo);
       return __fma_rn(gamma, __dsub_rn(S, 1.0 / v), 1.0);
     };
     // h < 0 between the floor and the root in both cases
@@ -443,13 +445,21 @@ __global__ void k_arrow_classify(int n, const double* __restrict__ d, ArrowWs w,
   }
 }
 
+// After a non-pole shift: (d_p - sigma) - mu to a neighbouring pole p cancels by more than 16.
+__device__ __forceinline__ bool ah_pole_difference_cancels(double dp, double s, double m) {
+  const double t = __dsub_rn(__dsub_rn(dp, s), m);
+  return 16.0 * fabs(t) < __dadd_rn(fabs(__dsub_rn(dp, s)), fabs(m));
+}
+
 // Remedies for the flagged eigenvalues, one lane group each (work counter):
 //  (R1) solve at the other neighbouring pole o when K' < K, K' <= T_Knu and ratio <= T_Knu
 //       (beyond that the eigenvector formula at d_o cancels);
 //  (R2) otherwise sigma = fl(lambda) of the first pole solution, moved into the interlacing
 //       interval of lambda_k (exterior ends from Weyl's bounds), and the non-pole solve,
 //       repeated at the new lambda while sigma is not nearer to lambda_k than to the
-//       interval's poles (at most 3 solves), as for D + rho z z^T.
+//       interval's poles (at most 3 solves), as for D + rho z z^T; when no binary64 number lies
+//       between lambda_k and a neighbouring pole, with the shift in double the working
+//       precision (at most 3 more solves).
 template <int L>
 __global__ void __launch_bounds__(L > 256 ? L : 256) k_arrow_fix(int n, const double* __restrict__ d, ArrowWs w,
                                                                    double T_Knu, int cap, bool fast, bool screen) {
@@ -508,6 +518,7 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_arrow_fix(int n, const do
       const double lo = lo_pole ? d[k] : fmin(d[n - 1], alpha) - zn;
       const double hi = hi_pole ? d[k - 1] : fmax(d[0], alpha) + zn;
       double sg = __dadd_rn(di, mu);                    // the first solution's lambda
+      bool solved = false;
       for (int round = 0; round < 3; round++) {
         if (lo_pole && !(sg > lo)) sg = dnext_up(lo);
         if (!lo_pole && !(sg >= lo)) sg = lo;
@@ -520,13 +531,52 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_arrow_fix(int n, const do
                                                  cap, fast, lane, gm, &ok, &st2, Ds, us);
         if (!ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
         if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)st2);
-        new_sig = sg; new_mu = m2; new_shift = -1;
+        new_sig = sg; new_mu = m2; new_shift = -1; solved = true;
         // repeat while sigma is not nearer to lambda_k than to the interval's poles
         double room = INFINITY;
         if (lo_pole) room = sg - lo;
         if (hi_pole) room = fmin(room, hi - sg);
         if (fabs(m2) < 0.5 * room) break;
         sg = __dadd_rn(sg, m2);
+      }
+      // no binary64 number between lambda_k and a neighbouring pole (the interval holds none, or
+      // the result's difference to a pole cancels): the shift in double the working precision,
+      // sigma = base + sgn tau with base the pole end nearer the lower end of the interval
+      // (d_k; d_{n-1} for k = n, whose interval lies below it), tau in (0, g) between two poles
+      // or up to the Weyl end; lambda - base is returned against the nearer pole
+      if (!solved || (lo_pole && ah_pole_difference_cancels(lo, new_sig, new_mu)) ||
+          (hi_pole && ah_pole_difference_cancels(hi, new_sig, new_mu))) {
+        const double sgn = lo_pole ? 1.0 : -1.0;
+        const double base = lo_pole ? lo : hi;
+        const dd g = (lo_pole && hi_pole) ? two_sum(hi, -lo) : dd{__dsub_rn(hi, lo), 0.0};
+        const double gw = __dadd_rn(g.hi, g.lo);
+        const double mid = (lo_pole && hi_pole) ? 0.5 * gw : gw;
+        const dd te = dd_add(two_sum(new_sig, -base), {new_mu, 0.0});
+        double tau = sgn * __dadd_rn(te.hi, te.lo), m2 = 0.0;
+        for (int round = 0; round < 3; round++) {
+          if (!(tau > 0.0) || !(tau <= gw) || (lo_pole && hi_pole && !(tau < gw))) tau = mid;
+          bool ok;
+          int st2;
+          m2 = solve_nonpole_arrow<L, true>(d, w.zl, w.zz, n, alpha, base, k > 0 ? k - 1 : -1, k < n ? k : -1, cap,
+                                            fast, lane, gm, &ok, &st2, Ds, us, sgn * tau);
+          if (!ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
+          if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)st2);
+          double room = tau;
+          if (lo_pole && hi_pole) room = fmin(room, gw - tau);
+          if (fabs(m2) < 0.5 * room) break;
+          tau = (round == 0) ? mid : __fma_rn(sgn, m2, tau);
+        }
+        const dd lm = two_sum(sgn * tau, m2);             // lambda - base
+        if (lo_pole && hi_pole && lm.hi > 0.5 * gw) {
+          const dd up = dd_add(lm, {-g.hi, -g.lo});       // lambda - d_{k-1}
+          new_sig = hi;
+          new_mu = __dadd_rn(up.hi, up.lo);
+        } else {
+          new_sig = base;
+          new_mu = __dadd_rn(lm.hi, lm.lo);
+        }
+        new_shift = -1;
+        if (lane == 0) atomicAdd(&w.counters[C_R2DD], 1u);
       }
     }
     if (lane == 0) {
@@ -588,10 +638,6 @@ __global__ void k_arrow_zero_solve(int n, const double* __restrict__ d, ArrowWs 
   }
 }
 
-__device__ __forceinline__ bool ah_pole_difference_cancels(double dp, double s, double m) {
-  const double t = __dsub_rn(__dsub_rn(dp, s), m);
-  return 16.0 * fabs(t) < __dadd_rn(fabs(__dsub_rn(dp, s)), fabs(m));
-}
 
 // Rows v_k = [x; -1] / ||.|| (one warp per row), lambda, sigma, mu, ||[x; -1]||.
 __global__ void __launch_bounds__(256) k_arrow_vectors(int n, const double* __restrict__ d,

@@ -546,6 +546,13 @@ __global__ void k_classify(Prob pb, Ws w, double T_Knu) {
   }
 }
 
+// After a non-pole shift: the difference d_p - lambda = (d_p - sigma) - mu to a neighbouring
+// pole p cancels by more than a factor 16 (lambda lies much nearer to the pole than sigma).
+__device__ __forceinline__ bool pole_difference_cancels(double dp, double s, double m) {
+  const double t = __dsub_rn(__dsub_rn(dp, s), m);
+  return 16.0 * fabs(t) < __dadd_rn(fabs(__dsub_rn(dp, s)), fabs(m));
+}
+
 // ---------------------------------------------------------------------------------
 // k_fix: remedies for the flagged eigenvalues, one lane group each.
 //  (R1) solve at the other neighbouring pole o when K' < K, K' <= T_Knu and ratio <= T_Knu
@@ -557,7 +564,9 @@ __global__ void k_classify(Prob pb, Ws w, double T_Knu) {
 //       side), accurately once lambda_k is the eigenvalue nearest to sigma; when |mu| is not
 //       below half the distance to the nearer pole end, the next shift is the midpoint (the
 //       Weyl bound for k = 0) and then the lambda found there (at most 3 solves: a first
-//       estimate with K_nu near 1/eps is noise).
+//       estimate with K_nu near 1/eps is noise).  When no binary64 number lies between
+//       lambda_k and a neighbouring pole, the shift is formed in double the working precision
+//       (at most 3 more solves).
 // A group with one of k_solve's buffers bisects from stored elements there, as k_solve does.
 // ---------------------------------------------------------------------------------
 template <int L>
@@ -627,6 +636,7 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double
         hi = __fma_rn(rho, group_sum<L>(zs, gm), d[0]);
       }
       double s = __dadd_rn(di, mu);                     // the first solution's lambda
+      bool solved = false;
       for (int round = 0; round < 3; round++) {
         if (!(s > lo)) s = dnext_up(lo);
         if (k > 0 && s >= hi) s = dnext_down(hi);
@@ -638,7 +648,7 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double
             solve_nonpole<L>(d, zl, zz, n, rho, s, k > 0 ? k - 1 : -1, k, cap, fast, lane, gm, &ok, &st2, Ds, us);
         if (!ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
         if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)st2);
-        new_sig = s; new_mu = m2; new_shift = -1;
+        new_sig = s; new_mu = m2; new_shift = -1; solved = true;
         // accurate when lambda_k is the eigenvalue nearest to sigma: every other eigenvalue lies
         // beyond the interval's poles.  Otherwise the next shift is one from which lambda_k is at
         // least as near as any other eigenvalue -- the midpoint of (d_k, d_{k-1}), or for k = 0
@@ -646,6 +656,42 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double
         const double room = (k > 0) ? fmin(s - lo, hi - s) : s - lo;
         if (fabs(m2) < 0.5 * room) break;
         s = (round == 0) ? (k > 0 ? __fma_rn(0.5, __dsub_rn(hi, lo), lo) : hi) : __dadd_rn(s, m2);
+      }
+      // no binary64 number between lambda_k and a neighbouring pole: the interval holds none, or
+      // the result's difference to a pole cancels.  Then (Sec. 2, remedy R2) the shift and its
+      // DPR1 matrix are formed in double the working precision: sigma = d_k + t, an unevaluated
+      // pair with t in (0, g), g = d_{k-1} - d_k (or up to the Weyl bound for k = 0), the rounds
+      // as above from the estimate; lambda - d_k = t + mu is returned against the nearer pole.
+      if (!solved || pole_difference_cancels(lo, new_sig, new_mu) ||
+          (k > 0 && pole_difference_cancels(hi, new_sig, new_mu))) {
+        const dd g = (k > 0) ? two_sum(hi, -lo) : dd{__dsub_rn(hi, lo), 0.0};
+        const double gw = __dadd_rn(g.hi, g.lo);
+        const double mid = (k > 0) ? 0.5 * gw : gw;
+        const dd te = dd_add(two_sum(new_sig, -lo), {new_mu, 0.0});
+        double t = __dadd_rn(te.hi, te.lo), m2 = 0.0;
+        for (int round = 0; round < 3; round++) {
+          if (!(t > 0.0) || (k > 0 && !(t < gw)) || (k == 0 && t > gw)) t = mid;
+          bool ok;
+          int st2 = 0;
+          m2 = solve_nonpole<L, true>(d, zl, zz, n, rho, lo, k > 0 ? k - 1 : -1, k, cap, fast, lane, gm, &ok, &st2,
+                                      Ds, us, t);
+          if (!ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
+          if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)st2);
+          const double room = (k > 0) ? fmin(t, gw - t) : t;
+          if (fabs(m2) < 0.5 * room) break;
+          t = (round == 0) ? mid : __dadd_rn(t, m2);
+        }
+        const dd lm = two_sum(t, m2);                   // lambda - d_k
+        if (k > 0 && lm.hi > 0.5 * gw) {
+          const dd up = dd_add(lm, {-g.hi, -g.lo});     // lambda - d_{k-1}
+          new_sig = hi;
+          new_mu = __dadd_rn(up.hi, up.lo);
+        } else {
+          new_sig = lo;
+          new_mu = __dadd_rn(lm.hi, lm.lo);
+        }
+        new_shift = -1;
+        if (lane == 0) atomicAdd(&w.counters[C_R2DD], 1u);
       }
     }
     if (lane == 0) {
@@ -778,10 +824,34 @@ __global__ void k_defl_positions(Prob pb, Ws w) {
 // j).  In a deflated problem the row of reduced eigenvalue k goes to output row rpos and
 // component q takes coef[q] * x_{src[q]}; deflated pairs are written by k_defl_rows.
 // ---------------------------------------------------------------------------------
-__device__ __forceinline__ bool pole_difference_cancels(double dp, double s, double m) {
-  const double t = __dsub_rn(__dsub_rn(dp, s), m);
-  return 16.0 * fabs(t) < __dadd_rn(fabs(__dsub_rn(dp, s)), fabs(m));
+// Scalar outputs of eigenpair g (reduced index k, output row `row`) in the caller's units --
+// lambda, sigma, mu times 2^a and ||x|| times 2^(b - a) -- and the range check: the pair needs
+// values outside the binary64 range (mu zero, subnormal or not finite: lambda within 2^-1022 of
+// its shift in normalised units; lambda or ||x|| not finite), or after a non-pole shift the
+// difference to a neighbouring pole still cancels (R2 in double the working precision did not
+// bring sigma next to lambda within its solves).
+__device__ __forceinline__ void pair_outputs(const Prob& pb, const Ws& w, int p, int64_t g, int64_t base, int k,
+                                             int row, const double* __restrict__ d, double s, double m, double nrm,
+                                             double scale, double c) {
+  const int ea = w.pexp[2 * p], eb = w.pexp[2 * p + 1];
+  const double lz = w.lamz[g];
+  const double lam = isnan(lz) ? __dadd_rn(s, m) : lz;
+  const double xn = nrm / scale;
+  pb.lambda[base + row] = scalbn(lam, ea);
+  if (pb.sigma) pb.sigma[base + row] = scalbn(s, ea);
+  if (pb.mu) pb.mu[base + row] = scalbn(m, ea);
+  if (pb.xnorm) pb.xnorm[base + row] = scalbn(xn, eb - ea);
+  bool out = !(fabs(m) >= 0x1p-1022) || !isfinite(m) || !isfinite(lam) || !(xn > 0.0) || !isfinite(xn) ||
+             !isfinite(c);
+  if (w.shift[g] < 0) out = out || pole_difference_cancels(d[k], s, m) ||
+                            (k > 0 && pole_difference_cancels(d[k - 1], s, m));
+  if (out) atomicOr(w.status, ST_RANGE);
 }
+
+#ifndef DPR1_VEC_PAIRS
+#define DPR1_VEC_PAIRS 1
+#endif
+constexpr bool kVecPairs = DPR1_VEC_PAIRS != 0;
 
 __global__ void __launch_bounds__(256) k_vectors(Prob pb, Ws w) {
   if (*w.status & ST_FATAL) return;
@@ -807,12 +877,43 @@ __global__ void __launch_bounds__(256) k_vectors(Prob pb, Ws w) {
     const bool store = vr && !defl;
     double q = 0.0;
     bool bad = false;
-    for (int j = lane; j < n; j += 32) {
-      const double den = __dsub_rn(__dsub_rn(d[j], s), m);
-      const double x = __dmul_rn(z[j], rcp_nr(den));
-      bad |= !rcp_in_range(den);
-      if (store) vr[j] = x;
-      q = __fma_rn(x, x, q);
+    // with a stored row: pairs of components j, j + 1 from a 16-byte aligned position j0, written
+    // and rescaled with 16-byte accesses (lane 0 takes an unaligned first and an unpaired last one)
+    const int j0 = (store && kVecPairs && (((uintptr_t)vr) & 15)) ? 1 : 0;
+    const int npair = (store && kVecPairs) ? (n - j0) >> 1 : 0;
+    const int jtail = j0 + 2 * npair;
+    if (store && kVecPairs) {
+      for (int t = lane; t < npair; t += 32) {
+        const int j = j0 + 2 * t;
+        const double den0 = __dsub_rn(__dsub_rn(d[j], s), m), den1 = __dsub_rn(__dsub_rn(d[j + 1], s), m);
+        double2 x;
+        x.x = __dmul_rn(z[j], rcp_nr(den0));
+        x.y = __dmul_rn(z[j + 1], rcp_nr(den1));
+        bad |= !rcp_in_range(den0) || !rcp_in_range(den1);
+        *reinterpret_cast<double2*>(vr + j) = x;
+        q = __fma_rn(x.x, x.x, q);
+        q = __fma_rn(x.y, x.y, q);
+      }
+      if (lane == 0) {
+        // the unaligned first component (j0 = 1) and the unpaired last one (jtail = n - 1)
+        for (int e = 0; e < 2; e++) {
+          const int j = e == 0 ? (j0 ? 0 : -1) : (jtail < n ? jtail : -1);
+          if (j < 0) continue;
+          const double den = __dsub_rn(__dsub_rn(d[j], s), m);
+          const double x = __dmul_rn(z[j], rcp_nr(den));
+          bad |= !rcp_in_range(den);
+          vr[j] = x;
+          q = __fma_rn(x, x, q);
+        }
+      }
+    } else {
+      for (int j = lane; j < n; j += 32) {
+        const double den = __dsub_rn(__dsub_rn(d[j], s), m);
+        const double x = __dmul_rn(z[j], rcp_nr(den));
+        bad |= !rcp_in_range(den);
+        if (store) vr[j] = x;
+        q = __fma_rn(x, x, q);
+      }
     }
     q = group_sum<32>(q, FULL);
     bad = group_any<32>(bad, FULL);
@@ -833,29 +934,21 @@ __global__ void __launch_bounds__(256) k_vectors(Prob pb, Ws w) {
     }
     const double nrm = sqrt(q);          // ||x|| * scale
     const double c = scale / nrm;
-    if (lane == 0) {
-      // outputs in the caller's units: lambda, sigma, mu times 2^a, ||x|| times 2^(b - a)
-      const int ea = w.pexp[2 * p], eb = w.pexp[2 * p + 1];
-      double lz = w.lamz[g];
-      const double lam = isnan(lz) ? __dadd_rn(s, m) : lz;
-      const double xn = nrm / scale;
-      pb.lambda[base + row] = scalbn(lam, ea);
-      if (pb.sigma) pb.sigma[base + row] = scalbn(s, ea);
-      if (pb.mu) pb.mu[base + row] = scalbn(m, ea);
-      if (pb.xnorm) pb.xnorm[base + row] = scalbn(xn, eb - ea);
-      // the pair needs values outside the binary64 range: mu zero, subnormal or not finite
-      // (lambda within 2^-1022 of its shift in normalised units), or lambda, ||x|| not finite
-      bool out = !(fabs(m) >= 0x1p-1022) || !isfinite(m) || !isfinite(lam) || !(xn > 0.0) || !isfinite(xn) ||
-                 !isfinite(c);
-      // after a non-pole shift (R2): d_p - lambda = (d_p - sigma) - mu to a neighbouring pole
-      // cancels by more than a factor 16 -- the case that needs sigma in double the working
-      // precision (not implemented), reported like the others
-      if (w.shift[g] < 0) out = out || pole_difference_cancels(d[k], s, m) ||
-                                (k > 0 && pole_difference_cancels(d[k - 1], s, m));
-      if (out) atomicOr(w.status, ST_RANGE);
-    }
+    if (lane == 0) pair_outputs(pb, w, p, g, base, k, row, d, s, m, nrm, scale, c);
     if (!vr) continue;
-    if (!defl && !rewrite) {
+    if (!defl && !rewrite && kVecPairs) {
+      for (int t = lane; t < npair; t += 32) {
+        const int j = j0 + 2 * t;
+        double2 x = *reinterpret_cast<const double2*>(vr + j);
+        x.x = __dmul_rn(x.x, c);
+        x.y = __dmul_rn(x.y, c);
+        *reinterpret_cast<double2*>(vr + j) = x;
+      }
+      if (lane == 0) {
+        if (j0) vr[0] = __dmul_rn(vr[0], c);
+        if (jtail < n) vr[n - 1] = __dmul_rn(vr[n - 1], c);
+      }
+    } else if (!defl && !rewrite) {
       for (int j = lane; j < n; j += 32) vr[j] = __dmul_rn(vr[j], c);
     } else if (!defl) {
       for (int j = lane; j < n; j += 32) vr[j] = __dmul_rn(z[j], rcp(__dsub_rn(__dsub_rn(d[j], s), m))) * c;
@@ -1228,6 +1321,7 @@ dpr1_status dpr1_workspace_stats(void* workspace, int64_t* out, dpr1_stream_t st
   out[7] = c[C_DEFL];
   out[8] = c[C_DD];
   out[9] = c[C_SCREEN];
+  out[10] = c[C_R2DD];
   return DPR1_OK;
 }
 

@@ -17,10 +17,34 @@
 #ifndef DPR1_STORED_UNROLL
 #define DPR1_STORED_UNROLL 2
 #endif
+// consecutive bisection steps the binary32 screen may fail to settle before it is given up
+// (a failure means the midpoint fell within the screen's error window of the root; after the
+// binary64 step the next midpoint lies a quarter of the bracket away and is often settled)
+#ifndef DPR1_SCREEN_TRIES
+#define DPR1_SCREEN_TRIES 2
+#endif
 
 namespace dpr1 {
 
 constexpr int kStoredUnroll = DPR1_STORED_UNROLL;
+constexpr int kScreenTries = DPR1_SCREEN_TRIES;
+
+// ---------------------------------------------------------------------------------
+// Shifts in double the working precision (remedy R2 when no binary64 number lies between
+// lambda and a neighbouring pole, Sec. 2): sigma = s + t, an unevaluated pair of binary64
+// numbers.  The difference d_j - sigma is formed in double-double and the matrix element
+// is its binary64 rounding; with OFS = false the shift is the binary64 number s and the
+// element is fl(d_j - s).
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ dd shift_diff(double dj, double s, double t) {
+  return dd_add(two_sum(dj, -s), {-t, 0.0});
+}
+
+template <bool OFS>
+__device__ __forceinline__ double elem_diff(double dj, double s, double t) {
+  if constexpr (OFS) return shift_diff(dj, s, t).hi;
+  else return __dsub_rn(dj, s);
+}
 
 // ---------------------------------------------------------------------------------
 // Secular sums
@@ -37,15 +61,16 @@ constexpr int kStoredUnroll = DPR1_STORED_UNROLL;
 // group recomputes the sum with the range-safe reciprocal (never the case for sane data).
 // With DERIV the pass also returns dS/dnu = sum_{j != i} zz_j / (1 - nu Delta_j)^2 (for the
 // accelerated solve); i = -1 excludes no term (non-pole shifts, Delta_j = d_j - sigma).
-template <int L, bool SAFE, bool DERIV>
+// With OFS the shift is di + dlo in double the working precision (elem_diff).
+template <int L, bool SAFE, bool DERIV, bool OFS = false>
 __device__ __forceinline__ double arrow_sum_pass(const double* __restrict__ d, const double* __restrict__ zz, int n,
                                                  int i, double di, double nu, int lane, unsigned gm, bool* bad,
-                                                 double* dsum) {
+                                                 double* dsum, double dlo = 0.0) {
   double s0 = 0.0, s1 = 0.0, q0 = 0.0, q1 = 0.0;
   bool b = false;
   int j = lane;
   for (; j + L < n; j += 2 * L) {
-    double D0 = __dsub_rn(d[j], di), D1 = __dsub_rn(d[j + L], di);
+    double D0 = elem_diff<OFS>(d[j], di, dlo), D1 = elem_diff<OFS>(d[j + L], di, dlo);
     double t0 = __fma_rn(-nu, D0, 1.0), t1 = __fma_rn(-nu, D1, 1.0);
     double x0 = __dmul_rn(D0, t0), x1 = __dmul_rn(D1, t1);
     if (!SAFE && !DERIV) {
@@ -78,7 +103,7 @@ __device__ __forceinline__ double arrow_sum_pass(const double* __restrict__ d, c
     }
   }
   if (j < n) {
-    double D0 = __dsub_rn(d[j], di);
+    double D0 = elem_diff<OFS>(d[j], di, dlo);
     double t0 = __fma_rn(-nu, D0, 1.0);
     double x0 = __dmul_rn(D0, t0);
     double r0;
@@ -96,22 +121,24 @@ __device__ __forceinline__ double arrow_sum_pass(const double* __restrict__ d, c
   return group_sum<L>(__dadd_rn(s0, s1), gm);
 }
 
-template <int L>
+template <int L, bool OFS = false>
 __device__ __forceinline__ double arrow_sum(const double* __restrict__ d, const double* __restrict__ zz, int n,
-                                            int i, double di, double nu, int lane, unsigned gm) {
+                                            int i, double di, double nu, int lane, unsigned gm, double dlo = 0.0) {
   bool bad;
-  double s = arrow_sum_pass<L, false, false>(d, zz, n, i, di, nu, lane, gm, &bad, nullptr);
-  if (group_any<L>(bad, gm)) s = arrow_sum_pass<L, true, false>(d, zz, n, i, di, nu, lane, gm, &bad, nullptr);
+  double s = arrow_sum_pass<L, false, false, OFS>(d, zz, n, i, di, nu, lane, gm, &bad, nullptr, dlo);
+  if (group_any<L>(bad, gm))
+    s = arrow_sum_pass<L, true, false, OFS>(d, zz, n, i, di, nu, lane, gm, &bad, nullptr, dlo);
   return s;
 }
 
 // the sum and its derivative with respect to nu
-template <int L>
+template <int L, bool OFS = false>
 __device__ __forceinline__ double arrow_sum_d(const double* __restrict__ d, const double* __restrict__ zz, int n,
-                                              int i, double di, double nu, int lane, unsigned gm, double* dsum) {
+                                              int i, double di, double nu, int lane, unsigned gm, double* dsum,
+                                              double dlo = 0.0) {
   bool bad;
-  double s = arrow_sum_pass<L, false, true>(d, zz, n, i, di, nu, lane, gm, &bad, dsum);
-  if (group_any<L>(bad, gm)) s = arrow_sum_pass<L, true, true>(d, zz, n, i, di, nu, lane, gm, &bad, dsum);
+  double s = arrow_sum_pass<L, false, true, OFS>(d, zz, n, i, di, nu, lane, gm, &bad, dsum, dlo);
+  if (group_any<L>(bad, gm)) s = arrow_sum_pass<L, true, true, OFS>(d, zz, n, i, di, nu, lane, gm, &bad, dsum, dlo);
   return s;
 }
 
@@ -124,10 +151,10 @@ __device__ __forceinline__ double arrow_sum_d(const double* __restrict__ d, cons
 // has the sign of t_a t_b times that sign and no numerator cancels.  Each lane reads only the
 // entries it wrote (index j = lane mod L).  A numerator or denominator outside the fast
 // reciprocal's range (extreme data) sends the group to the range-safe sum from d and zz.
-template <int L>
+template <int L, bool OFS = false>
 __device__ __forceinline__ double stored_sum(const double* __restrict__ Ds, const double* __restrict__ us,
                                              const double* __restrict__ d, const double* __restrict__ zz, int n,
-                                             int i, double di, double nu, int lane, unsigned gm) {
+                                             int i, double di, double nu, int lane, unsigned gm, double dlo = 0.0) {
   double s0 = 0.0;
   bool b = false;
   int j = lane;
@@ -157,7 +184,7 @@ __device__ __forceinline__ double stored_sum(const double* __restrict__ Ds, cons
   const double s = group_sum<L>(s0, gm);
   if (group_any<L>(b, gm)) {
     bool bad;
-    return arrow_sum_pass<L, true, false>(d, zz, n, i, di, nu, lane, gm, &bad, nullptr);
+    return arrow_sum_pass<L, true, false, OFS>(d, zz, n, i, di, nu, lane, gm, &bad, nullptr, dlo);
   }
   return s;
 }
@@ -228,10 +255,11 @@ __device__ __forceinline__ bool store_elem(double* __restrict__ Ds, double* __re
 // The sum and its derivative dS/dnu = sum_j zz_j / t_j^2 = sum_j (u_j / t_j)(Delta_j / t_j) from
 // the stored elements (the accelerated solve): one reciprocal of t_j per term, 8 binary64
 // instructions against 10 when Delta_j and Delta_j t_j are formed at every evaluation.
-template <int L>
+template <int L, bool OFS = false>
 __device__ __forceinline__ double stored_sum_d(const double* __restrict__ Ds, const double* __restrict__ us,
                                                const double* __restrict__ d, const double* __restrict__ zz, int n,
-                                               int i, double di, double nu, int lane, unsigned gm, double* dsum) {
+                                               int i, double di, double nu, int lane, unsigned gm, double* dsum,
+                                               double dlo = 0.0) {
   double s0 = 0.0, s1 = 0.0, q0 = 0.0, q1 = 0.0;
   bool b = false;
   int j = lane;
@@ -259,26 +287,28 @@ __device__ __forceinline__ double stored_sum_d(const double* __restrict__ Ds, co
   *dsum = group_sum<L>(__dadd_rn(q0, q1), gm);
   if (group_any<L>(b, gm)) {
     bool bad;
-    return arrow_sum_pass<L, true, true>(d, zz, n, i, di, nu, lane, gm, &bad, dsum);
+    return arrow_sum_pass<L, true, true, OFS>(d, zz, n, i, di, nu, lane, gm, &bad, dsum, dlo);
   }
   return s;
 }
 
 // The secular sums from the stored elements when the group has them (Ds != nullptr), else
 // formed from d and zz at every evaluation.
-template <int L>
+template <int L, bool OFS = false>
 __device__ __forceinline__ double elem_sum(const double* __restrict__ Ds, const double* __restrict__ us,
                                            const double* __restrict__ d, const double* __restrict__ zz, int n, int i,
-                                           double di, double nu, int lane, unsigned gm) {
-  return Ds ? stored_sum<L>(Ds, us, d, zz, n, i, di, nu, lane, gm) : arrow_sum<L>(d, zz, n, i, di, nu, lane, gm);
+                                           double di, double nu, int lane, unsigned gm, double dlo = 0.0) {
+  return Ds ? stored_sum<L, OFS>(Ds, us, d, zz, n, i, di, nu, lane, gm, dlo)
+            : arrow_sum<L, OFS>(d, zz, n, i, di, nu, lane, gm, dlo);
 }
 
-template <int L>
+template <int L, bool OFS = false>
 __device__ __forceinline__ double elem_sum_d(const double* __restrict__ Ds, const double* __restrict__ us,
                                              const double* __restrict__ d, const double* __restrict__ zz, int n,
-                                             int i, double di, double nu, int lane, unsigned gm, double* dsum) {
-  return Ds ? stored_sum_d<L>(Ds, us, d, zz, n, i, di, nu, lane, gm, dsum)
-            : arrow_sum_d<L>(d, zz, n, i, di, nu, lane, gm, dsum);
+                                             int i, double di, double nu, int lane, unsigned gm, double* dsum,
+                                             double dlo = 0.0) {
+  return Ds ? stored_sum_d<L, OFS>(Ds, us, d, zz, n, i, di, nu, lane, gm, dsum, dlo)
+            : arrow_sum_d<L, OFS>(d, zz, n, i, di, nu, lane, gm, dsum, dlo);
 }
 
 // Same terms with Delta_j = d_j - sigma for a non-pole shift (no excluded index):
@@ -301,13 +331,15 @@ __device__ __forceinline__ double shift_sum(const double* __restrict__ d, const 
 // With Ds != nullptr it also stores Dh = fl(d_j - s) and q = zz_j / Dh (0 and 0 at skip): the
 // elements of the inverse that stored_sum reads; with Df their binary32 copies (store_elem),
 // and *scr_ok tells whether the binary32 screen applies to them.
-template <int L>
+// With OFS the shift is s + slo in double the working precision: the difference is formed by
+// shift_diff and the stored element is its binary64 rounding (elem_diff).
+template <int L, bool OFS = false>
 __device__ __forceinline__ dd dd_pole_sum(const double* __restrict__ d, const double* __restrict__ zz,
                                           const double* __restrict__ zl, int n, int skip, double s, int lane,
                                           unsigned gm, double* sq, double* cub = nullptr,
                                           double* __restrict__ Ds = nullptr, double* __restrict__ us = nullptr,
                                           float* __restrict__ Df = nullptr, float* __restrict__ uf = nullptr,
-                                          bool* scr_ok = nullptr) {
+                                          bool* scr_ok = nullptr, double slo = 0.0) {
   double hi = 0.0, lo = 0.0, q2 = 0.0, c3 = 0.0;
   const double ms = -s;
   bool ok = Df != nullptr;
@@ -317,10 +349,17 @@ __device__ __forceinline__ dd dd_pole_sum(const double* __restrict__ d, const do
       continue;
     }
     const double dj = d[j];
-    const bool ge = fabs(dj) >= fabs(ms);
-    const double big = ge ? dj : ms, small = ge ? ms : dj;
-    const double Dh = __dadd_rn(big, small);
-    const double Dl = __dsub_rn(small, __dsub_rn(Dh, big));
+    double Dh, Dl;
+    if constexpr (OFS) {
+      const dd D = shift_diff(dj, s, slo);
+      Dh = D.hi;
+      Dl = D.lo;
+    } else {
+      const bool ge = fabs(dj) >= fabs(ms);
+      const double big = ge ? dj : ms, small = ge ? ms : dj;
+      Dh = __dadd_rn(big, small);
+      Dl = __dsub_rn(small, __dsub_rn(Dh, big));
+    }
     const double Zh = zz[j], Zl = zl[j];
     const double r = rcp(Dh);
     const double q = __dmul_rn(Zh, r);
@@ -378,6 +417,7 @@ __device__ double bisect(Phi phi, double side, double floor, double alo, double 
   bool have_lo = false, have_hi = false;    // the end point was evaluated (its side is known)
   bool scr_lo = false, scr_hi = false;      // its value came from the screen
   bool scr_on = true;
+  int scr_fail = 0;                         // consecutive steps the screen did not settle
   int it = 0, pushes = 0, nscr = 0;
   // ends that come from a soft estimate (eager_*) are checked before the bisection
   if (eager_hi) {
@@ -410,7 +450,8 @@ __device__ double bisect(Phi phi, double side, double floor, double alo, double 
       bool sc = false;
       if (scr_on) {
         sc = screen(side * dfrom(mid), &g);
-        scr_on = sc;
+        scr_fail = sc ? 0 : scr_fail + 1;
+        scr_on = scr_fail < kScreenTries;
       }
       if (!sc) g = phi(side * dfrom(mid));
       else nscr++;
@@ -808,24 +849,30 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
 // leftmost when gamma < 0; h < 0 on the pole side in both cases.  Returns mu = 1/nu
 // (lambda = sigma + mu); f(sigma) == 0 in double-double gives mu = 0.
 // ---------------------------------------------------------------------------------
-template <int L>
+// With OFS the shift is sigma + sigma_lo in double the working precision (remedy R2 when no
+// binary64 number lies between lambda and a neighbouring pole): the elements of the DPR1 matrix
+// are the binary64 roundings of the double-double differences d_j - sigma (elem_diff) and
+// f(sigma) is formed from those differences in double-double.
+template <int L, bool OFS = false>
 __device__ double solve_nonpole(const double* __restrict__ d, const double* __restrict__ zl,
                                 const double* __restrict__ zz, int n, double rho, double sigma, int above, int below,
                                 int cap, bool fast, int lane, unsigned gm, bool* ok, int* steps_out = nullptr,
-                                double* __restrict__ Ds = nullptr, double* __restrict__ us = nullptr) {
+                                double* __restrict__ Ds = nullptr, double* __restrict__ us = nullptr,
+                                double sigma_lo = 0.0) {
   // above / below: indices of the poles next to sigma (-1: none on that side)
   double un2, cub;
   // the double-double pass also stores the elements d_j - sigma and zeta_j^2 / (d_j - sigma)
   // for the solve when the group has a buffer (Ds, us as for solve_pole)
-  dd acc = dd_pole_sum<L>(d, zz, zl, n, -1, sigma, lane, gm, &un2, &cub, Ds, us);
+  dd acc = dd_pole_sum<L, OFS>(d, zz, zl, n, -1, sigma, lane, gm, &un2, &cub, Ds, us, nullptr, nullptr, nullptr,
+                               sigma_lo);
   dd f = dd_add({1.0, 0.0}, two_prod(acc.hi, rho));
   f = dd_add(f, {__dmul_rn(acc.lo, rho), 0.0});
   *ok = true;
   if (f.hi == 0.0 && f.lo == 0.0) return 0.0;
   double gamma = dd_to_double(dd_div({-rho, 0.0}, f));
   // extreme e_j = 1/(d_j - sigma): the poles next to sigma
-  const double emax = above >= 0 ? 1.0 / __dsub_rn(d[above], sigma) : -INFINITY;
-  const double emin = below >= 0 ? 1.0 / __dsub_rn(d[below], sigma) : INFINITY;
+  const double emax = above >= 0 ? 1.0 / elem_diff<OFS>(d[above], sigma, sigma_lo) : -INFINITY;
+  const double emin = below >= 0 ? 1.0 / elem_diff<OFS>(d[below], sigma, sigma_lo) : INFINITY;
   // Rayleigh quotient of u: (sum_j e_j u_j^2)/||u||^2 + gamma ||u||^2, a lower bound of the
   // largest and an upper bound of the smallest eigenvalue of diag(e) + gamma u u^T; with
   // sigma next to lambda, gamma ||u||^2 dominates and the bracket below is narrow.
@@ -848,13 +895,13 @@ __device__ double solve_nonpole(const double* __restrict__ d, const double* __re
   if (fast) {
     // F(t) = -h(side * t) = |gamma| (Psi(t) - 1/|gamma|), Psi = -side S; model pole: the
     // largest e_j on |nu| (with no pole above sigma, the one farthest below it)
-    const double E = (gamma > 0.0) ? (above >= 0 ? emax : 1.0 / __dsub_rn(d[n - 1], sigma))
-                                   : (below >= 0 ? -emin : -1.0 / __dsub_rn(d[0], sigma));
+    const double E = (gamma > 0.0) ? (above >= 0 ? emax : 1.0 / elem_diff<OFS>(d[n - 1], sigma, sigma_lo))
+                                   : (below >= 0 ? -emin : -1.0 / elem_diff<OFS>(d[0], sigma, sigma_lo));
     const double ag = fabs(gamma);
     auto ev = [&](double t, bool want, double* psi, double* dpsi) {
       double dS = 0.0;
-      const double S = want ? elem_sum_d<L>(Ds, us, d, zz, n, -1, sigma, side * t, lane, gm, &dS)
-                            : elem_sum<L>(Ds, us, d, zz, n, -1, sigma, side * t, lane, gm);
+      const double S = want ? elem_sum_d<L, OFS>(Ds, us, d, zz, n, -1, sigma, side * t, lane, gm, &dS, sigma_lo)
+                            : elem_sum<L, OFS>(Ds, us, d, zz, n, -1, sigma, side * t, lane, gm, sigma_lo);
       *psi = -side * S;
       *dpsi = -dS;
       return -__fma_rn(gamma, S, 1.0);
@@ -862,7 +909,7 @@ __device__ double solve_nonpole(const double* __restrict__ d, const double* __re
     nu = side * accel_solve(ev, floor, alo, ahi, E, -1.0 / ag, 0.0, ag, cap, ok, &steps);
   } else {
     auto phi = [&](double v) {
-      const double S = elem_sum<L>(Ds, us, d, zz, n, -1, sigma, v, lane, gm);
+      const double S = elem_sum<L, OFS>(Ds, us, d, zz, n, -1, sigma, v, lane, gm, sigma_lo);
       return __fma_rn(gamma, S, 1.0);
     };
     nu = bisect(phi, side, floor, alo, ahi, false, cap, ok, &steps);
