@@ -367,8 +367,10 @@ DPR1_API dpr1_status dpr1_eig_noalloc(int64_t n, const double* d, const double* 
  *   kernel, 5 evaluations in the remedy kernel, 6 eigenvalues recomputed from A^{-1},
  *   7 deflated pairs, 8 corners b formed in double-double by the bisection kernel,
  *   9 bisection steps (of those counted in 4 and 5) settled by the binary32 screen,
- *   10 R2 remedies that formed their shift in double the working precision (of those in 3).
- *   `out` holds 11 values.
+ *   10 R2 remedies that formed their shift in double the working precision (of those in 3),
+ *   11 screened steps (of those in 9) whose binary32 value exceeded the screen's error bound by
+ *   less than a factor 2.
+ *   `out` holds 12 values.
  */
 DPR1_API dpr1_status dpr1_workspace_stats(void* workspace, int64_t* out, dpr1_stream_t stream);
 

@@ -167,6 +167,7 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
                                        bool screen = false) {
   PoleResult r;
   r.screened = 0;
+  r.screened_near = 0;
   double sq;
   const double di = d[i];
   // the corner's pass also stores the elements of the inverse when the group has a buffer (and
@@ -249,6 +250,7 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
       const double G = __dadd_rn(X, inv / v);
       const double tol = 1.01 * (inv * (E32 + E64 + 0x1p-51 * aS) + 0x1p-51 * fabs(X));
       if (!(fabs(G) > tol)) return false;
+      if (fabs(G) <= 2.0 * tol) r.screened_near++;
       *g = G;
       return true;
     };
@@ -327,6 +329,7 @@ __global__ void __launch_bounds__(256) k_arrow_solve(int n, const double* __rest
                                         Dbuf ? Dbuf + n : nullptr, screen);
     if (lane == 0) {
       if (pr.screened) atomicAdd(&w.counters[C_SCREEN], (unsigned)pr.screened);
+      if (pr.screened_near) atomicAdd(&w.counters[C_SCREEN_NEAR], (unsigned)pr.screened_near);
       w.sig[k] = d[i];
       w.mu[k] = pr.mu;
       w.shift[k] = i;
@@ -503,6 +506,7 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_arrow_fix(int n, const do
       if (!pr.ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
       if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)pr.steps);
       if (lane == 0 && pr.screened) atomicAdd(&w.counters[C_SCREEN], (unsigned)pr.screened);
+      if (lane == 0 && pr.screened_near) atomicAdd(&w.counters[C_SCREEN_NEAR], (unsigned)pr.screened_near);
       new_sig = d[o]; new_mu = pr.mu; new_shift = o; done = true;
     }
     if (!done) {

@@ -44,6 +44,11 @@
 #ifndef DPR1_FIX_WARP_MAX_N
 #define DPR1_FIX_WARP_MAX_N 2048
 #endif
+// and so do fewer problems up to this mean size (each flagged eigenvalue's evaluations are then
+// short, and a block-wide group would pay a barrier per evaluation)
+#ifndef DPR1_FIX_SMALL_N
+#define DPR1_FIX_SMALL_N 1024
+#endif
 
 namespace dpr1 {
 
@@ -128,7 +133,8 @@ size_t term_bytes(int64_t total, int64_t nprob) {
   const double avg = (double)total / (double)nprob;
   const int64_t gpb = (32 * 8) / default_lanes(avg);
   int64_t groups = (int64_t)sm_count() * 2 * gpb;
-  const int64_t need = (total + gpb - 1) / gpb * gpb;
+  // a launch with blocks of gpb' <= gpb groups has at most total + gpb' - 1 of them
+  const int64_t need = total + gpb - 1;
   if (groups > need) groups = need;
   int64_t tn = total;
   if (nprob > 1) {
@@ -481,6 +487,7 @@ __global__ void __launch_bounds__(256, DPR1_SOLVE_MIN_BLOCKS)
     if (lane == 0) {
       if (pr.dd) atomicAdd(&w.counters[C_DD], 1u);
       if (pr.screened) atomicAdd(&w.counters[C_SCREEN], (unsigned)pr.screened);
+      if (pr.screened_near) atomicAdd(&w.counters[C_SCREEN_NEAR], (unsigned)pr.screened_near);
       w.sig[g] = d[i];
       w.mu[g] = pr.mu;
       w.shift[g] = i;
@@ -622,6 +629,7 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double
       if (!pr.ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
       if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)pr.steps);
       if (lane == 0 && pr.screened) atomicAdd(&w.counters[C_SCREEN], (unsigned)pr.screened);
+      if (lane == 0 && pr.screened_near) atomicAdd(&w.counters[C_SCREEN_NEAR], (unsigned)pr.screened_near);
       new_sig = d[o]; new_mu = pr.mu; new_shift = o; done = true;
     }
     if (!done) {
@@ -1079,6 +1087,8 @@ Options resolve(const dpr1_options* o) {
   r.T_zero = s->T_zero > 0 ? s->T_zero : def.T_zero;
   r.lanes = (s->lanes == 8 || s->lanes == 16 || s->lanes == 32) ? s->lanes : 0;
   r.warps = s->warps_per_block > 0 && s->warps_per_block <= 8 ? s->warps_per_block : 8;
+  r.warps_auto = !(s->warps_per_block > 0 && s->warps_per_block <= 8);
+  r.bps_auto = !(s->blocks_per_sm > 0 && s->blocks_per_sm <= 8);
   r.bps = s->blocks_per_sm > 0 && s->blocks_per_sm <= 8 ? s->blocks_per_sm : 2;
   r.cap = s->max_bisect >= 1 && s->max_bisect <= 4096 ? s->max_bisect : def.max_bisect;
   r.events = s->phase_events;
@@ -1094,29 +1104,31 @@ static void record(const Options& o, int t, cudaStream_t st) {
 }
 
 template <int L>
-static void launch_solve_fix(const Prob& pb, const Ws& w, const Options& o, int grid, double avg_n,
+static void launch_solve_fix(const Prob& pb, const Ws& w, const Options& o, int grid, int warps, double avg_n,
                              cudaStream_t st) {
   record(o, 0, st);
-  k_solve<L><<<grid, 32 * o.warps, 0, st>>>(pb, w, o.cap, o.fast, o.dd_mode, o.T_kappa, o.screen);
+  k_solve<L><<<grid, 32 * warps, 0, st>>>(pb, w, o.cap, o.fast, o.dd_mode, o.T_kappa, o.screen);
   record(o, 1, st);
   int64_t cg = (pb.total + 255) / 256;
   if (cg > sm_count() * 8) cg = sm_count() * 8;
   k_classify<<<cg > 0 ? (int)cg : 1, 256, 0, st>>>(pb, w, o.T_Knu);
-  if (pb.P < 64 || avg_n > DPR1_FIX_WARP_MAX_N) {
-    // few flagged eigenvalues (one or a few problems, or large ones): a block-wide group
-    // each finishes every item soonest
+  if ((pb.P < 64 && avg_n > DPR1_FIX_SMALL_N) || avg_n > DPR1_FIX_WARP_MAX_N) {
+    // few flagged eigenvalues of large problems: a block-wide group each finishes every item
+    // soonest
     int64_t fg = pb.total;                            // at most one block per eigenpair
     if (fg > sm_count() * DPR1_FIX_BLOCKS_PER_SM) fg = sm_count() * DPR1_FIX_BLOCKS_PER_SM;
     if (w.terms && fg > w.term_slots) fg = w.term_slots;   // every group with a buffer
     k_fix<DPR1_FIX_THREADS><<<fg > 0 ? (int)fg : 1, DPR1_FIX_THREADS, 0, st>>>(pb, w, o.T_Knu, o.cap, o.fast,
                                                                                   o.dd_mode, o.T_kappa, o.screen);
   } else {
-    // many small problems, many flagged items: one warp each (a block-wide group would
-    // leave most of its threads idle and pay a barrier per evaluation)
-    int64_t fg = (pb.total + 7) / 8;                  // at most one warp per eigenpair
-    if (fg > sm_count() * 4) fg = sm_count() * 4;
-    if (w.terms && fg * 8 > w.term_slots) fg = w.term_slots / 8 > 0 ? w.term_slots / 8 : 1;
-    k_fix<32><<<fg > 0 ? (int)fg : 1, 256, 0, st>>>(pb, w, o.T_Knu, o.cap, o.fast, o.dd_mode, o.T_kappa, o.screen);
+    // small problems, or many of them: one warp each (a block-wide group would leave most of
+    // its threads idle and pay a barrier per evaluation), in blocks of one warp, which the block
+    // scheduler spreads over the SMs -- with 8-warp blocks the first warps to reach the work
+    // counter, and so a few flagged eigenvalues, would share the binary64 pipes of a few SMs
+    int64_t fg = pb.total;                            // at most one warp per eigenpair
+    if (fg > sm_count() * 32) fg = sm_count() * 32;
+    if (w.terms && fg > w.term_slots) fg = w.term_slots;   // every group with a buffer
+    k_fix<32><<<fg > 0 ? (int)fg : 1, 32, 0, st>>>(pb, w, o.T_Knu, o.cap, o.fast, o.dd_mode, o.T_kappa, o.screen);
   }
   record(o, 2, st);
 }
@@ -1148,9 +1160,22 @@ static dpr1_status run_table(const Prob& pb, void* workspace, size_t wbytes, con
   if (dg > sms * 8) dg = sms * 8;
   k_deflate<<<dg > 0 ? dg : 1, 128, 0, st>>>(pb, w);
   int L = o.lanes ? o.lanes : default_lanes(avg_n);
-  int groups_per_block = (32 * o.warps) / L;
+  // Shape of the solve kernel.  Its time is set by the binary64 pipe of the busiest SM, so the
+  // eigenvalues must spread evenly over the SMs: with fewer lane groups than 8-warp blocks on
+  // every SM can hold, blocks of fewer warps, at most one per SM; with fewer than two such
+  // blocks per SM, one block per SM whose groups take eigenvalues from the work counter
+  // (a partly filled second wave would load some SMs twice).  Options may fix the shape.
+  int warps = o.warps;
+  int bps = o.bps;
+  const int64_t lanes_total = pb.total * L;
+  if (o.warps_auto) {
+    const int64_t w_need = (lanes_total + 32 * (int64_t)sms - 1) / (32 * (int64_t)sms);
+    warps = w_need >= 8 ? 8 : (int)(w_need > 0 ? w_need : 1);
+    if (o.bps_auto && lanes_total < (int64_t)32 * 8 * sms * bps) bps = 1;
+  }
+  int groups_per_block = (32 * warps) / L;
   int64_t want_blocks = (pb.total + groups_per_block - 1) / groups_per_block;
-  int grid = sms * o.bps;
+  int grid = sms * bps;
   if (want_blocks < grid) grid = want_blocks > 0 ? (int)want_blocks : 1;
   // the rest of the workspace holds the stored elements of the inverse for the solves: one
   // buffer for every lane group of the launch (for one problem, of its order), or none at all.
@@ -1167,9 +1192,9 @@ static dpr1_status run_table(const Prob& pb, void* workspace, size_t wbytes, con
       w.term_slots = groups;
     }
   }
-  if (L == 8) launch_solve_fix<8>(pb, w, o, grid, avg_n, st);
-  else if (L == 16) launch_solve_fix<16>(pb, w, o, grid, avg_n, st);
-  else launch_solve_fix<32>(pb, w, o, grid, avg_n, st);
+  if (L == 8) launch_solve_fix<8>(pb, w, o, grid, warps, avg_n, st);
+  else if (L == 16) launch_solve_fix<16>(pb, w, o, grid, warps, avg_n, st);
+  else launch_solve_fix<32>(pb, w, o, grid, warps, avg_n, st);
   k_zero_detect<<<sgrid, 256, 0, st>>>(pb, w, o.T_zero);
   k_zero_solve<<<4, 128, 0, st>>>(pb, w, o.cap, o.fast);
   k_defl_positions<<<sgrid, 256, 0, st>>>(pb, w);
@@ -1322,6 +1347,7 @@ dpr1_status dpr1_workspace_stats(void* workspace, int64_t* out, dpr1_stream_t st
   out[8] = c[C_DD];
   out[9] = c[C_SCREEN];
   out[10] = c[C_R2DD];
+  out[11] = c[C_SCREEN_NEAR];
   return DPR1_OK;
 }
 

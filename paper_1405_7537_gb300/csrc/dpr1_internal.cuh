@@ -46,6 +46,8 @@ struct Ws {
 struct Options {
   double T_Knu, T_zero;
   int lanes, warps, bps, cap;
+  bool warps_auto;   // warps per block of the solve kernel left to the library
+  bool bps_auto;     // and its blocks per SM
   void* const* events;
   bool fast;   // accelerated solve instead of bisection
   int dd_mode;       // corner b: 1 double-double when kappa_nu > T_kappa n, 2 always
@@ -56,7 +58,8 @@ struct Options {
 // hdr counters (Ws::counters index)
 enum : int {
   C_FIX_N = 1, C_FIX_Q = 2, C_ZERO_N = 3, C_EVAL_SOLVE = 4, C_EVAL_FIX = 5,
-  C_R2 = 6, C_R1 = 7, C_SOLVED = 8, C_DEFL = 9, C_DD = 10, C_SCREEN = 11, C_R2DD = 12
+  C_R2 = 6, C_R1 = 7, C_SOLVED = 8, C_DEFL = 9, C_DD = 10, C_SCREEN = 11, C_R2DD = 12,
+  C_SCREEN_NEAR = 13
 };
 
 // per-problem bits (Ws::pst)

@@ -652,6 +652,7 @@ struct PoleResult {
   bool dd;     // b was formed in double-double
   int steps;
   int screened;   // bisection steps settled by the binary32 screen
+  int screened_near;   // of those, steps whose margin over the screen's bound was below 2
 };
 
 // How the corner b is formed (Sec. 2.3): mode 1 in double the working precision when kappa_nu of
@@ -736,6 +737,7 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
                                  bool screen = false) {
   PoleResult r;
   r.screened = 0;
+  r.screened_near = 0;
   double wn2;
   bool used_dd, scr_ok = false;
   // the binary32 copies follow the two binary64 arrays (us = Ds + n)
@@ -824,6 +826,7 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
       const double tol = 1.01 * inv_zi2 * (E32 + E64 + 0x1p-51 * aS);
       const double G = __dsub_rn(__dsub_rn(b, v), __dmul_rn(S32, inv_zi2));
       if (!(fabs(G) > tol)) return false;
+      if (fabs(G) <= 2.0 * tol) r.screened_near++;
       *g = G;
       return true;
     };

@@ -208,6 +208,44 @@ def adjacent_poles(seed):
     return d, z, float(10.0 ** rng.uniform(-1.0, 1.0))
 
 
+def screen_stress(seed):
+    """Problems that put the binary32 screen of the bisection at its limits (kind = seed % 3):
+    0: clusters of poles at relative spacing 2^-s, s ~ U{18..22}, weights +-10^U(-8, 0) and
+       rho = 10^U(-2, 2);
+    1: a cluster of tiny poles 2^-70 (1 + j 2^-9) (differences near 2^-79) among poles of size
+       about 1, weights +-2^U(-40, -10): the stored differences and weights over differences
+       reach both ends of the screen's binary32 range (2^-80 and 2^60);
+    2: weights +-2^U(-31, -27) next to O(1) ones with rho = 1: eigenvalues within about 2^-58 of
+       their poles, so |nu| lies on both sides of the screen's limit 2^60."""
+    rng = np.random.default_rng(seed)
+    kind = seed % 3
+    if kind == 0:
+        n = int(rng.integers(200, 600))
+        cs = rng.uniform(-1.0, 1.0, max(1, n // 20))
+        d = []
+        while len(d) < n:
+            c = float(rng.choice(cs))
+            s = int(rng.integers(18, 23))
+            m = int(rng.integers(2, 12))
+            d += [c * (1.0 + k * 2.0 ** -s) for k in range(m)]
+        d = np.unique(np.array(d[:n]))[::-1].copy()
+        z = rng.choice([1.0, -1.0], d.size) * 10.0 ** rng.uniform(-8.0, 0.0, d.size)
+        return d, z, float(10.0 ** rng.uniform(-2.0, 2.0))
+    if kind == 1:
+        m = int(rng.integers(20, 60))
+        tiny = 2.0 ** -70 * (1.0 + np.arange(m) * 2.0 ** -9)
+        big = rng.uniform(-1.0, 1.0, int(rng.integers(40, 120)))
+        d = np.unique(np.concatenate([tiny, big]))[::-1].copy()
+        z = rng.choice([1.0, -1.0], d.size) * 2.0 ** rng.uniform(-40.0, -10.0, d.size)
+        return d, z, 1.0
+    n = int(rng.integers(100, 400))
+    d = _sorted_distinct_uniform(rng, n)
+    small = rng.random(n) < 0.5
+    z = np.where(small, 2.0 ** rng.uniform(-31.0, -27.0, n), rng.uniform(0.1, 1.0, n))
+    z *= rng.choice([1.0, -1.0], n)
+    return d, z, 1.0
+
+
 def arrowhead(n=16384, seed=6):
     """A real symmetric arrowhead [diag(d) z; z^T alpha] of order n + 1: d ~ U(-1, 1) sorted
     decreasing and distinct, z ~ U(-1, 1) redrawn while |z| <= 1e-3, alpha ~ U(-1, 1)."""

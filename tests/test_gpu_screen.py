@@ -167,3 +167,32 @@ def test_screen_fuzz(B):
                 r = B.eig(cu(d), cu(z), rho, options=o, check=False)
             out.append({k: v.cpu().numpy() for k, v in r.items() if v is not None})
         same_bits(out[0], out[1])
+
+
+def test_screen_at_its_bound(B):
+    """Steps placed where the screen's bound is tight (workloads.screen_stress): pole clusters at
+    relative spacing 2^-18 to 2^-22, tiny poles whose differences and weight quotients reach the
+    ends of the screen's binary32 range (2^-80, 2^60), and eigenvalues within about 2^-58 of
+    their poles (|nu| on both sides of the screen's limit 2^60).  Every output bit is the same
+    with the screen on and off, for single problems and their arrowheads, while many screened
+    steps cleared the bound by less than a factor 2 (the counter of such steps)."""
+    near = screened = 0
+    for seed in range(24):
+        d, z, rho = W.screen_stress(seed)
+        on, st = solve(B, d, z, rho, 1)
+        off, _ = solve(B, d, z, rho, 0)
+        same_bits(on, off)
+        near += st["screened_near_bound"]
+        screened += st["screened"]
+        if seed % 4 == 0:
+            alpha = float(np.random.default_rng(seed).uniform(-1, 1))
+            res = []
+            for screen in (1, 0):
+                ws = B.arrow_workspace(d.size)
+                r = B.eig_arrowhead(cu(d), cu(z), alpha, options=B.default_options(screen=screen), ws=ws,
+                                    check=False)
+                res.append({k: v.cpu().numpy() for k, v in r.items() if v is not None})
+                if screen:
+                    near += B.workspace_stats(ws)["screened_near_bound"]
+            same_bits(res[0], res[1])
+    assert screened > 0 and near >= 100, (near, screened)
