@@ -814,9 +814,27 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
     };
     // The screen settles a step when its g = fl(fl(b - v) - fl(S32 inv_zi2)) exceeds every
     // way the decision could differ from phi's: |S32 - S| <= E32 (screen_sum), |S64 - S| <= E64
-    // for phi's binary64 sum (at most (m + 64) 2^-52 of sum_j |T_j| <= A, m = ceil(n / L) terms
-    // per lane: twice the count of its roundings), and the roundings of the two products.
-    // fl(x - y) has the sign of x - y, so phi's sign then equals the sign of g.
+    // for phi's binary64 sum, and the roundings of the two products.  fl(x - y) has the sign of
+    // x - y, so phi's sign then equals the sign of g.  S is the exact sum of T_j = u_j / t_j over
+    // the stored elements, t_j = 1 - v Delta_j, and E64 = (m + 64) 2^-52 A, A >= sum_j |T_j|,
+    // m = ceil(n / L) terms per lane, covers each way phi can form its sum (u = 2^-53):
+    //  - stored_sum: t_j by one fma (relative error u: the fma rounds the exact 1 - v Delta_j
+    //    once), each group of four terms as one quotient of products of like sign (numerator
+    //    and denominator 3 roundings each, the one-ulp reciprocal and the product: at most 10u
+    //    of the group's sum of |T_j|), groups accumulated by fma (m/4 roundings) and the lane
+    //    group's sum tree (log2 L <= 5 levels): in all at most (m/4 + 15) u A;
+    //  - the range-safe fallback (terms rebuilt from d and zz): the same Delta_j = fl(d_j - d_i)
+    //    as stored, one more rounding per term than the stored u_j = fl(zz_j / Delta_j) carries
+    //    (2u), and five per term of its own: at most (m + 12) u A.  It runs only when a
+    //    numerator or denominator leaves the fast reciprocal's range, which the screen's own
+    //    range checks exclude: with |Delta| in [2^-80, 2^40), |u| in [2^-80, 2^60) and |v| <= 2^60,
+    //    |t| < 2^101, at most one t of a group lies below 2^-54 (distinct poles), and a non-zero
+    //    t not below 2^-106 (t is 1 - v Delta rounded once), so numerators and denominators lie
+    //    between 2^-300 and 2^410 unless some t is zero -- which a step the screen settles
+    //    excludes (|v Delta / t| <= 2^20 there): at such a step the fallback does not occur;
+    //  - block-wide groups of the remedies (L = 256): the warp trees and the sum of the 8 warp
+    //    partials, 13 levels, with m = ceil(n / 256): within (m/4 + 23) u A.
+    // All lie below (m + 64) 2u A.
     const double mlane = (double)((n + L - 1) / L);
     auto scr = [&](double v, double* g) -> bool {
       if (!scr_ok) return false;
