@@ -117,10 +117,11 @@ DPR1_API const char* dpr1_status_string(dpr1_status s);
 /*
  * Bytes of workspace for dpr1_eig on a problem of order n (the workspace must be
  * 256-byte aligned; its contents need not be initialised).  The size includes, at the end,
- * one buffer of 2n doubles per lane group of the solve kernel's default launch on the
+ * one buffer of 32n bytes per lane group of the solve kernel's default launch on the
  * current device (16 groups per SM for n > 384): there each group stores the elements of
  * the inverse of its shifted matrix, Delta_j = d_j - d_i and zeta_j^2 / Delta_j of Eq. (invAi),
- * once per eigenvalue, and every bisection step reads them instead of forming them again.
+ * once per eigenvalue (in binary64 and as pairs of binary32 numbers for the screens of the
+ * bisection steps), and every bisection step reads them instead of forming them again.
  * These buffers are optional: a smaller workspace is accepted down to the part without
  * them (every evaluation of the secular function then forms the elements again, with the same accuracy
  * bound); below that part the call returns DPR1_ERR_WORKSPACE.
@@ -368,9 +369,9 @@ DPR1_API dpr1_status dpr1_eig_noalloc(int64_t n, const double* d, const double* 
  *   7 deflated pairs, 8 corners b formed in double-double by the bisection kernel,
  *   9 bisection steps (of those counted in 4 and 5) settled by the binary32 screen,
  *   10 R2 remedies that formed their shift in double the working precision (of those in 3),
- *   11 screened steps (of those in 9) whose binary32 value exceeded the screen's error bound by
- *   less than a factor 2.
- *   `out` holds 12 values.
+ *   11 screened steps (of those in 9) whose screened value exceeded the screen's error bound by
+ *   less than a factor 2, 12 steps (of those in 9) settled by the double-float screen.
+ *   `out` holds 13 values.
  */
 DPR1_API dpr1_status dpr1_workspace_stats(void* workspace, int64_t* out, dpr1_stream_t stream);
 

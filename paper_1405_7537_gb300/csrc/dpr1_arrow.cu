@@ -168,14 +168,14 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
   PoleResult r;
   r.screened = 0;
   r.screened_near = 0;
+  r.screened_df = 0;
   double sq;
   const double di = d[i];
   // the corner's pass also stores the elements of the inverse when the group has a buffer (and
   // their binary32 copies for the screen, after the two binary64 arrays: us = Ds + n)
-  float* const Df = (Ds && screen && !fast) ? (float*)(us + n) : nullptr;
-  float* const uf = Df ? Df + n : nullptr;
+  float* const F = (Ds && screen && !fast) ? (float*)(us + n) : nullptr;
   bool scr_ok = false;
-  dd acc = dd_pole_sum<L>(d, zz, zl, n, i, di, lane, gm, &sq, nullptr, Ds, us, Df, uf, &scr_ok);
+  dd acc = dd_pole_sum<L>(d, zz, zl, n, i, di, lane, gm, &sq, nullptr, Ds, us, F, &scr_ok);
   dd B = dd_add(two_sum(di, -alpha), acc);
   const dd Zi = {zz[i], zl[i]};
   const double b = dd_to_double(dd_div(B, Zi));
@@ -241,18 +241,33 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
     // binary32 screen as in solve_pole; the extra pole's term fl(inv / v) is the same in both
     // evaluations, and the bound also covers the rounding of the intermediate difference X
     const double mlane = (double)((n + L - 1) / L);
-    auto scr = [&](double v, double* g) -> bool {
-      if (!scr_ok) return false;
-      double S32, E32, aS;
-      if (!screen_sum<L>(Df, uf, n, v, lane, gm, &S32, &E32, &aS)) return false;
+    auto decide = [&](double Sx, double Ex, double aS, double v, double* g) -> bool {
       const double E64 = (mlane + 64.0) * 0x1p-52 * aS;
-      const double X = __dsub_rn(__dsub_rn(b, v), __dmul_rn(S32, inv));
+      const double X = __dsub_rn(__dsub_rn(b, v), __dmul_rn(Sx, inv));
       const double G = __dadd_rn(X, inv / v);
-      const double tol = 1.01 * (inv * (E32 + E64 + 0x1p-51 * aS) + 0x1p-51 * fabs(X));
+      const double tol = 1.01 * (inv * (Ex + E64 + 0x1p-51 * aS) + 0x1p-51 * fabs(X));
       if (!(fabs(G) > tol)) return false;
       if (fabs(G) <= 2.0 * tol) r.screened_near++;
       *g = G;
       return true;
+    };
+    // the binary32 screen, then the double-float screen (as in solve_pole)
+    int f32_fail = 0;
+    auto scr = [&](double v, double* g) -> bool {
+      if (!scr_ok) return false;
+      double Sx, Ex, aS;
+      if (f32_fail < kScreen32Tries) {
+        if (screen_sum<L>(F, F + n, n, v, lane, gm, &Sx, &Ex, &aS) && decide(Sx, Ex, aS, v, g)) {
+          f32_fail = 0;
+          return true;
+        }
+        f32_fail++;
+      }
+      if (kScreenDf && screen_df_sum<L>(F, n, v, lane, gm, &Sx, &Ex, &aS) && decide(Sx, Ex, aS, v, g)) {
+        r.screened_df++;
+        return true;
+      }
+      return false;
     };
     // g > 0 below the root for the rightmost eigenvalue, g < 0 for the leftmost
     nu = bisect(phi, side, floor, alo, ahi, side > 0, cap, &ok, &steps, eager_lo, eager_hi, scr, &r.screened);
@@ -278,7 +293,7 @@ __global__ void __launch_bounds__(256) k_arrow_solve(int n, const double* __rest
   const int leader = (threadIdx.x & 31) & ~(L - 1);
   const double* __restrict__ zz = w.zz;
   const int64_t grp = (int64_t)blockIdx.x * (blockDim.x / L) + threadIdx.x / L;
-  double* const Dbuf = (w.terms && grp < w.term_slots && n <= w.term_n) ? w.terms + 3 * grp * w.term_n : nullptr;
+  double* const Dbuf = (w.terms && grp < w.term_slots && n <= w.term_n) ? w.terms + 4 * grp * w.term_n : nullptr;
   for (;;) {
     long long gl = 0;
     if (lane == 0) gl = (long long)atomicAdd(w.queue, 1ull);
@@ -330,6 +345,7 @@ __global__ void __launch_bounds__(256) k_arrow_solve(int n, const double* __rest
     if (lane == 0) {
       if (pr.screened) atomicAdd(&w.counters[C_SCREEN], (unsigned)pr.screened);
       if (pr.screened_near) atomicAdd(&w.counters[C_SCREEN_NEAR], (unsigned)pr.screened_near);
+      if (pr.screened_df) atomicAdd(&w.counters[C_SCREEN_DF], (unsigned)pr.screened_df);
       w.sig[k] = d[i];
       w.mu[k] = pr.mu;
       w.shift[k] = i;
@@ -357,7 +373,7 @@ __device__ double solve_nonpole_arrow(const double* __restrict__ d, const double
   double un2, cub;
   // the double-double pass also stores the elements for the solve when the group has a buffer
   const dd acc = dd_pole_sum<L, OFS>(d, zz, zl, n, -1, sigma, lane, gm, &un2, &cub, Ds, us, nullptr, nullptr,
-                                     nullptr, sigma_lo);
+                                     sigma_lo);
   const dd f = dd_add(OFS ? shift_diff(alpha, sigma, sigma_lo) : two_sum(alpha, -sigma), {-acc.hi, -acc.lo});
   *ok = true;
   *steps_out = 0;
@@ -474,7 +490,7 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_arrow_fix(int n, const do
   const int leader = (threadIdx.x & 31) & ~(L - 1);
   // the solve kernel has finished: its lane-group buffers are free for the remedies' solves
   const int64_t grp = (int64_t)blockIdx.x * (blockDim.x / L) + threadIdx.x / L;
-  double* const Ds = (w.terms && grp < w.term_slots && n <= w.term_n) ? w.terms + 3 * grp * w.term_n : nullptr;
+  double* const Ds = (w.terms && grp < w.term_slots && n <= w.term_n) ? w.terms + 4 * grp * w.term_n : nullptr;
   double* const us = Ds ? Ds + n : nullptr;
   __shared__ int item;
   for (;;) {
@@ -507,6 +523,7 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_arrow_fix(int n, const do
       if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)pr.steps);
       if (lane == 0 && pr.screened) atomicAdd(&w.counters[C_SCREEN], (unsigned)pr.screened);
       if (lane == 0 && pr.screened_near) atomicAdd(&w.counters[C_SCREEN_NEAR], (unsigned)pr.screened_near);
+      if (lane == 0 && pr.screened_df) atomicAdd(&w.counters[C_SCREEN_DF], (unsigned)pr.screened_df);
       new_sig = d[o]; new_mu = pr.mu; new_shift = o; done = true;
     }
     if (!done) {
@@ -745,7 +762,7 @@ static size_t arrow_term_bytes(int64_t n) {
 }
 
 // tb: workspace bytes beyond the required part, for the solves' stored elements (one
-// buffer of 2 n doubles per lane group, for as many groups as the bytes allow; the remedies
+// buffer of TERM_BYTES n bytes per lane group, for as many groups as the bytes allow; the remedies
 // reuse them after the solve kernel)
 template <int L>
 static void launch_arrow(int n, const double* d, const double* z, ArrowWs* w, const Options& o, char* tail,

@@ -38,7 +38,7 @@
 #endif
 // resident blocks per SM that the solve kernel's register budget is compiled for
 #ifndef DPR1_SOLVE_MIN_BLOCKS
-#define DPR1_SOLVE_MIN_BLOCKS 1
+#define DPR1_SOLVE_MIN_BLOCKS 2
 #endif
 // batches of 64 or more problems up to this mean size run the remedies one warp per item
 #ifndef DPR1_FIX_WARP_MAX_N
@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(256, DPR1_SOLVE_MIN_BLOCKS)
   const unsigned gm = group_mask<L>();
   const int leader = (threadIdx.x & 31) & ~(L - 1);
   const int64_t grp = (int64_t)blockIdx.x * (blockDim.x / L) + threadIdx.x / L;
-  double* const Dbuf = (w.terms && grp < w.term_slots) ? w.terms + 3 * grp * w.term_n : nullptr;
+  double* const Dbuf = (w.terms && grp < w.term_slots) ? w.terms + 4 * grp * w.term_n : nullptr;
   for (;;) {
     long long gl = 0;
     if (lane == 0) gl = (long long)atomicAdd(&w.counters64[0], 1ull);
@@ -488,6 +488,7 @@ __global__ void __launch_bounds__(256, DPR1_SOLVE_MIN_BLOCKS)
       if (pr.dd) atomicAdd(&w.counters[C_DD], 1u);
       if (pr.screened) atomicAdd(&w.counters[C_SCREEN], (unsigned)pr.screened);
       if (pr.screened_near) atomicAdd(&w.counters[C_SCREEN_NEAR], (unsigned)pr.screened_near);
+      if (pr.screened_df) atomicAdd(&w.counters[C_SCREEN_DF], (unsigned)pr.screened_df);
       w.sig[g] = d[i];
       w.mu[g] = pr.mu;
       w.shift[g] = i;
@@ -586,7 +587,7 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double
   const int leader = (threadIdx.x & 31) & ~(L - 1);
   // k_solve has finished: its lane-group buffers are free for the remedies' solves
   const int64_t grp = (int64_t)blockIdx.x * (blockDim.x / L) + threadIdx.x / L;
-  double* const Dbuf = (w.terms && grp < w.term_slots) ? w.terms + 3 * grp * w.term_n : nullptr;
+  double* const Dbuf = (w.terms && grp < w.term_slots) ? w.terms + 4 * grp * w.term_n : nullptr;
   __shared__ int item;
   for (;;) {
     int t = 0;
@@ -630,6 +631,7 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double
       if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)pr.steps);
       if (lane == 0 && pr.screened) atomicAdd(&w.counters[C_SCREEN], (unsigned)pr.screened);
       if (lane == 0 && pr.screened_near) atomicAdd(&w.counters[C_SCREEN_NEAR], (unsigned)pr.screened_near);
+      if (lane == 0 && pr.screened_df) atomicAdd(&w.counters[C_SCREEN_DF], (unsigned)pr.screened_df);
       new_sig = d[o]; new_mu = pr.mu; new_shift = o; done = true;
     }
     if (!done) {
@@ -1348,6 +1350,7 @@ dpr1_status dpr1_workspace_stats(void* workspace, int64_t* out, dpr1_stream_t st
   out[9] = c[C_SCREEN];
   out[10] = c[C_R2DD];
   out[11] = c[C_SCREEN_NEAR];
+  out[12] = c[C_SCREEN_DF];
   return DPR1_OK;
 }
 

@@ -35,8 +35,9 @@ struct Ws {
   double* prho;               // [P]: rho' = 2^(2b - a) rho
   double* pzsum;              // [P]: sum_j |zeta'_j| (for K_z of Eq. (knu2))
   // elements of the inverse for the secular evaluations (k_solve, k_fix): lane group g < term_slots owns
-  // TERM_BYTES term_n bytes at terms + 3 g term_n and uses them for problems of order n <= term_n:
-  // n doubles Delta_j, n doubles zz_j / Delta_j, then their binary32 copies (n floats each);
+  // TERM_BYTES term_n bytes at terms + 4 g term_n and uses them for problems of order n <= term_n:
+  // n doubles Delta_j, n doubles zz_j / Delta_j, then their binary32 copies and the low parts of
+  // the pairs (n floats each);
   // nullptr: every evaluation forms them from dr and zz
   double* terms;
   int64_t term_n;
@@ -59,7 +60,7 @@ struct Options {
 enum : int {
   C_FIX_N = 1, C_FIX_Q = 2, C_ZERO_N = 3, C_EVAL_SOLVE = 4, C_EVAL_FIX = 5,
   C_R2 = 6, C_R1 = 7, C_SOLVED = 8, C_DEFL = 9, C_DD = 10, C_SCREEN = 11, C_R2DD = 12,
-  C_SCREEN_NEAR = 13
+  C_SCREEN_NEAR = 13, C_SCREEN_DF = 14
 };
 
 // per-problem bits (Ws::pst)
@@ -70,9 +71,9 @@ enum : unsigned {
   PT_RANGE = 8u,       // rho' outside the normal range: skipped (solved as rho = 0) and reported
 };
 
-// bytes per element of a lane group's buffer: Delta_j, zz_j / Delta_j (binary64) and their
-// binary32 copies (the screen's)
-constexpr size_t TERM_BYTES = 24;
+// bytes per element of a lane group's buffer: Delta_j, zz_j / Delta_j (binary64), their binary32
+// copies (the binary32 screen's) and the low parts of the pairs (the double-float screen's)
+constexpr size_t TERM_BYTES = 32;
 
 size_t ws_layout(int64_t n, Ws* w, char* base);
 size_t term_bytes(int64_t total, int64_t nprob);

@@ -23,11 +23,21 @@
 #ifndef DPR1_SCREEN_TRIES
 #define DPR1_SCREEN_TRIES 2
 #endif
+// the double-float screen after the binary32 one, which is left after this many consecutive
+// failures
+#ifndef DPR1_SCREEN_DF
+#define DPR1_SCREEN_DF 1
+#endif
+#ifndef DPR1_SCREEN32_TRIES
+#define DPR1_SCREEN32_TRIES 2
+#endif
 
 namespace dpr1 {
 
 constexpr int kStoredUnroll = DPR1_STORED_UNROLL;
 constexpr int kScreenTries = DPR1_SCREEN_TRIES;
+constexpr bool kScreenDf = DPR1_SCREEN_DF != 0;
+constexpr int kScreen32Tries = DPR1_SCREEN32_TRIES;
 
 // ---------------------------------------------------------------------------------
 // Shifts in double the working precision (remedy R2 when no binary64 number lies between
@@ -237,19 +247,141 @@ __device__ __forceinline__ bool screen_sum(const float* __restrict__ Df, const f
   return !bad && m * 0x1p-24 < 0.25 && isfinite(sum) && isfinite(es);
 }
 
-// Stores the elements of the inverse at j: Delta_j and u_j = zz_j / Delta_j, and with Df their
-// binary32 copies.  Returns false when a copy is not a normal binary32 number in the screen's
-// range (|Delta| in [2^-80, 2^40), |u| in [2^-80, 2^60), or zero), which turns the screen off.
-__device__ __forceinline__ bool store_elem(double* __restrict__ Ds, double* __restrict__ us, float* __restrict__ Df,
-                                           float* __restrict__ uf, int j, double D, double u) {
+// x = hi + lo with hi = RN32(x) (the binary32 number nearest x, ties to even) and lo = x - hi
+// rounded to 24 bits, so |x - hi - lo| <= 2^-48 |x| (plus at most 2^-149 where lo is a subnormal
+// binary32 number, rounded a second time).  Formed with integer arithmetic on the bits of x: on GB300 a binary64 ->
+// binary32 conversion runs on the binary64 pipe at the fma rate, integer operations on their own
+// pipe at 32 times that.  Valid for x = 0 and 2^-126 <= |x| < 2^128; other x give 0 (callers
+// only use copies of x in the screens' ranges).
+__device__ __forceinline__ void split_f32x2(double x, float* hi, float* lo) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const unsigned sgn = (unsigned)(bits >> 63) << 31;
+  const int e = (int)((bits >> 52) & 0x7ffu);
+  if (e < 897 || e > 1150) {
+    *hi = 0.0f;
+    *lo = 0.0f;
+    return;
+  }
+  const long long m = (long long)((bits & 0xfffffffffffffull) | 0x10000000000000ull);   // 53 bits
+  long long q = m >> 29;                                                                  // 24 bits
+  const long long rem = m & 0x1fffffff;
+  if (rem > 0x10000000 || (rem == 0x10000000 && (q & 1))) q++;
+  const int rlo = (int)(m - (q << 29));            // x - hi in units of 2^(e - 1075), |.| <= 2^28
+  int ef = e - 896;                                // binary32 exponent field of hi
+  if (q == 0x1000000) {
+    q = 0x800000;
+    ef++;
+  }
+  *hi = (ef <= 254) ? __uint_as_float(sgn | ((unsigned)ef << 23) | (unsigned)(q & 0x7fffff)) : 0.0f;
+  // lo = rlo 2^k, k = e - 1075: the conversion rounds rlo to 24 bits; for k >= -126 the power of
+  // two is a normal binary32 number and the product is exact (|rlo| in [1, 2^28]); below, the
+  // scaling goes through 2^(k + 64) (exact) and 2^-64, which rounds once where the result is
+  // subnormal
+  const int k = e - 1075;
+  const float lf = __int2float_rn(rlo);
+  const float lv = (k >= -126) ? lf * __uint_as_float((unsigned)(k + 127) << 23)
+                               : (lf * __uint_as_float((unsigned)(k + 64 + 127) << 23)) * 0x1p-64f;
+  *lo = sgn ? -lv : lv;
+}
+
+// Stores the elements of the inverse at j: Delta_j and u_j = zz_j / Delta_j and, with F, their
+// binary32 copies and the low parts (F[j] = RN32(Delta_j), F[n + j] = RN32(u_j), F[2n + j] and
+// F[3n + j] the remainders: split_f32x2).  Returns false when a copy is not a normal binary32
+// number in the screens' range (|Delta| in [2^-80, 2^40), |u| in [2^-80, 2^60), or zero), which
+// turns the screens off.
+__device__ __forceinline__ bool store_elem(double* __restrict__ Ds, double* __restrict__ us, float* __restrict__ F,
+                                           int n, int j, double D, double u) {
   Ds[j] = D;
   us[j] = u;
-  if (!Df) return true;
-  Df[j] = __double2float_rn(D);
-  uf[j] = __double2float_rn(u);
+  if (!F) return true;
+  split_f32x2(D, F + j, F + 2 * n + j);
+  split_f32x2(u, F + n + j, F + 3 * n + j);
   const unsigned eD = (unsigned)(__double_as_longlong(D) >> 52) & 0x7ffu;
   const unsigned eu = (unsigned)(__double_as_longlong(u) >> 52) & 0x7ffu;
   return (D == 0.0 || (eD >= 943u && eD <= 1062u)) && (u == 0.0 || (eu >= 943u && eu <= 1082u));
+}
+
+// Double-float screen of a bisection step, for the steps the binary32 screen cannot settle.
+// The stored elements as pairs of binary32 numbers, Delta = Dh + Dl and u = uh + ul to 2^-48
+// (store_elem), and nu = vh + vl likewise; eps = 2^-24, w = |nu Delta / t|.  Each term
+// T_j = u_j / (1 - nu Delta_j) is formed as q1 + q2:
+//   p = nu Delta: ph + pe = vh Dh exactly (fma), pl = vh Dl + vl Dh + pe (two fma);
+//     |ph + pl - nu Delta| <= 8.01 eps^2 |nu Delta| (the splits of nu and Delta 2 eps^2, the
+//     rounded cross terms 5 eps^2, the dropped vl Dl eps^2);
+//   t = 1 - p: s + er = 1 - ph (TwoSum), (th, tl) = TwoSum(s, fl(er - pl));
+//     |th + tl - t| <= eps^2 |t| (1 + 11.2 w);
+//   a = u / t: r the binary32 reciprocal of th refined by one Newton step (within 1.07 eps),
+//     q1 = fl(uh r), q2 = fl(R r) with R = fl(fl(fl(uh - q1 th) + ul) - q1 tl) (fma; the exact
+//     residual u - q1 t is at most 4.1 eps |u|, its roundings 9.3 eps^2 |u|, the reciprocal's
+//     error on it 12.6 eps^2 |u / t|);
+//   so |q1 + q2 - T_j| <= eps^2 |T_j| (24 + 11.2 w) (1.001), bounded by eps^2 |q1| (32 + 16 w)
+//   (|T_j| <= |q1| (1 + 2.2 eps), and the computed w is within 3.1 eps of |nu Delta / t|).
+// Per lane the q1 are summed by TwoSum into (sh, sl) and each add = fl(er + q2) joins sl by one
+// rounding; both roundings are at most eps times |add| + |sl|, whose sum bl bounds them at run
+// time (a running error bound).  The lane sums go to binary64 exactly and are added in the lane
+// group's tree (at most 5 roundings of 2^-53 of sum |q1| in all).  Accumulators of positive terms
+// in binary32 (bl, sum |q1| (32 + 16 w), sum |q1|) are at most (m + 2) eps below their exact
+// values (m terms per lane), hence the factor g = 1 + 2 (m + 2) eps.  Subnormal binary32
+// intermediates add at most 2^-150 per operation (32 n 2^-149 in all) and, where nu Delta lies
+// below the binary32 normal range, relative errors below 2^-140.  The returned
+//   E = 1.05 g (eps^2 sum e_j + eps sum bl) + g (8 2^-53 + 2^-140) sum |q1| + 32 n 2^-149
+// bounds |S - sum_j T_j|, and A = 1.001 g sum |q1| + E >= sum_j |T_j|.  Ranges as screen_sum
+// (w <= 2^20: |t| >= 2^-21, every |q1| below 2^82).  Returns false when the screen does not
+// apply (a range, w, or a non-finite sum or bound).
+template <int L>
+__device__ __forceinline__ bool screen_df_sum(const float* __restrict__ F, int n, double nu, int lane, unsigned gm,
+                                              double* S, double* E, double* A) {
+  const float* __restrict__ Dh = F;
+  const float* __restrict__ uh = F + n;
+  const float* __restrict__ Dl = F + 2 * n;
+  const float* __restrict__ ul = F + 3 * n;
+  float vh, vl;
+  split_f32x2(nu, &vh, &vl);
+  const float av = fabsf(vh);
+  bool bad = !(av >= 0x1p-60f && av <= 0x1p60f);
+  float sh = 0.0f, sl = 0.0f, bl = 0.0f, e = 0.0f, a1 = 0.0f;
+  for (int j = lane; j < n; j += L) {
+    const float dh = Dh[j], dl = Dl[j], uhj = uh[j], ulj = ul[j];
+    const float ph = __fmul_rn(vh, dh);
+    const float pe = __fmaf_rn(vh, dh, -ph);
+    const float pl = __fmaf_rn(vh, dl, __fmaf_rn(vl, dh, pe));
+    const float s = __fsub_rn(1.0f, ph);
+    const float b0 = __fsub_rn(s, 1.0f);
+    const float er = __fadd_rn(__fsub_rn(1.0f, __fsub_rn(s, b0)), __fsub_rn(-ph, b0));
+    const float tl0 = __fsub_rn(er, pl);
+    const float th = __fadd_rn(s, tl0);
+    const float b1 = __fsub_rn(th, s);
+    const float tl = __fadd_rn(__fsub_rn(s, __fsub_rn(th, b1)), __fsub_rn(tl0, b1));
+    const float r0 = rcp_approx_f32(th);
+    const float r = __fmaf_rn(r0, __fmaf_rn(-th, r0, 1.0f), r0);
+    const float q1 = __fmul_rn(uhj, r);
+    const float e1 = __fmaf_rn(-q1, th, uhj);
+    const float R = __fmaf_rn(-q1, tl, __fadd_rn(e1, ulj));
+    const float q2 = __fmul_rn(R, r);
+    const float w = fabsf(__fmul_rn(ph, r));
+    bad |= !(w <= 0x1p20f);
+    const float s2 = __fadd_rn(sh, q1);
+    const float b2 = __fsub_rn(s2, sh);
+    const float er2 = __fadd_rn(__fsub_rn(sh, __fsub_rn(s2, b2)), __fsub_rn(q1, b2));
+    const float add = __fadd_rn(er2, q2);
+    sh = s2;
+    sl = __fadd_rn(sl, add);
+    bl = __fadd_rn(bl, __fadd_rn(fabsf(add), fabsf(sl)));
+    const float aq = fabsf(q1);
+    a1 = __fadd_rn(a1, aq);
+    e = __fmaf_rn(aq, __fmaf_rn(16.0f, w, 32.0f), e);
+  }
+  const double sum = group_sum<L>(__dadd_rn((double)sh, (double)sl), gm);
+  const double es = group_sum<L>((double)e, gm);
+  const double bs = group_sum<L>((double)bl, gm);
+  const double as = group_sum<L>((double)a1, gm);
+  bad = group_any<L>(bad, gm);
+  const double m = (double)((n + L - 1) / L);
+  const double g = 1.0 + 2.0 * (m + 2.0) * 0x1p-24;
+  *S = sum;
+  *E = 1.05 * g * (0x1p-48 * es + 0x1p-24 * bs) + g * (8.0 * 0x1p-53 + 0x1p-140) * as + 32.0 * (double)n * 0x1p-149;
+  *A = 1.001 * g * as + *E;
+  return !bad && m * 0x1p-24 < 0.25 && isfinite(sum) && isfinite(es) && isfinite(bs) && isfinite(as);
 }
 
 // The sum and its derivative dS/dnu = sum_j zz_j / t_j^2 = sum_j (u_j / t_j)(Delta_j / t_j) from
@@ -329,8 +461,8 @@ __device__ __forceinline__ double shift_sum(const double* __restrict__ d, const 
 // rounding error, and the errors and the e_q go to a second binary64 accumulator, which
 // gives the sum as accurately as accumulation in twice the working precision (Sec. 2.3).
 // With Ds != nullptr it also stores Dh = fl(d_j - s) and q = zz_j / Dh (0 and 0 at skip): the
-// elements of the inverse that stored_sum reads; with Df their binary32 copies (store_elem),
-// and *scr_ok tells whether the binary32 screen applies to them.
+// elements of the inverse that stored_sum reads; with F their binary32 copies and low parts
+// (store_elem), and *scr_ok tells whether the screens apply to them.
 // With OFS the shift is s + slo in double the working precision: the difference is formed by
 // shift_diff and the stored element is its binary64 rounding (elem_diff).
 template <int L, bool OFS = false>
@@ -338,14 +470,14 @@ __device__ __forceinline__ dd dd_pole_sum(const double* __restrict__ d, const do
                                           const double* __restrict__ zl, int n, int skip, double s, int lane,
                                           unsigned gm, double* sq, double* cub = nullptr,
                                           double* __restrict__ Ds = nullptr, double* __restrict__ us = nullptr,
-                                          float* __restrict__ Df = nullptr, float* __restrict__ uf = nullptr,
-                                          bool* scr_ok = nullptr, double slo = 0.0) {
+                                          float* __restrict__ F = nullptr, bool* scr_ok = nullptr,
+                                          double slo = 0.0) {
   double hi = 0.0, lo = 0.0, q2 = 0.0, c3 = 0.0;
   const double ms = -s;
-  bool ok = Df != nullptr;
+  bool ok = F != nullptr;
   for (int j = lane; j < n; j += L) {
     if (j == skip) {
-      if (Ds) ok &= store_elem(Ds, us, Df, uf, j, 0.0, 0.0);
+      if (Ds) ok &= store_elem(Ds, us, F, n, j, 0.0, 0.0);
       continue;
     }
     const double dj = d[j];
@@ -363,7 +495,7 @@ __device__ __forceinline__ dd dd_pole_sum(const double* __restrict__ d, const do
     const double Zh = zz[j], Zl = zl[j];
     const double r = rcp(Dh);
     const double q = __dmul_rn(Zh, r);
-    if (Ds) ok &= store_elem(Ds, us, Df, uf, j, Dh, q);
+    if (Ds) ok &= store_elem(Ds, us, F, n, j, Dh, q);
     const double eq = __dmul_rn(__dadd_rn(__fma_rn(-q, Dh, Zh), __fma_rn(-q, Dl, Zl)), r);
     const dd t = two_sum(hi, q);
     hi = t.hi;
@@ -653,6 +785,7 @@ struct PoleResult {
   int steps;
   int screened;   // bisection steps settled by the binary32 screen
   int screened_near;   // of those, steps whose margin over the screen's bound was below 2
+  int screened_df;     // of those, steps settled by the double-float screen
 };
 
 // How the corner b is formed (Sec. 2.3): mode 1 in double the working precision when kappa_nu of
@@ -677,20 +810,20 @@ __device__ __forceinline__ double corner_b(const double* __restrict__ d, const d
                                            const double* __restrict__ zl, int n, int i,
                                            double rho, int lane, unsigned gm, double* wn2, CornerRule cr,
                                            bool* used_dd, double* __restrict__ Ds, double* __restrict__ us,
-                                           float* __restrict__ Df, float* __restrict__ uf, bool* scr_ok) {
+                                           float* __restrict__ F, bool* scr_ok) {
   const double di = d[i];
-  bool ok = Df != nullptr;
+  bool ok = F != nullptr;
   if (cr.mode != 2) {
     double p = 0.0, q = 0.0, s2 = 0.0;
     for (int j = lane; j < n; j += L) {
       if (j == i) {
-        if (Ds) ok &= store_elem(Ds, us, Df, uf, j, 0.0, 0.0);
+        if (Ds) ok &= store_elem(Ds, us, F, n, j, 0.0, 0.0);
         continue;
       }
       const double D = __dsub_rn(d[j], di);
       const double r = rcp(D);
       const double t = __dmul_rn(zz[j], r);
-      if (Ds) ok &= store_elem(Ds, us, Df, uf, j, D, t);
+      if (Ds) ok &= store_elem(Ds, us, F, n, j, D, t);
       if (j < i) p = __dadd_rn(p, t);
       else q = __dadd_rn(q, t);
       s2 = __fma_rn(t, r, s2);
@@ -713,7 +846,7 @@ __device__ __forceinline__ double corner_b(const double* __restrict__ d, const d
     if (Ds) {
       for (int j = lane; j < n; j += L) {
         const double D = (j == i) ? 0.0 : __dsub_rn(d[j], di);
-        ok &= store_elem(Ds, us, Df, uf, j, D, (j == i) ? 0.0 : __dmul_rn(zz[j], rcp(D)));
+        ok &= store_elem(Ds, us, F, n, j, D, (j == i) ? 0.0 : __dmul_rn(zz[j], rcp(D)));
       }
     }
     *scr_ok = !group_any<L>(!ok, gm);
@@ -738,12 +871,12 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
   PoleResult r;
   r.screened = 0;
   r.screened_near = 0;
+  r.screened_df = 0;
   double wn2;
   bool used_dd, scr_ok = false;
-  // the binary32 copies follow the two binary64 arrays (us = Ds + n)
-  float* const Df = (Ds && screen && !fast) ? (float*)(us + n) : nullptr;
-  float* const uf = Df ? Df + n : nullptr;
-  double b = corner_b<L>(d, zz, zl, n, i, rho, lane, gm, &wn2, cr, &used_dd, Ds, us, Df, uf, &scr_ok);
+  // the binary32 copies and low parts follow the two binary64 arrays (us = Ds + n)
+  float* const F = (Ds && screen && !fast) ? (float*)(us + n) : nullptr;
+  double b = corner_b<L>(d, zz, zl, n, i, rho, lane, gm, &wn2, cr, &used_dd, Ds, us, F, &scr_ok);
   double side = (i == k) ? 1.0 : -1.0;
   double di = d[i];
   double inv_zi2 = 1.0 / zz[i];
@@ -836,17 +969,33 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
     //    partials, 13 levels, with m = ceil(n / 256): within (m/4 + 23) u A.
     // All lie below (m + 64) 2u A.
     const double mlane = (double)((n + L - 1) / L);
-    auto scr = [&](double v, double* g) -> bool {
-      if (!scr_ok) return false;
-      double S32, E32, aS;
-      if (!screen_sum<L>(Df, uf, n, v, lane, gm, &S32, &E32, &aS)) return false;
+    auto decide = [&](double Sx, double Ex, double aS, double v, double* g) -> bool {
       const double E64 = (mlane + 64.0) * 0x1p-52 * aS;
-      const double tol = 1.01 * inv_zi2 * (E32 + E64 + 0x1p-51 * aS);
-      const double G = __dsub_rn(__dsub_rn(b, v), __dmul_rn(S32, inv_zi2));
+      const double tol = 1.01 * inv_zi2 * (Ex + E64 + 0x1p-51 * aS);
+      const double G = __dsub_rn(__dsub_rn(b, v), __dmul_rn(Sx, inv_zi2));
       if (!(fabs(G) > tol)) return false;
       if (fabs(G) <= 2.0 * tol) r.screened_near++;
       *g = G;
       return true;
+    };
+    // the binary32 screen first; after kScreenTries consecutive failures (its window is reached)
+    // the double-float screen alone, whose window is narrower by about 2^22
+    int f32_fail = 0;
+    auto scr = [&](double v, double* g) -> bool {
+      if (!scr_ok) return false;
+      double Sx, Ex, aS;
+      if (f32_fail < kScreen32Tries) {
+        if (screen_sum<L>(F, F + n, n, v, lane, gm, &Sx, &Ex, &aS) && decide(Sx, Ex, aS, v, g)) {
+          f32_fail = 0;
+          return true;
+        }
+        f32_fail++;
+      }
+      if (kScreenDf && screen_df_sum<L>(F, n, v, lane, gm, &Sx, &Ex, &aS) && decide(Sx, Ex, aS, v, g)) {
+        r.screened_df++;
+        return true;
+      }
+      return false;
     };
     // g(nu) > 0 below the root for the rightmost; for the leftmost, |nu| below the root
     // means nu above it, where g < 0.
@@ -884,7 +1033,7 @@ __device__ double solve_nonpole(const double* __restrict__ d, const double* __re
   double un2, cub;
   // the double-double pass also stores the elements d_j - sigma and zeta_j^2 / (d_j - sigma)
   // for the solve when the group has a buffer (Ds, us as for solve_pole)
-  dd acc = dd_pole_sum<L, OFS>(d, zz, zl, n, -1, sigma, lane, gm, &un2, &cub, Ds, us, nullptr, nullptr, nullptr,
+  dd acc = dd_pole_sum<L, OFS>(d, zz, zl, n, -1, sigma, lane, gm, &un2, &cub, Ds, us, nullptr, nullptr,
                                sigma_lo);
   dd f = dd_add({1.0, 0.0}, two_prod(acc.hi, rho));
   f = dd_add(f, {__dmul_rn(acc.lo, rho), 0.0});
