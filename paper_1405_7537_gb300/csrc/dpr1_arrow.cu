@@ -242,7 +242,7 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
     // evaluations, and the bound also covers the rounding of the intermediate difference X
     const double mlane = (double)((n + L - 1) / L);
     auto decide = [&](double Sx, double Ex, double aS, double v, double* g) -> bool {
-      const double E64 = (mlane + 64.0) * 0x1p-52 * aS;
+      const double E64 = stored_sum_error<L>(mlane, aS);
       const double X = __dsub_rn(__dsub_rn(b, v), __dmul_rn(Sx, inv));
       const double G = __dadd_rn(X, inv / v);
       const double tol = 1.01 * (inv * (Ex + E64 + 0x1p-51 * aS) + 0x1p-51 * fabs(X));

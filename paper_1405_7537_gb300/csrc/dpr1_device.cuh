@@ -42,6 +42,14 @@ __device__ __forceinline__ dd two_sum(double a, double b) {
   return {s, e};
 }
 
+// TwoSum in binary32: returns s = fl(a + b) and sets *e with s + *e = a + b exactly
+__device__ __forceinline__ float two_sum_f(float a, float b, float* e) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  *e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return s;
+}
+
 __device__ __forceinline__ dd fast_two_sum(double a, double b) {  // |a| >= |b| or a == 0
   double s = __dadd_rn(a, b);
   return {s, __dsub_rn(b, __dsub_rn(s, a))};
@@ -144,6 +152,14 @@ __device__ __forceinline__ double group_sum(double v, unsigned gm) {
     __syncthreads();
   }
   return v;
+}
+
+// roundings on the path of group_sum from one lane's value to the total
+template <int L>
+__host__ __device__ constexpr int tree_roundings() {
+  int t = 0;
+  for (int o = (L < 32 ? L : 32) / 2; o > 0; o >>= 1) t++;
+  return L > 32 ? t + L / 32 - 1 : t;
 }
 
 template <int L>

@@ -28,6 +28,10 @@
 #ifndef DPR1_SCREEN_DF
 #define DPR1_SCREEN_DF 1
 #endif
+// the checks of the bracket's ends also try the screen
+#ifndef DPR1_SCREEN_ENDS
+#define DPR1_SCREEN_ENDS 1
+#endif
 #ifndef DPR1_SCREEN32_TRIES
 #define DPR1_SCREEN32_TRIES 2
 #endif
@@ -38,6 +42,7 @@ constexpr int kStoredUnroll = DPR1_STORED_UNROLL;
 constexpr int kScreenTries = DPR1_SCREEN_TRIES;
 constexpr bool kScreenDf = DPR1_SCREEN_DF != 0;
 constexpr int kScreen32Tries = DPR1_SCREEN32_TRIES;
+constexpr bool kScreenEnds = DPR1_SCREEN_ENDS != 0;
 
 // ---------------------------------------------------------------------------------
 // Shifts in double the working precision (remedy R2 when no binary64 number lies between
@@ -199,6 +204,27 @@ __device__ __forceinline__ double stored_sum(const double* __restrict__ Ds, cons
   return s;
 }
 
+// A bound on |S64 - S| at a bisection step a screen settles: S is the exact sum of
+// T_j = u_j / t_j, t_j = 1 - nu Delta_j, over the stored elements, S64 the sum stored_sum
+// returns, A >= sum_j |T_j|, m = ceil(n / L) terms per lane, u = 2^-53.
+//  - t_j is one fma (the exact 1 - nu Delta_j rounded once): u |T_j| per term.
+//  - A group of four terms is one quotient of products of like sign: each numerator of a pair
+//    2 roundings, each pair product 1, the numerator of the four 2 more (5 in all), the
+//    denominator 3, the reciprocal within one ulp (2u) and the product exact inside the fma:
+//    10u of the group's value; a pair or a single term fewer.  With t_j's: 11u of sum |T_j|.
+//  - The fma accumulation rounds at most m/4 + 2 times by u of a partial sum of like-sign
+//    terms (at most A), and the lane group's tree tree_roundings<L> times.
+// In all (m/4 + 13 + tree_roundings<L>) u A to first order; the bound adds u A for the rest.
+// The range-safe fallback of stored_sum does not run at such a step: the screens settle a step
+// only for stored elements in their ranges (|Delta| in [2^-80, 2^40), |u| in [2^-80, 2^60),
+// |nu| <= 2^60) and with |nu Delta_j / t_j| <= 2^20, so every |t_j| lies in [2^-22, 2^101) and
+// every numerator and denominator of stored_sum between 2^-160 and 2^410, inside the fast
+// reciprocal's range.
+template <int L>
+__device__ __forceinline__ double stored_sum_error(double m, double A) {
+  return (0.25 * m + 14.0 + (double)tree_roundings<L>()) * 0x1p-53 * A;
+}
+
 // Binary32 screen of a bisection step.  From the binary32 copies Df_j = fl32(Delta_j) and
 // uf_j = fl32(u_j) and vf = fl32(nu) (each within eps = 2^-24 relative) each lane forms
 // t = fl(1 - vf Df) (one fma), r = 1/t (approximate reciprocal and one Newton step: within
@@ -316,15 +342,20 @@ __device__ __forceinline__ bool store_elem(double* __restrict__ Ds, double* __re
 //     error on it 12.6 eps^2 |u / t|);
 //   so |q1 + q2 - T_j| <= eps^2 |T_j| (24 + 11.2 w) (1.001), bounded by eps^2 |q1| (32 + 16 w)
 //   (|T_j| <= |q1| (1 + 2.2 eps), and the computed w is within 3.1 eps of |nu Delta / t|).
-// Per lane the q1 are summed by TwoSum into (sh, sl) and each add = fl(er + q2) joins sl by one
-// rounding; both roundings are at most eps times |add| + |sl|, whose sum bl bounds them at run
-// time (a running error bound).  The lane sums go to binary64 exactly and are added in the lane
-// group's tree (at most 5 roundings of 2^-53 of sum |q1| in all).  Accumulators of positive terms
-// in binary32 (bl, sum |q1| (32 + 16 w), sum |q1|) are at most (m + 2) eps below their exact
-// values (m terms per lane), hence the factor g = 1 + 2 (m + 2) eps.  Subnormal binary32
-// intermediates add at most 2^-150 per operation (32 n 2^-149 in all) and, where nu Delta lies
-// below the binary32 normal range, relative errors below 2^-140.  The returned
-//   E = 1.05 g (eps^2 sum e_j + eps sum bl) + g (8 2^-53 + 2^-140) sum |q1| + 32 n 2^-149
+// Per lane the terms are summed in three binary32 levels (sh, sl, sll): q1 joins sh by TwoSum,
+// its error er and q2 are added exactly (TwoSum: a + ae = er + q2) and a joins sl by TwoSum;
+// only c = fl(ae + se) (se the last TwoSum's error) and sll = fl(sll + c) round, each by at
+// most eps times |c| and |sll|, whose sum bl bounds them at run time (a running error bound).
+// With two levels instead (fl(er + q2) added to sl), the roundings of sl grow like
+// m^(3/2) eps^2 sum |q1| and, near the root, exceed the terms' own error.  The lane sum goes to
+// binary64 with two roundings and is added in the lane group's tree (tree_roundings more), each
+// at most 2^-53 of sum |q1|.  Accumulators of positive terms in binary32 (bl,
+// sum |q1| (32 + 16 w), sum |q1|) are at most (m + 2) eps below their exact values (m terms per
+// lane), hence the factor g = 1 + 2 (m + 2) eps.  Subnormal binary32 intermediates add at most
+// 2^-150 per operation (48 n 2^-149 in all) and, where nu Delta lies below the binary32 normal
+// range, relative errors below 2^-140.  The returned
+//   E = 1.05 g (eps^2 sum e_j + eps sum bl) + g ((2 + tree_roundings) 2^-53 + 2^-140) sum |q1|
+//       + 48 n 2^-149
 // bounds |S - sum_j T_j|, and A = 1.001 g sum |q1| + E >= sum_j |T_j|.  Ranges as screen_sum
 // (w <= 2^20: |t| >= 2^-21, every |q1| below 2^82).  Returns false when the screen does not
 // apply (a range, w, or a non-finite sum or bound).
@@ -339,7 +370,7 @@ __device__ __forceinline__ bool screen_df_sum(const float* __restrict__ F, int n
   split_f32x2(nu, &vh, &vl);
   const float av = fabsf(vh);
   bool bad = !(av >= 0x1p-60f && av <= 0x1p60f);
-  float sh = 0.0f, sl = 0.0f, bl = 0.0f, e = 0.0f, a1 = 0.0f;
+  float sh = 0.0f, sl = 0.0f, sll = 0.0f, bl = 0.0f, e = 0.0f, a1 = 0.0f;
   for (int j = lane; j < n; j += L) {
     const float dh = Dh[j], dl = Dl[j], uhj = uh[j], ulj = ul[j];
     const float ph = __fmul_rn(vh, dh);
@@ -360,18 +391,18 @@ __device__ __forceinline__ bool screen_df_sum(const float* __restrict__ F, int n
     const float q2 = __fmul_rn(R, r);
     const float w = fabsf(__fmul_rn(ph, r));
     bad |= !(w <= 0x1p20f);
-    const float s2 = __fadd_rn(sh, q1);
-    const float b2 = __fsub_rn(s2, sh);
-    const float er2 = __fadd_rn(__fsub_rn(sh, __fsub_rn(s2, b2)), __fsub_rn(q1, b2));
-    const float add = __fadd_rn(er2, q2);
-    sh = s2;
-    sl = __fadd_rn(sl, add);
-    bl = __fadd_rn(bl, __fadd_rn(fabsf(add), fabsf(sl)));
+    float er2, a, ae, se;
+    sh = two_sum_f(sh, q1, &er2);
+    a = two_sum_f(er2, q2, &ae);
+    sl = two_sum_f(sl, a, &se);
+    const float c = __fadd_rn(ae, se);
+    sll = __fadd_rn(sll, c);
+    bl = __fadd_rn(bl, __fadd_rn(fabsf(c), fabsf(sll)));
     const float aq = fabsf(q1);
     a1 = __fadd_rn(a1, aq);
     e = __fmaf_rn(aq, __fmaf_rn(16.0f, w, 32.0f), e);
   }
-  const double sum = group_sum<L>(__dadd_rn((double)sh, (double)sl), gm);
+  const double sum = group_sum<L>(__dadd_rn(__dadd_rn((double)sh, (double)sl), (double)sll), gm);
   const double es = group_sum<L>((double)e, gm);
   const double bs = group_sum<L>((double)bl, gm);
   const double as = group_sum<L>((double)a1, gm);
@@ -379,7 +410,8 @@ __device__ __forceinline__ bool screen_df_sum(const float* __restrict__ F, int n
   const double m = (double)((n + L - 1) / L);
   const double g = 1.0 + 2.0 * (m + 2.0) * 0x1p-24;
   *S = sum;
-  *E = 1.05 * g * (0x1p-48 * es + 0x1p-24 * bs) + g * (8.0 * 0x1p-53 + 0x1p-140) * as + 32.0 * (double)n * 0x1p-149;
+  *E = 1.05 * g * (0x1p-48 * es + 0x1p-24 * bs) + g * ((2.0 + tree_roundings<L>()) * 0x1p-53 + 0x1p-140) * as +
+       48.0 * (double)n * 0x1p-149;
   *A = 1.001 * g * as + *E;
   return !bad && m * 0x1p-24 < 0.25 && isfinite(sum) && isfinite(es) && isfinite(bs) && isfinite(as);
 }
@@ -551,25 +583,34 @@ __device__ double bisect(Phi phi, double side, double floor, double alo, double 
   bool scr_on = true;
   int scr_fail = 0;                         // consecutive steps the screen did not settle
   int it = 0, pushes = 0, nscr = 0;
+  // an end check: the screen when it settles the point, else phi (*sc tells which)
+  auto check = [&](uint64_t x, bool* sc) -> double {
+    double g;
+    *sc = kScreenEnds && screen(side * dfrom(x), &g);
+    if (*sc) nscr++;
+    else g = phi(side * dfrom(x));
+    steps++;
+    return g;
+  };
   // ends that come from a soft estimate (eager_*) are checked before the bisection
   if (eager_hi) {
     for (; pushes < 64; pushes++) {
-      double g = phi(side * dfrom(hi));
-      steps++;
+      bool sc;
+      double g = check(hi, &sc);
       bool below = below_positive ? (g > 0.0) : (g < 0.0);
-      if (!below) { ghi = g; have_hi = true; break; }
-      lo = hi; glo = g; have_lo = true;
+      if (!below) { ghi = g; have_hi = true; scr_hi = sc; break; }
+      lo = hi; glo = g; have_lo = true; scr_lo = sc;
       if (hi >= top) break;
       hi = (top - hi > span) ? hi + span : top;
       span *= 2;
     }
   }
   if (eager_lo && !have_lo && lo > fl) {
-    double g = phi(side * dfrom(lo));
-    steps++;
+    bool sc;
+    double g = check(lo, &sc);
     bool below = below_positive ? (g > 0.0) : (g < 0.0);
-    if (below) { glo = g; have_lo = true; }
-    else { hi = lo; ghi = g; have_hi = true; lo = fl; }
+    if (below) { glo = g; have_lo = true; scr_lo = sc; }
+    else { hi = lo; ghi = g; have_hi = true; scr_hi = sc; lo = fl; }
   }
   for (;;) {
     // bisection on the bit patterns; every evaluation moves one end and makes it known
@@ -596,30 +637,30 @@ __device__ double bisect(Phi phi, double side, double floor, double alo, double 
     // an end the bisection never moved is only an estimate: check it now (usually the root
     // lies strictly inside and both ends have moved, so this costs nothing)
     if (!have_hi) {
-      double g = phi(side * dfrom(hi));
-      steps++;
+      bool sc;
+      double g = check(hi, &sc);
       bool below = below_positive ? (g > 0.0) : (g < 0.0);
       if (below && pushes < 64 && hi < top) {
         // the root lies beyond the estimate: push the far end out geometrically
-        lo = hi; glo = g; have_lo = true; scr_lo = false;
+        lo = hi; glo = g; have_lo = true; scr_lo = sc;
         hi = (top - hi > span) ? hi + span : top;
         span *= 2;
         pushes++;
         continue;
       }
-      ghi = g; have_hi = !below; scr_hi = false;
+      ghi = g; have_hi = !below; scr_hi = sc;
       if (below) { good = false; break; }
     }
     if (!have_lo && lo > fl) {
-      double g = phi(side * dfrom(lo));
-      steps++;
+      bool sc;
+      double g = check(lo, &sc);
       bool below = below_positive ? (g > 0.0) : (g < 0.0);
       if (!below) {
         // the root lies below the near estimate: fall back to the floor
-        hi = lo; ghi = g; have_hi = true; scr_hi = false; lo = fl;
+        hi = lo; ghi = g; have_hi = true; scr_hi = sc; lo = fl;
         continue;
       }
-      glo = g; have_lo = true; scr_lo = false;
+      glo = g; have_lo = true; scr_lo = sc;
     }
     break;
   }
@@ -945,32 +986,13 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
       double S = elem_sum<L>(Ds, us, d, zz, n, i, di, v, lane, gm);
       return __dsub_rn(__dsub_rn(b, v), __dmul_rn(S, inv_zi2));
     };
-    // The screen settles a step when its g = fl(fl(b - v) - fl(S32 inv_zi2)) exceeds every
-    // way the decision could differ from phi's: |S32 - S| <= E32 (screen_sum), |S64 - S| <= E64
-    // for phi's binary64 sum, and the roundings of the two products.  fl(x - y) has the sign of
-    // x - y, so phi's sign then equals the sign of g.  S is the exact sum of T_j = u_j / t_j over
-    // the stored elements, t_j = 1 - v Delta_j, and E64 = (m + 64) 2^-52 A, A >= sum_j |T_j|,
-    // m = ceil(n / L) terms per lane, covers each way phi can form its sum (u = 2^-53):
-    //  - stored_sum: t_j by one fma (relative error u: the fma rounds the exact 1 - v Delta_j
-    //    once), each group of four terms as one quotient of products of like sign (numerator
-    //    and denominator 3 roundings each, the one-ulp reciprocal and the product: at most 10u
-    //    of the group's sum of |T_j|), groups accumulated by fma (m/4 roundings) and the lane
-    //    group's sum tree (log2 L <= 5 levels): in all at most (m/4 + 15) u A;
-    //  - the range-safe fallback (terms rebuilt from d and zz): the same Delta_j = fl(d_j - d_i)
-    //    as stored, one more rounding per term than the stored u_j = fl(zz_j / Delta_j) carries
-    //    (2u), and five per term of its own: at most (m + 12) u A.  It runs only when a
-    //    numerator or denominator leaves the fast reciprocal's range, which the screen's own
-    //    range checks exclude: with |Delta| in [2^-80, 2^40), |u| in [2^-80, 2^60) and |v| <= 2^60,
-    //    |t| < 2^101, at most one t of a group lies below 2^-54 (distinct poles), and a non-zero
-    //    t not below 2^-106 (t is 1 - v Delta rounded once), so numerators and denominators lie
-    //    between 2^-300 and 2^410 unless some t is zero -- which a step the screen settles
-    //    excludes (|v Delta / t| <= 2^20 there): at such a step the fallback does not occur;
-    //  - block-wide groups of the remedies (L = 256): the warp trees and the sum of the 8 warp
-    //    partials, 13 levels, with m = ceil(n / 256): within (m/4 + 23) u A.
-    // All lie below (m + 64) 2u A.
+    // The screen settles a step when its g = fl(fl(b - v) - fl(Sx inv_zi2)) exceeds every
+    // way the decision could differ from phi's: |Sx - S| <= Ex (the screen's bound),
+    // |S64 - S| <= stored_sum_error for phi's binary64 sum, and the roundings of the two
+    // products.  fl(x - y) has the sign of x - y, so phi's sign then equals the sign of g.
     const double mlane = (double)((n + L - 1) / L);
     auto decide = [&](double Sx, double Ex, double aS, double v, double* g) -> bool {
-      const double E64 = (mlane + 64.0) * 0x1p-52 * aS;
+      const double E64 = stored_sum_error<L>(mlane, aS);
       const double tol = 1.01 * inv_zi2 * (Ex + E64 + 0x1p-51 * aS);
       const double G = __dsub_rn(__dsub_rn(b, v), __dmul_rn(Sx, inv_zi2));
       if (!(fabs(G) > tol)) return false;
