@@ -5,11 +5,13 @@ every product and sum in the oracle rounds exactly as written.
 """
 import os
 import subprocess
+import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liboracle.so")
 SOURCES = [os.path.join(HERE, "dpr1_oracle.c"), os.path.join(HERE, "quad_ref.c")]
+_LOCK = threading.Lock()
 
 
 def _stale():
@@ -20,16 +22,19 @@ def _stale():
 
 
 def build_oracle(force=False):
-    """Builds the oracle library if it is missing or older than its sources; returns its path."""
-    if not force and not _stale():
+    """Builds the oracle library if it is missing or older than its sources; returns its path.
+    Safe to call from several threads and processes at once: one thread of a process builds, and
+    each build writes a file of its own that replaces the library in one step."""
+    with _LOCK:
+        if not force and not _stale():
+            return LIB
+        os.makedirs(BUILD, exist_ok=True)
+        tmp = LIB + ".%d.%d.tmp" % (os.getpid(), threading.get_ident())
+        cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+               "-o", tmp] + SOURCES + ["-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, LIB)
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    tmp = LIB + ".%d.tmp" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
-           "-o", tmp] + SOURCES + ["-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
 
 
 if __name__ == "__main__":
