@@ -362,16 +362,19 @@ DPR1_API dpr1_status dpr1_eig_noalloc(int64_t n, const double* d, const double* 
 /*
  * Instrumentation (no counterpart in the paper): synchronises `stream` and copies the
  * counters of the last dpr1_eig / dpr1_eig_batched / dpr1_arrow_eig call on `workspace` into
- * out[0..8]:
+ * out[0..14]:
  *   0 eigenvalues solved by the bisection kernel, 1 eigenvalues flagged by K_nu,
  *   2 remedies taken with R1, 3 with R2, 4 secular-function evaluations in the bisection
  *   kernel, 5 evaluations in the remedy kernel, 6 eigenvalues recomputed from A^{-1},
  *   7 deflated pairs, 8 corners b formed in double-double by the bisection kernel,
  *   9 bisection steps (of those counted in 4 and 5) settled by the binary32 screen,
  *   10 R2 remedies that formed their shift in double the working precision (of those in 3),
- *   11 screened steps (of those in 9) whose screened value exceeded the screen's error bound by
- *   less than a factor 2, 12 steps (of those in 9) settled by the double-float screen.
- *   `out` holds 13 values.
+ *   11 screened evaluations (bisection steps of 9 and probes of 14) whose screened value
+ *   exceeded the screen's error bound by less than a factor 2, 12 screened evaluations (steps
+ *   of 9 and probes of 14) settled by the double-float screen, 13 bisection steps (of those
+ *   counted in 4 and 5) decided by bounds that screened probes certified, without an
+ *   evaluation, 14 screened probes that placed those bounds (not counted in 4 and 5).
+ *   `out` holds 15 values.
  */
 DPR1_API dpr1_status dpr1_workspace_stats(void* workspace, int64_t* out, dpr1_stream_t stream);
 

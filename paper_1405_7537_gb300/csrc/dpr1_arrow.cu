@@ -169,6 +169,8 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
   r.screened = 0;
   r.screened_near = 0;
   r.screened_df = 0;
+  r.inferred = 0;
+  r.probes = 0;
   double sq;
   const double di = d[i];
   // the corner's pass also stores the elements of the inverse when the group has a buffer (and
@@ -241,7 +243,7 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
     // binary32 screen as in solve_pole; the extra pole's term fl(inv / v) is the same in both
     // evaluations, and the bound also covers the rounding of the intermediate difference X
     const double mlane = (double)((n + L - 1) / L);
-    auto decide = [&](double Sx, double Ex, double aS, double v, double* g) -> bool {
+    auto decide = [&](double Sx, double Ex, double aS, double v, double* g, double* tl) -> bool {
       const double E64 = stored_sum_error<L>(mlane, aS);
       const double X = __dsub_rn(__dsub_rn(b, v), __dmul_rn(Sx, inv));
       const double G = __dadd_rn(X, inv / v);
@@ -249,28 +251,46 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
       if (!(fabs(G) > tol)) return false;
       if (fabs(G) <= 2.0 * tol) r.screened_near++;
       *g = G;
+      *tl = tol;
       return true;
     };
     // the binary32 screen, then the double-float screen (as in solve_pole)
     int f32_fail = 0;
-    auto scr = [&](double v, double* g) -> bool {
+    auto scr = [&](double v, double* g, double* tl, int mode, double* psi, double* dpsi) -> bool {
       if (!scr_ok) return false;
-      double Sx, Ex, aS;
-      if (f32_fail < kScreen32Tries) {
-        if (screen_sum<L>(F, F + n, n, v, lane, gm, &Sx, &Ex, &aS) && decide(Sx, Ex, aS, v, g)) {
-          f32_fail = 0;
-          return true;
+      double Sx, Ex, aS, dS = 0.0;
+      bool ok = false;
+      if (mode == 0 || (mode < 0 && f32_fail < kScreen32Tries)) {
+        ok = (psi ? screen_sum<L, true>(F, F + n, n, v, lane, gm, &Sx, &Ex, &aS, &dS)
+                  : screen_sum<L>(F, F + n, n, v, lane, gm, &Sx, &Ex, &aS)) &&
+             decide(Sx, Ex, aS, v, g, tl);
+        if (ok) {
+          if (mode < 0) f32_fail = 0;
+        } else {
+          if (mode == 0) return false;
+          f32_fail++;
         }
-        f32_fail++;
       }
-      if (kScreenDf && screen_df_sum<L>(F, n, v, lane, gm, &Sx, &Ex, &aS) && decide(Sx, Ex, aS, v, g)) {
+      if (!ok) {
+        if (mode == 1) f32_fail = kScreen32Tries;   // the probes have reached the binary32 window
+        ok = kScreenDf &&
+             (psi ? screen_df_sum<L, true>(F, n, v, lane, gm, &Sx, &Ex, &aS, &dS)
+                  : screen_df_sum<L>(F, n, v, lane, gm, &Sx, &Ex, &aS)) &&
+             decide(Sx, Ex, aS, v, g, tl);
+        if (!ok) return false;
         r.screened_df++;
-        return true;
       }
-      return false;
+      // Psi and Psi' on t = |nu| as the accelerated solve forms them (with the pole at 0)
+      if (psi) {
+        const double t = fabs(v), ex = inv / t;
+        *psi = -side * __dmul_rn(Sx, inv) + ex;
+        *dpsi = -__dmul_rn(dS, inv) - ex / t;
+      }
+      return true;
     };
     // g > 0 below the root for the rightmost eigenvalue, g < 0 for the leftmost
-    nu = bisect(phi, side, floor, alo, ahi, side > 0, cap, &ok, &steps, eager_lo, eager_hi, scr, &r.screened);
+    nu = bisect(phi, side, floor, alo, ahi, side > 0, cap, &ok, &steps, eager_lo, eager_hi, scr, &r.screened,
+                kPredict && scr_ok, E, side * b, &r.inferred, &r.probes);
   }
   r.nu = nu;
   r.mu = 1.0 / nu;
@@ -346,6 +366,8 @@ __global__ void __launch_bounds__(256) k_arrow_solve(int n, const double* __rest
       if (pr.screened) atomicAdd(&w.counters[C_SCREEN], (unsigned)pr.screened);
       if (pr.screened_near) atomicAdd(&w.counters[C_SCREEN_NEAR], (unsigned)pr.screened_near);
       if (pr.screened_df) atomicAdd(&w.counters[C_SCREEN_DF], (unsigned)pr.screened_df);
+      if (pr.inferred) atomicAdd(&w.counters[C_INFER], (unsigned)pr.inferred);
+      if (pr.probes) atomicAdd(&w.counters[C_PROBE], (unsigned)pr.probes);
       w.sig[k] = d[i];
       w.mu[k] = pr.mu;
       w.shift[k] = i;
@@ -524,6 +546,8 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_arrow_fix(int n, const do
       if (lane == 0 && pr.screened) atomicAdd(&w.counters[C_SCREEN], (unsigned)pr.screened);
       if (lane == 0 && pr.screened_near) atomicAdd(&w.counters[C_SCREEN_NEAR], (unsigned)pr.screened_near);
       if (lane == 0 && pr.screened_df) atomicAdd(&w.counters[C_SCREEN_DF], (unsigned)pr.screened_df);
+      if (lane == 0 && pr.inferred) atomicAdd(&w.counters[C_INFER], (unsigned)pr.inferred);
+      if (lane == 0 && pr.probes) atomicAdd(&w.counters[C_PROBE], (unsigned)pr.probes);
       new_sig = d[o]; new_mu = pr.mu; new_shift = o; done = true;
     }
     if (!done) {

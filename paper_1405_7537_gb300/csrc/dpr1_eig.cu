@@ -489,6 +489,8 @@ __global__ void __launch_bounds__(256, DPR1_SOLVE_MIN_BLOCKS)
       if (pr.screened) atomicAdd(&w.counters[C_SCREEN], (unsigned)pr.screened);
       if (pr.screened_near) atomicAdd(&w.counters[C_SCREEN_NEAR], (unsigned)pr.screened_near);
       if (pr.screened_df) atomicAdd(&w.counters[C_SCREEN_DF], (unsigned)pr.screened_df);
+      if (pr.inferred) atomicAdd(&w.counters[C_INFER], (unsigned)pr.inferred);
+      if (pr.probes) atomicAdd(&w.counters[C_PROBE], (unsigned)pr.probes);
       w.sig[g] = d[i];
       w.mu[g] = pr.mu;
       w.shift[g] = i;
@@ -632,6 +634,8 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double
       if (lane == 0 && pr.screened) atomicAdd(&w.counters[C_SCREEN], (unsigned)pr.screened);
       if (lane == 0 && pr.screened_near) atomicAdd(&w.counters[C_SCREEN_NEAR], (unsigned)pr.screened_near);
       if (lane == 0 && pr.screened_df) atomicAdd(&w.counters[C_SCREEN_DF], (unsigned)pr.screened_df);
+      if (lane == 0 && pr.inferred) atomicAdd(&w.counters[C_INFER], (unsigned)pr.inferred);
+      if (lane == 0 && pr.probes) atomicAdd(&w.counters[C_PROBE], (unsigned)pr.probes);
       new_sig = d[o]; new_mu = pr.mu; new_shift = o; done = true;
     }
     if (!done) {
@@ -1351,6 +1355,8 @@ dpr1_status dpr1_workspace_stats(void* workspace, int64_t* out, dpr1_stream_t st
   out[10] = c[C_R2DD];
   out[11] = c[C_SCREEN_NEAR];
   out[12] = c[C_SCREEN_DF];
+  out[13] = c[C_INFER];
+  out[14] = c[C_PROBE];
   return DPR1_OK;
 }
 

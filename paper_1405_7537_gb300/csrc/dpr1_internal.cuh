@@ -56,11 +56,11 @@ struct Options {
   bool screen;       // binary32 screen of the bisection steps (same results)
 };
 
-// hdr counters (Ws::counters index)
+// hdr counters (Ws::counters index; 16 and 17 are hdr[24..25], the solve queue)
 enum : int {
   C_FIX_N = 1, C_FIX_Q = 2, C_ZERO_N = 3, C_EVAL_SOLVE = 4, C_EVAL_FIX = 5,
   C_R2 = 6, C_R1 = 7, C_SOLVED = 8, C_DEFL = 9, C_DD = 10, C_SCREEN = 11, C_R2DD = 12,
-  C_SCREEN_NEAR = 13, C_SCREEN_DF = 14
+  C_SCREEN_NEAR = 13, C_SCREEN_DF = 14, C_INFER = 18, C_PROBE = 19
 };
 
 // per-problem bits (Ws::pst)

@@ -32,6 +32,14 @@
 #ifndef DPR1_SCREEN_ENDS
 #define DPR1_SCREEN_ENDS 1
 #endif
+// screened probes before the bisection that certify bounds next to the root (at most
+// DPR1_PREDICT_STEPS; they stop once the certified bracket is at most kPredictStop doubles wide)
+#ifndef DPR1_PREDICT
+#define DPR1_PREDICT 1
+#endif
+#ifndef DPR1_PREDICT_STEPS
+#define DPR1_PREDICT_STEPS 12
+#endif
 #ifndef DPR1_SCREEN32_TRIES
 #define DPR1_SCREEN32_TRIES 2
 #endif
@@ -43,6 +51,9 @@ constexpr int kScreenTries = DPR1_SCREEN_TRIES;
 constexpr bool kScreenDf = DPR1_SCREEN_DF != 0;
 constexpr int kScreen32Tries = DPR1_SCREEN32_TRIES;
 constexpr bool kScreenEnds = DPR1_SCREEN_ENDS != 0;
+constexpr bool kPredict = DPR1_PREDICT != 0;
+constexpr int kPredictSteps = DPR1_PREDICT_STEPS;
+constexpr uint64_t kPredictStop = 4;
 
 // ---------------------------------------------------------------------------------
 // Shifts in double the working precision (remedy R2 when no binary64 number lies between
@@ -242,12 +253,15 @@ __device__ __forceinline__ double stored_sum_error(double m, double A) {
 // |S - sum_j T_j|, and A = 1.02 sum_j e_j / (6 eps) + E >= sum_j |T_j|.  The copies and nu
 // must lie in the ranges checked by store_elem and here (|nu| in [2^-60, 2^60], so |p| <= 2^100).
 // Returns false when the screen does not apply (a range, w, or a non-finite sum or bound).
-template <int L>
+// With SLOPE it also returns *dS ~ dS/dnu = sum_j (u_j / t_j)(Delta_j / t_j) (no bound: the
+// probes of the bisection only place points with it).
+template <int L, bool SLOPE = false>
 __device__ __forceinline__ bool screen_sum(const float* __restrict__ Df, const float* __restrict__ uf, int n,
-                                           double nu, int lane, unsigned gm, double* S, double* E, double* A) {
+                                           double nu, int lane, unsigned gm, double* S, double* E, double* A,
+                                           double* dS = nullptr) {
   const float vf = __double2float_rn(nu);
   const float av = fabsf(vf);
-  float sh = 0.0f, sl = 0.0f, e = 0.0f;
+  float sh = 0.0f, sl = 0.0f, e = 0.0f, sd = 0.0f;
   bool bad = !(av >= 0x1p-60f && av <= 0x1p60f);
   for (int j = lane; j < n; j += L) {
     const float D = Df[j], u = uf[j];
@@ -256,6 +270,7 @@ __device__ __forceinline__ bool screen_sum(const float* __restrict__ Df, const f
     const float r = __fmaf_rn(r0, __fmaf_rn(-t, r0, 1.0f), r0);
     const float a = __fmul_rn(u, r);
     const float w = fabsf(__fmul_rn(__fmul_rn(vf, D), r));
+    if (SLOPE) sd = __fmaf_rn(a, __fmul_rn(D, r), sd);
     bad |= !(w <= 0x1p20f);
     const float sn = __fadd_rn(sh, a);
     const float bb = __fsub_rn(sn, sh);
@@ -265,6 +280,7 @@ __device__ __forceinline__ bool screen_sum(const float* __restrict__ Df, const f
   }
   const double sum = group_sum<L>(__dadd_rn((double)sh, (double)sl), gm);
   const double es = group_sum<L>((double)e, gm);
+  if (SLOPE) *dS = group_sum<L>((double)sd, gm);
   bad = group_any<L>(bad, gm);
   const double m = (double)((n + L - 1) / L);
   *S = sum;
@@ -359,9 +375,10 @@ __device__ __forceinline__ bool store_elem(double* __restrict__ Ds, double* __re
 // bounds |S - sum_j T_j|, and A = 1.001 g sum |q1| + E >= sum_j |T_j|.  Ranges as screen_sum
 // (w <= 2^20: |t| >= 2^-21, every |q1| below 2^82).  Returns false when the screen does not
 // apply (a range, w, or a non-finite sum or bound).
-template <int L>
+// With SLOPE it also returns *dS as screen_sum does (from the high parts).
+template <int L, bool SLOPE = false>
 __device__ __forceinline__ bool screen_df_sum(const float* __restrict__ F, int n, double nu, int lane, unsigned gm,
-                                              double* S, double* E, double* A) {
+                                              double* S, double* E, double* A, double* dS = nullptr) {
   const float* __restrict__ Dh = F;
   const float* __restrict__ uh = F + n;
   const float* __restrict__ Dl = F + 2 * n;
@@ -370,7 +387,7 @@ __device__ __forceinline__ bool screen_df_sum(const float* __restrict__ F, int n
   split_f32x2(nu, &vh, &vl);
   const float av = fabsf(vh);
   bool bad = !(av >= 0x1p-60f && av <= 0x1p60f);
-  float sh = 0.0f, sl = 0.0f, sll = 0.0f, bl = 0.0f, e = 0.0f, a1 = 0.0f;
+  float sh = 0.0f, sl = 0.0f, sll = 0.0f, bl = 0.0f, e = 0.0f, a1 = 0.0f, sd = 0.0f;
   for (int j = lane; j < n; j += L) {
     const float dh = Dh[j], dl = Dl[j], uhj = uh[j], ulj = ul[j];
     const float ph = __fmul_rn(vh, dh);
@@ -386,6 +403,7 @@ __device__ __forceinline__ bool screen_df_sum(const float* __restrict__ F, int n
     const float r0 = rcp_approx_f32(th);
     const float r = __fmaf_rn(r0, __fmaf_rn(-th, r0, 1.0f), r0);
     const float q1 = __fmul_rn(uhj, r);
+    if (SLOPE) sd = __fmaf_rn(q1, __fmul_rn(dh, r), sd);
     const float e1 = __fmaf_rn(-q1, th, uhj);
     const float R = __fmaf_rn(-q1, tl, __fadd_rn(e1, ulj));
     const float q2 = __fmul_rn(R, r);
@@ -406,6 +424,7 @@ __device__ __forceinline__ bool screen_df_sum(const float* __restrict__ F, int n
   const double es = group_sum<L>((double)e, gm);
   const double bs = group_sum<L>((double)bl, gm);
   const double as = group_sum<L>((double)a1, gm);
+  if (SLOPE) *dS = group_sum<L>((double)sd, gm);
   bad = group_any<L>(bad, gm);
   const double m = (double)((n + L - 1) / L);
   const double g = 1.0 + 2.0 * (m + 2.0) * 0x1p-24;
@@ -554,20 +573,68 @@ __device__ __forceinline__ dd dd_pole_sum(const double* __restrict__ d, const do
 // sums are identical in every lane).  Returns nu with the smaller |phi| of the final
 // adjacent pair; *ok = false if the cap was reached.
 // ---------------------------------------------------------------------------------
+// Root of the pole model of F = fscale (a0 - a1 t + Psi) fitted to Psi(t) and Psi'(t) (see the
+// accelerated solve below); Newton's step where the model has no usable pole.
+__device__ __forceinline__ double model_root(double t, double F, double psi, double dpsi, double E, double a0,
+                                             double a1, double fscale) {
+  const double x0 = __dsub_rn(t, E);
+  if (x0 > 0.0 && x0 <= 1.0e300 && dpsi < 0.0) {
+    const double s = -dpsi * x0 * x0;
+    const double c = __fma_rn(dpsi, x0, psi);
+    const double A = (a0 + c) - a1 * E;
+    double x;
+    if (a1 > 0.0) {
+      const double disc = (A != 0.0) ? fabs(A) * sqrt(1.0 + (4.0 * a1 * s / A) / A) : sqrt(4.0 * a1 * s);
+      x = (A > 0.0) ? (A + disc) / (2.0 * a1) : (2.0 * s) / (disc - A);
+    } else {
+      x = (A < 0.0) ? -s / A : INFINITY;
+    }
+    return E + x;
+  }
+  // no usable pole: Newton's step on F = fscale (a0 - a1 t + Psi)
+  const double dF = fscale * (dpsi - a1);
+  return (dF < 0.0) ? t - F / dF : NAN;
+}
+
 // No screen: every step evaluates phi.
 struct NoScreen {
-  __device__ bool operator()(double, double*) const { return false; }
+  __device__ bool operator()(double, double*, double*, int, double* = nullptr, double* = nullptr) const {
+    return false;
+  }
 };
 
-// screen(nu, &g) may settle a step without phi: it returns true with g of the sign phi(nu)
-// would have (the bisection then takes the same decision).  Once it fails, the remaining steps
-// (closer to the root) use phi only; an end whose value came from the screen is evaluated by phi
-// before the final choice, so the result is the one of phi alone.  *screened counts the steps
-// the screen settled.
+// screen(nu, &g, &tol, mode, psi, dpsi) may settle a step without phi: it returns true with g of
+// the sign phi(nu) would have and |g| > tol (the bisection then takes the same decision); mode -1
+// lets the screen choose its precision, 0 asks for binary32 only and 1 for the double-float
+// screen only; with psi != nullptr it also returns Psi and Psi' (below) from the screened sums.
+// Once it fails kScreenTries times in a row, the remaining steps (closer to the root) use phi
+// only; an end whose value came from the screen is evaluated by phi before the final choice, so
+// the result is the one of phi alone.  *screened counts the steps the screen settled.
+//
+// Certified bounds.  On t = |nu| the exact secular function of the stored elements has the form
+// F(t) = a0 - t + Psi(t), Psi(t) = sum_j c_j / (t - e_j) > 0 with c_j > 0 and every pole e_j
+// below the bracket, so F is strictly decreasing there, and the error of phi is at most
+// alpha Psi(t) + beta |a0 - t| + gamma |F(t)| with alpha, beta, gamma far below 1 (the stored sum's
+// bound, the roundings of b - nu, of the products and of the last difference).  Where F > 0,
+// lowering t raises F by at least the change of t plus that of Psi, and the bound by at most
+// beta times the first and alpha times the second, so F minus the bound only grows; where F < 0
+// the same holds for raising t.  A point where a screen settled the step has |F| above the bound
+// (its tolerance covers the screen's error, the bound and the roundings); hence every t below a
+// point settled "below" (above a point settled "above") gets phi's decision "below" ("above")
+// without an evaluation.  With `predict`, screened probes set such bounds cl and ch next to the
+// root: from the upper end, the accelerated solve's pole model (model_root: pole `pole`, F =
+// a0 - t + Psi) fitted to each probe's screened value and slope gives the next probe, first with
+// the binary32 screen, then, once its steps shrink below twice its tolerance over the slope (or
+// it cannot settle a probe), with the double-float screen; one double-float step later two probes
+// at that estimate minus and plus twice the tolerance over the slope certify both sides.  The
+// bisection then follows its own path from its own bracket and takes every midpoint outside
+// (cl, ch) from them (*inferred counts those steps, *probes the screened probes).  The steps, the
+// decisions and the result are those of the bisection without the probes.
 template <class Phi, class Scr = NoScreen>
 __device__ double bisect(Phi phi, double side, double floor, double alo, double ahi, bool below_positive, int cap,
                          bool* ok, int* steps_out, bool eager_lo = false, bool eager_hi = false, Scr screen = Scr(),
-                         int* screened = nullptr) {
+                         int* screened = nullptr, bool predict = false, double pole = 0.0, double a0 = 0.0,
+                         int* inferred = nullptr, int* probes = nullptr) {
   int steps = 0;
   bool good = true;
   if (!(floor >= 0.0)) floor = 0.0;
@@ -579,14 +646,23 @@ __device__ double bisect(Phi phi, double side, double floor, double alo, double 
   uint64_t span = hi - lo + 64;
   double glo = 0.0, ghi = 0.0;
   bool have_lo = false, have_hi = false;    // the end point was evaluated (its side is known)
-  bool scr_lo = false, scr_hi = false;      // its value came from the screen
+  bool scr_lo = false, scr_hi = false;      // its value came from the screen (or a certified bound)
   bool scr_on = true;
   int scr_fail = 0;                         // consecutive steps the screen did not settle
-  int it = 0, pushes = 0, nscr = 0;
-  // an end check: the screen when it settles the point, else phi (*sc tells which)
+  int it = 0, pushes = 0, nscr = 0, ninf = 0, nprobe = 0;
+  // certified bounds: phi decides "below" at every t <= dfrom(cl), "above" at every t >= dfrom(ch)
+  uint64_t cl = 0, ch = ~0ull;
+  // an end check: a certified bound, the screen when it settles the point, else phi (*sc: the
+  // value is not phi's)
   auto check = [&](uint64_t x, bool* sc) -> double {
-    double g;
-    *sc = kScreenEnds && screen(side * dfrom(x), &g);
+    double g, tol;
+    if (x <= cl || x >= ch) {
+      *sc = true;
+      steps++;
+      ninf++;
+      return ((x <= cl) == below_positive) ? 1.0 : -1.0;
+    }
+    *sc = kScreenEnds && screen(side * dfrom(x), &g, &tol, -1, nullptr, nullptr);
     if (*sc) nscr++;
     else g = phi(side * dfrom(x));
     steps++;
@@ -612,6 +688,70 @@ __device__ double bisect(Phi phi, double side, double floor, double alo, double 
     if (below) { glo = g; have_lo = true; scr_lo = sc; }
     else { hi = lo; ghi = g; have_hi = true; scr_hi = sc; lo = fl; }
   }
+  if (predict) {
+    int level = 0;           // 0: binary32 probes, 1: double-float probes
+    int phase = 0;           // 0: model steps, 1: certify below the estimate, 2: certify above it
+    double est = 0.0, delta = 0.0;
+    uint64_t x = hi;
+    for (int p = 0; p < kPredictSteps; p++) {
+      const uint64_t bl = cl > lo ? cl : lo, bh = ch < hi ? ch : hi;
+      if (bh <= bl || bh - bl <= kPredictStop) break;
+      if (x <= bl || x >= bh) {
+        if (phase == 0 && x == bh && x == hi && !have_hi) {
+          // the first probe: the upper end itself
+        } else if (phase == 1) {
+          phase = 2;                          // the lower side is certified already
+          x = dbits(est + delta);
+          continue;
+        } else if (phase == 2) {
+          break;
+        } else {
+          x = bl + ((bh - bl) >> 1);
+        }
+      }
+      const double t = dfrom(x);
+      double g, tol, psi = 0.0, dpsi = 0.0;
+      nprobe++;
+      const bool sc = screen(side * t, &g, &tol, level, phase == 0 ? &psi : nullptr, &dpsi);
+      if (!sc) {
+        if (phase == 0 && level == 0 && kScreenDf) {
+          level = 1;                          // within the binary32 screen's reach of the root
+          continue;
+        }
+        break;
+      }
+      const bool below = below_positive ? (g > 0.0) : (g < 0.0);
+      if (below) cl = x > cl ? x : cl;
+      else ch = x < ch ? x : ch;
+      if (phase == 1) {
+        phase = 2;
+        x = dbits(est + delta);
+        continue;
+      }
+      if (phase == 2) break;
+      const double F = below_positive ? g : -g;
+      const double slope = dpsi - 1.0;
+      if (!(slope < 0.0)) break;
+      double tc = model_root(t, F, psi, dpsi, pole, a0, 1.0, 1.0);
+      const double tl = dfrom(bl), th = dfrom(bh);
+      if (!(tc > tl && tc < th)) tc = below ? fmin(t + fabs(F / slope), th) : fmax(t - fabs(F / slope), tl);
+      const double dl = 2.0 * tol / -slope;
+      if (level == 0 && kScreenDf && fabs(tc - t) <= dl) {
+        level = 1;                            // converged at the binary32 screen's resolution
+        x = dbits(tc);
+        continue;
+      }
+      if (level == 1) {
+        // one double-float model step from within the binary32 screen's reach: certify
+        est = tc;
+        delta = dl;
+        phase = 1;
+        x = dbits(est - delta);
+        continue;
+      }
+      x = dbits(tc);
+    }
+  }
   for (;;) {
     // bisection on the bit patterns; every evaluation moves one end and makes it known
     int phase = 0;
@@ -619,15 +759,22 @@ __device__ double bisect(Phi phi, double side, double floor, double alo, double 
       if (phase >= cap) { good = false; break; }
       phase++;
       uint64_t mid = lo + ((hi - lo) >> 1);
-      double g;
+      double g, tol;
       bool sc = false;
-      if (scr_on) {
-        sc = screen(side * dfrom(mid), &g);
-        scr_fail = sc ? 0 : scr_fail + 1;
-        scr_on = scr_fail < kScreenTries;
+      if (mid <= cl || mid >= ch) {
+        // a certified bound decides the step
+        sc = true;
+        ninf++;
+        g = ((mid <= cl) == below_positive) ? 1.0 : -1.0;
+      } else {
+        if (scr_on) {
+          sc = screen(side * dfrom(mid), &g, &tol, -1, nullptr, nullptr);
+          scr_fail = sc ? 0 : scr_fail + 1;
+          scr_on = scr_fail < kScreenTries;
+        }
+        if (!sc) g = phi(side * dfrom(mid));
+        else nscr++;
       }
-      if (!sc) g = phi(side * dfrom(mid));
-      else nscr++;
       bool below = below_positive ? (g > 0.0) : (g < 0.0);
       if (below) { lo = mid; glo = g; have_lo = true; scr_lo = sc; }
       else { hi = mid; ghi = g; have_hi = true; scr_hi = sc; }
@@ -669,6 +816,8 @@ __device__ double bisect(Phi phi, double side, double floor, double alo, double 
   if (have_hi && scr_hi) { ghi = phi(side * dfrom(hi)); steps++; }
   steps += it;
   if (screened) *screened = nscr;
+  if (inferred) *inferred = ninf;
+  if (probes) *probes = nprobe;
   double alo_g = have_lo ? fabs(glo) : INFINITY;
   double ahi_g = have_hi ? fabs(ghi) : INFINITY;
   if (isnan(alo_g)) alo_g = INFINITY;
@@ -699,27 +848,6 @@ __device__ double bisect(Phi phi, double side, double floor, double alo, double 
 // lo + 1, lo + 4, ... a point above it when the model puts the root at the lower end), and
 // the loop ends, like bisect, with an adjacent pair of doubles across the sign change.
 // ---------------------------------------------------------------------------------
-__device__ __forceinline__ double model_root(double t, double F, double psi, double dpsi, double E, double a0,
-                                             double a1, double fscale) {
-  const double x0 = __dsub_rn(t, E);
-  if (x0 > 0.0 && x0 <= 1.0e300 && dpsi < 0.0) {
-    const double s = -dpsi * x0 * x0;
-    const double c = __fma_rn(dpsi, x0, psi);
-    const double A = (a0 + c) - a1 * E;
-    double x;
-    if (a1 > 0.0) {
-      const double disc = (A != 0.0) ? fabs(A) * sqrt(1.0 + (4.0 * a1 * s / A) / A) : sqrt(4.0 * a1 * s);
-      x = (A > 0.0) ? (A + disc) / (2.0 * a1) : (2.0 * s) / (disc - A);
-    } else {
-      x = (A < 0.0) ? -s / A : INFINITY;
-    }
-    return E + x;
-  }
-  // no usable pole: Newton's step on F = fscale (a0 - a1 t + Psi)
-  const double dF = fscale * (dpsi - a1);
-  return (dF < 0.0) ? t - F / dF : NAN;
-}
-
 // ev(t, want, &psi, &dpsi) returns F(t) times a positive constant fscale and, when want is
 // set, Psi(t) and Psi'(t) (back-off steps, which usually close the bracket, skip them).
 // floor, alo, ahi as in bisect.
@@ -827,6 +955,8 @@ struct PoleResult {
   int screened;   // bisection steps settled by the binary32 screen
   int screened_near;   // of those, steps whose margin over the screen's bound was below 2
   int screened_df;     // of those, steps settled by the double-float screen
+  int inferred;        // bisection steps decided by certified bounds (no evaluation)
+  int probes;          // screened probes that placed those bounds
 };
 
 // How the corner b is formed (Sec. 2.3): mode 1 in double the working precision when kappa_nu of
@@ -913,6 +1043,8 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
   r.screened = 0;
   r.screened_near = 0;
   r.screened_df = 0;
+  r.inferred = 0;
+  r.probes = 0;
   double wn2;
   bool used_dd, scr_ok = false;
   // the binary32 copies and low parts follow the two binary64 arrays (us = Ds + n)
@@ -991,37 +1123,54 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
     // |S64 - S| <= stored_sum_error for phi's binary64 sum, and the roundings of the two
     // products.  fl(x - y) has the sign of x - y, so phi's sign then equals the sign of g.
     const double mlane = (double)((n + L - 1) / L);
-    auto decide = [&](double Sx, double Ex, double aS, double v, double* g) -> bool {
+    auto decide = [&](double Sx, double Ex, double aS, double v, double* g, double* tl) -> bool {
       const double E64 = stored_sum_error<L>(mlane, aS);
       const double tol = 1.01 * inv_zi2 * (Ex + E64 + 0x1p-51 * aS);
       const double G = __dsub_rn(__dsub_rn(b, v), __dmul_rn(Sx, inv_zi2));
       if (!(fabs(G) > tol)) return false;
       if (fabs(G) <= 2.0 * tol) r.screened_near++;
       *g = G;
+      *tl = tol;
       return true;
     };
     // the binary32 screen first; after kScreenTries consecutive failures (its window is reached)
     // the double-float screen alone, whose window is narrower by about 2^22
     int f32_fail = 0;
-    auto scr = [&](double v, double* g) -> bool {
+    auto scr = [&](double v, double* g, double* tl, int mode, double* psi, double* dpsi) -> bool {
       if (!scr_ok) return false;
-      double Sx, Ex, aS;
-      if (f32_fail < kScreen32Tries) {
-        if (screen_sum<L>(F, F + n, n, v, lane, gm, &Sx, &Ex, &aS) && decide(Sx, Ex, aS, v, g)) {
-          f32_fail = 0;
-          return true;
+      double Sx, Ex, aS, dS = 0.0;
+      bool ok = false;
+      if (mode == 0 || (mode < 0 && f32_fail < kScreen32Tries)) {
+        ok = (psi ? screen_sum<L, true>(F, F + n, n, v, lane, gm, &Sx, &Ex, &aS, &dS)
+                  : screen_sum<L>(F, F + n, n, v, lane, gm, &Sx, &Ex, &aS)) &&
+             decide(Sx, Ex, aS, v, g, tl);
+        if (ok) {
+          if (mode < 0) f32_fail = 0;
+        } else {
+          if (mode == 0) return false;
+          f32_fail++;
         }
-        f32_fail++;
       }
-      if (kScreenDf && screen_df_sum<L>(F, n, v, lane, gm, &Sx, &Ex, &aS) && decide(Sx, Ex, aS, v, g)) {
+      if (!ok) {
+        if (mode == 1) f32_fail = kScreen32Tries;   // the probes have reached the binary32 window
+        ok = kScreenDf &&
+             (psi ? screen_df_sum<L, true>(F, n, v, lane, gm, &Sx, &Ex, &aS, &dS)
+                  : screen_df_sum<L>(F, n, v, lane, gm, &Sx, &Ex, &aS)) &&
+             decide(Sx, Ex, aS, v, g, tl);
+        if (!ok) return false;
         r.screened_df++;
-        return true;
       }
-      return false;
+      // Psi and Psi' on t = |nu| as the accelerated solve forms them (F = side b - t + Psi)
+      if (psi) {
+        *psi = -side * __dmul_rn(Sx, inv_zi2);
+        *dpsi = -__dmul_rn(dS, inv_zi2);
+      }
+      return true;
     };
     // g(nu) > 0 below the root for the rightmost; for the leftmost, |nu| below the root
     // means nu above it, where g < 0.
-    nu = bisect(phi, side, floor, alo, ahi, side > 0, cap, &ok, &steps, eager_lo, eager_hi, scr, &r.screened);
+    nu = bisect(phi, side, floor, alo, ahi, side > 0, cap, &ok, &steps, eager_lo, eager_hi, scr, &r.screened,
+                kPredict && scr_ok, E, side * b, &r.inferred, &r.probes);
   }
   r.nu = nu;
   r.mu = 1.0 / nu;
