@@ -44,6 +44,17 @@
 #define DPR1_SCREEN32_TRIES 2
 #endif
 
+// The loops over the stored elements (stored_sum and the two screens) as calls of their own: the
+// bisection's state is saved once per evaluation instead of crowding the loops' registers
+#ifndef DPR1_NOINLINE_SUMS
+#define DPR1_NOINLINE_SUMS 1
+#endif
+#if DPR1_NOINLINE_SUMS
+#define DPR1_SUM_INLINE __noinline__
+#else
+#define DPR1_SUM_INLINE __forceinline__
+#endif
+
 namespace dpr1 {
 
 constexpr int kStoredUnroll = DPR1_STORED_UNROLL;
@@ -178,7 +189,7 @@ __device__ __forceinline__ double arrow_sum_d(const double* __restrict__ d, cons
 // entries it wrote (index j = lane mod L).  A numerator or denominator outside the fast
 // reciprocal's range (extreme data) sends the group to the range-safe sum from d and zz.
 template <int L, bool OFS = false>
-__device__ __forceinline__ double stored_sum(const double* __restrict__ Ds, const double* __restrict__ us,
+__device__ DPR1_SUM_INLINE double stored_sum(const double* __restrict__ Ds, const double* __restrict__ us,
                                              const double* __restrict__ d, const double* __restrict__ zz, int n,
                                              int i, double di, double nu, int lane, unsigned gm, double dlo = 0.0) {
   double s0 = 0.0;
@@ -256,7 +267,7 @@ __device__ __forceinline__ double stored_sum_error(double m, double A) {
 // With SLOPE it also returns *dS ~ dS/dnu = sum_j (u_j / t_j)(Delta_j / t_j) (no bound: the
 // probes of the bisection only place points with it).
 template <int L, bool SLOPE = false>
-__device__ __forceinline__ bool screen_sum(const float* __restrict__ Df, const float* __restrict__ uf, int n,
+__device__ DPR1_SUM_INLINE bool screen_sum(const float* __restrict__ Df, const float* __restrict__ uf, int n,
                                            double nu, int lane, unsigned gm, double* S, double* E, double* A,
                                            double* dS = nullptr) {
   const float vf = __double2float_rn(nu);
@@ -377,7 +388,7 @@ __device__ __forceinline__ bool store_elem(double* __restrict__ Ds, double* __re
 // apply (a range, w, or a non-finite sum or bound).
 // With SLOPE it also returns *dS as screen_sum does (from the high parts).
 template <int L, bool SLOPE = false>
-__device__ __forceinline__ bool screen_df_sum(const float* __restrict__ F, int n, double nu, int lane, unsigned gm,
+__device__ DPR1_SUM_INLINE bool screen_df_sum(const float* __restrict__ F, int n, double nu, int lane, unsigned gm,
                                               double* S, double* E, double* A, double* dS = nullptr) {
   const float* __restrict__ Dh = F;
   const float* __restrict__ uh = F + n;
@@ -647,24 +658,35 @@ __device__ double bisect(Phi phi, double side, double floor, double alo, double 
   double glo = 0.0, ghi = 0.0;
   bool have_lo = false, have_hi = false;    // the end point was evaluated (its side is known)
   bool scr_lo = false, scr_hi = false;      // its value came from the screen (or a certified bound)
+  double llo = 0.0, lhi = 0.0;              // then a lower bound on |phi| there
   bool scr_on = true;
   int scr_fail = 0;                         // consecutive steps the screen did not settle
   int it = 0, pushes = 0, nscr = 0, ninf = 0, nprobe = 0;
-  // certified bounds: phi decides "below" at every t <= dfrom(cl), "above" at every t >= dfrom(ch)
+  // certified bounds: phi decides "below" at every t <= dfrom(cl), "above" at every t >= dfrom(ch),
+  // and |phi| is at least Lcl (Lch) there
   uint64_t cl = 0, ch = ~0ull;
+  double Lcl = 0.0, Lch = 0.0;
+  // a lower bound on |phi| from a screened value g and its tolerance: |phi - g| <= tol plus
+  // roundings of g's size
+  auto lower = [](double g, double tol) { return fmax(fabs(g) * (1.0 - 0x1p-50) - 2.0 * tol, 0.0); };
   // an end check: a certified bound, the screen when it settles the point, else phi (*sc: the
   // value is not phi's)
-  auto check = [&](uint64_t x, bool* sc) -> double {
+  auto check = [&](uint64_t x, bool* sc, double* lb) -> double {
     double g, tol;
     if (x <= cl || x >= ch) {
       *sc = true;
+      *lb = (x <= cl) ? Lcl : Lch;
       steps++;
       ninf++;
       return ((x <= cl) == below_positive) ? 1.0 : -1.0;
     }
     *sc = kScreenEnds && screen(side * dfrom(x), &g, &tol, -1, nullptr, nullptr);
-    if (*sc) nscr++;
-    else g = phi(side * dfrom(x));
+    if (*sc) {
+      nscr++;
+      *lb = lower(g, tol);
+    } else {
+      g = phi(side * dfrom(x));
+    }
     steps++;
     return g;
   };
@@ -672,10 +694,11 @@ __device__ double bisect(Phi phi, double side, double floor, double alo, double 
   if (eager_hi) {
     for (; pushes < 64; pushes++) {
       bool sc;
-      double g = check(hi, &sc);
+      double lb;
+      double g = check(hi, &sc, &lb);
       bool below = below_positive ? (g > 0.0) : (g < 0.0);
-      if (!below) { ghi = g; have_hi = true; scr_hi = sc; break; }
-      lo = hi; glo = g; have_lo = true; scr_lo = sc;
+      if (!below) { ghi = g; have_hi = true; scr_hi = sc; lhi = lb; break; }
+      lo = hi; glo = g; have_lo = true; scr_lo = sc; llo = lb;
       if (hi >= top) break;
       hi = (top - hi > span) ? hi + span : top;
       span *= 2;
@@ -683,10 +706,11 @@ __device__ double bisect(Phi phi, double side, double floor, double alo, double 
   }
   if (eager_lo && !have_lo && lo > fl) {
     bool sc;
-    double g = check(lo, &sc);
+    double lb;
+    double g = check(lo, &sc, &lb);
     bool below = below_positive ? (g > 0.0) : (g < 0.0);
-    if (below) { glo = g; have_lo = true; scr_lo = sc; }
-    else { hi = lo; ghi = g; have_hi = true; scr_hi = sc; lo = fl; }
+    if (below) { glo = g; have_lo = true; scr_lo = sc; llo = lb; }
+    else { hi = lo; ghi = g; have_hi = true; scr_hi = sc; lhi = lb; lo = fl; }
   }
   if (predict) {
     int level = 0;           // 0: binary32 probes, 1: double-float probes
@@ -721,8 +745,13 @@ __device__ double bisect(Phi phi, double side, double floor, double alo, double 
         break;
       }
       const bool below = below_positive ? (g > 0.0) : (g < 0.0);
-      if (below) cl = x > cl ? x : cl;
-      else ch = x < ch ? x : ch;
+      if (below) {
+        cl = x;
+        Lcl = lower(g, tol);
+      } else {
+        ch = x;
+        Lch = lower(g, tol);
+      }
       if (phase == 1) {
         phase = 2;
         x = dbits(est + delta);
@@ -759,13 +788,14 @@ __device__ double bisect(Phi phi, double side, double floor, double alo, double 
       if (phase >= cap) { good = false; break; }
       phase++;
       uint64_t mid = lo + ((hi - lo) >> 1);
-      double g, tol;
+      double g, tol, lb = 0.0;
       bool sc = false;
       if (mid <= cl || mid >= ch) {
         // a certified bound decides the step
         sc = true;
         ninf++;
         g = ((mid <= cl) == below_positive) ? 1.0 : -1.0;
+        lb = (mid <= cl) ? Lcl : Lch;
       } else {
         if (scr_on) {
           sc = screen(side * dfrom(mid), &g, &tol, -1, nullptr, nullptr);
@@ -773,11 +803,14 @@ __device__ double bisect(Phi phi, double side, double floor, double alo, double 
           scr_on = scr_fail < kScreenTries;
         }
         if (!sc) g = phi(side * dfrom(mid));
-        else nscr++;
+        else {
+          nscr++;
+          lb = lower(g, tol);
+        }
       }
       bool below = below_positive ? (g > 0.0) : (g < 0.0);
-      if (below) { lo = mid; glo = g; have_lo = true; scr_lo = sc; }
-      else { hi = mid; ghi = g; have_hi = true; scr_hi = sc; }
+      if (below) { lo = mid; glo = g; have_lo = true; scr_lo = sc; llo = lb; }
+      else { hi = mid; ghi = g; have_hi = true; scr_hi = sc; lhi = lb; }
       it++;
     }
     if (!good) break;
@@ -785,35 +818,50 @@ __device__ double bisect(Phi phi, double side, double floor, double alo, double 
     // lies strictly inside and both ends have moved, so this costs nothing)
     if (!have_hi) {
       bool sc;
-      double g = check(hi, &sc);
+      double lb;
+      double g = check(hi, &sc, &lb);
       bool below = below_positive ? (g > 0.0) : (g < 0.0);
       if (below && pushes < 64 && hi < top) {
         // the root lies beyond the estimate: push the far end out geometrically
-        lo = hi; glo = g; have_lo = true; scr_lo = sc;
+        lo = hi; glo = g; have_lo = true; scr_lo = sc; llo = lb;
         hi = (top - hi > span) ? hi + span : top;
         span *= 2;
         pushes++;
         continue;
       }
-      ghi = g; have_hi = !below; scr_hi = sc;
+      ghi = g; have_hi = !below; scr_hi = sc; lhi = lb;
       if (below) { good = false; break; }
     }
     if (!have_lo && lo > fl) {
       bool sc;
-      double g = check(lo, &sc);
+      double lb;
+      double g = check(lo, &sc, &lb);
       bool below = below_positive ? (g > 0.0) : (g < 0.0);
       if (!below) {
         // the root lies below the near estimate: fall back to the floor
-        hi = lo; ghi = g; have_hi = true; scr_hi = sc; lo = fl;
+        hi = lo; ghi = g; have_hi = true; scr_hi = sc; lhi = lb; lo = fl;
         continue;
       }
-      glo = g; have_lo = true; scr_lo = sc;
+      glo = g; have_lo = true; scr_lo = sc; llo = lb;
     }
     break;
   }
-  // the final choice compares the values of phi at the two ends
-  if (have_lo && scr_lo) { glo = phi(side * dfrom(lo)); steps++; }
-  if (have_hi && scr_hi) { ghi = phi(side * dfrom(hi)); steps++; }
+  // the final choice compares the values of phi at the two ends.  An end known only from a
+  // screen or a certified bound is evaluated unless its lower bound on |phi| already exceeds the
+  // other end's |phi| (then the other end is the choice, as it would be after the evaluation);
+  // of two such ends the one with the smaller bound is evaluated first.
+  if (have_lo && scr_lo && have_hi && scr_hi) {
+    if (llo <= lhi) { glo = phi(side * dfrom(lo)); steps++; scr_lo = false; }
+    else { ghi = phi(side * dfrom(hi)); steps++; scr_hi = false; }
+  }
+  if (have_lo && scr_lo) {
+    if (have_hi && !scr_hi && llo > fabs(ghi)) glo = INFINITY;
+    else { glo = phi(side * dfrom(lo)); steps++; }
+  }
+  if (have_hi && scr_hi) {
+    if (have_lo && !scr_lo && lhi > fabs(glo)) ghi = INFINITY;
+    else { ghi = phi(side * dfrom(hi)); steps++; }
+  }
   steps += it;
   if (screened) *screened = nscr;
   if (inferred) *inferred = ninf;
