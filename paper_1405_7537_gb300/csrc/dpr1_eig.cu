@@ -40,6 +40,14 @@
 #ifndef DPR1_SOLVE_MIN_BLOCKS
 #define DPR1_SOLVE_MIN_BLOCKS 2
 #endif
+// the shift test's sign from the binary32 pass (shift_test_f32) where its bound decides it
+#ifndef DPR1_SHIFT32
+#define DPR1_SHIFT32 1
+#endif
+// the upper bracket end from the shift test's partial sums (only with the binary64 pass)
+#ifndef DPR1_SHIFT_AHI
+#define DPR1_SHIFT_AHI 0
+#endif
 // batches of 64 or more problems up to this mean size run the remedies one warp per item
 #ifndef DPR1_FIX_WARP_MAX_N
 #define DPR1_FIX_WARP_MAX_N 2048
@@ -51,6 +59,9 @@
 #endif
 
 namespace dpr1 {
+
+constexpr bool kShiftAhi = DPR1_SHIFT_AHI != 0;
+constexpr bool kShift32 = DPR1_SHIFT32 != 0 && !kShiftAhi;
 
 // ---------------------------------------------------------------------------------
 // Workspace layout
@@ -460,24 +471,29 @@ __global__ void __launch_bounds__(256, DPR1_SOLVE_MIN_BLOCKS)
     } else {
       double dk = d[k];
       double tau = __dmul_rn(__dsub_rn(d[k - 1], dk), 0.5);
-      double sp = 0.0, sn = 0.0;
-      for (int j = lane; j < n; j += L) {
-        double den = __dsub_rn(__dsub_rn(d[j], dk), tau);
-        double t = __dmul_rn(zz[j], rcp(den));
-        if (j < k) sp = __dadd_rn(sp, t);
-        else sn = __dadd_rn(sn, t);
+      double sp = 0.0, sn = 0.0, F = 0.0, EF = 0.0;
+      // the binary32 pass decides where its bound settles the sign (the binary64 pass's sign)
+      const bool f32 = kShift32 && screen && shift_test_f32<L>(d, zz, n, dk, tau, rho, lane, gm, &F, &EF) &&
+                       fabs(F) > EF;
+      if (!f32) {
+        for (int j = lane; j < n; j += L) {
+          double den = __dsub_rn(__dsub_rn(d[j], dk), tau);
+          double t = __dmul_rn(zz[j], rcp(den));
+          if (j < k) sp = __dadd_rn(sp, t);
+          else sn = __dadd_rn(sn, t);
+        }
+        sp = group_sum<L>(sp, gm);
+        sn = group_sum<L>(sn, gm);
+        F = 1.0 + rho * (sp + sn);
       }
-      sp = group_sum<L>(sp, gm);
-      sn = group_sum<L>(sn, gm);
-      double F = 1.0 + rho * (sp + sn);
+      alo = 1.0 / tau;
+      ahi = INFINITY;
       if (F > 0.0) {
         i = k;
-        alo = 1.0 / tau;
-        ahi = (1.0 + rho * sp) / (rho * zz[k]);
+        if (kShiftAhi) ahi = (1.0 + rho * sp) / (rho * zz[k]);
       } else {
         i = k - 1;
-        alo = 1.0 / tau;
-        ahi = (-1.0 - rho * sn) / (rho * zz[k - 1]);
+        if (kShiftAhi) ahi = (-1.0 - rho * sn) / (rho * zz[k - 1]);
       }
     }
     const bool stored = Dbuf && n <= w.term_n;

@@ -337,6 +337,82 @@ __device__ __forceinline__ void split_f32x2(double x, float* hi, float* lo) {
   *lo = sgn ? -lv : lv;
 }
 
+// RN32(x) (the binary32 number nearest x, ties to even) by integer operations, for x = 0 and
+// 2^-126 <= |x| < 2^128; *ok = false for other x (the result is then 0).
+__device__ __forceinline__ float rn32(double x, bool* ok) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const unsigned sgn = (unsigned)(bits >> 63) << 31;
+  const int e = (int)((bits >> 52) & 0x7ffu);
+  if (e < 897 || e > 1150) {
+    *ok = (bits << 1) == 0;
+    return 0.0f;
+  }
+  const unsigned long long m = (bits & 0xfffffffffffffull) | 0x10000000000000ull;   // 53 bits
+  unsigned q = (unsigned)(m >> 29);                                                   // 24 bits
+  const unsigned rem = (unsigned)(m & 0x1fffffffu);
+  if (rem > 0x10000000u || (rem == 0x10000000u && (q & 1u))) q++;
+  int ef = e - 896;
+  if (q == 0x1000000u) {
+    q = 0x800000u;
+    ef++;
+  }
+  *ok = ef <= 254;
+  return *ok ? __uint_as_float(sgn | ((unsigned)ef << 23) | (q & 0x7fffffu)) : 0.0f;
+}
+
+// Shift test of Algorithm 1 in binary32: F = 1 + rho sum_j zz_j / ((d_j - d_k) - tau).  Each lane
+// forms Delta_j = fl(d_j - d_k) in binary64 (one subtraction) and the rest in binary32 from
+// Df = RN32(Delta_j), zf = RN32(zz_j), tf = RN32(tau) (integer conversions): den = fl(Df - tf),
+// r = 1/den (approximate reciprocal and one Newton step, 1.07 eps), t = fl(zf r), summed by Sum2.
+// With eps = 2^-24, |den - ((d_j - d_k) - tau)| <= eps (|Df| + tf) (1 + 2^-28) + eps |den| and
+// w = (|Df| + tf) |r|, the term is within e_j = |t| eps (1.01 w + 4.2) of zz_j / ((d_j - d_k) - tau)
+// (the conversions of zz and Delta, the reciprocal, the product and Sum2's share), valid while
+// w <= 2^20 (else the lane reports failure); a weight below the binary32 range (zf = 0) adds at
+// most 2^-125 |r|.  Returns F32 and a bound E on |F32 - F| for the exact F and on |F64 - F| for
+// the binary64 pass of k_solve (two roundings of each difference, the one-ulp reciprocal and the
+// product: u (w + 4) per term, m = ceil(n / L) accumulations per lane, the tree and the last
+// sum), so a decision on the sign of F32 with |F32| > E is the binary64 pass's decision.
+template <int L>
+__device__ __noinline__ bool shift_test_f32(const double* __restrict__ d, const double* __restrict__ zz, int n,
+                                            double dk, double tau, double rho, int lane, unsigned gm, double* F,
+                                            double* E) {
+  bool ok = true;
+  const float tf = rn32(tau, &ok);
+  float sh = 0.0f, sl = 0.0f, e = 0.0f, a1 = 0.0f;
+  for (int j = lane; j < n; j += L) {
+    bool okd, okz;
+    const float Df = rn32(__dsub_rn(d[j], dk), &okd);
+    const float zf = rn32(zz[j], &okz);
+    const float den = __fsub_rn(Df, tf);
+    const float r0 = rcp_approx_f32(den);
+    const float r = __fmaf_rn(r0, __fmaf_rn(-den, r0, 1.0f), r0);
+    const float t = __fmul_rn(zf, r);
+    const float ar = fabsf(r);
+    const float w = __fmul_rn(__fadd_rn(fabsf(Df), tf), ar);
+    ok &= okd && (w <= 0x1p20f);
+    const float at = fabsf(t);
+    e = __fmaf_rn(at, __fmaf_rn(1.01f, w, 4.2f), e);
+    if (!okz) e = __fmaf_rn(ar, 0x1p-125f, e);
+    a1 = __fadd_rn(a1, at);
+    float er;
+    sh = two_sum_f(sh, t, &er);
+    sl = __fadd_rn(sl, er);
+  }
+  const double S = group_sum<L>(__dadd_rn((double)sh, (double)sl), gm);
+  const double es = group_sum<L>((double)e, gm);
+  const double as = group_sum<L>((double)a1, gm);
+  ok = !group_any<L>(!ok, gm);
+  const double m = (double)((n + L - 1) / L);
+  const double g = 1.0 + 2.0 * (m + 2.0) * 0x1p-24;
+  const double F32 = 1.0 + rho * S;
+  const double E32 = rho * (1.05 * g * 0x1p-24 * es + (2.0 + tree_roundings<L>()) * 0x1p-53 * g * as +
+                            4.0 * (double)n * 0x1p-149);
+  const double E64 = 1.01 * 0x1p-53 * rho * g * (es + (m + 16.0 + tree_roundings<L>()) * as);
+  *F = F32;
+  *E = 1.01 * (E32 + E64 + 0x1p-50 * (1.0 + rho * g * as));
+  return ok && isfinite(F32) && isfinite(*E);
+}
+
 // Stores the elements of the inverse at j: Delta_j and u_j = zz_j / Delta_j and, with F, their
 // binary32 copies and the low parts (F[j] = RN32(Delta_j), F[n + j] = RN32(u_j), F[2n + j] and
 // F[3n + j] the remainders: split_f32x2).  Returns false when a copy is not a normal binary32
