@@ -84,7 +84,7 @@ typedef struct {
   double T_zero;         /* near-zero recompute when T_zero |lambda| < distance to its poles (64) */
   int lanes;             /* threads per eigenvalue in the solve kernels: 0 = auto, else 8, 16 or 32 */
   int warps_per_block;   /* 0 = auto */
-  int blocks_per_sm;     /* 0 = auto */
+  int blocks_per_sm;     /* 0 = auto (up to 4 blocks of the solve kernel per SM), else 1..8 */
   int max_bisect;        /* iteration cap per bisection (default 96; 1..4096 accepted, other values
                             give the default).  A bisection phase that reaches it stops and the
                             call reports DPR1_ERR_NOT_CONVERGED; bisection to adjacent doubles
@@ -118,7 +118,7 @@ DPR1_API const char* dpr1_status_string(dpr1_status s);
  * Bytes of workspace for dpr1_eig on a problem of order n (the workspace must be
  * 256-byte aligned; its contents need not be initialised).  The size includes, at the end,
  * one buffer of 32n bytes per lane group of the solve kernel's default launch on the
- * current device (16 groups per SM for n > 384): there each group stores the elements of
+ * current device (32 groups per SM for n > 384): there each group stores the elements of
  * the inverse of its shifted matrix, Delta_j = d_j - d_i and zeta_j^2 / Delta_j of Eq. (invAi),
  * once per eigenvalue (in binary64 and as pairs of binary32 numbers for the screens of the
  * bisection steps), and every bisection step reads them instead of forming them again.

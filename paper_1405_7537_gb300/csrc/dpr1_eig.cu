@@ -38,7 +38,7 @@
 #endif
 // resident blocks per SM that the solve kernel's register budget is compiled for
 #ifndef DPR1_SOLVE_MIN_BLOCKS
-#define DPR1_SOLVE_MIN_BLOCKS 2
+#define DPR1_SOLVE_MIN_BLOCKS 4
 #endif
 // the shift test's sign from the binary32 pass (shift_test_f32) where its bound decides it
 #ifndef DPR1_SHIFT32
@@ -136,14 +136,15 @@ size_t ws_layout2(int64_t total, int64_t nprob, bool batched, Ws* w, char* base)
 static int default_lanes(double avg_n) { return avg_n <= 96 ? 8 : (avg_n <= 384 ? 16 : 32); }
 
 // Bytes of the stored-element buffers appended to the workspace: TERM_BYTES term_n bytes for
-// each lane group of k_solve's default launch (8 warps per block, 2 blocks per SM), term_n = n for
+// each lane group of k_solve's default launch (8 warps per block, DPR1_SOLVE_MIN_BLOCKS blocks per
+// SM), term_n = n for
 // one problem and max(2048, 4 n_avg) (at most total) for a batch; problems of larger order,
 // and groups beyond the buffers under other launch options, form the elements per evaluation.
 size_t term_bytes(int64_t total, int64_t nprob) {
   if (total <= 0 || nprob <= 0) return 0;
   const double avg = (double)total / (double)nprob;
   const int64_t gpb = (32 * 8) / default_lanes(avg);
-  int64_t groups = (int64_t)sm_count() * 2 * gpb;
+  int64_t groups = (int64_t)sm_count() * DPR1_SOLVE_MIN_BLOCKS * gpb;
   // a launch with blocks of gpb' <= gpb groups has at most total + gpb' - 1 of them
   const int64_t need = total + gpb - 1;
   if (groups > need) groups = need;
@@ -1111,7 +1112,7 @@ Options resolve(const dpr1_options* o) {
   r.warps = s->warps_per_block > 0 && s->warps_per_block <= 8 ? s->warps_per_block : 8;
   r.warps_auto = !(s->warps_per_block > 0 && s->warps_per_block <= 8);
   r.bps_auto = !(s->blocks_per_sm > 0 && s->blocks_per_sm <= 8);
-  r.bps = s->blocks_per_sm > 0 && s->blocks_per_sm <= 8 ? s->blocks_per_sm : 2;
+  r.bps = s->blocks_per_sm > 0 && s->blocks_per_sm <= 8 ? s->blocks_per_sm : DPR1_SOLVE_MIN_BLOCKS;
   r.cap = s->max_bisect >= 1 && s->max_bisect <= 4096 ? s->max_bisect : def.max_bisect;
   r.events = s->phase_events;
   r.fast = s->zero_finder == 1;
@@ -1184,16 +1185,20 @@ static dpr1_status run_table(const Prob& pb, void* workspace, size_t wbytes, con
   int L = o.lanes ? o.lanes : default_lanes(avg_n);
   // Shape of the solve kernel.  Its time is set by the binary64 pipe of the busiest SM, so the
   // eigenvalues must spread evenly over the SMs: with fewer lane groups than 8-warp blocks on
-  // every SM can hold, blocks of fewer warps, at most one per SM; with fewer than two such
-  // blocks per SM, one block per SM whose groups take eigenvalues from the work counter
-  // (a partly filled second wave would load some SMs twice).  Options may fix the shape.
+  // every SM can hold, blocks of fewer warps, at most one per SM; else as many 8-warp blocks per
+  // SM (up to the default, all resident at once) as the lane groups fill completely, whose
+  // groups take eigenvalues from the work counter (a partly filled extra block per SM would load
+  // some SMs more than others).  Options may fix the shape.
   int warps = o.warps;
   int bps = o.bps;
   const int64_t lanes_total = pb.total * L;
   if (o.warps_auto) {
     const int64_t w_need = (lanes_total + 32 * (int64_t)sms - 1) / (32 * (int64_t)sms);
     warps = w_need >= 8 ? 8 : (int)(w_need > 0 ? w_need : 1);
-    if (o.bps_auto && lanes_total < (int64_t)32 * 8 * sms * bps) bps = 1;
+    if (o.bps_auto) {
+      const int64_t fill = lanes_total / ((int64_t)32 * 8 * sms);
+      if (fill < bps) bps = fill > 1 ? (int)fill : 1;
+    }
   }
   int groups_per_block = (32 * warps) / L;
   int64_t want_blocks = (pb.total + groups_per_block - 1) / groups_per_block;

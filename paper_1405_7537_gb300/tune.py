@@ -18,7 +18,7 @@ import torch
 from . import binding as B
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "tune_cache.json")
-CANDIDATES = [(l, w, b) for l in (8, 16, 32) for w in (4, 8) for b in (1, 2, 4)]
+CANDIDATES = [(l, w, b) for l in (8, 16, 32) for w in (4, 8) for b in ((1, 2, 4) if w == 8 else (1, 2, 4, 8))]
 
 
 def size_key(sizes, zero_finder=0):
