@@ -303,7 +303,7 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
 
 // One lane group per eigenvalue k = 0..n (persistent grid, work counter).
 template <int L>
-__global__ void __launch_bounds__(256) k_arrow_solve(int n, const double* __restrict__ d,
+__global__ void __launch_bounds__(256, DPR1_SOLVE_MIN_BLOCKS) k_arrow_solve(int n, const double* __restrict__ d,
                                                      const double* __restrict__ z, ArrowWs w, int cap,
                                                      bool fast, bool screen) {
   if (*w.status & ST_FATAL_A) return;
@@ -778,11 +778,12 @@ static int64_t arrow_groups(int64_t n, int L, int warps, int bps) {
   return fixg > need ? fixg : need;
 }
 
-// bytes of the stored-element buffers for the default launch (8 warps per block, 2 blocks per SM)
+// bytes of the stored-element buffers for the default launch (8 warps per block,
+// DPR1_SOLVE_MIN_BLOCKS blocks per SM)
 static size_t arrow_term_bytes(int64_t n) {
   if (n <= 0) return 0;
   const int64_t tn = (n + 31) & ~(int64_t)31;
-  return (size_t)arrow_groups(n, arrow_lanes(n), 8, 2) * TERM_BYTES * (size_t)tn;
+  return (size_t)arrow_groups(n, arrow_lanes(n), 8, DPR1_SOLVE_MIN_BLOCKS) * TERM_BYTES * (size_t)tn;
 }
 
 // tb: workspace bytes beyond the required part, for the solves' stored elements (one

@@ -36,10 +36,6 @@
 #ifndef DPR1_FIX_BLOCKS_PER_SM
 #define DPR1_FIX_BLOCKS_PER_SM 2
 #endif
-// resident blocks per SM that the solve kernel's register budget is compiled for
-#ifndef DPR1_SOLVE_MIN_BLOCKS
-#define DPR1_SOLVE_MIN_BLOCKS 4
-#endif
 // the shift test's sign from the binary32 pass (shift_test_f32) where its bound decides it
 #ifndef DPR1_SHIFT32
 #define DPR1_SHIFT32 1

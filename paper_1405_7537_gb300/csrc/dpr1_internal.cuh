@@ -7,6 +7,12 @@
 
 #include "../../include/dpr1.h"
 
+// resident blocks per SM that the solve kernels' register budget is compiled for (and their
+// default launch and stored-element buffers are sized for)
+#ifndef DPR1_SOLVE_MIN_BLOCKS
+#define DPR1_SOLVE_MIN_BLOCKS 4
+#endif
+
 namespace dpr1 {
 
 // Views into the caller's workspace for one problem (see ws_layout).
