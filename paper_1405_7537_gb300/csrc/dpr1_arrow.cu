@@ -159,7 +159,7 @@ __global__ void k_arrow_check(int n, const double* __restrict__ d, const double*
 
 // Extreme eigenvalue nu of (A - d_i I)^{-1} on the side of eigenvalue k (rightmost when
 // i == k, leftmost when i == k - 1); [alo, ahi] an estimate of the bracket of |nu|.
-template <int L>
+template <int L, bool NI = false>
 __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const double* __restrict__ zl,
                                        const double* __restrict__ zz, int n, double alpha, int k, int i, double alo,
                                        double ahi, int cap, bool fast, int lane, unsigned gm,
@@ -237,7 +237,7 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
     nu = side * accel_solve(ev, floor, alo, ahi, E, side * b, 1.0, 1.0, cap, &ok, &steps);
   } else {
     auto phi = [&](double v) {
-      const double S = elem_sum<L>(Ds, us, d, zz, n, i, di, v, lane, gm);
+      const double S = elem_sum<L, false, NI>(Ds, us, d, zz, n, i, di, v, lane, gm);
       return __dadd_rn(__dsub_rn(__dsub_rn(b, v), __dmul_rn(S, inv)), inv / v);
     };
     // binary32 screen as in solve_pole; the extra pole's term fl(inv / v) is the same in both
@@ -261,8 +261,8 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
       double Sx, Ex, aS, dS = 0.0;
       bool ok = false;
       if (mode == 0 || (mode < 0 && f32_fail < kScreen32Tries)) {
-        ok = (psi ? screen_sum<L, true>(F, F + n, n, v, lane, gm, &Sx, &Ex, &aS, &dS)
-                  : screen_sum<L>(F, F + n, n, v, lane, gm, &Sx, &Ex, &aS)) &&
+        ok = (psi ? screen_sum_x<NI, L, true>(F, F + n, n, v, lane, gm, &Sx, &Ex, &aS, &dS)
+                  : screen_sum_x<NI, L>(F, F + n, n, v, lane, gm, &Sx, &Ex, &aS)) &&
              decide(Sx, Ex, aS, v, g, tl);
         if (ok) {
           if (mode < 0) f32_fail = 0;
@@ -274,8 +274,8 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
       if (!ok) {
         if (mode == 1) f32_fail = kScreen32Tries;   // the probes have reached the binary32 window
         ok = kScreenDf &&
-             (psi ? screen_df_sum<L, true>(F, n, v, lane, gm, &Sx, &Ex, &aS, &dS)
-                  : screen_df_sum<L>(F, n, v, lane, gm, &Sx, &Ex, &aS)) &&
+             (psi ? screen_df_sum_x<NI, L, true>(F, n, v, lane, gm, &Sx, &Ex, &aS, &dS)
+                  : screen_df_sum_x<NI, L>(F, n, v, lane, gm, &Sx, &Ex, &aS)) &&
              decide(Sx, Ex, aS, v, g, tl);
         if (!ok) return false;
         r.screened_df++;
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(256, DPR1_SOLVE_MIN_BLOCKS) k_arrow_solve(int 
       }
       if (!(ahi > alo)) ahi = INFINITY;
     }
-    PoleResult pr = solve_pole_arrow<L>(d, w.zl, zz, n, alpha, k, i, alo, ahi, cap, fast, lane, gm, Dbuf,
+    PoleResult pr = solve_pole_arrow<L, true>(d, w.zl, zz, n, alpha, k, i, alo, ahi, cap, fast, lane, gm, Dbuf,
                                         Dbuf ? Dbuf + n : nullptr, screen);
     if (lane == 0) {
       if (pr.screened) atomicAdd(&w.counters[C_SCREEN], (unsigned)pr.screened);

@@ -44,6 +44,15 @@
 #ifndef DPR1_SHIFT_AHI
 #define DPR1_SHIFT_AHI 0
 #endif
+// the solve kernel for problems of mean order above DPR1_SOLVE_LARGE_N: compiled for
+// DPR1_SOLVE_MIN_BLOCKS resident blocks per SM with its sums out of line; below, for
+// DPR1_SOLVE_SMALL_BLOCKS with its sums inlined (the loops are short there and a call costs)
+#ifndef DPR1_SOLVE_LARGE_N
+#define DPR1_SOLVE_LARGE_N 2048
+#endif
+#ifndef DPR1_SOLVE_SMALL_BLOCKS
+#define DPR1_SOLVE_SMALL_BLOCKS 2
+#endif
 // batches of 64 or more problems up to this mean size run the remedies one warp per item
 #ifndef DPR1_FIX_WARP_MAX_N
 #define DPR1_FIX_WARP_MAX_N 2048
@@ -431,8 +440,8 @@ __global__ void k_deflate(Prob pb, Ws w) {
 //   k = 1:           mu in [rho zeta_1^2, rho ||z||^2] -> nu in [1/(rho ||z||^2), 1/(rho zeta_1^2)]
 // (solve_pole checks the near end, so a wrong sign of a rounded F costs steps, not accuracy).
 // ---------------------------------------------------------------------------------
-template <int L>
-__global__ void __launch_bounds__(256, DPR1_SOLVE_MIN_BLOCKS)
+template <int L, int MINB, bool NI>
+__global__ void __launch_bounds__(256, MINB)
     k_solve(Prob pb, Ws w, int cap, bool fast, int dd_mode, double T_kappa, bool screen) {
   if (*w.status & ST_FATAL) return;
   const int lane = threadIdx.x & (L - 1);
@@ -494,7 +503,7 @@ __global__ void __launch_bounds__(256, DPR1_SOLVE_MIN_BLOCKS)
       }
     }
     const bool stored = Dbuf && n <= w.term_n;
-    PoleResult pr = solve_pole<L>(d, zl, zz, n, rho, k, i, alo, ahi, cap, fast, lane, gm,
+    PoleResult pr = solve_pole<L, NI>(d, zl, zz, n, rho, k, i, alo, ahi, cap, fast, lane, gm,
                                   CornerRule{dd_mode, T_kappa, w.pzsum[p]}, stored ? Dbuf : nullptr,
                                   stored ? Dbuf + n : nullptr, screen);
     if (lane == 0) {
@@ -592,7 +601,7 @@ __device__ __forceinline__ bool pole_difference_cancels(double dp, double s, dou
 //       (at most 3 more solves).
 // A group with one of k_solve's buffers bisects from stored elements there, as k_solve does.
 // ---------------------------------------------------------------------------------
-template <int L>
+template <int L, bool NI>
 __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double T_Knu, int cap, bool fast,
                                                            int dd_mode, double T_kappa, bool screen) {
   if (*w.status & ST_FATAL) return;
@@ -640,7 +649,7 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double
     // R1 is solved only when it will be taken (K' and the ratio come from k_classify); R2 starts
     // from the first estimate otherwise, and its clamp and safe second shift cover a poor one
     if (o >= 0 && o < n && o != i && K2 < K && K2 <= T_Knu && ratio <= T_Knu) {
-      PoleResult pr = solve_pole<L>(d, zl, zz, n, rho, k, o, 0.0, INFINITY, cap, fast, lane, gm,
+      PoleResult pr = solve_pole<L, NI>(d, zl, zz, n, rho, k, o, 0.0, INFINITY, cap, fast, lane, gm,
                                     CornerRule{dd_mode, T_kappa, w.pzsum[p]}, Ds, us, screen);
       if (!pr.ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
       if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)pr.steps);
@@ -672,7 +681,7 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double
         bool ok;
         int st2 = 0;
         const double m2 =
-            solve_nonpole<L>(d, zl, zz, n, rho, s, k > 0 ? k - 1 : -1, k, cap, fast, lane, gm, &ok, &st2, Ds, us);
+            solve_nonpole<L, false, NI>(d, zl, zz, n, rho, s, k > 0 ? k - 1 : -1, k, cap, fast, lane, gm, &ok, &st2, Ds, us);
         if (!ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
         if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)st2);
         new_sig = s; new_mu = m2; new_shift = -1; solved = true;
@@ -700,7 +709,7 @@ __global__ void __launch_bounds__(L > 256 ? L : 256) k_fix(Prob pb, Ws w, double
           if (!(t > 0.0) || (k > 0 && !(t < gw)) || (k == 0 && t > gw)) t = mid;
           bool ok;
           int st2 = 0;
-          m2 = solve_nonpole<L, true>(d, zl, zz, n, rho, lo, k > 0 ? k - 1 : -1, k, cap, fast, lane, gm, &ok, &st2,
+          m2 = solve_nonpole<L, true, NI>(d, zl, zz, n, rho, lo, k > 0 ? k - 1 : -1, k, cap, fast, lane, gm, &ok, &st2,
                                       Ds, us, t);
           if (!ok && lane == 0) atomicOr(w.status, ST_NOT_CONVERGED);
           if (lane == 0) atomicAdd(&w.counters[C_EVAL_FIX], (unsigned)st2);
@@ -1126,7 +1135,12 @@ template <int L>
 static void launch_solve_fix(const Prob& pb, const Ws& w, const Options& o, int grid, int warps, double avg_n,
                              cudaStream_t st) {
   record(o, 0, st);
-  k_solve<L><<<grid, 32 * warps, 0, st>>>(pb, w, o.cap, o.fast, o.dd_mode, o.T_kappa, o.screen);
+  if (L == 32 && avg_n > DPR1_SOLVE_LARGE_N)
+    k_solve<32, DPR1_SOLVE_MIN_BLOCKS, true><<<grid, 32 * warps, 0, st>>>(pb, w, o.cap, o.fast, o.dd_mode, o.T_kappa,
+                                                                          o.screen);
+  else
+    k_solve<L, DPR1_SOLVE_SMALL_BLOCKS, false><<<grid, 32 * warps, 0, st>>>(pb, w, o.cap, o.fast, o.dd_mode, o.T_kappa,
+                                                                           o.screen);
   record(o, 1, st);
   int64_t cg = (pb.total + 255) / 256;
   if (cg > sm_count() * 8) cg = sm_count() * 8;
@@ -1137,7 +1151,7 @@ static void launch_solve_fix(const Prob& pb, const Ws& w, const Options& o, int 
     int64_t fg = pb.total;                            // at most one block per eigenpair
     if (fg > sm_count() * DPR1_FIX_BLOCKS_PER_SM) fg = sm_count() * DPR1_FIX_BLOCKS_PER_SM;
     if (w.terms && fg > w.term_slots) fg = w.term_slots;   // every group with a buffer
-    k_fix<DPR1_FIX_THREADS><<<fg > 0 ? (int)fg : 1, DPR1_FIX_THREADS, 0, st>>>(pb, w, o.T_Knu, o.cap, o.fast,
+    k_fix<DPR1_FIX_THREADS, true><<<fg > 0 ? (int)fg : 1, DPR1_FIX_THREADS, 0, st>>>(pb, w, o.T_Knu, o.cap, o.fast,
                                                                                   o.dd_mode, o.T_kappa, o.screen);
   } else {
     // small problems, or many of them: one warp each (a block-wide group would leave most of
@@ -1147,7 +1161,7 @@ static void launch_solve_fix(const Prob& pb, const Ws& w, const Options& o, int 
     int64_t fg = pb.total;                            // at most one warp per eigenpair
     if (fg > sm_count() * 32) fg = sm_count() * 32;
     if (w.terms && fg > w.term_slots) fg = w.term_slots;   // every group with a buffer
-    k_fix<32><<<fg > 0 ? (int)fg : 1, 32, 0, st>>>(pb, w, o.T_Knu, o.cap, o.fast, o.dd_mode, o.T_kappa, o.screen);
+    k_fix<32, false><<<fg > 0 ? (int)fg : 1, 32, 0, st>>>(pb, w, o.T_Knu, o.cap, o.fast, o.dd_mode, o.T_kappa, o.screen);
   }
   record(o, 2, st);
 }
@@ -1187,6 +1201,10 @@ static dpr1_status run_table(const Prob& pb, void* workspace, size_t wbytes, con
   // some SMs more than others).  Options may fix the shape.
   int warps = o.warps;
   int bps = o.bps;
+  // problems of small order run the solve kernel compiled for fewer resident blocks (its sums
+  // inlined; DPR1_SOLVE_LARGE_N)
+  if (o.bps_auto && !(L == 32 && avg_n > DPR1_SOLVE_LARGE_N) && bps > DPR1_SOLVE_SMALL_BLOCKS)
+    bps = DPR1_SOLVE_SMALL_BLOCKS;
   const int64_t lanes_total = pb.total * L;
   if (o.warps_auto) {
     const int64_t w_need = (lanes_total + 32 * (int64_t)sms - 1) / (32 * (int64_t)sms);

@@ -44,16 +44,6 @@
 #define DPR1_SCREEN32_TRIES 2
 #endif
 
-// The loops over the stored elements (stored_sum and the two screens) as calls of their own: the
-// bisection's state is saved once per evaluation instead of crowding the loops' registers
-#ifndef DPR1_NOINLINE_SUMS
-#define DPR1_NOINLINE_SUMS 1
-#endif
-#if DPR1_NOINLINE_SUMS
-#define DPR1_SUM_INLINE __noinline__
-#else
-#define DPR1_SUM_INLINE __forceinline__
-#endif
 
 namespace dpr1 {
 
@@ -189,7 +179,7 @@ __device__ __forceinline__ double arrow_sum_d(const double* __restrict__ d, cons
 // entries it wrote (index j = lane mod L).  A numerator or denominator outside the fast
 // reciprocal's range (extreme data) sends the group to the range-safe sum from d and zz.
 template <int L, bool OFS = false>
-__device__ DPR1_SUM_INLINE double stored_sum(const double* __restrict__ Ds, const double* __restrict__ us,
+__device__ __forceinline__ double stored_sum(const double* __restrict__ Ds, const double* __restrict__ us,
                                              const double* __restrict__ d, const double* __restrict__ zz, int n,
                                              int i, double di, double nu, int lane, unsigned gm, double dlo = 0.0) {
   double s0 = 0.0;
@@ -267,7 +257,7 @@ __device__ __forceinline__ double stored_sum_error(double m, double A) {
 // With SLOPE it also returns *dS ~ dS/dnu = sum_j (u_j / t_j)(Delta_j / t_j) (no bound: the
 // probes of the bisection only place points with it).
 template <int L, bool SLOPE = false>
-__device__ DPR1_SUM_INLINE bool screen_sum(const float* __restrict__ Df, const float* __restrict__ uf, int n,
+__device__ __forceinline__ bool screen_sum(const float* __restrict__ Df, const float* __restrict__ uf, int n,
                                            double nu, int lane, unsigned gm, double* S, double* E, double* A,
                                            double* dS = nullptr) {
   const float vf = __double2float_rn(nu);
@@ -464,7 +454,7 @@ __device__ __forceinline__ bool store_elem(double* __restrict__ Ds, double* __re
 // apply (a range, w, or a non-finite sum or bound).
 // With SLOPE it also returns *dS as screen_sum does (from the high parts).
 template <int L, bool SLOPE = false>
-__device__ DPR1_SUM_INLINE bool screen_df_sum(const float* __restrict__ F, int n, double nu, int lane, unsigned gm,
+__device__ __forceinline__ bool screen_df_sum(const float* __restrict__ F, int n, double nu, int lane, unsigned gm,
                                               double* S, double* E, double* A, double* dS = nullptr) {
   const float* __restrict__ Dh = F;
   const float* __restrict__ uh = F + n;
@@ -522,6 +512,42 @@ __device__ DPR1_SUM_INLINE bool screen_df_sum(const float* __restrict__ F, int n
   return !bad && m * 0x1p-24 < 0.25 && isfinite(sum) && isfinite(es) && isfinite(bs) && isfinite(as);
 }
 
+// The loops over the stored elements as calls of their own (NI) or inlined.  Out of line, the
+// caller's state is saved once per evaluation instead of crowding the loop's registers: the
+// better form for the solve kernel of large problems, compiled for four blocks per SM (64
+// registers), where the loops are long; inlined for problems of small order, where the loops are
+// short and the call's cost counts.
+template <int L, bool OFS>
+__device__ __noinline__ double stored_sum_call(const double* __restrict__ Ds, const double* __restrict__ us,
+                                               const double* __restrict__ d, const double* __restrict__ zz, int n,
+                                               int i, double di, double nu, int lane, unsigned gm, double dlo) {
+  return stored_sum<L, OFS>(Ds, us, d, zz, n, i, di, nu, lane, gm, dlo);
+}
+template <int L, bool SLOPE>
+__device__ __noinline__ bool screen_sum_call(const float* __restrict__ Df, const float* __restrict__ uf, int n,
+                                             double nu, int lane, unsigned gm, double* S, double* E, double* A,
+                                             double* dS) {
+  return screen_sum<L, SLOPE>(Df, uf, n, nu, lane, gm, S, E, A, dS);
+}
+template <int L, bool SLOPE>
+__device__ __noinline__ bool screen_df_sum_call(const float* __restrict__ F, int n, double nu, int lane,
+                                                unsigned gm, double* S, double* E, double* A, double* dS) {
+  return screen_df_sum<L, SLOPE>(F, n, nu, lane, gm, S, E, A, dS);
+}
+template <bool NI, int L, bool SLOPE = false>
+__device__ __forceinline__ bool screen_sum_x(const float* __restrict__ Df, const float* __restrict__ uf, int n,
+                                             double nu, int lane, unsigned gm, double* S, double* E, double* A,
+                                             double* dS = nullptr) {
+  if constexpr (NI) return screen_sum_call<L, SLOPE>(Df, uf, n, nu, lane, gm, S, E, A, dS);
+  else return screen_sum<L, SLOPE>(Df, uf, n, nu, lane, gm, S, E, A, dS);
+}
+template <bool NI, int L, bool SLOPE = false>
+__device__ __forceinline__ bool screen_df_sum_x(const float* __restrict__ F, int n, double nu, int lane, unsigned gm,
+                                                double* S, double* E, double* A, double* dS = nullptr) {
+  if constexpr (NI) return screen_df_sum_call<L, SLOPE>(F, n, nu, lane, gm, S, E, A, dS);
+  else return screen_df_sum<L, SLOPE>(F, n, nu, lane, gm, S, E, A, dS);
+}
+
 // The sum and its derivative dS/dnu = sum_j zz_j / t_j^2 = sum_j (u_j / t_j)(Delta_j / t_j) from
 // the stored elements (the accelerated solve): one reciprocal of t_j per term, 8 binary64
 // instructions against 10 when Delta_j and Delta_j t_j are formed at every evaluation.
@@ -564,12 +590,13 @@ __device__ __forceinline__ double stored_sum_d(const double* __restrict__ Ds, co
 
 // The secular sums from the stored elements when the group has them (Ds != nullptr), else
 // formed from d and zz at every evaluation.
-template <int L, bool OFS = false>
+template <int L, bool OFS = false, bool NI = false>
 __device__ __forceinline__ double elem_sum(const double* __restrict__ Ds, const double* __restrict__ us,
                                            const double* __restrict__ d, const double* __restrict__ zz, int n, int i,
                                            double di, double nu, int lane, unsigned gm, double dlo = 0.0) {
-  return Ds ? stored_sum<L, OFS>(Ds, us, d, zz, n, i, di, nu, lane, gm, dlo)
-            : arrow_sum<L, OFS>(d, zz, n, i, di, nu, lane, gm, dlo);
+  if (!Ds) return arrow_sum<L, OFS>(d, zz, n, i, di, nu, lane, gm, dlo);
+  if constexpr (NI) return stored_sum_call<L, OFS>(Ds, us, d, zz, n, i, di, nu, lane, gm, dlo);
+  else return stored_sum<L, OFS>(Ds, us, d, zz, n, i, di, nu, lane, gm, dlo);
 }
 
 template <int L, bool OFS = false>
@@ -1157,7 +1184,7 @@ __device__ __forceinline__ double corner_b(const double* __restrict__ d, const d
 // Brackets of |nu| from the shift test (see the derivation in k_solve's comment).  Ds, us: the
 // lane group's private buffers of n doubles each for the elements of the inverse (evaluations
 // with stored_sum), or nullptr (each evaluation forms them from d and zz).
-template <int L>
+template <int L, bool NI = false>
 __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __restrict__ zl,
                                  const double* __restrict__ zz, int n, double rho, int k, int i, double alo,
                                  double ahi, int cap, bool fast, int lane, unsigned gm, CornerRule cr,
@@ -1239,7 +1266,7 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
     nu = side * accel_solve(ev, floor, alo, ahi, E, side * b, 1.0, 1.0, cap, &ok, &steps);
   } else {
     auto phi = [&](double v) {
-      double S = elem_sum<L>(Ds, us, d, zz, n, i, di, v, lane, gm);
+      double S = elem_sum<L, false, NI>(Ds, us, d, zz, n, i, di, v, lane, gm);
       return __dsub_rn(__dsub_rn(b, v), __dmul_rn(S, inv_zi2));
     };
     // The screen settles a step when its g = fl(fl(b - v) - fl(Sx inv_zi2)) exceeds every
@@ -1265,8 +1292,8 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
       double Sx, Ex, aS, dS = 0.0;
       bool ok = false;
       if (mode == 0 || (mode < 0 && f32_fail < kScreen32Tries)) {
-        ok = (psi ? screen_sum<L, true>(F, F + n, n, v, lane, gm, &Sx, &Ex, &aS, &dS)
-                  : screen_sum<L>(F, F + n, n, v, lane, gm, &Sx, &Ex, &aS)) &&
+        ok = (psi ? screen_sum_x<NI, L, true>(F, F + n, n, v, lane, gm, &Sx, &Ex, &aS, &dS)
+                  : screen_sum_x<NI, L>(F, F + n, n, v, lane, gm, &Sx, &Ex, &aS)) &&
              decide(Sx, Ex, aS, v, g, tl);
         if (ok) {
           if (mode < 0) f32_fail = 0;
@@ -1278,8 +1305,8 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
       if (!ok) {
         if (mode == 1) f32_fail = kScreen32Tries;   // the probes have reached the binary32 window
         ok = kScreenDf &&
-             (psi ? screen_df_sum<L, true>(F, n, v, lane, gm, &Sx, &Ex, &aS, &dS)
-                  : screen_df_sum<L>(F, n, v, lane, gm, &Sx, &Ex, &aS)) &&
+             (psi ? screen_df_sum_x<NI, L, true>(F, n, v, lane, gm, &Sx, &Ex, &aS, &dS)
+                  : screen_df_sum_x<NI, L>(F, n, v, lane, gm, &Sx, &Ex, &aS)) &&
              decide(Sx, Ex, aS, v, g, tl);
         if (!ok) return false;
         r.screened_df++;
@@ -1318,7 +1345,7 @@ __device__ PoleResult solve_pole(const double* __restrict__ d, const double* __r
 // binary64 number lies between lambda and a neighbouring pole): the elements of the DPR1 matrix
 // are the binary64 roundings of the double-double differences d_j - sigma (elem_diff) and
 // f(sigma) is formed from those differences in double-double.
-template <int L, bool OFS = false>
+template <int L, bool OFS = false, bool NI = false>
 __device__ double solve_nonpole(const double* __restrict__ d, const double* __restrict__ zl,
                                 const double* __restrict__ zz, int n, double rho, double sigma, int above, int below,
                                 int cap, bool fast, int lane, unsigned gm, bool* ok, int* steps_out = nullptr,
@@ -1366,7 +1393,7 @@ __device__ double solve_nonpole(const double* __restrict__ d, const double* __re
     auto ev = [&](double t, bool want, double* psi, double* dpsi) {
       double dS = 0.0;
       const double S = want ? elem_sum_d<L, OFS>(Ds, us, d, zz, n, -1, sigma, side * t, lane, gm, &dS, sigma_lo)
-                            : elem_sum<L, OFS>(Ds, us, d, zz, n, -1, sigma, side * t, lane, gm, sigma_lo);
+                            : elem_sum<L, OFS, NI>(Ds, us, d, zz, n, -1, sigma, side * t, lane, gm, sigma_lo);
       *psi = -side * S;
       *dpsi = -dS;
       return -__fma_rn(gamma, S, 1.0);
@@ -1374,7 +1401,7 @@ __device__ double solve_nonpole(const double* __restrict__ d, const double* __re
     nu = side * accel_solve(ev, floor, alo, ahi, E, -1.0 / ag, 0.0, ag, cap, ok, &steps);
   } else {
     auto phi = [&](double v) {
-      const double S = elem_sum<L, OFS>(Ds, us, d, zz, n, -1, sigma, v, lane, gm, sigma_lo);
+      const double S = elem_sum<L, OFS, NI>(Ds, us, d, zz, n, -1, sigma, v, lane, gm, sigma_lo);
       return __fma_rn(gamma, S, 1.0);
     };
     nu = bisect(phi, side, floor, alo, ahi, false, cap, ok, &steps);
