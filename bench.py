@@ -57,6 +57,13 @@ ACCEL_OPS_PER_TERM = 8    # the same with its slope (mul, mul, fma)
 # TwoProd of the square (2), quotient and its first-order correction (5), compensated
 # accumulation (7)
 DD_OPS_PER_TERM = 20
+# binary32 operations per term of the screens (screen_sum: the term's fma, the Newton step of the
+# reciprocal, the quotient, w, the compensated sum and the bound; screen_df_sum: the double-float
+# term, its division and three TwoSum levels with the running bound), and the weight of a binary32
+# operation against a binary64 one: 128 binary32 lanes against 2 binary64 lanes per SM and clock
+B32_OPS_PER_TERM = 14
+DF_OPS_PER_TERM = 50
+FP32_PER_FP64 = 64
 # the binary64 pass over the corner's terms that decides whether b needs double-double
 # (kappa_nu of Eq. (knu2)): sub, div, mul, add
 B64_OPS_PER_TERM = 4
@@ -698,24 +705,35 @@ def run_ours(args):
 
     # roofline of the dominant kernel (the bisection kernel k_solve)
     evals = stats["evals_solve"]
-    # steps the binary32 screen settled are binary32 work: not counted as binary64 operations
+    # bisection steps settled by a screen or decided by a certified bound take no binary64
+    # evaluation; the screens' sums (bisection steps and probes) are binary32 work
     screened = stats.get("screened", 0)
+    inferred = stats.get("inferred", 0)
+    probes = stats.get("probes", 0)
+    df = stats.get("screened_double_float", 0)
     n_dd = stats["double_double"]
     corner = B64_OPS_PER_TERM * n + DD_OPS_PER_TERM * n_dd
+    ops32 = 0
     if zf == 0:
-        ops = (n - 1) * (OPS_PER_TERM * (evals - screened + n) + corner)
-        kname = "k_solve (shift test, corner b, bisection)"
-        odef = ("(n-1) x (5 ops (sub, fma, mul, div, add) per secular term x (bisection evaluations in "
+        b64_evals = evals - screened - inferred
+        ops64 = (n - 1) * (OPS_PER_TERM * (b64_evals + n) + corner)
+        ops32 = (n - 1) * (B32_OPS_PER_TERM * max(screened + probes - df, 0) + DF_OPS_PER_TERM * df)
+        kname = "k_solve (shift test, corner b, screened bisection)"
+        odef = ("binary64: (n-1) x (5 ops (sub, fma, mul, div, add) per secular term x (bisection evaluations in "
                 "binary64 + the shift-test pass) + per eigenvalue the 4-op binary64 pass of the corner b (sub, "
                 "div, mul, add) + for the eigenvalues whose kappa_nu asks for it 20 ops per double-double term "
-                "of b (TwoSum 6, TwoProd 2, quotient and correction 5, compensated accumulation 7)); the "
-                "bisection steps the binary32 screen settled are not counted")
+                "of b (TwoSum 6, TwoProd 2, quotient and correction 5, compensated accumulation 7)); binary32: "
+                "(n-1) x (14 ops per term of a binary32 screen + 50 per term of a double-float screen) over the "
+                "settled screens of bisection steps and probes; a binary32 op counts 1/64 of a binary64 op "
+                "(128 against 2 lanes per SM and clock); steps decided by certified bounds are not counted")
     else:
-        ops = (n - 1) * (ACCEL_OPS_PER_TERM * evals + OPS_PER_TERM * n + corner)
+        b64_evals = evals
+        ops64 = (n - 1) * (ACCEL_OPS_PER_TERM * evals + OPS_PER_TERM * n + corner)
         kname = "k_solve (shift test, corner b, accelerated bracketed solve)"
         odef = ("(n-1) x (8 ops per secular term and evaluation (5 for the value, 3 for the slope) + per "
                 "eigenvalue the 5-op shift-test pass and the 4-op binary64 corner pass + 20 ops per "
                 "double-double term for the eigenvalues whose kappa_nu asks for it)")
+    ops = ops64 + ops32 / FP32_PER_FP64
     t_solve = statistics.mean(solve_ms) * 1e-3
     achieved = ops / t_solve
     # live binary64 fma rate of this GPU at this clock (same process, after the timed region)
@@ -730,15 +748,22 @@ def run_ours(args):
     pe1.synchronize()
     measured_fma = sms * 4 * 256 * 4096 * 8 / (pe0.elapsed_time(pe1) * 1e-3)
     roof = {"bound": "alu", "kernel": kname,
-            "achieved": achieved / 1e12, "peak": NOMINAL_FP64_OPS / 1e12, "unit": "T binary64-op/s",
+            "achieved": achieved / 1e12, "peak": NOMINAL_FP64_OPS / 1e12,
+            "unit": "T binary64-op/s" if zf else "T binary64-op-equivalent/s",
             "frac": achieved / NOMINAL_FP64_OPS, "traffic": committed_traffic(n, zf),
             "peak_source": "nominal GB300 binary64 1.25 TFLOP/s = 2 fma/clk/SM x 152 SMs x 2070 MHz "
                            "(MEASURED_PEAKS.json has no binary64 entry)",
             "measured_fma_rate": measured_fma / 1e12,
             "frac_of_measured_fma_rate": achieved / measured_fma,
             "ops_per_launch": ops, "ops_definition": odef,
+            "binary64_ops": ops64, "binary32_ops": ops32,
+            "binary64_frac": ops64 / t_solve / NOMINAL_FP64_OPS,
+            "binary32_frac": ops32 / t_solve / (FP32_PER_FP64 * NOMINAL_FP64_OPS),
             "launch_ms": 1e3 * t_solve, "bisection_evaluations": evals,
-            "binary32_screened_evaluations": screened, "double_double_corners": n_dd}
+            "binary64_evaluations": b64_evals, "screened_steps": screened, "inferred_steps": inferred,
+            "screened_probes": probes, "double_float_settled": df, "double_double_corners": n_dd,
+            # the plain bisection's terms (every step and the shift-test pass) per second
+            "term_rate": (n - 1) * (evals + n) / t_solve}
 
     # the eigenvector phase (k_vectors and the short near-zero and deflation kernels before it):
     # the n^2 write of V against the measured copy rate, and its binary64 work against the peak
