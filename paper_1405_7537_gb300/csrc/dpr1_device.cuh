@@ -154,6 +154,63 @@ __device__ __forceinline__ double group_sum(double v, unsigned gm) {
   return v;
 }
 
+// The same sum in binary32 (every lane gets the identical total: the xor tree adds the same two
+// operands in both lanes of a pair, and the block path sums the warp partials in warp order).
+// Each of the tree_roundings<L>() additions rounds once by at most 2^-24 of its result.
+template <int L>
+__device__ __forceinline__ float group_sum_f(float v, unsigned gm) {
+  constexpr int W = L < 32 ? L : 32;
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(gm, v, o));
+  if constexpr (L > 32) {
+    __shared__ float part[L / 32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    v = part[0];
+#pragma unroll
+    for (int t = 1; t < L / 32; t++) v = __fadd_rn(v, part[t]);
+    __syncthreads();
+  }
+  return v;
+}
+
+// The sum of the pairs hi + lo of binary32 numbers: each level adds the high parts by TwoSum
+// (exact: its error is the same in both lanes of a pair) and the low parts and that error with
+// two roundings, each at most 2^-24 of the low part; identical total in every lane.
+template <int L>
+__device__ __forceinline__ void group_sum2_f(float* hi, float* lo, unsigned gm) {
+  constexpr int W = L < 32 ? L : 32;
+  float h = *hi, l = *lo;
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(gm, h, o), ol = __shfl_xor_sync(gm, l, o);
+    float e;
+    const float s = __fadd_rn(h, oh);
+    const float bb = __fsub_rn(s, h);
+    e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(oh, bb));
+    h = s;
+    l = __fadd_rn(__fadd_rn(l, ol), e);
+  }
+  if constexpr (L > 32) {
+    __shared__ float ph[L / 32], pl[L / 32];
+    if ((threadIdx.x & 31) == 0) { ph[threadIdx.x >> 5] = h; pl[threadIdx.x >> 5] = l; }
+    __syncthreads();
+    h = ph[0];
+    l = pl[0];
+#pragma unroll
+    for (int t = 1; t < L / 32; t++) {
+      const float s = __fadd_rn(h, ph[t]);
+      const float bb = __fsub_rn(s, h);
+      const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(ph[t], bb));
+      h = s;
+      l = __fadd_rn(__fadd_rn(l, pl[t]), e);
+    }
+    __syncthreads();
+  }
+  *hi = h;
+  *lo = l;
+}
+
 // roundings on the path of group_sum from one lane's value to the total
 template <int L>
 __host__ __device__ constexpr int tree_roundings() {

@@ -279,9 +279,13 @@ __device__ __forceinline__ bool screen_sum(const float* __restrict__ Df, const f
     sh = sn;
     e = __fmaf_rn(fabsf(a), __fmaf_rn(2.5f, w, 6.0f), e);
   }
-  const double sum = group_sum<L>(__dadd_rn((double)sh, (double)sl), gm);
-  const double es = group_sum<L>((double)e, gm);
-  if (SLOPE) *dS = group_sum<L>((double)sd, gm);
+  // the lane group's sums in binary32: the pairs (sh, sl) by TwoSum (the low parts' roundings
+  // stay far below eps A, inside the bound's 5% margin), the bound's sum raised by 2^-20 to cover
+  // its own tree_roundings (at most 16)
+  group_sum2_f<L>(&sh, &sl, gm);
+  const double sum = __dadd_rn((double)sh, (double)sl);
+  const double es = (double)group_sum_f<L>(e, gm) * (1.0 + 0x1p-20);
+  if (SLOPE) *dS = (double)group_sum_f<L>(sd, gm);
   bad = group_any<L>(bad, gm);
   const double m = (double)((n + L - 1) / L);
   *S = sum;
@@ -388,9 +392,11 @@ __device__ __noinline__ bool shift_test_f32(const double* __restrict__ d, const 
     sh = two_sum_f(sh, t, &er);
     sl = __fadd_rn(sl, er);
   }
-  const double S = group_sum<L>(__dadd_rn((double)sh, (double)sl), gm);
-  const double es = group_sum<L>((double)e, gm);
-  const double as = group_sum<L>((double)a1, gm);
+  // the lane group's sums in binary32 as in screen_sum
+  group_sum2_f<L>(&sh, &sl, gm);
+  const double S = __dadd_rn((double)sh, (double)sl);
+  const double es = (double)group_sum_f<L>(e, gm) * (1.0 + 0x1p-20);
+  const double as = (double)group_sum_f<L>(a1, gm) * (1.0 + 0x1p-20);
   ok = !group_any<L>(!ok, gm);
   const double m = (double)((n + L - 1) / L);
   const double g = 1.0 + 2.0 * (m + 2.0) * 0x1p-24;
@@ -498,10 +504,12 @@ __device__ __forceinline__ bool screen_df_sum(const float* __restrict__ F, int n
     e = __fmaf_rn(aq, __fmaf_rn(16.0f, w, 32.0f), e);
   }
   const double sum = group_sum<L>(__dadd_rn(__dadd_rn((double)sh, (double)sl), (double)sll), gm);
-  const double es = group_sum<L>((double)e, gm);
-  const double bs = group_sum<L>((double)bl, gm);
-  const double as = group_sum<L>((double)a1, gm);
-  if (SLOPE) *dS = group_sum<L>((double)sd, gm);
+  // the bound's sums of positive terms in binary32, raised by 2^-20 to cover their own
+  // tree_roundings (at most 16)
+  const double es = (double)group_sum_f<L>(e, gm) * (1.0 + 0x1p-20);
+  const double bs = (double)group_sum_f<L>(bl, gm) * (1.0 + 0x1p-20);
+  const double as = (double)group_sum_f<L>(a1, gm) * (1.0 + 0x1p-20);
+  if (SLOPE) *dS = (double)group_sum_f<L>(sd, gm);
   bad = group_any<L>(bad, gm);
   const double m = (double)((n + L - 1) / L);
   const double g = 1.0 + 2.0 * (m + 2.0) * 0x1p-24;
