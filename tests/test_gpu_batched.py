@@ -173,3 +173,37 @@ def test_autotuner_per_zero_finder(B, tmp_path, monkeypatch):
     lam1 = bt.lam.clone()
     bt.solve(dt, zt, rt, check=True)
     assert torch.max(torch.abs(lam1 - bt.lam) / torch.abs(bt.lam)).item() <= tol(int(sizes.max()))
+
+
+@pytest.mark.parametrize("lanes", [0, 8, 32])
+def test_every_pair_written_once(B, lanes):
+    """Every (problem, k) of a batch is solved exactly once and every output slot is written: the
+    outputs start as NaN, the work counter's solved count equals the number of eigenpairs (each
+    index leaves the queue once), and for every problem (not a sample) each row of V is a unit
+    vector, the eigenvalues keep the order of the poles (strict interlacing on the pairs), and
+    their sum is the trace sum(d) + rho ||z||^2."""
+    offs, d, z, rho = W.batch(P=384, seed=31, nmin=1, nmax=400)
+    sizes = np.diff(offs)
+    bt = B.Batch(sizes)
+    for t in (bt.lam, bt.sigma, bt.mu, bt.xnorm, bt.Vt):
+        t.fill_(float("nan"))
+    bt.solve(cu(d), cu(z), cu(rho), options=B.default_options(lanes=lanes), check=True)
+    torch.cuda.synchronize()
+    st = B.workspace_stats(bt.ws)
+    assert st["solved"] + st["deflated"] == bt.total, st
+    lam, sig, mu, Vt = (t.cpu().numpy() for t in (bt.lam, bt.sigma, bt.mu, bt.Vt))
+    assert np.all(np.isfinite(lam)) and np.all(np.isfinite(sig)) and np.all(np.isfinite(mu))
+    assert np.all(np.isfinite(Vt))
+    for p in range(bt.P):
+        a, b = int(offs[p]), int(offs[p + 1])
+        n = b - a
+        if n == 0:
+            continue
+        dp, zp, rp = d[a:b], z[a:b], float(rho[p])
+        V = Vt[int(bt.voffs_host[p]):int(bt.voffs_host[p]) + n * n].reshape(n, n)
+        assert np.max(np.abs(np.sum(V * V, axis=1) - 1.0)) <= 1e-13 * max(n, 8), p
+        lp = lam[a:b]
+        assert np.all(lp[:-1] >= lp[1:]), p                  # decreasing, with the poles
+        assert np.all(lp >= dp) and np.all(lp[1:] <= dp[:-1]), p
+        scale = np.sum(np.abs(dp)) + rp * np.sum(zp * zp)
+        assert abs(np.sum(lp) - (np.sum(dp) + rp * np.sum(zp * zp))) <= 64 * n * 2.0 ** -53 * scale, p
