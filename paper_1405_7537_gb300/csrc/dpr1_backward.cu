@@ -16,7 +16,7 @@
 //   c = v_p vbar_p + P,  g_p = vbar_p S2 - v_p P,
 //   Lam = dL/dlambda_k + sum_{j != p} g_j v_j / s_j,  T_p = g_p v_p / s_p,  lambdabar = Lam + T_p,
 //   dbar_p += Lam v_p^2 - T_p S2,   zbar_p += (g_p / s_p (S2 - v_p^2) - 2 Lam v_p) / ||x||.
-// Work split: warp w of a fixed set of NWB warps takes rows k = w, w + NWB, ... and keeps
+// Work split: warp w of a set of nwb(n) warps takes rows k = w, w + nwb, ... and keeps
 // its own partial rows of dbar and zbar in the workspace (no atomics), and a final kernel
 // sums the partials in warp order, so the result does not depend on scheduling.
 // The problem is normalised as in the forward (D' = 2^-a D, z' = 2^-b z, rho' = 2^(2b-a) rho,
@@ -34,19 +34,23 @@
 
 namespace dpr1 {
 
-// warps of the row kernel: 152 blocks of 7 warps, one block per SM of a GB300 (a fixed
-// number, so that the partial sums and their order do not depend on the device)
-constexpr int WPB = 7;
-constexpr int NWB = 152 * WPB;
+// warps of the row kernel: 152 blocks of wpb(n) warps, one block per SM of a GB300 (a number
+// fixed by n, so that the partial sums and their order do not depend on the device).  Large
+// orders take more warps: the kernel is latency-bound, and with enough rows per warp (10 at
+// n = 32768 with 21 warps per block) the extra partial rows cost little (backward at n = 32768:
+// 130.7 ms with 7 warps per block, 89.0 with 14, 83.7 with 21; at n = 4096 the 7-warp blocks
+// are fastest, 1.88 against 2.33 and 3.32 ms).
+__host__ __device__ inline int wpb(int64_t n) { return n > 24576 ? 21 : (n > 8192 ? 14 : 7); }
+__host__ __device__ inline int nwb(int64_t n) { return 152 * wpb(n); }
 
 static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct BwdWs {
   unsigned* status;
   int* ex;      // status words 2, 3: the exponents a, b of the normalisation
-  double* pd;   // [NWB][n]
-  double* pz;   // [NWB][n]
-  double* pr;   // [NWB]
+  double* pd;   // [nwb][n]
+  double* pz;   // [nwb][n]
+  double* pr;   // [nwb]
   double* ds;   // [n] d' = 2^-a d
   double* zs;   // [n] z' = 2^-b z
 };
@@ -55,9 +59,10 @@ static size_t bwd_layout(int64_t n, BwdWs* w, char* base) {
   size_t nn = (size_t)(n > 0 ? n : 1);
   size_t off = 0;
   size_t o_st = off; off += 256;
-  size_t o_pd = off; off += a256(sizeof(double) * nn * NWB);
-  size_t o_pz = off; off += a256(sizeof(double) * nn * NWB);
-  size_t o_pr = off; off += a256(sizeof(double) * NWB);
+  const size_t nw = (size_t)nwb(n);
+  size_t o_pd = off; off += a256(sizeof(double) * nn * nw);
+  size_t o_pz = off; off += a256(sizeof(double) * nn * nw);
+  size_t o_pr = off; off += a256(sizeof(double) * nw);
   size_t o_ds = off; off += a256(sizeof(double) * nn);
   size_t o_zs = off; off += a256(sizeof(double) * nn);
   if (w && base) {
@@ -99,11 +104,13 @@ __global__ void k_bwd_scale(int n, const double* __restrict__ d, const double* _
   }
 }
 
+template <int WPB>
 __global__ void __launch_bounds__(32 * WPB, 1) k_bwd_rows(int n, double rho_in, const double* __restrict__ sig,
                                                   const double* __restrict__ mu, const double* __restrict__ gl,
                                                   const double* __restrict__ gV, int64_t ldg, BwdWs w) {
   const int lane = threadIdx.x & 31;
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  constexpr int NWB = 152 * WPB;
   if (wid >= NWB) return;
   const int ea = w.ex[0], eb = w.ex[1];
   const double* __restrict__ d = w.ds;
@@ -206,10 +213,11 @@ __global__ void __launch_bounds__(32 * WPB, 1) k_bwd_rows(int n, double rho_in, 
   }
 }
 
-// grad_d[j] = sum_w pd[w][j] in warp order (w < min(n, NWB)); likewise grad_z and grad_rho.
+// grad_d[j] = sum_w pd[w][j] in warp order (w < min(n, nwb(n))); likewise grad_z and grad_rho.
 __global__ void k_bwd_reduce(int n, BwdWs w, double* __restrict__ gd, double* __restrict__ gz,
                              double* __restrict__ grho) {
-  const int nw = n < NWB ? n : NWB;
+  const int nwt = nwb(n);
+  const int nw = n < nwt ? n : nwt;
   const int ea = w.ex[0], eb = w.ex[1];
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     double a = 0.0, b = 0.0;
@@ -258,7 +266,10 @@ dpr1_status dpr1_eig_backward(int64_t n, const double* d, const double* z, doubl
   if (g > 4 * sm_count()) g = 4 * sm_count();
   k_bwd_norm<<<1, 256, 0, st>>>((int)n, d, z, w);
   k_bwd_scale<<<g, 256, 0, st>>>((int)n, d, z, w);
-  k_bwd_rows<<<NWB / WPB, 32 * WPB, 0, st>>>((int)n, rho, sigma, mu, grad_lambda, grad_Vt, ldg, w);
+  const int wp = wpb(n);
+  if (wp == 21) k_bwd_rows<21><<<152, 32 * 21, 0, st>>>((int)n, rho, sigma, mu, grad_lambda, grad_Vt, ldg, w);
+  else if (wp == 14) k_bwd_rows<14><<<152, 32 * 14, 0, st>>>((int)n, rho, sigma, mu, grad_lambda, grad_Vt, ldg, w);
+  else k_bwd_rows<7><<<152, 32 * 7, 0, st>>>((int)n, rho, sigma, mu, grad_lambda, grad_Vt, ldg, w);
   k_bwd_reduce<<<g, 256, 0, st>>>((int)n, w, grad_d, grad_z, grad_rho);
   return cudaGetLastError() == cudaSuccess ? DPR1_OK : DPR1_ERR_CUDA;
 }
