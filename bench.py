@@ -67,6 +67,25 @@ FP32_PER_FP64 = 64
 # the binary64 pass over the corner's terms that decides whether b needs double-double
 # (kappa_nu of Eq. (knu2)): sub, div, mul, add
 B64_OPS_PER_TERM = 4
+# the binary32 pass of the shift test (shift_test_f32): per term one binary64 subtraction and 16
+# binary32 operations (difference, reciprocal and its Newton step, quotient, w, the bound's two
+# fma, the magnitude sum, TwoSum and the low-part sum); its conversions to binary32 are integer work
+SHIFT32_B64_OPS_PER_TERM = 1
+SHIFT32_OPS_PER_TERM = 16
+# an eigenvector component (Eq. (eigenvecAi)): 2 sub, 1 div, 1 mul, 1 fma (sum of squares), 1 mul
+# (rescale); the solve kernel's lane groups write rows once its queue is empty
+VEC_OPS_PER_ELEMENT = 6
+
+
+def shift_test_ops(n, stats, screen=True):
+    """Binary64 and binary32 operations of the shift tests of one launch (Algorithm 1, the
+    choice of the pole): the eigenvalues k >= 1 each take the binary32 pass (with the screen
+    on) and, where its bound does not settle the sign, the 5-op binary64 pass."""
+    tests = n - 1
+    s32 = stats.get("shift_binary32", 0) if screen else 0
+    ops64 = (n - 1) * (OPS_PER_TERM * (tests - s32) + (SHIFT32_B64_OPS_PER_TERM * tests if screen else 0))
+    ops32 = (n - 1) * SHIFT32_OPS_PER_TERM * tests if screen else 0
+    return ops64, ops32
 # kernels one dpr1_eig call launches: k_norm, k_scan, k_deflate, k_solve, k_classify, k_fix, k_zero_detect,
 # k_zero_solve, k_defl_positions, k_vectors, k_defl_rows, k_trivial
 LAUNCHES_PER_CALL = 12
@@ -444,20 +463,26 @@ def bench_accel(B, dev, d, z, rho, ws, out, flush, steps, bisection_ms):
         raise B.DPR1Error(st, "accelerated timed")
     t = statistics.mean(ms)
     solve = statistics.mean(p[0] for p in ph)
-    ops = (n - 1) * (ACCEL_OPS_PER_TERM * stats["evals_solve"] + (OPS_PER_TERM + B64_OPS_PER_TERM) * n
-                     + DD_OPS_PER_TERM * stats["double_double"])
+    sh64, sh32 = shift_test_ops(n, stats)
+    ops = ((n - 1) * (ACCEL_OPS_PER_TERM * stats["evals_solve"] + B64_OPS_PER_TERM * n
+                      + DD_OPS_PER_TERM * stats["double_double"]) + sh64 + sh32 / FP32_PER_FP64
+           + VEC_OPS_PER_ELEMENT * n * stats.get("tail_rows", 0))
     return {"zero_finder": "accelerated bracketed solve (nearest-pole rational model, value and slope)",
             "value": n / (t * 1e-3), "unit": "eigenpairs/s", "ms_per_step": t, "steps": len(ms),
             "phases_ms": {"solve": solve, "remedies": statistics.mean(p[1] for p in ph),
                           "eigenvectors": statistics.mean(p[2] for p in ph)},
             "evaluations": stats["evals_solve"], "evaluations_per_eigenpair": stats["evals_solve"] / n,
             "speedup_vs_bisection": bisection_ms / t,
-            "solve_kernel_rate": {"achieved": ops / (solve * 1e-3) / 1e12, "unit": "T binary64-op/s",
+            "solve_kernel_rate": {"achieved": ops / (solve * 1e-3) / 1e12, "unit": "T binary64-op-equivalent/s",
                                   "frac": ops / (solve * 1e-3) / NOMINAL_FP64_OPS,
                                   "ops_definition": "(n-1) x (8 ops per secular term and evaluation (5 for the "
-                                                    "value, 3 for the slope) + per eigenvalue the 5-op shift-test "
-                                                    "pass and the 4-op binary64 corner pass + 20 ops per "
-                                                    "double-double term where kappa_nu asks for it)"},
+                                                    "value, 3 for the slope) + per eigenvalue the 4-op binary64 "
+                                                    "corner pass + 20 ops per double-double term where kappa_nu "
+                                                    "asks for it) + the shift tests: per term 1 binary64 and 16 "
+                                                    "binary32 ops of the binary32 pass, and 5 binary64 ops where "
+                                                    "that pass leaves the sign open; the eigenvector rows its "
+                                                    "lane groups write once its queue is empty, 6 binary64 ops "
+                                                    "per component; a binary32 op counts 1/64"},
             "double_double_corners": stats["double_double"]}
 
 
@@ -712,27 +737,37 @@ def run_ours(args):
     probes = stats.get("probes", 0)
     df = stats.get("screened_double_float", 0)
     n_dd = stats["double_double"]
+    tail_rows = stats.get("tail_rows", 0)
     corner = B64_OPS_PER_TERM * n + DD_OPS_PER_TERM * n_dd
     ops32 = 0
     if zf == 0:
         b64_evals = evals - screened - inferred
-        ops64 = (n - 1) * (OPS_PER_TERM * (b64_evals + n) + corner)
-        ops32 = (n - 1) * (B32_OPS_PER_TERM * max(screened + probes - df, 0) + DF_OPS_PER_TERM * df)
+        sh64, sh32 = shift_test_ops(n, stats)
+        ops64 = (n - 1) * (OPS_PER_TERM * b64_evals + corner) + sh64 + VEC_OPS_PER_ELEMENT * n * tail_rows
+        ops32 = (n - 1) * (B32_OPS_PER_TERM * max(screened + probes - df, 0) + DF_OPS_PER_TERM * df) + sh32
         kname = "k_solve (shift test, corner b, screened bisection)"
-        odef = ("binary64: (n-1) x (5 ops (sub, fma, mul, div, add) per secular term x (bisection evaluations in "
-                "binary64 + the shift-test pass) + per eigenvalue the 4-op binary64 pass of the corner b (sub, "
+        odef = ("binary64: (n-1) x (5 ops (sub, fma, mul, div, add) per secular term x the bisection "
+                "evaluations in binary64 + per eigenvalue the 4-op binary64 pass of the corner b (sub, "
                 "div, mul, add) + for the eigenvalues whose kappa_nu asks for it 20 ops per double-double term "
                 "of b (TwoSum 6, TwoProd 2, quotient and correction 5, compensated accumulation 7)); binary32: "
                 "(n-1) x (14 ops per term of a binary32 screen + 50 per term of a double-float screen) over the "
-                "settled screens of bisection steps and probes; a binary32 op counts 1/64 of a binary64 op "
-                "(128 against 2 lanes per SM and clock); steps decided by certified bounds are not counted")
+                "settled screens of bisection steps and probes; the shift tests: per term 1 binary64 and 16 "
+                "binary32 ops of the binary32 pass, and the 5-op binary64 pass where the binary32 pass leaves "
+                "the sign open; the eigenvector rows written by the kernel's lane groups once its queue is "
+                "empty, 6 binary64 ops per component; a binary32 op counts 1/64 of a binary64 op (128 against "
+                "2 lanes per SM and clock); steps decided by certified bounds are not counted")
     else:
         b64_evals = evals
-        ops64 = (n - 1) * (ACCEL_OPS_PER_TERM * evals + OPS_PER_TERM * n + corner)
+        sh64, sh32 = shift_test_ops(n, stats)
+        ops64 = (n - 1) * (ACCEL_OPS_PER_TERM * evals + corner) + sh64 + VEC_OPS_PER_ELEMENT * n * tail_rows
+        ops32 = sh32
         kname = "k_solve (shift test, corner b, accelerated bracketed solve)"
         odef = ("(n-1) x (8 ops per secular term and evaluation (5 for the value, 3 for the slope) + per "
-                "eigenvalue the 5-op shift-test pass and the 4-op binary64 corner pass + 20 ops per "
-                "double-double term for the eigenvalues whose kappa_nu asks for it)")
+                "eigenvalue the 4-op binary64 corner pass + 20 ops per double-double term for the eigenvalues "
+                "whose kappa_nu asks for it) + the shift tests: per term 1 binary64 and 16 binary32 ops of "
+                "the binary32 pass, and 5 binary64 ops where it leaves the sign open; the eigenvector rows "
+                "written by its lane groups once its queue is empty, 6 binary64 ops per component; a binary32 "
+                "op counts 1/64")
     ops = ops64 + ops32 / FP32_PER_FP64
     t_solve = statistics.mean(solve_ms) * 1e-3
     achieved = ops / t_solve
@@ -749,7 +784,7 @@ def run_ours(args):
     measured_fma = sms * 4 * 256 * 4096 * 8 / (pe0.elapsed_time(pe1) * 1e-3)
     roof = {"bound": "alu", "kernel": kname,
             "achieved": achieved / 1e12, "peak": NOMINAL_FP64_OPS / 1e12,
-            "unit": "T binary64-op/s" if zf else "T binary64-op-equivalent/s",
+            "unit": "T binary64-op-equivalent/s",
             "frac": achieved / NOMINAL_FP64_OPS, "traffic": committed_traffic(n, zf),
             "peak_source": "nominal GB300 binary64 1.25 TFLOP/s = 2 fma/clk/SM x 152 SMs x 2070 MHz "
                            "(MEASURED_PEAKS.json has no binary64 entry)",
@@ -762,6 +797,8 @@ def run_ours(args):
             "launch_ms": 1e3 * t_solve, "bisection_evaluations": evals,
             "binary64_evaluations": b64_evals, "screened_steps": screened, "inferred_steps": inferred,
             "screened_probes": probes, "double_float_settled": df, "double_double_corners": n_dd,
+            "shift_tests_binary32": stats.get("shift_binary32", 0),
+            "eigenvector_rows_written": tail_rows,
             # the plain bisection's terms (every step and the shift-test pass) per second
             "term_rate": (n - 1) * (evals + n) / t_solve}
 
@@ -769,14 +806,18 @@ def run_ours(args):
     # the n^2 write of V against the measured copy rate, and its binary64 work against the peak
     t_vec = statistics.mean(vec_ms) * 1e-3
     hbm_peak = measured_hbm_gbs()
-    v_bytes = 8.0 * n * n
-    v_ops = 6.0 * n * n
+    # the rows k_vectors writes: those the solve kernel's tail did not, and the tail's rows whose
+    # pair the remedies changed
+    vec_rows = stats.get("vector_rows", n - tail_rows)
+    v_bytes = 8.0 * n * vec_rows
+    v_ops = float(VEC_OPS_PER_ELEMENT) * n * vec_rows
     hbm_frac = v_bytes / t_vec / (hbm_peak[0] * 1e9)
     alu_frac = v_ops / t_vec / NOMINAL_FP64_OPS
     phase_roofs = {"eigenvectors": {
         "bound": "alu" if alu_frac >= hbm_frac else "hbm", "ms": 1e3 * t_vec,
         "hbm": {"achieved": v_bytes / t_vec / 1e9, "peak": hbm_peak[0], "unit": "GB/s", "frac": hbm_frac,
-                "peak_source": hbm_peak[1], "bytes_definition": "8 n^2 bytes of V written once"},
+                "peak_source": hbm_peak[1], "rows": vec_rows,
+                "bytes_definition": "8 n bytes per row of V that k_vectors writes, once"},
         "alu": {"achieved": v_ops / t_vec / 1e12, "peak": NOMINAL_FP64_OPS / 1e12, "unit": "T binary64-op/s",
                 "frac": alu_frac, "ops_definition": "per element: 2 sub, 1 div, 1 mul, 1 fma (sum of squares), "
                                                     "1 mul (rescale)"}}}

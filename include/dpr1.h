@@ -122,9 +122,13 @@ DPR1_API const char* dpr1_status_string(dpr1_status s);
  * the inverse of its shifted matrix, Delta_j = d_j - d_i and zeta_j^2 / Delta_j of Eq. (invAi),
  * once per eigenvalue (in binary64 and as pairs of binary32 numbers for the screens of the
  * bisection steps), and every bisection step reads them instead of forming them again.
- * These buffers are optional: a smaller workspace is accepted down to the part without
+ * For n > 2048 it also includes 36n bytes (and 256 of alignment) after the buffers, where
+ * the solve kernel's lane groups that find its queue empty record the eigenvector rows they
+ * write (Eq. (eigenvecAi)) for the eigenvalues solved by then.
+ * These parts are optional: a smaller workspace is accepted down to the part without
  * them (every evaluation of the secular function then forms the elements again, with the same accuracy
- * bound); below that part the call returns DPR1_ERR_WORKSPACE.
+ * bound, and the eigenvector kernel writes every row); below that part the call returns
+ * DPR1_ERR_WORKSPACE.  The results are the same bits with or without them.
  */
 DPR1_API size_t dpr1_workspace_size(int64_t n);
 
@@ -362,7 +366,7 @@ DPR1_API dpr1_status dpr1_eig_noalloc(int64_t n, const double* d, const double* 
 /*
  * Instrumentation (no counterpart in the paper): synchronises `stream` and copies the
  * counters of the last dpr1_eig / dpr1_eig_batched / dpr1_arrow_eig call on `workspace` into
- * out[0..14]:
+ * out[0..17]:
  *   0 eigenvalues solved by the bisection kernel, 1 eigenvalues flagged by K_nu,
  *   2 remedies taken with R1, 3 with R2, 4 secular-function evaluations in the bisection
  *   kernel, 5 evaluations in the remedy kernel, 6 eigenvalues recomputed from A^{-1},
@@ -373,8 +377,12 @@ DPR1_API dpr1_status dpr1_eig_noalloc(int64_t n, const double* d, const double* 
  *   exceeded the screen's error bound by less than a factor 2, 12 screened evaluations (steps
  *   of 9 and probes of 14) settled by the double-float screen, 13 bisection steps (of those
  *   counted in 4 and 5) decided by bounds that screened probes certified, without an
- *   evaluation, 14 screened probes that placed those bounds (not counted in 4 and 5).
- *   `out` holds 15 values.
+ *   evaluation, 14 screened probes that placed those bounds (not counted in 4 and 5),
+ *   15 shift tests of the bisection kernel whose sign the binary32 pass settled (the others
+ *   take the binary64 pass), 16 eigenvector rows written by the bisection kernel's lane
+ *   groups after its queue ran out (the eigenvector kernel writes the others), 17 eigenvector
+ *   rows written by the eigenvector kernel (the others, and those of 16 whose pair a remedy or
+ *   the near-zero path changed).  `out` holds 18 values.
  */
 DPR1_API dpr1_status dpr1_workspace_stats(void* workspace, int64_t* out, dpr1_stream_t stream);
 

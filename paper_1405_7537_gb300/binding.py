@@ -275,7 +275,7 @@ def probe_reciprocal(x):
 
 STAT_NAMES = ("solved", "flagged", "r1", "r2", "evals_solve", "evals_fix", "zero_path", "deflated", "double_double",
               "screened", "r2_double_double", "screened_near_bound", "screened_double_float", "inferred",
-              "probes")
+              "probes", "shift_binary32", "tail_rows", "vector_rows")
 
 
 def workspace_stats(ws, stream=None):

@@ -62,11 +62,22 @@
 #ifndef DPR1_FIX_SMALL_N
 #define DPR1_FIX_SMALL_N 1024
 #endif
+// lane groups of the solve kernel that find its queue empty write the eigenvector rows of the
+// eigenvalues solved so far (one problem of order above DPR1_SOLVE_LARGE_N with eigenvectors)
+#ifndef DPR1_TAIL_ROWS
+#define DPR1_TAIL_ROWS 1
+#endif
+// eigenvector rows as pairs of components with 16-byte accesses
+#ifndef DPR1_VEC_PAIRS
+#define DPR1_VEC_PAIRS 1
+#endif
 
 namespace dpr1 {
 
 constexpr bool kShiftAhi = DPR1_SHIFT_AHI != 0;
 constexpr bool kShift32 = DPR1_SHIFT32 != 0 && !kShiftAhi;
+constexpr bool kTailRows = DPR1_TAIL_ROWS != 0;
+constexpr bool kVecPairs = DPR1_VEC_PAIRS != 0;
 
 // ---------------------------------------------------------------------------------
 // Workspace layout
@@ -133,6 +144,8 @@ size_t ws_layout2(int64_t total, int64_t nprob, bool batched, Ws* w, char* base)
     w->terms = nullptr;
     w->term_n = 0;
     w->term_slots = 0;
+    w->vrow = nullptr;
+    w->vstate = nullptr;
   }
   return off;
 }
@@ -145,6 +158,13 @@ static int default_lanes(double avg_n) { return avg_n <= 96 ? 8 : (avg_n <= 384 
 // SM), term_n = n for
 // one problem and max(2048, 4 n_avg) (at most total) for a batch; problems of larger order,
 // and groups beyond the buffers under other launch options, form the elements per evaluation.
+// Bytes of the records of the eigenvector rows the solve kernel's tail writes (after the buffers,
+// 256-byte aligned): one problem of order above DPR1_SOLVE_LARGE_N.
+static size_t tail_bytes(int64_t total, int64_t nprob) {
+  if (!kTailRows || nprob != 1 || total <= DPR1_SOLVE_LARGE_N) return 0;
+  return 256 + align256(sizeof(double) * 4 * (size_t)total) + align256(sizeof(unsigned) * (size_t)total);
+}
+
 size_t term_bytes(int64_t total, int64_t nprob) {
   if (total <= 0 || nprob <= 0) return 0;
   const double avg = (double)total / (double)nprob;
@@ -160,7 +180,7 @@ size_t term_bytes(int64_t total, int64_t nprob) {
     if (tn > total) tn = total;
   }
   tn = (tn + 31) & ~(int64_t)31;
-  return (size_t)groups * TERM_BYTES * (size_t)tn;
+  return (size_t)groups * TERM_BYTES * (size_t)tn + tail_bytes(total, nprob);
 }
 
 size_t ws_layout(int64_t n, Ws* w, char* base) { return ws_layout2(n, 1, false, w, base); }
@@ -440,6 +460,120 @@ __global__ void k_deflate(Prob pb, Ws w) {
 //   k = 1:           mu in [rho zeta_1^2, rho ||z||^2] -> nu in [1/(rho ||z||^2), 1/(rho zeta_1^2)]
 // (solve_pole checks the near end, so a wrong sign of a rounded F costs steps, not accuracy).
 // ---------------------------------------------------------------------------------
+// ---------------------------------------------------------------------------------
+// One eigenvector row by a warp (Eq. (eigenvecAi)): x_j = zeta_j / ((d_j - sigma) - mu) (for a
+// pole shift d_i, x_i = -zeta_i / mu), ||x|| with a scaled fallback when the plain sum of squares
+// over- or underflows.  With vr the row v = x / ||x|| is written there: the first pass stores
+// x_j as it forms them (pairs of components from a 16-byte aligned position, lane 0 taking an
+// unaligned first and an unpaired last one) and the second rescales them in place.  Returns
+// *nrm = ||x|| scale and *scale (v_j = x_j scale / *nrm).
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ void row_values(const double* __restrict__ d, const double* __restrict__ z, int n,
+                                           double s, double m, double* __restrict__ vr, int lane, double* nrm_out,
+                                           double* scale_out) {
+  const bool store = vr != nullptr;
+  double q = 0.0;
+  bool bad = false;
+  const int j0 = (store && kVecPairs && (((uintptr_t)vr) & 15)) ? 1 : 0;
+  const int npair = (store && kVecPairs) ? (n - j0) >> 1 : 0;
+  const int jtail = j0 + 2 * npair;
+  if (store && kVecPairs) {
+    for (int t = lane; t < npair; t += 32) {
+      const int j = j0 + 2 * t;
+      const double den0 = __dsub_rn(__dsub_rn(d[j], s), m), den1 = __dsub_rn(__dsub_rn(d[j + 1], s), m);
+      double2 x;
+      x.x = __dmul_rn(z[j], rcp_nr(den0));
+      x.y = __dmul_rn(z[j + 1], rcp_nr(den1));
+      bad |= !rcp_in_range(den0) || !rcp_in_range(den1);
+      *reinterpret_cast<double2*>(vr + j) = x;
+      q = __fma_rn(x.x, x.x, q);
+      q = __fma_rn(x.y, x.y, q);
+    }
+    if (lane == 0) {
+      // the unaligned first component (j0 = 1) and the unpaired last one (jtail = n - 1)
+      for (int e = 0; e < 2; e++) {
+        const int j = e == 0 ? (j0 ? 0 : -1) : (jtail < n ? jtail : -1);
+        if (j < 0) continue;
+        const double den = __dsub_rn(__dsub_rn(d[j], s), m);
+        const double x = __dmul_rn(z[j], rcp_nr(den));
+        bad |= !rcp_in_range(den);
+        vr[j] = x;
+        q = __fma_rn(x, x, q);
+      }
+    }
+  } else {
+    for (int j = lane; j < n; j += 32) {
+      const double den = __dsub_rn(__dsub_rn(d[j], s), m);
+      const double x = __dmul_rn(z[j], rcp_nr(den));
+      bad |= !rcp_in_range(den);
+      if (store) vr[j] = x;
+      q = __fma_rn(x, x, q);
+    }
+  }
+  q = group_sum<32>(q, FULL);
+  bad = group_any<32>(bad, FULL);
+  double scale = 1.0;                  // v_j = x_j * scale / sqrt(q)
+  bool rewrite = false;                // the stored x_j are not usable: write v_j from scratch
+  if (bad || !(q < 1e300) || !(q > 1e-280)) {
+    double mx = 0.0;
+    for (int j = lane; j < n; j += 32) mx = fmax(mx, fabs(__dmul_rn(z[j], rcp(__dsub_rn(__dsub_rn(d[j], s), m)))));
+    mx = group_max<32>(mx, FULL);
+    scale = 1.0 / mx;
+    q = 0.0;
+    for (int j = lane; j < n; j += 32) {
+      double x = __dmul_rn(z[j], rcp(__dsub_rn(__dsub_rn(d[j], s), m))) * scale;
+      q = __fma_rn(x, x, q);
+    }
+    q = group_sum<32>(q, FULL);
+    rewrite = true;
+  }
+  const double nrm = sqrt(q);          // ||x|| * scale
+  const double c = scale / nrm;
+  *nrm_out = nrm;
+  *scale_out = scale;
+  if (!store) return;
+  if (!rewrite && kVecPairs) {
+    for (int t = lane; t < npair; t += 32) {
+      const int j = j0 + 2 * t;
+      double2 x = *reinterpret_cast<const double2*>(vr + j);
+      x.x = __dmul_rn(x.x, c);
+      x.y = __dmul_rn(x.y, c);
+      *reinterpret_cast<double2*>(vr + j) = x;
+    }
+    if (lane == 0) {
+      if (j0) vr[0] = __dmul_rn(vr[0], c);
+      if (jtail < n) vr[n - 1] = __dmul_rn(vr[n - 1], c);
+    }
+  } else if (!rewrite) {
+    for (int j = lane; j < n; j += 32) vr[j] = __dmul_rn(vr[j], c);
+  } else {
+    for (int j = lane; j < n; j += 32) vr[j] = __dmul_rn(z[j], rcp(__dsub_rn(__dsub_rn(d[j], s), m))) * c;
+  }
+}
+
+// A row written by the solve kernel's tail, out of line (the solve loop keeps its registers),
+// and its record: the pair it was formed from, ||x|| scale and the scale.
+__device__ __noinline__ void tail_row(const double* __restrict__ d, const double* __restrict__ z, int n, double s,
+                                      double m, double* __restrict__ vr, int lane, double* __restrict__ rec) {
+  double nrm, scale;
+  row_values(d, z, n, s, m, vr, lane, &nrm, &scale);
+  if (lane == 0) {
+    rec[0] = s;
+    rec[1] = m;
+    rec[2] = nrm;
+    rec[3] = scale;
+  }
+}
+
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 template <int L, int MINB, bool NI>
 __global__ void __launch_bounds__(256, MINB)
     k_solve(Prob pb, Ws w, int cap, bool fast, int dd_mode, double T_kappa, bool screen) {
@@ -453,7 +587,36 @@ __global__ void __launch_bounds__(256, MINB)
     long long gl = 0;
     if (lane == 0) gl = (long long)atomicAdd(&w.counters64[0], 1ull);
     gl = __shfl_sync(gm, gl, leader, 32);
-    if (gl >= pb.total) break;
+    if (gl >= pb.total) {
+      if constexpr (kTailRows && L == 32 && NI) {
+        // the queue is empty: write the eigenvector rows of the eigenvalues solved so far (one
+        // problem without deflation), sweeping all rows once in order.  A row whose eigenvalue is
+        // still being solved is left to k_vectors (writing it here would lengthen the kernel's
+        // last, slowest solves), and so is one whose pair a later kernel changes.  Bisection
+        // only: the accelerated solve's eigenvalues take even times and leave no idle tail.
+        if (!fast && w.vstate && pb.P == 1 && pb.Vt && w.nred[0] == pb.total) {
+          const int n = (int)pb.total;
+          for (;;) {
+            unsigned r = 0, st = 0;
+            if (lane == 0) {
+              r = atomicAdd(&w.counters[C_TROW], 1u);
+              if (r < (unsigned)n) st = ld_acquire(w.vstate + r);
+            }
+            r = __shfl_sync(gm, r, 0, 32);
+            st = __shfl_sync(gm, st, 0, 32);
+            if (r >= (unsigned)n) break;
+            if (st != 1u) continue;
+            tail_row(w.dr, w.zr, n, __ldcg(w.sig + r), __ldcg(w.mu + r), pb.Vt + (int64_t)r * pb.ldv0, lane,
+                     w.vrow + 4 * (int64_t)r);
+            if (lane == 0) {
+              w.vstate[r] = 2u;
+              atomicAdd(&w.counters[C_TAILROWS], 1u);
+            }
+          }
+        }
+      }
+      break;
+    }
     const int64_t g = gl;
     const int p = p_owner(pb, w, g);
     if (w.pst[p] & PT_TRIVIAL) continue;
@@ -467,6 +630,7 @@ __global__ void __launch_bounds__(256, MINB)
     const double* __restrict__ zz = w.zz + base;
     int i;
     double alo, ahi;
+    bool shift32 = false;
     if (k == 0) {
       double s = 0.0;
       for (int j = lane; j < n; j += L) s = __dadd_rn(s, zz[j]);
@@ -481,6 +645,7 @@ __global__ void __launch_bounds__(256, MINB)
       // the binary32 pass decides where its bound settles the sign (the binary64 pass's sign)
       const bool f32 = kShift32 && screen && shift_test_f32<L>(d, zz, n, dk, tau, rho, lane, gm, &F, &EF) &&
                        fabs(F) > EF;
+      shift32 = f32;
       if (!f32) {
         for (int j = lane; j < n; j += L) {
           double den = __dsub_rn(__dsub_rn(d[j], dk), tau);
@@ -513,6 +678,7 @@ __global__ void __launch_bounds__(256, MINB)
       if (pr.screened_df) atomicAdd(&w.counters[C_SCREEN_DF], (unsigned)pr.screened_df);
       if (pr.inferred) atomicAdd(&w.counters[C_INFER], (unsigned)pr.inferred);
       if (pr.probes) atomicAdd(&w.counters[C_PROBE], (unsigned)pr.probes);
+      if (shift32) atomicAdd(&w.counters[C_SHIFT32], 1u);
       w.sig[g] = d[i];
       w.mu[g] = pr.mu;
       w.shift[g] = i;
@@ -520,6 +686,7 @@ __global__ void __launch_bounds__(256, MINB)
       atomicAdd(&w.counters[C_EVAL_SOLVE], (unsigned)pr.steps);
       atomicAdd(&w.counters[C_SOLVED], 1u);
       if (!pr.ok) atomicOr(w.status, ST_NOT_CONVERGED);
+      if (w.vstate) st_release(w.vstate + g, 1u);     // (sigma, mu) written: the row may be formed
     }
   }
 }
@@ -858,7 +1025,9 @@ __global__ void k_defl_positions(Prob pb, Ws w) {
 // the squares, the second rescales the row in place (FP64 work once, the row written twice).
 // Writes lambda, sigma, mu, ||x|| and row k of the problem's V^T block (coalesced along
 // j).  In a deflated problem the row of reduced eigenvalue k goes to output row rpos and
-// component q takes coef[q] * x_{src[q]}; deflated pairs are written by k_defl_rows.
+// component q takes coef[q] * x_{src[q]}; deflated pairs are written by k_defl_rows.  A row the
+// solve kernel's tail wrote (row_values, the same arithmetic) is kept when its record holds the
+// final (sigma, mu); rows whose pair the remedies or the near-zero path changed are written anew.
 // ---------------------------------------------------------------------------------
 // Scalar outputs of eigenpair g (reduced index k, output row `row`) in the caller's units --
 // lambda, sigma, mu times 2^a and ||x|| times 2^(b - a) -- and the range check: the pair needs
@@ -884,11 +1053,6 @@ __device__ __forceinline__ void pair_outputs(const Prob& pb, const Ws& w, int p,
   if (out) atomicOr(w.status, ST_RANGE);
 }
 
-#ifndef DPR1_VEC_PAIRS
-#define DPR1_VEC_PAIRS 1
-#endif
-constexpr bool kVecPairs = DPR1_VEC_PAIRS != 0;
-
 __global__ void __launch_bounds__(256) k_vectors(Prob pb, Ws w) {
   if (*w.status & ST_FATAL) return;
   const int lane = threadIdx.x & 31;
@@ -908,93 +1072,29 @@ __global__ void __launch_bounds__(256) k_vectors(Prob pb, Ws w) {
     const double s = w.sig[g], m = w.mu[g];
     const int row = defl ? w.rpos[g] : k;
     double* vr = pb.Vt ? pb.Vt + p_vbase(pb, p) + (int64_t)row * p_ld(pb, p) : nullptr;
-    // First pass: x_j (fast reciprocal, range flag) and sum x_j^2; without deflation x_j is
-    // stored in its row at once and the second pass only rescales it.
-    const bool store = vr && !defl;
-    double q = 0.0;
-    bool bad = false;
-    // with a stored row: pairs of components j, j + 1 from a 16-byte aligned position j0, written
-    // and rescaled with 16-byte accesses (lane 0 takes an unaligned first and an unpaired last one)
-    const int j0 = (store && kVecPairs && (((uintptr_t)vr) & 15)) ? 1 : 0;
-    const int npair = (store && kVecPairs) ? (n - j0) >> 1 : 0;
-    const int jtail = j0 + 2 * npair;
-    if (store && kVecPairs) {
-      for (int t = lane; t < npair; t += 32) {
-        const int j = j0 + 2 * t;
-        const double den0 = __dsub_rn(__dsub_rn(d[j], s), m), den1 = __dsub_rn(__dsub_rn(d[j + 1], s), m);
-        double2 x;
-        x.x = __dmul_rn(z[j], rcp_nr(den0));
-        x.y = __dmul_rn(z[j + 1], rcp_nr(den1));
-        bad |= !rcp_in_range(den0) || !rcp_in_range(den1);
-        *reinterpret_cast<double2*>(vr + j) = x;
-        q = __fma_rn(x.x, x.x, q);
-        q = __fma_rn(x.y, x.y, q);
-      }
-      if (lane == 0) {
-        // the unaligned first component (j0 = 1) and the unpaired last one (jtail = n - 1)
-        for (int e = 0; e < 2; e++) {
-          const int j = e == 0 ? (j0 ? 0 : -1) : (jtail < n ? jtail : -1);
-          if (j < 0) continue;
-          const double den = __dsub_rn(__dsub_rn(d[j], s), m);
-          const double x = __dmul_rn(z[j], rcp_nr(den));
-          bad |= !rcp_in_range(den);
-          vr[j] = x;
-          q = __fma_rn(x, x, q);
-        }
-      }
-    } else {
-      for (int j = lane; j < n; j += 32) {
-        const double den = __dsub_rn(__dsub_rn(d[j], s), m);
-        const double x = __dmul_rn(z[j], rcp_nr(den));
-        bad |= !rcp_in_range(den);
-        if (store) vr[j] = x;
-        q = __fma_rn(x, x, q);
+    if (w.vstate && vr && !defl && w.vstate[g] == 2u) {
+      // the solve kernel's tail wrote the row: kept if it was formed from the final pair
+      const double* rec = w.vrow + 4 * g;
+      if (__double_as_longlong(rec[0]) == __double_as_longlong(s) &&
+          __double_as_longlong(rec[1]) == __double_as_longlong(m)) {
+        if (lane == 0) pair_outputs(pb, w, p, g, base, k, row, d, s, m, rec[2], rec[3], rec[3] / rec[2]);
+        continue;
       }
     }
-    q = group_sum<32>(q, FULL);
-    bad = group_any<32>(bad, FULL);
-    double scale = 1.0;                  // v_j = x_j * scale / sqrt(q)
-    bool rewrite = false;                // the stored x_j are not usable: write v_j from scratch
-    if (bad || !(q < 1e300) || !(q > 1e-280)) {
-      double mx = 0.0;
-      for (int j = lane; j < n; j += 32) mx = fmax(mx, fabs(__dmul_rn(z[j], rcp(__dsub_rn(__dsub_rn(d[j], s), m)))));
-      mx = group_max<32>(mx, FULL);
-      scale = 1.0 / mx;
-      q = 0.0;
-      for (int j = lane; j < n; j += 32) {
-        double x = __dmul_rn(z[j], rcp(__dsub_rn(__dsub_rn(d[j], s), m))) * scale;
-        q = __fma_rn(x, x, q);
-      }
-      q = group_sum<32>(q, FULL);
-      rewrite = true;
-    }
-    const double nrm = sqrt(q);          // ||x|| * scale
+    // without deflation the row is written with its norm; a deflated row is written below
+    double nrm, scale;
+    row_values(d, z, n, s, m, defl ? nullptr : vr, lane, &nrm, &scale);
     const double c = scale / nrm;
-    if (lane == 0) pair_outputs(pb, w, p, g, base, k, row, d, s, m, nrm, scale, c);
-    if (!vr) continue;
-    if (!defl && !rewrite && kVecPairs) {
-      for (int t = lane; t < npair; t += 32) {
-        const int j = j0 + 2 * t;
-        double2 x = *reinterpret_cast<const double2*>(vr + j);
-        x.x = __dmul_rn(x.x, c);
-        x.y = __dmul_rn(x.y, c);
-        *reinterpret_cast<double2*>(vr + j) = x;
-      }
-      if (lane == 0) {
-        if (j0) vr[0] = __dmul_rn(vr[0], c);
-        if (jtail < n) vr[n - 1] = __dmul_rn(vr[n - 1], c);
-      }
-    } else if (!defl && !rewrite) {
-      for (int j = lane; j < n; j += 32) vr[j] = __dmul_rn(vr[j], c);
-    } else if (!defl) {
-      for (int j = lane; j < n; j += 32) vr[j] = __dmul_rn(z[j], rcp(__dsub_rn(__dsub_rn(d[j], s), m))) * c;
-    } else {
-      for (int qq = lane; qq < nfull; qq += 32) {
-        int sj = w.src[base + qq];
-        double v = 0.0;
-        if (sj >= 0) v = w.coef[base + qq] * (__dmul_rn(z[sj], rcp(__dsub_rn(__dsub_rn(d[sj], s), m))) * c);
-        vr[qq] = v;
-      }
+    if (lane == 0) {
+      pair_outputs(pb, w, p, g, base, k, row, d, s, m, nrm, scale, c);
+      if (vr) atomicAdd(&w.counters[C_VECROWS], 1u);
+    }
+    if (!vr || !defl) continue;
+    for (int qq = lane; qq < nfull; qq += 32) {
+      int sj = w.src[base + qq];
+      double v = 0.0;
+      if (sj >= 0) v = w.coef[base + qq] * (__dmul_rn(z[sj], rcp(__dsub_rn(__dsub_rn(d[sj], s), m))) * c);
+      vr[qq] = v;
     }
   }
 }
@@ -1226,11 +1326,23 @@ static dpr1_status run_table(const Prob& pb, void* workspace, size_t wbytes, con
     const size_t tb = wbytes - base;
     const int64_t groups = (int64_t)grid * groups_per_block;
     int64_t tn = (int64_t)(tb / (TERM_BYTES * (size_t)groups)) & ~(int64_t)31;
-    if (pb.P == 1 && tn < pb.total) tn = (pb.total + 31) & ~(int64_t)31;
+    if (pb.P == 1) tn = (pb.total + 31) & ~(int64_t)31;
     if (tn >= 32 && (size_t)groups * TERM_BYTES * (size_t)tn <= tb) {
       w.terms = (double*)((char*)workspace + base);
       w.term_n = tn;
       w.term_slots = groups;
+      // after the buffers, the records of the eigenvector rows the solve kernel's tail writes
+      // (one problem, solved by the kernel's large form, with eigenvectors)
+      if (kTailRows && pb.P == 1 && pb.Vt && L == 32 && avg_n > DPR1_SOLVE_LARGE_N) {
+        const size_t at = align256(base + (size_t)groups * TERM_BYTES * (size_t)tn);
+        const size_t rec = align256(sizeof(double) * 4 * (size_t)pb.total);
+        if (at + rec + align256(sizeof(unsigned) * (size_t)pb.total) <= wbytes) {
+          w.vrow = (double*)((char*)workspace + at);
+          w.vstate = (unsigned*)((char*)workspace + at + rec);
+          if (cudaMemsetAsync(w.vstate, 0, sizeof(unsigned) * (size_t)pb.total, st) != cudaSuccess)
+            return DPR1_ERR_CUDA;
+        }
+      }
     }
   }
   if (L == 8) launch_solve_fix<8>(pb, w, o, grid, warps, avg_n, st);
@@ -1392,6 +1504,9 @@ dpr1_status dpr1_workspace_stats(void* workspace, int64_t* out, dpr1_stream_t st
   out[12] = c[C_SCREEN_DF];
   out[13] = c[C_INFER];
   out[14] = c[C_PROBE];
+  out[15] = c[C_SHIFT32];
+  out[16] = c[C_TAILROWS];
+  out[17] = c[C_VECROWS];
   return DPR1_OK;
 }
 

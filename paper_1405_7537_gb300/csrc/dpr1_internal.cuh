@@ -48,6 +48,11 @@ struct Ws {
   double* terms;
   int64_t term_n;
   int64_t term_slots;
+  // eigenvector rows written by the solve kernel's lane groups once its queue is empty (one
+  // problem without deflation): vstate[g] 0 unsolved, 1 solved, 2 row written; vrow[4 g ..]
+  // the sigma, mu, ||x|| (scaled) and scale it was formed with; nullptr: k_vectors writes every row
+  double* vrow;
+  unsigned* vstate;
 };
 
 struct Options {
@@ -66,7 +71,8 @@ struct Options {
 enum : int {
   C_FIX_N = 1, C_FIX_Q = 2, C_ZERO_N = 3, C_EVAL_SOLVE = 4, C_EVAL_FIX = 5,
   C_R2 = 6, C_R1 = 7, C_SOLVED = 8, C_DEFL = 9, C_DD = 10, C_SCREEN = 11, C_R2DD = 12,
-  C_SCREEN_NEAR = 13, C_SCREEN_DF = 14, C_INFER = 18, C_PROBE = 19
+  C_SCREEN_NEAR = 13, C_SCREEN_DF = 14, C_INFER = 18, C_PROBE = 19, C_SHIFT32 = 20, C_TROW = 21,
+  C_TAILROWS = 22, C_VECROWS = 23
 };
 
 // per-problem bits (Ws::pst)

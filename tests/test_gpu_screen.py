@@ -73,6 +73,7 @@ def test_screen_changes_no_bit(B, case):
     off, st_off = solve(B, d, z, rho, 0, **opt)
     same_bits(on, off)
     assert st_off["screened"] == 0 and st_off["inferred"] == 0 and st_off["probes"] == 0
+    assert st_off["shift_binary32"] == 0
     assert (st_on["r1"], st_on["r2"], st_on["flagged"]) == (st_off["r1"], st_off["r2"], st_off["flagged"])
     # binary64 evaluations with the screens: all steps less those settled by a screen or a
     # certified bound (plus at most two end re-evaluations per solve)
@@ -80,6 +81,8 @@ def test_screen_changes_no_bit(B, case):
         settled = st_on["screened"] + st_on["inferred"]
         assert settled > 0.4 * st_off["evals_solve"], (st_on, st_off)
         assert st_on["evals_solve"] - settled < 0.6 * st_off["evals_solve"], (st_on, st_off)
+        # the shift tests the binary32 pass settles (of the n - 1 with k >= 1)
+        assert st_on["shift_binary32"] > 0.5 * d.size, st_on
 
 
 def test_screen_in_a_batch(B):
