@@ -64,6 +64,10 @@ struct ArrowWs {
   double* terms;
   int64_t term_n;
   int64_t term_slots;
+  // the eigenvector rows the solve kernel's tail writes, as Ws::vrow and Ws::vstate (nullptr: the
+  // vectors kernel writes every row)
+  double* vrow;
+  unsigned* vstate;
 };
 
 static size_t arrow_layout(int64_t n, ArrowWs* w, char* base) {
@@ -101,11 +105,17 @@ static size_t arrow_layout(int64_t n, ArrowWs* w, char* base) {
     w->terms = nullptr;
     w->term_n = 0;
     w->term_slots = 0;
+    w->vrow = nullptr;
+    w->vstate = nullptr;
   }
   return off;
 }
 
 constexpr unsigned ST_FATAL_A = ST_NONFINITE | ST_UNSORTED | ST_BADARG;
+// the solve kernel's shift test from the binary32 pass where its bound decides the sign
+constexpr bool kArrowShift32 = DPR1_SHIFT32 != 0;
+// orders n above which the solve kernel's tail writes eigenvector rows
+constexpr int64_t kArrowTailMinN = 2048;
 constexpr unsigned AH_ZERO_POLE = 1u;   // header word 1: some d_j == 0 (no near-zero recompute)
 // remedies kernel: block-wide lane groups, two blocks per SM (as for D + rho z z^T)
 constexpr int AH_FIX_THREADS = 256;
@@ -301,11 +311,76 @@ __device__ PoleResult solve_pole_arrow(const double* __restrict__ d, const doubl
   return r;
 }
 
-// One lane group per eigenvalue k = 0..n (persistent grid, work counter).
+// One eigenvector row v = [x; -1] / ||.|| by a warp: x_j = zeta_j / ((d_j - sigma) - mu), ||[x; -1]||
+// with a scaled fallback when the plain sum of squares overflows or a reciprocal leaves the fast
+// range.  With vr the row is written (x_j stored as formed, then rescaled in place; the last
+// component -c by lane 0).  Returns *nrm = ||[x; -1]|| scale and *scale.
+__device__ __forceinline__ void arrow_row_values(const double* __restrict__ d, const double* __restrict__ z, int n,
+                                                 double s, double m, double* __restrict__ vr, int lane,
+                                                 double* nrm_out, double* scale_out) {
+  double q = 0.0;
+  bool bad = false;
+  for (int j = lane; j < n; j += 32) {
+    const double den = __dsub_rn(__dsub_rn(d[j], s), m);
+    const double x = __dmul_rn(z[j], rcp_nr(den));
+    bad |= !rcp_in_range(den);
+    if (vr) vr[j] = x;
+    q = __fma_rn(x, x, q);
+  }
+  q = group_sum<32>(q, FULL);
+  q = __dadd_rn(q, 1.0);                        // the last component, -1
+  bad = group_any<32>(bad, FULL);
+  double scale = 1.0;
+  bool rewrite = false;
+  if (bad || !(q < 1e300)) {
+    double mx = 1.0;
+    for (int j = lane; j < n; j += 32) mx = fmax(mx, fabs(__dmul_rn(z[j], rcp(__dsub_rn(__dsub_rn(d[j], s), m)))));
+    mx = group_max<32>(mx, FULL);
+    scale = 1.0 / mx;
+    q = 0.0;
+    for (int j = lane; j < n; j += 32) {
+      const double x = __dmul_rn(z[j], rcp(__dsub_rn(__dsub_rn(d[j], s), m))) * scale;
+      q = __fma_rn(x, x, q);
+    }
+    q = group_sum<32>(q, FULL);
+    q = __fma_rn(scale, scale, q);
+    rewrite = true;
+  }
+  const double nrm = sqrt(q);
+  const double c = scale / nrm;
+  *nrm_out = nrm;
+  *scale_out = scale;
+  if (!vr) return;
+  if (lane == 0) vr[n] = -c;
+  if (!rewrite) {
+    for (int j = lane; j < n; j += 32) vr[j] = __dmul_rn(vr[j], c);
+  } else {
+    for (int j = lane; j < n; j += 32) vr[j] = __dmul_rn(z[j], rcp(__dsub_rn(__dsub_rn(d[j], s), m))) * c;
+  }
+}
+
+// A row written by the solve kernel's tail, out of line, and its record (pair, norm, scale).
+__device__ __noinline__ void arrow_tail_row(const double* __restrict__ d, const double* __restrict__ z, int n,
+                                            double s, double m, double* __restrict__ vr, int lane,
+                                            double* __restrict__ rec) {
+  double nrm, scale;
+  arrow_row_values(d, z, n, s, m, vr, lane, &nrm, &scale);
+  if (lane == 0) {
+    rec[0] = s;
+    rec[1] = m;
+    rec[2] = nrm;
+    rec[3] = scale;
+  }
+}
+
+// One lane group per eigenvalue k = 0..n (persistent grid, work counter).  Once the counter is
+// exhausted, with eigenvectors and the rows' records in the workspace, the groups (warps) sweep the
+// rows once in order and write those of the eigenvalues solved so far (as k_solve's tail does);
+// k_arrow_vectors writes the others and rewrites a row whose pair the remedies changed.
 template <int L>
 __global__ void __launch_bounds__(256, DPR1_SOLVE_MIN_BLOCKS) k_arrow_solve(int n, const double* __restrict__ d,
                                                      const double* __restrict__ z, ArrowWs w, int cap,
-                                                     bool fast, bool screen) {
+                                                     bool fast, bool screen, double* __restrict__ Vt, int64_t ldv) {
   if (*w.status & ST_FATAL_A) return;
   const double alpha = w.scal[0];       // d, z and alpha are the normalised copies
   const int lane = threadIdx.x & (L - 1);
@@ -318,9 +393,33 @@ __global__ void __launch_bounds__(256, DPR1_SOLVE_MIN_BLOCKS) k_arrow_solve(int 
     long long gl = 0;
     if (lane == 0) gl = (long long)atomicAdd(w.queue, 1ull);
     gl = __shfl_sync(gm, gl, leader, 32);
-    if (gl > n) break;
+    if (gl > n) {
+      if constexpr (kTailRows && L == 32) {
+        if (!fast && w.vstate && Vt) {
+          for (;;) {
+            unsigned r = 0, st = 0;
+            if (lane == 0) {
+              r = atomicAdd(&w.counters[C_TROW], 1u);
+              if (r <= (unsigned)n) st = ld_acquire(w.vstate + r);
+            }
+            r = __shfl_sync(gm, r, 0, 32);
+            st = __shfl_sync(gm, st, 0, 32);
+            if (r > (unsigned)n) break;
+            if (st != 1u) continue;
+            arrow_tail_row(d, z, n, __ldcg(w.sig + r), __ldcg(w.mu + r), Vt + (int64_t)r * ldv, lane,
+                           w.vrow + 4 * (int64_t)r);
+            if (lane == 0) {
+              w.vstate[r] = 2u;
+              atomicAdd(&w.counters[C_TAILROWS], 1u);
+            }
+          }
+        }
+      }
+      break;
+    }
     const int k = (int)gl;
     int i;
+    bool shift32 = false;
     double alo = 0.0, ahi = INFINITY;
     if (k == 0 || k == n) {
       // exterior: the 2 x 2 principal matrix [d_i zeta_i; zeta_i alpha] bounds |mu| from
@@ -336,27 +435,36 @@ __global__ void __launch_bounds__(256, DPR1_SOLVE_MIN_BLOCKS) k_arrow_solve(int 
       alo = 1.0 / (fmax(gap, 0.0) + sqrt(s));
       ahi = 1.0 / mlo;
     } else {
-      // shift test at the midpoint m = d_k + tau: F = f(m), f decreasing
+      // shift test at the midpoint m = d_k + tau: F = f(m), f decreasing; the binary32 pass
+      // decides where its bound settles the sign (the binary64 pass's sign), else the binary64
+      // pass runs
       const double dk = d[k];
       const double tau = __dmul_rn(__dsub_rn(d[k - 1], dk), 0.5);
-      double sp = 0.0, sn = 0.0;
-      for (int j = lane; j < n; j += L) {
-        const double t = __dmul_rn(zz[j], rcp(__dsub_rn(__dsub_rn(d[j], dk), tau)));
-        if (j < k) sp = __dadd_rn(sp, t);
-        else sn = __dadd_rn(sn, t);
+      const double c = __dsub_rn(__dsub_rn(alpha, dk), tau);
+      double sp = 0.0, sn = 0.0, F = 0.0, EF = 0.0;
+      shift32 = kArrowShift32 && screen && shift_test_arrow_f32<L>(d, zz, n, dk, tau, c, lane, gm, &F, &EF) &&
+                fabs(F) > EF;
+      if (!shift32) {
+        for (int j = lane; j < n; j += L) {
+          const double t = __dmul_rn(zz[j], rcp(__dsub_rn(__dsub_rn(d[j], dk), tau)));
+          if (j < k) sp = __dadd_rn(sp, t);
+          else sn = __dadd_rn(sn, t);
+        }
+        sp = group_sum<L>(sp, gm);
+        sn = group_sum<L>(sn, gm);
+        F = c - (sp + sn);
       }
-      sp = group_sum<L>(sp, gm);
-      sn = group_sum<L>(sn, gm);
-      const double F = ((alpha - dk) - tau) - (sp + sn);
       alo = 1.0 / tau;
+      // the upper bracket end from the binary64 pass's partial sums is left out when the
+      // binary32 pass may decide (both paths then start the bisection from the same bracket):
+      //   mu in (0, tau]:   zeta_k^2 nu <= sum_{j<k} zeta_j^2/((d_j - d_k) - tau) + d_k - alpha + tau
+      //   mu in [-tau, 0):  zeta_{k-1}^2 |nu| <= -sum_{j>=k} zeta_j^2/((d_j - d_k) - tau) + alpha - d_{k-1} + tau
       if (F < 0.0) {
-        // mu in (0, tau]: zeta_k^2 nu <= sum_{j<k} zeta_j^2/((d_j - d_k) - tau) + d_k - alpha + tau
         i = k;
-        ahi = (sp + (dk - alpha) + tau) / zz[k];
+        if (!kArrowShift32) ahi = (sp + (dk - alpha) + tau) / zz[k];
       } else {
-        // mu in [-tau, 0): zeta_{k-1}^2 |nu| <= -sum_{j>=k} zeta_j^2/((d_j - d_k) - tau) + alpha - d_{k-1} + tau
         i = k - 1;
-        ahi = (-sn + (alpha - d[k - 1]) + tau) / zz[k - 1];
+        if (!kArrowShift32) ahi = (-sn + (alpha - d[k - 1]) + tau) / zz[k - 1];
       }
       if (!(ahi > alo)) ahi = INFINITY;
     }
@@ -368,12 +476,14 @@ __global__ void __launch_bounds__(256, DPR1_SOLVE_MIN_BLOCKS) k_arrow_solve(int 
       if (pr.screened_df) atomicAdd(&w.counters[C_SCREEN_DF], (unsigned)pr.screened_df);
       if (pr.inferred) atomicAdd(&w.counters[C_INFER], (unsigned)pr.inferred);
       if (pr.probes) atomicAdd(&w.counters[C_PROBE], (unsigned)pr.probes);
+      if (shift32) atomicAdd(&w.counters[C_SHIFT32], 1u);
       w.sig[k] = d[i];
       w.mu[k] = pr.mu;
       w.shift[k] = i;
       atomicAdd(&w.counters[C_EVAL_SOLVE], (unsigned)pr.steps);
       atomicAdd(&w.counters[C_SOLVED], 1u);
       if (!pr.ok) atomicOr(w.status, ST_NOT_CONVERGED);
+      if (w.vstate) st_release(w.vstate + k, 1u);     // (sigma, mu) written: the row may be formed
     }
   }
 }
@@ -684,7 +794,9 @@ __global__ void k_arrow_zero_solve(int n, const double* __restrict__ d, ArrowWs 
 }
 
 
-// Rows v_k = [x; -1] / ||.|| (one warp per row), lambda, sigma, mu, ||[x; -1]||.
+// Rows v_k = [x; -1] / ||.|| (one warp per row), lambda, sigma, mu, ||[x; -1]||.  A row the solve
+// kernel's tail wrote (arrow_row_values, the same arithmetic) is kept when its record holds the
+// final (sigma, mu).
 __global__ void __launch_bounds__(256) k_arrow_vectors(int n, const double* __restrict__ d,
                                                        const double* __restrict__ z, ArrowWs w,
                                                        double* __restrict__ lambda, double* __restrict__ Vt,
@@ -697,35 +809,21 @@ __global__ void __launch_bounds__(256) k_arrow_vectors(int n, const double* __re
   for (int64_t k = wid; k <= n; k += nw) {
     const double s = w.sig[k], m = w.mu[k];
     double* vr = Vt ? Vt + k * ldv : nullptr;
-    double q = 0.0;
-    bool bad = false;
-    for (int j = lane; j < n; j += 32) {
-      const double den = __dsub_rn(__dsub_rn(d[j], s), m);
-      const double x = __dmul_rn(z[j], rcp_nr(den));
-      bad |= !rcp_in_range(den);
-      if (vr) vr[j] = x;
-      q = __fma_rn(x, x, q);
-    }
-    q = group_sum<32>(q, FULL);
-    q = __dadd_rn(q, 1.0);                        // the last component, -1
-    bad = group_any<32>(bad, FULL);
-    double scale = 1.0;
-    bool rewrite = false;
-    if (bad || !(q < 1e300)) {
-      double mx = 1.0;
-      for (int j = lane; j < n; j += 32) mx = fmax(mx, fabs(__dmul_rn(z[j], rcp(__dsub_rn(__dsub_rn(d[j], s), m)))));
-      mx = group_max<32>(mx, FULL);
-      scale = 1.0 / mx;
-      q = 0.0;
-      for (int j = lane; j < n; j += 32) {
-        const double x = __dmul_rn(z[j], rcp(__dsub_rn(__dsub_rn(d[j], s), m))) * scale;
-        q = __fma_rn(x, x, q);
+    double nrm, scale;
+    bool kept = false;
+    if (w.vstate && vr && w.vstate[k] == 2u) {
+      const double* rec = w.vrow + 4 * k;
+      if (__double_as_longlong(rec[0]) == __double_as_longlong(s) &&
+          __double_as_longlong(rec[1]) == __double_as_longlong(m)) {
+        nrm = rec[2];
+        scale = rec[3];
+        kept = true;
       }
-      q = group_sum<32>(q, FULL);
-      q = __fma_rn(scale, scale, q);
-      rewrite = true;
     }
-    const double nrm = sqrt(q);
+    if (!kept) {
+      arrow_row_values(d, z, n, s, m, vr, lane, &nrm, &scale);
+      if (vr && lane == 0) atomicAdd(&w.counters[C_VECROWS], 1u);
+    }
     const double c = scale / nrm;
     if (lane == 0) {
       // outputs in the caller's units (lambda, sigma, mu times 2^a; x is scale-free)
@@ -737,7 +835,6 @@ __global__ void __launch_bounds__(256) k_arrow_vectors(int n, const double* __re
       if (sigma) sigma[k] = scalbn(s, a);
       if (mu) mu[k] = scalbn(m, a);
       if (xnorm) xnorm[k] = xn;
-      if (vr) vr[n] = -c;
       // outside the binary64 range of the normalised problem, or a cancelling pole difference
       // after a non-pole shift (as for D + rho z z^T)
       bool out = !(fabs(m) >= 0x1p-1022) || !isfinite(m) || !isfinite(lam) || !(xn > 0.0) || !isfinite(xn) ||
@@ -745,12 +842,6 @@ __global__ void __launch_bounds__(256) k_arrow_vectors(int n, const double* __re
       if (w.shift[k] < 0) out = out || (k < n && ah_pole_difference_cancels(d[k], s, m)) ||
                                 (k > 0 && ah_pole_difference_cancels(d[k - 1], s, m));
       if (out) atomicOr(w.status, ST_RANGE);
-    }
-    if (!vr) continue;
-    if (!rewrite) {
-      for (int j = lane; j < n; j += 32) vr[j] = __dmul_rn(vr[j], c);
-    } else {
-      for (int j = lane; j < n; j += 32) vr[j] = __dmul_rn(z[j], rcp(__dsub_rn(__dsub_rn(d[j], s), m))) * c;
     }
   }
 }
@@ -780,18 +871,26 @@ static int64_t arrow_groups(int64_t n, int L, int warps, int bps) {
 
 // bytes of the stored-element buffers for the default launch (8 warps per block,
 // DPR1_SOLVE_MIN_BLOCKS blocks per SM)
+// bytes of the records of the rows the solve kernel's tail writes (after the buffers, 256-byte
+// aligned): 4 doubles and a state word per row, for n above kArrowTailMinN
+static size_t arrow_tail_bytes(int64_t n) {
+  if (!kTailRows || n <= kArrowTailMinN) return 0;
+  return 256 + a256a(sizeof(double) * 4 * (size_t)(n + 1)) + a256a(sizeof(unsigned) * (size_t)(n + 1));
+}
+
 static size_t arrow_term_bytes(int64_t n) {
   if (n <= 0) return 0;
   const int64_t tn = (n + 31) & ~(int64_t)31;
-  return (size_t)arrow_groups(n, arrow_lanes(n), 8, DPR1_SOLVE_MIN_BLOCKS) * TERM_BYTES * (size_t)tn;
+  return (size_t)arrow_groups(n, arrow_lanes(n), 8, DPR1_SOLVE_MIN_BLOCKS) * TERM_BYTES * (size_t)tn +
+         arrow_tail_bytes(n);
 }
 
 // tb: workspace bytes beyond the required part, for the solves' stored elements (one
 // buffer of TERM_BYTES n bytes per lane group, for as many groups as the bytes allow; the remedies
 // reuse them after the solve kernel)
 template <int L>
-static void launch_arrow(int n, const double* d, const double* z, ArrowWs* w, const Options& o, char* tail,
-                         size_t tb, cudaStream_t st) {
+static dpr1_status launch_arrow(int n, const double* d, const double* z, ArrowWs* w, const Options& o, char* tail,
+                                size_t tb, double* Vt, int64_t ldv, cudaStream_t st) {
   const int groups_per_block = (32 * o.warps) / L;
   int64_t want = ((int64_t)n + 1 + groups_per_block - 1) / groups_per_block;
   int grid = sm_count() * o.bps;
@@ -806,9 +905,21 @@ static void launch_arrow(int n, const double* d, const double* z, ArrowWs* w, co
       w->terms = (double*)tail;
       w->term_n = tn;
       w->term_slots = need;
+      // after the buffers, the records of the eigenvector rows the solve kernel's tail writes
+      if (kTailRows && L == 32 && Vt && !o.fast && n > kArrowTailMinN) {
+        const size_t at = a256a((size_t)need * TERM_BYTES * (size_t)tn);
+        const size_t rec = a256a(sizeof(double) * 4 * (size_t)(n + 1));
+        if (at + rec + a256a(sizeof(unsigned) * (size_t)(n + 1)) <= tb) {
+          w->vrow = (double*)(tail + at);
+          w->vstate = (unsigned*)(tail + at + rec);
+          if (cudaMemsetAsync(w->vstate, 0, sizeof(unsigned) * (size_t)(n + 1), st) != cudaSuccess)
+            return DPR1_ERR_CUDA;
+        }
+      }
     }
   }
-  k_arrow_solve<L><<<grid, 32 * o.warps, 0, st>>>(n, d, z, *w, o.cap, o.fast, o.screen);
+  k_arrow_solve<L><<<grid, 32 * o.warps, 0, st>>>(n, d, z, *w, o.cap, o.fast, o.screen, Vt, ldv);
+  return DPR1_OK;
 }
 
 }  // namespace dpr1
@@ -852,9 +963,11 @@ dpr1_status dpr1_arrow_eig(int64_t n, const double* d, const double* z, double a
   const double* ds = w.ds;
   const double* zs = w.zs;
   const int L = o.lanes ? o.lanes : arrow_lanes(n);
-  if (L == 8) launch_arrow<8>((int)n, ds, zs, &w, o, tail, tb, st);
-  else if (L == 16) launch_arrow<16>((int)n, ds, zs, &w, o, tail, tb, st);
-  else launch_arrow<32>((int)n, ds, zs, &w, o, tail, tb, st);
+  dpr1_status ls;
+  if (L == 8) ls = launch_arrow<8>((int)n, ds, zs, &w, o, tail, tb, Vt, ldv, st);
+  else if (L == 16) ls = launch_arrow<16>((int)n, ds, zs, &w, o, tail, tb, Vt, ldv, st);
+  else ls = launch_arrow<32>((int)n, ds, zs, &w, o, tail, tb, Vt, ldv, st);
+  if (ls != DPR1_OK) return ls;
   int kg = (int)((n + 1 + 255) / 256);
   if (kg > sms * 8) kg = sms * 8;
   k_arrow_classify<<<kg, 256, 0, st>>>((int)n, ds, w, o.T_Knu);

@@ -275,4 +275,16 @@ __device__ __forceinline__ double dnext_up(double x) {
 __device__ __forceinline__ double dnext_down(double x) { return -dnext_up(-x); }
 __device__ __forceinline__ double dfrom(uint64_t u) { return __longlong_as_double((long long)u); }
 
+// a flag store that orders this thread's earlier writes before it, and a load that orders this
+// thread's later reads after it (device scope): with them, a thread that sees the flag sees the
+// data written before it
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 }  // namespace dpr1

@@ -36,10 +36,6 @@
 #ifndef DPR1_FIX_BLOCKS_PER_SM
 #define DPR1_FIX_BLOCKS_PER_SM 2
 #endif
-// the shift test's sign from the binary32 pass (shift_test_f32) where its bound decides it
-#ifndef DPR1_SHIFT32
-#define DPR1_SHIFT32 1
-#endif
 // the upper bracket end from the shift test's partial sums (only with the binary64 pass)
 #ifndef DPR1_SHIFT_AHI
 #define DPR1_SHIFT_AHI 0
@@ -62,11 +58,6 @@
 #ifndef DPR1_FIX_SMALL_N
 #define DPR1_FIX_SMALL_N 1024
 #endif
-// lane groups of the solve kernel that find its queue empty write the eigenvector rows of the
-// eigenvalues solved so far (one problem of order above DPR1_SOLVE_LARGE_N with eigenvectors)
-#ifndef DPR1_TAIL_ROWS
-#define DPR1_TAIL_ROWS 1
-#endif
 // eigenvector rows as pairs of components with 16-byte accesses
 #ifndef DPR1_VEC_PAIRS
 #define DPR1_VEC_PAIRS 1
@@ -76,7 +67,6 @@ namespace dpr1 {
 
 constexpr bool kShiftAhi = DPR1_SHIFT_AHI != 0;
 constexpr bool kShift32 = DPR1_SHIFT32 != 0 && !kShiftAhi;
-constexpr bool kTailRows = DPR1_TAIL_ROWS != 0;
 constexpr bool kVecPairs = DPR1_VEC_PAIRS != 0;
 
 // ---------------------------------------------------------------------------------
@@ -563,15 +553,6 @@ __device__ __noinline__ void tail_row(const double* __restrict__ d, const double
     rec[2] = nrm;
     rec[3] = scale;
   }
-}
-
-__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
 }
 
 template <int L, int MINB, bool NI>

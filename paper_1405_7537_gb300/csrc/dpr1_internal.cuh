@@ -12,8 +12,19 @@
 #ifndef DPR1_SOLVE_MIN_BLOCKS
 #define DPR1_SOLVE_MIN_BLOCKS 4
 #endif
+// the shift test's sign from the binary32 pass where its bound decides it
+#ifndef DPR1_SHIFT32
+#define DPR1_SHIFT32 1
+#endif
+// lane groups of a solve kernel that find its queue empty write the eigenvector rows of the
+// eigenvalues solved so far (one problem of order above 2048, with eigenvectors)
+#ifndef DPR1_TAIL_ROWS
+#define DPR1_TAIL_ROWS 1
+#endif
 
 namespace dpr1 {
+
+constexpr bool kTailRows = DPR1_TAIL_ROWS != 0;
 
 // Views into the caller's workspace for one problem (see ws_layout).
 struct Ws {

@@ -362,14 +362,15 @@ __device__ __forceinline__ float rn32(double x, bool* ok) {
 // w = (|Df| + tf) |r|, the term is within e_j = |t| eps (1.01 w + 4.2) of zz_j / ((d_j - d_k) - tau)
 // (the conversions of zz and Delta, the reciprocal, the product and Sum2's share), valid while
 // w <= 2^20 (else the lane reports failure); a weight below the binary32 range (zf = 0) adds at
-// most 2^-125 |r|.  Returns F32 and a bound E on |F32 - F| for the exact F and on |F64 - F| for
-// the binary64 pass of k_solve (two roundings of each difference, the one-ulp reciprocal and the
-// product: u (w + 4) per term, m = ceil(n / L) accumulations per lane, the tree and the last
-// sum), so a decision on the sign of F32 with |F32| > E is the binary64 pass's decision.
+// most 2^-125 |r|.  shift_sum_f32 returns the sum S32 with es = sum e_j and as = sum |t_j| (each
+// rounded up); the tests below bound |F32 - F| for the exact F and |F64 - F| for the binary64 pass
+// of the solve kernel (two roundings of each difference, the one-ulp reciprocal and the product:
+// u (w + 4) per term, m = ceil(n / L) accumulations per lane, the tree and the last sum), so a
+// decision on the sign of F32 with |F32| > E is the binary64 pass's decision.
 template <int L>
-__device__ __noinline__ bool shift_test_f32(const double* __restrict__ d, const double* __restrict__ zz, int n,
-                                            double dk, double tau, double rho, int lane, unsigned gm, double* F,
-                                            double* E) {
+__device__ __forceinline__ bool shift_sum_f32(const double* __restrict__ d, const double* __restrict__ zz, int n,
+                                              double dk, double tau, int lane, unsigned gm, double* S, double* es_out,
+                                              double* as_out) {
   bool ok = true;
   const float tf = rn32(tau, &ok);
   float sh = 0.0f, sl = 0.0f, e = 0.0f, a1 = 0.0f;
@@ -394,10 +395,19 @@ __device__ __noinline__ bool shift_test_f32(const double* __restrict__ d, const 
   }
   // the lane group's sums in binary32 as in screen_sum
   group_sum2_f<L>(&sh, &sl, gm);
-  const double S = __dadd_rn((double)sh, (double)sl);
-  const double es = (double)group_sum_f<L>(e, gm) * (1.0 + 0x1p-20);
-  const double as = (double)group_sum_f<L>(a1, gm) * (1.0 + 0x1p-20);
-  ok = !group_any<L>(!ok, gm);
+  *S = __dadd_rn((double)sh, (double)sl);
+  *es_out = (double)group_sum_f<L>(e, gm) * (1.0 + 0x1p-20);
+  *as_out = (double)group_sum_f<L>(a1, gm) * (1.0 + 0x1p-20);
+  return !group_any<L>(!ok, gm);
+}
+
+// D + rho z z^T: F = 1 + rho S.
+template <int L>
+__device__ __noinline__ bool shift_test_f32(const double* __restrict__ d, const double* __restrict__ zz, int n,
+                                            double dk, double tau, double rho, int lane, unsigned gm, double* F,
+                                            double* E) {
+  double S, es, as;
+  const bool ok = shift_sum_f32<L>(d, zz, n, dk, tau, lane, gm, &S, &es, &as);
   const double m = (double)((n + L - 1) / L);
   const double g = 1.0 + 2.0 * (m + 2.0) * 0x1p-24;
   const double F32 = 1.0 + rho * S;
@@ -406,6 +416,26 @@ __device__ __noinline__ bool shift_test_f32(const double* __restrict__ d, const 
   const double E64 = 1.01 * 0x1p-53 * rho * g * (es + (m + 16.0 + tree_roundings<L>()) * as);
   *F = F32;
   *E = 1.01 * (E32 + E64 + 0x1p-50 * (1.0 + rho * g * as));
+  return ok && isfinite(F32) && isfinite(*E);
+}
+
+// The arrowhead [D z; z^T alpha]: F = c - S with c = fl(fl(alpha - d_k) - tau), the value the
+// binary64 pass subtracts its sum fl(sp + sn) from; fl(c - x) has the sign of c - x, so the
+// binary64 decision is the sign of c - fl(sp + sn), within the same bound of c - S32.
+template <int L>
+__device__ __noinline__ bool shift_test_arrow_f32(const double* __restrict__ d, const double* __restrict__ zz, int n,
+                                                  double dk, double tau, double c, int lane, unsigned gm, double* F,
+                                                  double* E) {
+  double S, es, as;
+  const bool ok = shift_sum_f32<L>(d, zz, n, dk, tau, lane, gm, &S, &es, &as);
+  const double m = (double)((n + L - 1) / L);
+  const double g = 1.0 + 2.0 * (m + 2.0) * 0x1p-24;
+  const double F32 = __dsub_rn(c, S);
+  const double E32 = 1.05 * g * 0x1p-24 * es + (2.0 + tree_roundings<L>()) * 0x1p-53 * g * as +
+                     4.0 * (double)n * 0x1p-149;
+  const double E64 = 1.01 * 0x1p-53 * g * (es + (m + 16.0 + tree_roundings<L>()) * as);
+  *F = F32;
+  *E = 1.01 * (E32 + E64 + 0x1p-50 * (fabs(c) + g * as));
   return ok && isfinite(F32) && isfinite(*E);
 }
 

@@ -132,9 +132,10 @@ def test_arrowhead_screen_changes_no_bit(B, kind):
         res.append({k: v.cpu().numpy() for k, v in r.items() if v is not None})
         st.append(B.workspace_stats(ws))
     same_bits(res[0], res[1])
-    assert st[1]["screened"] == 0 and st[1]["inferred"] == 0
+    assert st[1]["screened"] == 0 and st[1]["inferred"] == 0 and st[1]["shift_binary32"] == 0
     if kind == "uniform":
         assert st[0]["screened"] + st[0]["inferred"] > 0.4 * st[1]["evals_solve"], st
+        assert st[0]["shift_binary32"] > 0.5 * d.size, st
 
 
 def _fuzz_problem(rng, t):

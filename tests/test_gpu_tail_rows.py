@@ -1,4 +1,4 @@
-"""Eigenvector rows written by the bisection kernel's tail change no bit.
+"""Eigenvector rows written by the bisection kernels' tails change no bit.
 
 Once the solve kernel's work queue is empty (one problem of order above 2048, with eigenvectors),
 its lane groups write the rows of V^T (Eq. (eigenvecAi)) of the eigenvalues solved by then, with
@@ -29,11 +29,14 @@ def cu(x):
     return torch.tensor(np.array(x, dtype=np.float64, copy=True), device="cuda")
 
 
-def records_bytes(n):
-    # the records after the stored-element buffers for n a multiple of 64: 36 n bytes (four
-    # doubles and a state word per row) and 256 of alignment
-    assert n % 64 == 0
-    return 36 * n + 256
+def a256(x):
+    return (x + 255) // 256 * 256
+
+
+def records_bytes(rows):
+    # the records after the stored-element buffers: four doubles and a state word per row, each
+    # array 256-byte aligned, and 256 bytes of alignment slack
+    return 256 + a256(32 * rows) + a256(4 * rows)
 
 
 def run(B, d, z, rho, ws, out=None):
@@ -112,3 +115,33 @@ def test_no_tail_rows_with_the_accelerated_solve(B):
     B.eig(cu(d), cu(z), rho, ws=ws, options=B.default_options(zero_finder=1))
     st = B.workspace_stats(ws)
     assert st["tail_rows"] == 0 and st["vector_rows"] == n, st
+
+
+@pytest.mark.parametrize("kind", ["uniform", "clustered"])
+def test_arrowhead_tail_rows_change_no_bit(B, kind):
+    """The arrowhead solve kernel's tail writes rows [x; -1] / ||.|| the same way: the same bits
+    with and without the records, the remedies' changed pairs rewritten by k_arrow_vectors."""
+    n = 9000
+    if kind == "uniform":
+        d, z, alpha = W.arrowhead(n, 38)
+    else:
+        rng = np.random.default_rng(39)
+        c = rng.uniform(-1, 1, 300)
+        d = np.unique(rng.choice(c, n) + rng.choice([1.0, -1.0], n) * 10.0 ** rng.uniform(-12, -3, n))[::-1].copy()
+        n = d.size
+        z = rng.choice([1.0, -1.0], n) * 10.0 ** rng.uniform(-10, 0, n)
+        alpha = 1e-3
+    full = B.arrow_workspace(n)
+    size = int(B.lib().dpr1_arrow_workspace_size(n))
+    part = torch.empty(size - records_bytes(n + 1), dtype=torch.uint8, device="cuda")
+    res, st = [], []
+    for ws in (full, part):
+        r = B.eig_arrowhead(cu(d), cu(z), alpha, ws=ws)
+        res.append(r)
+        st.append(B.workspace_stats(ws))
+    same_bits(res[0], res[1])
+    assert st[1]["tail_rows"] == 0 and st[1]["vector_rows"] == n + 1, st[1]
+    assert st[0]["tail_rows"] > 0, st[0]
+    assert st[0]["tail_rows"] + st[0]["vector_rows"] >= n + 1, st[0]
+    if kind == "clustered":
+        assert st[0]["r1"] + st[0]["r2"] > 0, st[0]
