@@ -190,7 +190,9 @@ DPR1_API dpr1_status dpr1_eig_batched(int64_t nprob, int64_t total_n, const int6
                                       const dpr1_options* opt, dpr1_stream_t stream);
 
 /*
- * Bytes of workspace for dpr1_eig_backward on order n (256-byte aligned, uninitialised).
+ * Bytes of workspace for dpr1_eig_backward on order n (256-byte aligned, uninitialised):
+ * three rows of n doubles (partial rows of the gradients of d and z, and the current row's
+ * reciprocals) for each of 1064, 2128 or 3192 warps (n <= 8192, <= 24576, above).
  */
 DPR1_API size_t dpr1_backward_workspace_size(int64_t n);
 
