@@ -10,12 +10,14 @@
 //   k_scan      input checks, scaled copies of d, z, z^2 in the workspace, deflation tests (Sec. 1)
 //   k_deflate   exact deflation (zeta_j == 0, ties) for the problems that need it
 //   k_solve     per eigenvalue (one lane group): shift test, corner b in double-double,
-//               bisection for the extreme eigenvalue nu of the arrowhead inverse
+//               bisection for the extreme eigenvalue nu of the arrowhead inverse; once its
+//               queue is empty, the eigenvector rows of the eigenvalues solved by then
 //   k_classify  K_nu of Eq. (K0) from the neighbouring eigenvalues; picks R1 / R2 candidates
 //   k_fix       R1 (the other pole) and R2 (non-pole shift, f(sigma) in double-double)
 //   k_zero_*    eigenvalues much closer to zero than to their poles: lambda from A^{-1}
-//   k_vectors   lambda, (sigma, mu), ||x|| (scaled back) and the rows of V^T, v = x / ||x||;
-//               pairs outside the binary64 range are reported (DPR1_ERR_RANGE)
+//   k_vectors   lambda, (sigma, mu), ||x|| (scaled back) and the rows of V^T, v = x / ||x||,
+//               that k_solve did not write or whose pair changed since; pairs outside the
+//               binary64 range are reported (DPR1_ERR_RANGE)
 //   k_defl_*    output rows of deflated problems; k_trivial for rho == 0 (and rho' out of range)
 // All work lists are global, so the persistent kernels balance the whole batch.
 #include <cuda_runtime.h>
