@@ -397,17 +397,24 @@ __global__ void __launch_bounds__(256, DPR1_SOLVE_MIN_BLOCKS) k_arrow_solve(int 
       if constexpr (kTailRows && L == 32) {
         if (!fast && w.vstate && Vt) {
           for (;;) {
+            // lane 0 claims the next row, reads its pair after the acquire load and passes it on
             unsigned r = 0, st = 0;
+            double sr = 0.0, mr = 0.0;
             if (lane == 0) {
               r = atomicAdd(&w.counters[C_TROW], 1u);
               if (r <= (unsigned)n) st = ld_acquire(w.vstate + r);
+              if (st == 1u) {
+                sr = w.sig[r];
+                mr = w.mu[r];
+              }
             }
             r = __shfl_sync(gm, r, 0, 32);
             st = __shfl_sync(gm, st, 0, 32);
             if (r > (unsigned)n) break;
             if (st != 1u) continue;
-            arrow_tail_row(d, z, n, __ldcg(w.sig + r), __ldcg(w.mu + r), Vt + (int64_t)r * ldv, lane,
-                           w.vrow + 4 * (int64_t)r);
+            sr = __shfl_sync(gm, sr, 0, 32);
+            mr = __shfl_sync(gm, mr, 0, 32);
+            arrow_tail_row(d, z, n, sr, mr, Vt + (int64_t)r * ldv, lane, w.vrow + 4 * (int64_t)r);
             if (lane == 0) {
               w.vstate[r] = 2u;
               atomicAdd(&w.counters[C_TAILROWS], 1u);

@@ -580,17 +580,25 @@ __global__ void __launch_bounds__(256, MINB)
         if (!fast && w.vstate && pb.P == 1 && pb.Vt && w.nred[0] == pb.total) {
           const int n = (int)pb.total;
           for (;;) {
+            // lane 0 claims the next row and, once its acquire load sees the pair written, reads
+            // the pair and passes it to the other lanes
             unsigned r = 0, st = 0;
+            double sr = 0.0, mr = 0.0;
             if (lane == 0) {
               r = atomicAdd(&w.counters[C_TROW], 1u);
               if (r < (unsigned)n) st = ld_acquire(w.vstate + r);
+              if (st == 1u) {
+                sr = w.sig[r];
+                mr = w.mu[r];
+              }
             }
             r = __shfl_sync(gm, r, 0, 32);
             st = __shfl_sync(gm, st, 0, 32);
             if (r >= (unsigned)n) break;
             if (st != 1u) continue;
-            tail_row(w.dr, w.zr, n, __ldcg(w.sig + r), __ldcg(w.mu + r), pb.Vt + (int64_t)r * pb.ldv0, lane,
-                     w.vrow + 4 * (int64_t)r);
+            sr = __shfl_sync(gm, sr, 0, 32);
+            mr = __shfl_sync(gm, mr, 0, 32);
+            tail_row(w.dr, w.zr, n, sr, mr, pb.Vt + (int64_t)r * pb.ldv0, lane, w.vrow + 4 * (int64_t)r);
             if (lane == 0) {
               w.vstate[r] = 2u;
               atomicAdd(&w.counters[C_TAILROWS], 1u);
