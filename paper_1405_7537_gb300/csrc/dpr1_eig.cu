@@ -142,8 +142,14 @@ size_t ws_layout2(int64_t total, int64_t nprob, bool batched, Ws* w, char* base)
   return off;
 }
 
-// Lane-group width of k_solve for an average problem order (when the options leave it open).
-static int default_lanes(double avg_n) { return avg_n <= 96 ? 8 : (avg_n <= 384 ? 16 : 32); }
+// Lane-group width of k_solve for an average problem order (when the options leave it open).  In a
+// batch, eight lanes up to a mean order of 384 (problems of orders 96-384: 33.3 ms against 39.8 with
+// 16 lanes and 48.3 with 32 for 425k eigenpairs; orders 16-96: 18.2 against 24.9 and 32.5) and a
+// warp above (orders 384-2048: 108.4 ms against 115.8 with 16 lanes and 140.3 with 8).
+static int default_lanes(double avg_n, int64_t nprob = 1) {
+  if (nprob > 1) return avg_n <= 384 ? 8 : 32;
+  return avg_n <= 96 ? 8 : (avg_n <= 384 ? 16 : 32);
+}
 
 // Bytes of the stored-element buffers appended to the workspace: TERM_BYTES term_n bytes for
 // each lane group of k_solve's default launch (8 warps per block, DPR1_SOLVE_MIN_BLOCKS blocks per
@@ -160,7 +166,7 @@ static size_t tail_bytes(int64_t total, int64_t nprob) {
 size_t term_bytes(int64_t total, int64_t nprob) {
   if (total <= 0 || nprob <= 0) return 0;
   const double avg = (double)total / (double)nprob;
-  const int64_t gpb = (32 * 8) / default_lanes(avg);
+  const int64_t gpb = (32 * 8) / default_lanes(avg, nprob);
   int64_t groups = (int64_t)sm_count() * DPR1_SOLVE_MIN_BLOCKS * gpb;
   // a launch with blocks of gpb' <= gpb groups has at most total + gpb' - 1 of them
   const int64_t need = total + gpb - 1;
@@ -1283,7 +1289,7 @@ static dpr1_status run_table(const Prob& pb, void* workspace, size_t wbytes, con
   int dg = (pb.P + 3) / 4;                              // a warp per problem
   if (dg > sms * 8) dg = sms * 8;
   k_deflate<<<dg > 0 ? dg : 1, 128, 0, st>>>(pb, w);
-  int L = o.lanes ? o.lanes : default_lanes(avg_n);
+  int L = o.lanes ? o.lanes : default_lanes(avg_n, pb.P);
   // Shape of the solve kernel.  Its time is set by the binary64 pipe of the busiest SM, so the
   // eigenvalues must spread evenly over the SMs: with fewer lane groups than 8-warp blocks on
   // every SM can hold, blocks of fewer warps, at most one per SM; else as many 8-warp blocks per
