@@ -128,7 +128,8 @@ DPR1_API const char* dpr1_status_string(dpr1_status s);
  * These parts are optional: a smaller workspace is accepted down to the part without
  * them (every evaluation of the secular function then forms the elements again, with the same accuracy
  * bound, and the eigenvector kernel writes every row); below that part the call returns
- * DPR1_ERR_WORKSPACE.  The results are the same bits with or without them.
+ * DPR1_ERR_WORKSPACE.  The row records change no bit of the results; without the buffers the
+ * sums group their terms differently, so a result may differ in its last bits, within the bound.
  */
 DPR1_API size_t dpr1_workspace_size(int64_t n);
 
